@@ -1,0 +1,45 @@
+"""Exact C_Q = Q H^T by direct kernel sums, FP64.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
+
+Sec. 3.2: Q H^T = [Q h^(1) ... Q h^(n)] with (Q h^(k))_i = sum_j K(x_i, x_j) h_j^(k),
+where h^(k) is the k-th column of H^T (the k-th ray). Only the cells a ray
+crosses carry a nonzero h_j, so the sum runs over the support of H.
+"""
+from __future__ import annotations
+
+from typing import Optional
+
+import numpy as np
+import scipy.sparse as sp
+
+from .kf import KernelFn
+
+
+def h_csr(rowptr: np.ndarray, col: np.ndarray, val: np.ndarray, m: int) -> sp.csr_matrix:
+    """The n x m measurement operator as a scipy CSR matrix."""
+    n = rowptr.shape[0] - 1
+    return sp.csr_matrix((np.asarray(val, np.float64), np.asarray(col, np.int64), np.asarray(rowptr, np.int64)),
+                         shape=(n, m))
+
+
+def qht(points: np.ndarray, kern: KernelFn, H: sp.csr_matrix, rows: Optional[np.ndarray] = None,
+        chunk: Optional[int] = None) -> np.ndarray:
+    """Rows `rows` (default: all) of Q H^T, summed directly over the support of H.
+
+    (Q H^T)_{ik} = sum_{j : H_kj != 0} K(x_i, x_j) H_kj.
+    """
+    H = sp.csr_matrix(H)
+    m = points.shape[0]
+    rows = np.arange(m) if rows is None else np.asarray(rows, dtype=np.int64)
+    Ht = H.T.tocsr()                                   # m x n
+    support = np.unique(H.indices)                     # cells crossed by any ray
+    Hs = Ht[support].toarray()                         # |support| x n, dense
+    ys = points[support]
+    out = np.zeros((rows.shape[0], H.shape[0]))
+    if chunk is None:                                  # bound the kernel block to ~4e6 entries
+        chunk = int(max(1, min(512, 4_000_000 // max(1, support.shape[0]))))
+    for a in range(0, rows.shape[0], chunk):
+        r = rows[a:a + chunk]
+        out[a:a + r.shape[0]] = kern(points[r], ys) @ Hs
+    return out

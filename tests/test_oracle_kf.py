@@ -1,0 +1,149 @@
+"""Pins of the FP64 Kalman-filter oracles (oracle/kf.py) against closed forms.
+
+Each check comes from the mathematics, not from the oracle's own formulas:
+  * Q = 0, one step: the Gaussian linear-regression posterior in information
+    form (P0^-1 + H^T R^-1 H)^-1 (Sec. 2.2, Eqs. KF_forecast..KF_Pa with Q = 0).
+  * Q = 0, T steps with the same H: batch regression with T H^T R^-1 H.
+  * m = n = 1: the scalar Kalman recursion written out by hand.
+  * Q != 0: the random-walk posterior of x_T from the joint Gaussian of
+    (x_T, y_1..y_T) (Eq. random_walk: Cov(x_s, x_t) = P0 + min(s,t) Q).
+  * invariants: P symmetric, PSD, positive diagonal, variance not increased by an update.
+  * Alg. 2 (cross-covariance form) equals Alg. 1 (Sec. 3.1: equivalent formulation).
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import kf, qht
+from paper_1404_3816_gb300 import workload as W
+
+
+def _small_problem(seed=0, grid=(7, 6), n=5, T=4):
+    rng = np.random.default_rng(seed)
+    pts = W.grid_points(grid)
+    m = pts.shape[0]
+    P0 = kf.covariance_matrix(pts, kf.gcf(1.0, 3.0, 1))
+    Q = kf.covariance_matrix(pts, kf.gcf(0.05, 2.0, 2))
+    H = rng.uniform(0.0, 1.0, (n, m)) * (rng.uniform(size=(n, m)) < 0.4)
+    R = rng.uniform(0.5, 1.5, n) * 1e-2
+    x0 = rng.normal(size=m)
+    Y = rng.normal(size=(T, n))
+    return pts, P0, Q, H, R, x0, Y
+
+
+def test_q0_one_step_equals_regression_posterior():
+    _, P0, _, H, R, x0, Y = _small_problem(1)
+    out = kf.kf_full(P0, np.zeros_like(P0), H, R, x0, Y[:1])
+    Ri = np.diag(1.0 / R)
+    info = np.linalg.inv(P0) + H.T @ Ri @ H
+    Ppost = np.linalg.inv(info)
+    xpost = Ppost @ (np.linalg.solve(P0, x0) + H.T @ Ri @ Y[0])
+    assert np.allclose(out["P"], Ppost, rtol=1e-8, atol=1e-10)
+    assert np.allclose(out["x"], xpost, rtol=1e-8, atol=1e-9)
+
+
+def test_q0_T_steps_equals_batch_regression():
+    _, P0, _, H, R, x0, Y = _small_problem(2, T=5)
+    out = kf.kf_full(P0, np.zeros_like(P0), H, R, x0, Y)
+    Ri = np.diag(1.0 / R)
+    T = Y.shape[0]
+    info = np.linalg.inv(P0) + T * H.T @ Ri @ H
+    Ppost = np.linalg.inv(info)
+    xpost = Ppost @ (np.linalg.solve(P0, x0) + H.T @ Ri @ Y.sum(axis=0))
+    assert np.allclose(out["P"], Ppost, rtol=1e-7, atol=1e-10)
+    assert np.allclose(out["x"], xpost, rtol=1e-7, atol=1e-9)
+
+
+def test_scalar_recursion_by_hand():
+    p0, q, h, r, x = 2.0, 0.3, 1.7, 0.4, 0.5
+    ys = [1.0, -0.2, 0.7]
+    out = kf.kf_full(np.array([[p0]]), np.array([[q]]), np.array([[h]]), np.array([r]), np.array([x]),
+                     np.array(ys)[:, None], record=True)
+    p = p0
+    for t, y in enumerate(ys):
+        p = p + q
+        k = p * h / (h * h * p + r)
+        x = x + k * (y - h * x)
+        p = p * r / (h * h * p + r)
+        assert out["xs"][t][0] == pytest.approx(x, rel=1e-13)
+        assert out["vars"][t][0] == pytest.approx(p, rel=1e-13)
+
+
+def _joint_gaussian_posterior(P0, Q, H, R, x0, Y):
+    """E[x_T | y_1..y_T] and Cov from Cov(x_s, x_t) = P0 + min(s, t) Q."""
+    T, n = Y.shape
+    Sxx = P0 + T * Q
+    Sxy = np.hstack([(P0 + t * Q) @ H.T for t in range(1, T + 1)])
+    Syy = np.zeros((T * n, T * n))
+    for s in range(1, T + 1):
+        for t in range(1, T + 1):
+            blk = H @ (P0 + min(s, t) * Q) @ H.T
+            if s == t:
+                blk = blk + np.diag(R)
+            Syy[(s - 1) * n:s * n, (t - 1) * n:t * n] = blk
+    resid = (Y - (H @ x0)[None, :]).reshape(-1)
+    G = np.linalg.solve(Syy, Sxy.T).T
+    return x0 + G @ resid, Sxx - G @ Sxy.T
+
+
+def test_random_walk_matches_joint_gaussian():
+    _, P0, Q, H, R, x0, Y = _small_problem(3, T=4)
+    out = kf.kf_full(P0, Q, H, R, x0, Y)
+    xm, Pm = _joint_gaussian_posterior(P0, Q, H, R, x0, Y)
+    assert np.allclose(out["x"], xm, rtol=1e-8, atol=1e-9)
+    assert np.allclose(out["P"], Pm, rtol=1e-8, atol=1e-10)
+
+
+def test_cross_covariance_form_matches_joint_gaussian():
+    _, P0, Q, H, R, x0, Y = _small_problem(4, T=4)
+    out = kf.hikf_cross(Q @ H.T, P0 @ H.T, np.diag(P0).copy(), np.diag(Q), H, R, x0, Y)
+    xm, Pm = _joint_gaussian_posterior(P0, Q, H, R, x0, Y)
+    assert np.allclose(out["x"], xm, rtol=1e-8, atol=1e-9)
+    assert np.allclose(out["var"], np.diag(Pm), rtol=1e-8, atol=1e-10)
+    assert np.allclose(out["C"], Pm @ H.T, rtol=1e-8, atol=1e-10)
+
+
+def test_pins_catch_planted_mistakes():
+    """A dropped diag(Q) in the variance prediction, or a skipped C_Q in the
+    cross-covariance prediction, must break the joint-Gaussian pin."""
+    _, P0, Q, H, R, x0, Y = _small_problem(5, T=3)
+    xm, Pm = _joint_gaussian_posterior(P0, Q, H, R, x0, Y)
+    bad_var = kf.hikf_cross(Q @ H.T, P0 @ H.T, np.diag(P0).copy(), 0.0, H, R, x0, Y)
+    assert not np.allclose(bad_var["var"], np.diag(Pm), rtol=1e-6)
+    bad_cq = kf.hikf_cross(0.0 * Q @ H.T, P0 @ H.T, np.diag(P0).copy(), np.diag(Q), H, R, x0, Y)
+    assert not np.allclose(bad_cq["x"], xm, rtol=1e-6)
+
+
+def test_invariants_on_crosswell_workload():
+    w = W.small(grid=(12, 10), n=6, steps=5, seed=9)
+    Y, _ = W.measurements(w)
+    Hd = w.h_dense()
+    Q = kf.covariance_matrix(w.points, kf.gcf(w.q.theta, w.q.length, w.q.pow))
+    P0 = kf.covariance_matrix(w.points, kf.gcf(w.p0.theta, w.p0.length, w.p0.pow))
+    P = P0.copy()
+    for t in range(Y.shape[0]):
+        prior = np.diag(P + Q).copy()
+        out = kf.kf_full(P, Q, Hd, w.r_diag, w.x0, Y[t:t + 1])
+        P = out["P"]
+        assert np.linalg.norm(P - P.T) <= 1e-12 * np.linalg.norm(P)
+        assert np.all(np.diag(P) > 0)
+        np.linalg.cholesky(P + 1e-12 * np.eye(P.shape[0]))  # PSD
+        assert np.all(np.diag(P) <= prior + 1e-12)
+
+
+def test_cross_form_equals_full_kf_every_step():
+    """Alg. 2 with exact C_Q = Q H^T reproduces Alg. 1 (the identity of Sec. 3.1)."""
+    w = W.small(grid=(24, 20), n=10, steps=8, seed=7)
+    Y, _ = W.measurements(w)
+    H = qht.h_csr(w.h_rowptr, w.h_col, w.h_val, w.m)
+    kq = kf.gcf(w.q.theta, w.q.length, w.q.pow)
+    k0 = kf.gcf(w.p0.theta, w.p0.length, w.p0.pow)
+    Q = kf.covariance_matrix(w.points, kq)
+    P0 = kf.covariance_matrix(w.points, k0)
+    full = kf.kf_full(P0, Q, H, w.r_diag, w.x0, Y, record=True)
+    cq = qht.qht(w.points, kq, H)
+    c0 = qht.qht(w.points, k0, H)
+    cross = kf.hikf_cross(cq, c0, np.full(w.m, w.p0.theta), w.q.theta, H, w.r_diag, w.x0, Y, record=True)
+    for t in range(Y.shape[0]):
+        assert kf.relative_error(cross["xs"][t], full["xs"][t]) < 1e-11
+        assert kf.relative_error(cross["vars"][t], full["vars"][t]) < 1e-11

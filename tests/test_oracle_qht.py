@@ -1,0 +1,39 @@
+"""Pins of the exact product C_Q = Q H^T (oracle/qht.py), Sec. 3.2 column form."""
+import numpy as np
+import pytest
+
+from oracle import kf, qht
+from paper_1404_3816_gb300 import workload as W
+
+
+def test_constant_kernel_gives_ray_lengths():
+    # K == theta (correlation length far beyond the domain): (Q H^T)_ik = theta * sum_j H_kj
+    # = theta * |receiver_k - source_k| for every cell i (the traveltime operator integrates length)
+    w = W.small(grid=(20, 16), n=8, seed=3)
+    H = qht.h_csr(w.h_rowptr, w.h_col, w.h_val, w.m)
+    cq = qht.qht(w.points, kf.gcf(0.7, 1e30, 1), H)
+    lengths = np.linalg.norm(w.receivers - w.sources, axis=1)
+    assert np.allclose(cq, 0.7 * lengths[None, :], rtol=1e-12)
+
+
+@pytest.mark.parametrize("pow_, expect", [(1, np.exp(-5.0 / 8.0)), (2, np.exp(-25.0 / 64.0))])
+def test_single_source_values_at_3_4_5_distance(pow_, expect):
+    pts = W.grid_points((10, 10))
+    m = pts.shape[0]
+    j0 = 1 * 10 + 2                               # cell (1, 2)
+    rowptr = np.array([0, 1])
+    H = qht.h_csr(rowptr, np.array([j0]), np.array([2.5]), m)
+    cq = qht.qht(pts, kf.gcf(0.01, 8.0, pow_), H)
+    i = (1 + 3) * 10 + (2 + 4)                    # 3 cells along x, 4 along y: distance 5
+    assert cq[i, 0] == pytest.approx(2.5 * 0.01 * expect, rel=1e-14)
+    assert cq[j0, 0] == pytest.approx(2.5 * 0.01, rel=1e-14)
+
+
+def test_sparse_sum_equals_dense_product():
+    w = W.small(grid=(16, 14), n=6, seed=4)
+    H = qht.h_csr(w.h_rowptr, w.h_col, w.h_val, w.m)
+    k = kf.gcf(w.q.theta, w.q.length, w.q.pow)
+    dense = kf.covariance_matrix(w.points, k) @ w.h_dense().T
+    rows = np.array([0, 5, 77, w.m - 1])
+    assert np.allclose(qht.qht(w.points, k, H), dense, rtol=1e-12, atol=1e-15)
+    assert np.allclose(qht.qht(w.points, k, H, rows), dense[rows], rtol=1e-12, atol=1e-15)
