@@ -1,0 +1,327 @@
+"""HiKF steps/s on one GB300 (or N independent replicas), one JSON line.
+
+A step is one measurement update of Alg. 2 (prediction + correction) on the
+2D crosswell workload m = 1024 x 1024 = 2^20 cells, n = 256 rays, the
+exponential kernel of length 64 (the H^2 precomputation runs once before the
+timed region and is reported as `create_ms`). The timed region runs with the
+measurement sequence already resident in HBM; `e2e` repeats it through the
+host-pointer C ABI (y copied in, mean and variance copied out every step).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|mixed]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+
+Under torchrun (N > 1) every rank runs its own filter (an independent
+monitoring stream, weak scaling); value = all ranks' steps / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "HiKF steps/s at m=2^20,n=256 (mixed vs FP32, err<=1e-5); served p50/p99 ms"
+CONFIG_NAME = "crosswell2d_m1048576_n256"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="hikf", choices=["hikf", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed"])
+    ap.add_argument("--order", type=int, default=8)
+    ap.add_argument("--config", default=CONFIG_NAME)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    return ap.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled while the timed region runs
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = Path(os.environ.get("TMPDIR", "/tmp")) / f"hikf_clocks_{os.getpid()}.csv"
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not self.path.exists():
+            return None
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.path.read_text().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        try:
+            self.path.unlink()
+        except Exception:
+            pass
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+        "fallback"
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("step.cu", "sweep_tc.cu"):
+        p = ROOT / "paper_1404_3816_gb300" / "csrc" / f
+        if p.exists():
+            h.update(p.read_bytes())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(precision: str, n: int):
+    """DRAM bytes per sweep launch from the committed ncu summary, if the source is unchanged."""
+    p = ROOT / "profiles" / f"sweep_{precision}_m1048576_n{n}.json"
+    if not p.exists():
+        return None
+    d = json.loads(p.read_text())
+    if d.get("source_hash") != source_hash():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg (FP64 numpy, Alg. 2) on a bounded sample of the same workload
+# ---------------------------------------------------------------------------
+def oracle_steps(w, steps: int, rng_seed: int = 0):
+    """Time `steps` O-cross updates at the full m, n of the workload.
+
+    The exact C_Q of this size is out of reach on a CPU (m * nnz kernel sums), so
+    the sample feeds a PSD stand-in C_Q = G (H G)^T (G: m x 8, seeded); the update
+    arithmetic timed here does not depend on the values of C_Q.
+    """
+    from oracle import kf, qht
+    H = qht.h_csr(w.h_rowptr, w.h_col, w.h_val, w.m)
+    g = np.random.default_rng(rng_seed).standard_normal((w.m, 8)) * 0.01
+    cq = g @ np.asarray(H @ g).T
+    c0 = 100.0 * cq
+    Y = np.random.default_rng(rng_seed + 1).standard_normal((steps, w.n)) * 1e-2
+    t0 = time.perf_counter()
+    kf.hikf_cross(cq, c0, np.full(w.m, 1.0), 0.01, H, w.r_diag, w.x0, Y)
+    dt = time.perf_counter() - t0
+    return dt
+
+
+def cpu_threads() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    from paper_1404_3816_gb300 import workload as W
+    w = W.config(args.config)
+    for _ in range(max(0, args.warmup)):
+        oracle_steps(w, 1)
+    steps = max(1, args.steps)
+    dt = oracle_steps(w, steps)
+    value = steps / dt
+    line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * dt / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": args.config, "m": w.m, "n": w.n, "kernel": "exp L=64",
+                       "note": "FP64 numpy oracle of Alg. 2 on the host cores"},
+            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": cpu_threads(), "kind": "oracle",
+                             "sample": f"{steps} O-cross updates at m={w.m}, n={w.n} with a PSD stand-in C_Q"},
+            "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    rank, world, local = dist_info()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    import torch
+    import torch.distributed as dist
+    from paper_1404_3816_gb300 import binding, workload as W
+
+    assert torch.cuda.is_available(), "bench.py needs a GPU"
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    binding.load()
+
+    w = W.config(args.config, seed=W._cfg_table()[args.config]["seed"] + rank)
+    total = args.warmup + args.steps
+    Y, _ = W.measurements(w, steps=total)
+    dY = torch.tensor(Y, dtype=torch.float64, device="cuda")
+
+    f = binding.Filter.from_workload(w, cheb_order=args.order, precision=args.precision)
+    info = f.info()
+    stream = torch.cuda.ExternalStream(f.stream)
+
+    for t in range(args.warmup):
+        f.assimilate_device(dY[t])
+    f.sync()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    f.profile(True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        for t in range(args.warmup, total):
+            f.assimilate_device(dY[t])
+        ev1.record(stream)
+        ev1.synchronize()
+    f.sync()
+    torch.cuda.synchronize()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    sweep_ms, sweep_n = f.profile_read()
+    f.profile(False)
+    clocks = clk.summary()
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+        dist.barrier()
+    steps_total = args.steps * world
+    value = steps_total / (elapsed_ms / 1000.0)
+
+    # e2e through the C ABI with host buffers: y in, mean and variance out, every step
+    ne2e = max(1, args.e2e_steps)
+    pin_y = torch.tensor(Y[:ne2e], dtype=torch.float64).pin_memory()
+    out_x = torch.empty(w.m, dtype=torch.float64).pin_memory()
+    out_v = torch.empty(w.m, dtype=torch.float64).pin_memory()
+    y_np = pin_y.numpy()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for t in range(ne2e):
+        f.assimilate(y_np[t])
+        f.mean_into(out_x)
+        f.variance_into(out_v)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        tt = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e_value = ne2e * world / e2e_s
+
+    # roofline of the sweep (dominant kernel)
+    pk, pk_kind = peaks()
+    m, n = w.m, w.n
+    per_launch_ms = sweep_ms / max(1, sweep_n)
+    bytes_alg = 12.0 * m * n + 24.0 * m          # read C, C_Q, write C (FP32); x, var r/w (FP64)
+    flops_alg = 2.0 * m * n * n + 6.0 * m * n
+    if args.precision == "fp32":
+        sm_max = float(pk.get("sm_max_mhz", 2070.0))
+        peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12   # FP32 FMA lanes x 2 flop x max SM clock
+        achieved = flops_alg / (per_launch_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": ncu_traffic(args.precision, n),
+                "kernel": "sweep (FP32 CUDA cores)",
+                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (MEASURED_PEAKS sm_max_mhz)"}
+    else:
+        peak = float(pk["hbm_gbs"])
+        achieved = bytes_alg / (per_launch_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": ncu_traffic(args.precision, n), "kernel": "sweep (tcgen05)",
+                "peak_source": f"hbm_gbs of {pk_kind}"}
+    roof["ms_per_launch"] = per_launch_ms
+    roof["alg_bytes_per_launch"] = bytes_alg
+    roof["alg_flops_per_launch"] = flops_alg
+
+    line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "tf32x3",
+            "data": "synthetic",
+            "config": {"workload": args.config, "m": m, "n": n, "dim": 2, "kernel": "exp, L=64, theta=0.01",
+                       "p0": "exp, L=64, theta=1", "R": "1e-3 I", "cheb_order": args.order,
+                       "tree_depth": info["depth"], "precision": args.precision,
+                       "create_ms": info["create_ms"], "device_bytes": info["device_bytes"],
+                       "l2": "no flush: every step streams C and C_Q (2 GB FP32) > L2",
+                       "parallelism": f"replicas x{world}"},
+            "gpu_launches": int(info["sweep_launches"]) * args.steps,
+            "e2e": {"value": e2e_value, "unit": "steps/s", "h2d_bytes_per_step": 8 * n,
+                    "d2h_bytes_per_step": 16 * m, "steps": ne2e},
+            "roofline": roof, "clocks": clocks}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        steps = 3
+        dt = oracle_steps(w, steps)
+        line["cpu_baseline"] = {"value": steps / dt, "unit": "steps/s", "cores": cpu_threads(), "kind": "oracle",
+                                "sample": f"{steps} FP64 O-cross updates at m={m}, n={n} (numpy, PSD stand-in C_Q);"
+                                          " H^2 precompute not included"}
+    f.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

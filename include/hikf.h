@@ -1,0 +1,209 @@
+/*
+ * hikf.h — C ABI of the GB300 HiKF library (libhikf.so).
+ *
+ * HiKF (Li, Ambikasaran, Darve, Kitanidis, "A Kalman filter powered by
+ * H^2-matrices for quasi-continuous data assimilation problems") is the
+ * random-walk Kalman filter (Sec. 2.1, Eq. random_walk: x_t = x_{t-1} + w_t;
+ * Eq. measurement: z_t = H x_t + v_t; w ~ N(0,Q), v ~ N(0,R)) carried by the
+ * m x n cross-covariance C = P H^T instead of the m x m covariance P
+ * (Alg. 2). The model-error cross-covariance C_Q = Q H^T is computed once by a
+ * black-box FMM (Chebyshev-interpolated H^2 product, Sec. 3.2-3.3), and each
+ * measurement update costs O(n^2 m) (Sec. 3.4).
+ *
+ * Conventions shared by every call:
+ *   - All pointers are plain host or device pointers as stated per argument;
+ *     no C++ or torch types cross this interface.
+ *   - Every input is copied during the call; the caller keeps ownership of
+ *     its buffers and may free them when the call returns (for the *_device
+ *     and *_async calls: when the handle's stream has passed the call).
+ *   - Vectors over the m grid points are in the CALLER's point order (the
+ *     order of `points` given to hikf_create); the library's internal tree
+ *     order never leaks out.
+ *   - Every call returns a status; nothing aborts or throws across the ABI.
+ *     hikf_last_error() gives a one-line message for the last failure.
+ *   - A handle is used by one host thread at a time; distinct handles are
+ *     independent (they may share a device and run concurrently).
+ *   - All device memory of a handle is allocated in hikf_create and freed in
+ *     hikf_destroy; a measurement update allocates nothing.
+ */
+#ifndef HIKF_H
+#define HIKF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hikf_handle hikf_t; /* opaque; owns all of its device memory */
+
+typedef enum {
+  HIKF_OK = 0,
+  HIKF_EINVAL = 1,   /* invalid argument: null pointer, size out of range, non-finite value */
+  HIKF_ENOMEM = 2,   /* a device or pinned-host allocation failed */
+  HIKF_ECUDA = 3,    /* a CUDA runtime call failed (message in hikf_last_error) */
+  HIKF_ENOTPD = 4,   /* H C_{t+1|t} + R was not positive definite; the step was not applied */
+  HIKF_ETIMEOUT = 5, /* a bounded device-side wait ran out */
+  HIKF_ESTATE = 6    /* the handle holds an unreported error or the call is out of order */
+} hikf_status;
+
+/* Exponent of the generalised covariance function (Eq. Q):
+ * K(r) = theta * exp(-(r / length)^pow); pow = 1 exponential, pow = 2 Gaussian
+ * (Sec. 3.3, kernels 1-2). theta = 0 gives the zero kernel. */
+enum { HIKF_KERNEL_EXP = 1, HIKF_KERNEL_GAUSS = 2 };
+
+typedef struct {
+  int pow;       /* HIKF_KERNEL_EXP or HIKF_KERNEL_GAUSS */
+  double theta;  /* variance scale, >= 0 (theta = K(0) = diag of the covariance) */
+  double length; /* correlation length l > 0, in the units of `points` */
+} hikf_kernel;
+
+/* Arithmetic of the device path.
+ *   FP32:  C, C_Q and the H^2 product in FP32 on the CUDA cores; the n x n
+ *          solve refined to FP64-level accuracy; diag(P) and the state in FP64.
+ *   MIXED: as FP32, with the per-step O(n^2 m) product on the tensor cores
+ *          (tcgen05, split TF32 operands, FP32 accumulation).
+ *   FP64:  everything in FP64 (small problems; the FP64 rate of this part is low). */
+enum { HIKF_PREC_FP32 = 0, HIKF_PREC_MIXED = 1, HIKF_PREC_FP64 = 2 };
+
+typedef struct {
+  int cheb_order;    /* Chebyshev nodes per axis p, 2..12 (3D: 2..8). Default 8. */
+  int leaf_size;     /* target points per leaf for the automatic depth. Default 64. */
+  int max_depth;     /* uniform tree depth L; -1 = automatic (smallest L with
+                        m <= leaf_size * 2^(dim L)). Default -1. */
+  int precision;     /* HIKF_PREC_*. Default HIKF_PREC_FP32. */
+  void* cuda_stream; /* cudaStream_t the handle runs on; NULL = a stream the handle
+                        creates and owns. Default NULL. */
+} hikf_options;
+
+/* Fill *opt with the defaults listed above. */
+hikf_status hikf_options_default(hikf_options* opt);
+
+/*
+ * hikf_create — precomputation of Alg. 2 (C_Q = Q H^T by the H^2 approach) and
+ * initialisation (Sec. 3.1: x_{0|0}, C_{0|0} = P_0 H^T; delta^2_{0|0} = diag(P_0)).
+ *
+ *   out       receives the new handle (set to NULL on failure).
+ *   dim       2 or 3.
+ *   m         number of grid points (state size), 1 <= m <= 2^31 - 1.
+ *   points    host, m x dim FP64, row-major: point i is points[i*dim .. i*dim+dim-1].
+ *   q         model-error covariance kernel Q (Eq. Q); theta > 0.
+ *   n         number of measurements (rays), 1 <= n <= 512.
+ *   h_rowptr  host, n+1 int64: CSR row pointers of H (n x m), h_rowptr[0] = 0.
+ *   h_col     host, nnz int64 column indices in [0, m) (any order within a row;
+ *             duplicates are summed).
+ *   h_val     host, nnz FP64 values (Sec. 4.1: H_ij = length of ray i in cell j).
+ *   r_diag    host, n FP64 > 0: the diagonal of R (Eq. R: R = sigma^2 I).
+ *   x0        host, m FP64 initial mean x_{0|0}; NULL = zero (Sec. 4.2).
+ *   p0        initial covariance kernel P_0; theta = 0 gives P_0 = 0 (Sec. 4.2).
+ *             If p0 has q's pow and length, C_0 = (p0.theta / q.theta) C_Q and no
+ *             second H^2 product is run.
+ *   opt       NULL = defaults.
+ * Errors: HIKF_EINVAL (sizes, null pointers, non-finite or negative values,
+ * column index out of range), HIKF_ENOMEM, HIKF_ECUDA.
+ */
+hikf_status hikf_create(hikf_t** out, int dim, int64_t m, const double* points, hikf_kernel q, int n,
+                        const int64_t* h_rowptr, const int64_t* h_col, const double* h_val,
+                        const double* r_diag, const double* x0, hikf_kernel p0, const hikf_options* opt);
+
+/*
+ * hikf_create_with_cq — as hikf_create, but C_Q and C_{0|0} are given instead
+ * of computed (host, m x n FP64 row-major, caller's point order). Use it to
+ * check the measurement update separately from the H^2 product. The kernel q
+ * only provides diag(Q) = q.theta and p0 only delta^2_0 = p0.theta.
+ */
+hikf_status hikf_create_with_cq(hikf_t** out, int dim, int64_t m, const double* points, hikf_kernel q,
+                                int n, const int64_t* h_rowptr, const int64_t* h_col, const double* h_val,
+                                const double* r_diag, const double* x0, hikf_kernel p0,
+                                const double* cq, const double* c0, const hikf_options* opt);
+
+/*
+ * hikf_assimilate — one prediction + correction step of Alg. 2 with the
+ * measurement y_{t+1} (host, n FP64):
+ *   C_{t+1|t} = C_{t|t} + C_Q;  delta^2_{t+1|t} = delta^2_{t|t} + diag(Q)
+ *   K = C_{t+1|t} (H C_{t+1|t} + R)^{-1}
+ *   x_{t+1|t+1} = x_{t+1|t} + K (y_{t+1} - H x_{t+1|t})
+ *   delta^2_{t+1|t+1} = delta^2_{t+1|t} - sum_j K_ij (C_{t+1|t})_ij
+ *   C_{t+1|t+1} = C_{t+1|t} - K H C_{t+1|t}
+ * Synchronous: returns when the step is complete. Transactional: on any error
+ * (HIKF_EINVAL for a non-finite y, HIKF_ENOTPD) the state is unchanged.
+ */
+hikf_status hikf_assimilate(hikf_t* h, const double* y);
+
+/*
+ * hikf_assimilate_device — the same step with y (n FP64) in DEVICE memory,
+ * enqueued on the handle's stream without waiting. A failure inside the step
+ * (non-finite y, HIKF_ENOTPD) leaves the state unchanged, turns the following
+ * enqueued steps into no-ops, and is reported by the next hikf_sync (or any
+ * synchronous call), after which the handle works again.
+ */
+hikf_status hikf_assimilate_device(hikf_t* h, const double* d_y);
+
+/* Wait for the handle's stream; return and clear a latched step error. */
+hikf_status hikf_sync(hikf_t* h);
+
+/* Posterior mean x_{t|t} / variance delta^2_{t|t} (Alg. 2) into host `out`
+ * (m FP64, caller's point order). Synchronous. */
+hikf_status hikf_get_mean(hikf_t* h, double* out);
+hikf_status hikf_get_variance(hikf_t* h, double* out);
+
+/* The same into DEVICE `d_out` (m FP64, caller's order), enqueued on the stream. */
+hikf_status hikf_get_mean_device(hikf_t* h, double* d_out);
+hikf_status hikf_get_variance_device(hikf_t* h, double* d_out);
+
+/* Test hooks: the H^2 product C_Q and the current C_{t|t} (host, m x n FP64,
+ * row-major, caller's order); the tree permutation (host, m int64: entry s is
+ * the caller index of the s-th point in tree order). Synchronous. */
+hikf_status hikf_get_cq(hikf_t* h, double* out);
+hikf_status hikf_get_cross(hikf_t* h, double* out);
+hikf_status hikf_get_perm(hikf_t* h, int64_t* out);
+
+typedef struct {
+  int64_t m;
+  int n;
+  int dim;
+  int depth;          /* uniform tree depth L */
+  int cheb_order;     /* p */
+  int precision;      /* HIKF_PREC_* */
+  int64_t step;       /* measurement updates applied */
+  int64_t device_bytes; /* device memory held by the handle */
+  double create_ms;   /* wall time of the precomputation */
+  int sweep_launches; /* kernel launches of one measurement update */
+} hikf_info_t;
+
+hikf_status hikf_info(const hikf_t* h, hikf_info_t* info);
+
+/* Timing of the sweep, the O(n^2 m) pass of every update: while enabled,
+ * CUDA events on the handle's stream bracket each sweep launch (up to 4096
+ * launches; later ones are not recorded). Enabling resets the record. */
+hikf_status hikf_profile_enable(hikf_t* h, int enable);
+
+/* Total duration (ms) of the recorded sweep launches and their number.
+ * Synchronous. */
+hikf_status hikf_profile_read(hikf_t* h, double* sweep_ms, int64_t* sweep_launches);
+
+/* The CUDA stream of the handle (a cudaStream_t). */
+void* hikf_stream(const hikf_t* h);
+
+/* One-line message for the last failure on this handle (h != NULL) or of the
+ * last failed hikf_create on this thread (h == NULL). Never NULL. */
+const char* hikf_last_error(const hikf_t* h);
+
+/* Free the handle and all of its device memory. NULL is ignored. */
+void hikf_destroy(hikf_t* h);
+
+/*
+ * hikf_h2_qht — the H^2 product alone (Alg. 2 precomputation, Sec. 3.2:
+ * Q H^T = [Q h^(1) ... Q h^(n)]), without a filter. Arguments as in
+ * hikf_create; `out` is host m x n FP64, row-major, caller's point order.
+ * Allocates its device memory for the call and frees it before returning.
+ */
+hikf_status hikf_h2_qht(int dim, int64_t m, const double* points, hikf_kernel k, int n,
+                        const int64_t* h_rowptr, const int64_t* h_col, const double* h_val,
+                        const hikf_options* opt, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HIKF_H */

@@ -1,0 +1,291 @@
+"""ctypes binding of libhikf.so: argument marshalling only.
+
+Every step of the filter runs in the CUDA library; this module converts numpy
+arrays and torch device tensors into plain pointers and sizes, calls the C ABI
+of ``include/hikf.h`` and turns status codes into exceptions. If the library
+is missing it raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from pathlib import Path
+from typing import Optional
+
+import numpy as np
+
+LIB_PATH = Path(__file__).resolve().parent / "_lib" / "libhikf.so"
+
+HIKF_OK, HIKF_EINVAL, HIKF_ENOMEM, HIKF_ECUDA, HIKF_ENOTPD, HIKF_ETIMEOUT, HIKF_ESTATE = range(7)
+STATUS_NAMES = {0: "HIKF_OK", 1: "HIKF_EINVAL", 2: "HIKF_ENOMEM", 3: "HIKF_ECUDA", 4: "HIKF_ENOTPD",
+                5: "HIKF_ETIMEOUT", 6: "HIKF_ESTATE"}
+KERNEL_EXP, KERNEL_GAUSS = 1, 2
+PREC_FP32, PREC_MIXED, PREC_FP64 = 0, 1, 2
+PRECISIONS = {"fp32": PREC_FP32, "mixed": PREC_MIXED, "fp64": PREC_FP64}
+
+# every symbol include/hikf.h declares
+EXPORTED = ["hikf_options_default", "hikf_create", "hikf_create_with_cq", "hikf_assimilate",
+            "hikf_assimilate_device", "hikf_sync", "hikf_get_mean", "hikf_get_variance",
+            "hikf_get_mean_device", "hikf_get_variance_device", "hikf_get_cq", "hikf_get_cross",
+            "hikf_get_perm", "hikf_info", "hikf_stream", "hikf_last_error", "hikf_destroy", "hikf_h2_qht",
+            "hikf_profile_enable", "hikf_profile_read"]
+
+
+class HikfError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Kernel(C.Structure):
+    _fields_ = [("pow", C.c_int), ("theta", C.c_double), ("length", C.c_double)]
+
+
+class Options(C.Structure):
+    _fields_ = [("cheb_order", C.c_int), ("leaf_size", C.c_int), ("max_depth", C.c_int),
+                ("precision", C.c_int), ("cuda_stream", C.c_void_p)]
+
+
+class Info(C.Structure):
+    _fields_ = [("m", C.c_int64), ("n", C.c_int), ("dim", C.c_int), ("depth", C.c_int),
+                ("cheb_order", C.c_int), ("precision", C.c_int), ("step", C.c_int64),
+                ("device_bytes", C.c_int64), ("create_ms", C.c_double), ("sweep_launches", C.c_int)]
+
+
+_lib = None
+
+
+def load(path: Optional[os.PathLike] = None) -> C.CDLL:
+    """Load libhikf.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = Path(path) if path else LIB_PATH
+    if not p.exists():
+        raise FileNotFoundError(f"{p} not found: build it with `python -m paper_1404_3816_gb300.build`")
+    lib = C.CDLL(str(p))
+    dp, ip, vp = C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_void_p
+    H = C.c_void_p
+    lib.hikf_options_default.argtypes = [C.POINTER(Options)]
+    lib.hikf_create.argtypes = [C.POINTER(H), C.c_int, C.c_int64, dp, Kernel, C.c_int, ip, ip, dp, dp, dp,
+                                Kernel, C.POINTER(Options)]
+    lib.hikf_create_with_cq.argtypes = [C.POINTER(H), C.c_int, C.c_int64, dp, Kernel, C.c_int, ip, ip, dp, dp,
+                                        dp, Kernel, dp, dp, C.POINTER(Options)]
+    lib.hikf_assimilate.argtypes = [H, dp]
+    lib.hikf_assimilate_device.argtypes = [H, vp]
+    lib.hikf_sync.argtypes = [H]
+    for nm in ("hikf_get_mean", "hikf_get_variance", "hikf_get_cq", "hikf_get_cross"):
+        getattr(lib, nm).argtypes = [H, dp]
+    lib.hikf_get_mean_device.argtypes = [H, vp]
+    lib.hikf_get_variance_device.argtypes = [H, vp]
+    lib.hikf_get_perm.argtypes = [H, ip]
+    lib.hikf_info.argtypes = [H, C.POINTER(Info)]
+    lib.hikf_stream.argtypes = [H]
+    lib.hikf_stream.restype = C.c_void_p
+    lib.hikf_last_error.argtypes = [H]
+    lib.hikf_last_error.restype = C.c_char_p
+    lib.hikf_destroy.argtypes = [H]
+    lib.hikf_destroy.restype = None
+    lib.hikf_profile_enable.argtypes = [H, C.c_int]
+    lib.hikf_profile_read.argtypes = [H, dp, ip]
+    lib.hikf_h2_qht.argtypes = [C.c_int, C.c_int64, dp, Kernel, C.c_int, ip, ip, dp, C.POINTER(Options), dp]
+    for nm in EXPORTED:
+        fn = getattr(lib, nm)
+        if fn.restype is C.c_int or nm not in ("hikf_stream", "hikf_last_error", "hikf_destroy"):
+            if nm not in ("hikf_stream", "hikf_last_error", "hikf_destroy"):
+                fn.restype = C.c_int
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _dp(a: Optional[np.ndarray]):
+    if a is None:
+        return None
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _ip(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_int64))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _i64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int64))
+
+
+def kernel_struct(spec) -> Kernel:
+    """From an object with .pow/.theta/.length or a (pow, theta, length) tuple."""
+    if isinstance(spec, tuple):
+        return Kernel(int(spec[0]), float(spec[1]), float(spec[2]))
+    return Kernel(int(spec.pow), float(spec.theta), float(spec.length))
+
+
+def options(cheb_order: int = 8, leaf_size: int = 64, max_depth: int = -1, precision="fp32",
+            stream=None) -> Options:
+    o = Options()
+    load().hikf_options_default(C.byref(o))
+    o.cheb_order = int(cheb_order)
+    o.leaf_size = int(leaf_size)
+    o.max_depth = int(max_depth)
+    o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    if stream is not None:
+        o.cuda_stream = C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+    return o
+
+
+def _check(code: int, h=None):
+    if code != HIKF_OK:
+        msg = load().hikf_last_error(h)
+        raise HikfError(code, msg.decode() if msg else "")
+
+
+class Filter:
+    """One HiKF filter (a handle of the C ABI)."""
+
+    def __init__(self, points, q, h_rowptr, h_col, h_val, r_diag, x0=None, p0=None, cq=None, c0=None,
+                 **opts):
+        lib = load()
+        self._keep = []
+        pts = _f64(points)
+        m, dim = pts.shape
+        rowptr, col, val = _i64(h_rowptr), _i64(h_col), _f64(h_val)
+        rd = _f64(r_diag)
+        n = rowptr.shape[0] - 1
+        x0a = None if x0 is None else _f64(x0)
+        p0k = kernel_struct(p0) if p0 is not None else Kernel(int(getattr(q, "pow", 1)), 0.0, 1.0)
+        o = options(**opts)
+        self.h = C.c_void_p()
+        if cq is None:
+            code = lib.hikf_create(C.byref(self.h), dim, m, _dp(pts), kernel_struct(q), n, _ip(rowptr), _ip(col),
+                                   _dp(val), _dp(rd), _dp(x0a), p0k, C.byref(o))
+        else:
+            cqa, c0a = _f64(cq), _f64(c0)
+            code = lib.hikf_create_with_cq(C.byref(self.h), dim, m, _dp(pts), kernel_struct(q), n, _ip(rowptr),
+                                           _ip(col), _dp(val), _dp(rd), _dp(x0a), p0k, _dp(cqa), _dp(c0a),
+                                           C.byref(o))
+        if code != HIKF_OK:
+            self.h = None
+            _check(code, None)
+        self.m, self.n, self.dim = m, n, dim
+
+    @classmethod
+    def from_workload(cls, w, **opts):
+        """Build from a ``workload.Workload`` (points, kernels, CSR H, R, x0)."""
+        opts.setdefault("cheb_order", w.cheb_order)
+        opts.setdefault("leaf_size", w.leaf_size)
+        return cls(w.points, w.q, w.h_rowptr, w.h_col, w.h_val, w.r_diag, w.x0, w.p0, **opts)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().hikf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # --- measurement update -------------------------------------------------
+    def assimilate(self, y):
+        ya = _f64(y)
+        assert ya.shape == (self.n,)
+        _check(load().hikf_assimilate(self.h, _dp(ya)), self.h)
+
+    def assimilate_device(self, d_y):
+        """y as a device pointer (int) or a CUDA tensor of n float64; asynchronous."""
+        ptr = d_y.data_ptr() if hasattr(d_y, "data_ptr") else int(d_y)
+        _check(load().hikf_assimilate_device(self.h, C.c_void_p(ptr)), self.h)
+
+    def sync(self):
+        _check(load().hikf_sync(self.h), self.h)
+
+    # --- outputs --------------------------------------------------------------
+    def mean(self) -> np.ndarray:
+        out = np.empty(self.m)
+        _check(load().hikf_get_mean(self.h, _dp(out)), self.h)
+        return out
+
+    def variance(self) -> np.ndarray:
+        out = np.empty(self.m)
+        _check(load().hikf_get_variance(self.h, _dp(out)), self.h)
+        return out
+
+    def mean_into(self, out) -> None:
+        """Host (numpy, possibly pinned) or device (torch CUDA tensor) m-vector of float64."""
+        if hasattr(out, "is_cuda") and out.is_cuda:
+            _check(load().hikf_get_mean_device(self.h, C.c_void_p(out.data_ptr())), self.h)
+        else:
+            _check(load().hikf_get_mean(self.h, C.cast(C.c_void_p(_host_ptr(out)), C.POINTER(C.c_double))),
+                   self.h)
+
+    def variance_into(self, out) -> None:
+        if hasattr(out, "is_cuda") and out.is_cuda:
+            _check(load().hikf_get_variance_device(self.h, C.c_void_p(out.data_ptr())), self.h)
+        else:
+            _check(load().hikf_get_variance(self.h, C.cast(C.c_void_p(_host_ptr(out)), C.POINTER(C.c_double))),
+                   self.h)
+
+    def cq(self) -> np.ndarray:
+        out = np.empty((self.m, self.n))
+        _check(load().hikf_get_cq(self.h, _dp(out)), self.h)
+        return out
+
+    def cross(self) -> np.ndarray:
+        out = np.empty((self.m, self.n))
+        _check(load().hikf_get_cross(self.h, _dp(out)), self.h)
+        return out
+
+    def perm(self) -> np.ndarray:
+        out = np.empty(self.m, dtype=np.int64)
+        _check(load().hikf_get_perm(self.h, _ip(out)), self.h)
+        return out
+
+    def info(self) -> dict:
+        i = Info()
+        _check(load().hikf_info(self.h, C.byref(i)), self.h)
+        return {k: getattr(i, k) for k, _ in Info._fields_}
+
+    def profile(self, enable: bool = True):
+        _check(load().hikf_profile_enable(self.h, int(enable)), self.h)
+
+    def profile_read(self):
+        """(total sweep ms, number of recorded sweep launches)."""
+        ms = C.c_double()
+        cnt = C.c_int64()
+        _check(load().hikf_profile_read(self.h, C.byref(ms), C.byref(cnt)), self.h)
+        return ms.value, cnt.value
+
+    @property
+    def stream(self) -> int:
+        return int(load().hikf_stream(self.h) or 0)
+
+
+def _host_ptr(a) -> int:
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def h2_qht(points, kernel, h_rowptr, h_col, h_val, **opts) -> np.ndarray:
+    """The H^2 product Q H^T alone (m x n, caller order)."""
+    lib = load()
+    pts = _f64(points)
+    m, dim = pts.shape
+    rowptr, col, val = _i64(h_rowptr), _i64(h_col), _f64(h_val)
+    n = rowptr.shape[0] - 1
+    out = np.empty((m, n))
+    o = options(**opts)
+    _check(lib.hikf_h2_qht(dim, m, _dp(pts), kernel_struct(kernel), n, _ip(rowptr), _ip(col), _dp(val),
+                           C.byref(o), _dp(out)), None)
+    return out

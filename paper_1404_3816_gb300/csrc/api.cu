@@ -1,0 +1,631 @@
+// C ABI of the HiKF library: handle lifetime, precomputation and the
+// measurement update (Alg. 2), see include/hikf.h.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "hikf_internal.cuh"
+#include "step.cuh"
+
+namespace hikf {
+
+Status make_status(hikf_status c, const std::string& m) {
+  Status s;
+  s.code = c;
+  s.msg = m;
+  return s;
+}
+
+Status cuda_status(cudaError_t e, const char* what, const char* file, int line) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e) + " (" + file + ":" + std::to_string(line) + ")";
+  return make_status(e == cudaErrorMemoryAllocation ? HIKF_ENOMEM : HIKF_ECUDA, m);
+}
+
+Status Arena::alloc(void** p, size_t nbytes) {
+  *p = nullptr;
+  if (count >= 64) return make_status(HIKF_ENOMEM, "arena full");
+  if (nbytes == 0) nbytes = 16;
+  cudaError_t e = cudaMalloc(p, nbytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return cuda_status(e, "cudaMalloc", __FILE__, __LINE__);
+  }
+  ptrs[count++] = *p;
+  bytes += (int64_t)nbytes;
+  return Status::Ok();
+}
+
+void Arena::release() {
+  for (int i = 0; i < count; ++i) cudaFree(ptrs[i]);
+  count = 0;
+  bytes = 0;
+}
+
+int padded_ld(int n) { return (n + 31) / 32 * 32; }
+
+namespace {
+
+constexpr int kThreads = 256;
+inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
+
+template <typename T>
+__global__ void rows_to_tree(const double* __restrict__ src, const int64_t* __restrict__ perm, int64_t m, int n,
+                             int ld, T* __restrict__ dst) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m * ld) return;
+  int64_t s = t / ld;
+  int c = (int)(t % ld);
+  dst[t] = c < n ? (T)src[perm[s] * n + c] : (T)0;
+}
+
+template <typename T>
+__global__ void rows_to_caller(const T* __restrict__ src, const int64_t* __restrict__ perm, int64_t m, int n, int ld,
+                               double* __restrict__ dst) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m * n) return;
+  int64_t s = t / n;
+  int c = (int)(t % n);
+  dst[perm[s] * n + c] = (double)src[s * ld + c];
+}
+
+__global__ void vec_to_caller(const double* __restrict__ src, const int64_t* __restrict__ perm, int64_t m,
+                              double* __restrict__ dst) {
+  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < m) dst[perm[s]] = src[s];
+}
+
+__global__ void vec_to_tree(const double* __restrict__ src, const int64_t* __restrict__ perm, int64_t m,
+                            double* __restrict__ dst) {
+  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < m) dst[s] = src ? src[perm[s]] : 0.0;
+}
+
+__global__ void fill_kernel(double* __restrict__ v, int64_t m, double val) {
+  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < m) v[s] = val;
+}
+
+template <typename T>
+__global__ void scale_kernel(const T* __restrict__ src, T* __restrict__ dst, int64_t count, double f) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < count) dst[t] = (T)((double)src[t] * f);
+}
+
+__global__ void count_step(const int* __restrict__ flag, long long* __restrict__ step) {
+  if (*flag == 0) *step += 1;
+}
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+}  // namespace hikf
+
+using hikf::Status;
+
+struct hikf_handle {
+  int dim = 2;
+  int64_t m = 0;
+  int n = 0;
+  int ld = 0;
+  int nt = 0;
+  int prec = HIKF_PREC_FP32;
+  int order = 8;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int sms = 1;
+  hikf::Arena arena;
+  hikf::Tree tree;
+  hikf::SparseH H;
+  void* C = nullptr;
+  void* CQ = nullptr;
+  double* x = nullptr;
+  double* var = nullptr;
+  double theta_q = 0.0;
+  double* rd = nullptr;
+  double* hcq_sym = nullptr;
+  double* S = nullptr;
+  hikf::ChainArgs chain;
+  void* Msw = nullptr;
+  double* e = nullptr;
+  double* a = nullptr;
+  double* ybuf = nullptr;
+  double* outbuf = nullptr;
+  long long* dstep = nullptr;
+  int* flag = nullptr;
+  std::string err;
+  double create_ms = 0.0;
+  int launches = 0;
+  // sweep timing (hikf_profile_enable)
+  bool prof = false;
+  int prof_count = 0;
+  std::vector<cudaEvent_t> ev;
+
+  bool fp64() const { return prec == HIKF_PREC_FP64; }
+};
+
+namespace {
+
+hikf_status fail(hikf_t* h, const Status& s) {
+  if (h) h->err = s.msg; else hikf::g_create_error = s.msg;
+  return s.code;
+}
+
+Status validate_common(int dim, int64_t m, const double* points, int n, const int64_t* rowptr, const int64_t* col,
+                       const double* val, const double* r_diag, const double* x0, const hikf_options& o) {
+  using hikf::make_status;
+  if (dim != 2 && dim != 3) return make_status(HIKF_EINVAL, "dim must be 2 or 3");
+  if (m < 1 || m > 2147483647LL) return make_status(HIKF_EINVAL, "m out of range [1, 2^31-1]");
+  if (n < 1 || n > hikf::kMaxN) return make_status(HIKF_EINVAL, "n out of range [1, 512]");
+  if (!points || !rowptr || !r_diag) return make_status(HIKF_EINVAL, "null input pointer");
+  if (rowptr[0] != 0) return make_status(HIKF_EINVAL, "h_rowptr[0] must be 0");
+  for (int r = 0; r < n; ++r)
+    if (rowptr[r + 1] < rowptr[r]) return make_status(HIKF_EINVAL, "h_rowptr not monotone");
+  const int64_t nnz = rowptr[n];
+  if (nnz > 0 && (!col || !val)) return make_status(HIKF_EINVAL, "null h_col/h_val");
+  if (nnz > 2147483647LL) return make_status(HIKF_EINVAL, "nnz too large");
+  for (int64_t k = 0; k < nnz; ++k) {
+    if (col[k] < 0 || col[k] >= m) return make_status(HIKF_EINVAL, "h_col index out of range");
+    if (!std::isfinite(val[k])) return make_status(HIKF_EINVAL, "non-finite h_val");
+  }
+  for (int64_t i = 0; i < m * dim; ++i)
+    if (!std::isfinite(points[i])) return make_status(HIKF_EINVAL, "non-finite point coordinate");
+  for (int r = 0; r < n; ++r)
+    if (!(r_diag[r] > 0.0) || !std::isfinite(r_diag[r])) return make_status(HIKF_EINVAL, "r_diag must be > 0");
+  if (x0)
+    for (int64_t i = 0; i < m; ++i)
+      if (!std::isfinite(x0[i])) return make_status(HIKF_EINVAL, "non-finite x0");
+  const int pmax = dim == 2 ? hikf::kMaxOrder2D : hikf::kMaxOrder3D;
+  if (o.cheb_order < 2 || o.cheb_order > pmax) return make_status(HIKF_EINVAL, "cheb_order out of range");
+  if (o.leaf_size < 1) return make_status(HIKF_EINVAL, "leaf_size must be >= 1");
+  const int dmax = dim == 2 ? hikf::kMaxDepth2D : hikf::kMaxDepth3D;
+  if (o.max_depth > dmax) return make_status(HIKF_EINVAL, "max_depth too large");
+  if (o.precision != HIKF_PREC_FP32 && o.precision != HIKF_PREC_FP64 && o.precision != HIKF_PREC_MIXED)
+    return make_status(HIKF_EINVAL, "unknown precision");
+  return Status::Ok();
+}
+
+Status validate_kernel(const hikf_kernel& k, bool allow_zero) {
+  using hikf::make_status;
+  if (k.pow != HIKF_KERNEL_EXP && k.pow != HIKF_KERNEL_GAUSS) return make_status(HIKF_EINVAL, "kernel pow must be 1 or 2");
+  if (!std::isfinite(k.theta) || k.theta < 0.0 || (!allow_zero && k.theta == 0.0))
+    return make_status(HIKF_EINVAL, "kernel theta out of range");
+  if (k.theta != 0.0 && (!(k.length > 0.0) || !std::isfinite(k.length)))
+    return make_status(HIKF_EINVAL, "kernel length must be > 0");
+  return Status::Ok();
+}
+
+template <typename T>
+Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const double* x0, const double* cq,
+                   const double* c0, const double* r_diag) {
+  cudaStream_t s = h->stream;
+  const int64_t m = h->m;
+  const int n = h->n, ld = h->ld;
+  T *C = nullptr, *CQ = nullptr;
+  HIKF_TRY(hikf::arena_alloc(h->arena, &C, (size_t)m * ld));
+  HIKF_TRY(hikf::arena_alloc(h->arena, &CQ, (size_t)m * ld));
+  h->C = C;
+  h->CQ = CQ;
+  if (cq) {
+    double* d = nullptr;
+    HIKF_CUDA(cudaMallocAsync((void**)&d, sizeof(double) * (size_t)m * n, s));
+    HIKF_CUDA(cudaMemcpyAsync(d, cq, sizeof(double) * (size_t)m * n, cudaMemcpyHostToDevice, s));
+    hikf::rows_to_tree<T><<<hikf::nblk(m * ld, 256), 256, 0, s>>>(d, h->tree.perm, m, n, ld, CQ);
+    HIKF_LAUNCH_CHECK("rows_to_tree");
+    HIKF_CUDA(cudaMemcpyAsync(d, c0, sizeof(double) * (size_t)m * n, cudaMemcpyHostToDevice, s));
+    hikf::rows_to_tree<T><<<hikf::nblk(m * ld, 256), 256, 0, s>>>(d, h->tree.perm, m, n, ld, C);
+    HIKF_LAUNCH_CHECK("rows_to_tree");
+    HIKF_CUDA(cudaFreeAsync(d, s));
+  } else {
+    hikf::FmmParams fp;
+    fp.order = h->order;
+    fp.pow = q.pow;
+    fp.theta = q.theta;
+    fp.length = q.length;
+    HIKF_TRY(hikf::h2_product<T>(h->tree, h->H, fp, CQ, ld, s));
+    if (p0.theta == 0.0) {
+      HIKF_CUDA(cudaMemsetAsync(C, 0, sizeof(T) * (size_t)m * ld, s));
+    } else if (p0.pow == q.pow && p0.length == q.length) {
+      // P_0 = (theta_0 / theta_Q) Q  =>  C_0 = P_0 H^T = (theta_0 / theta_Q) C_Q
+      hikf::scale_kernel<T><<<hikf::nblk(m * ld, 256), 256, 0, s>>>(CQ, C, m * ld, p0.theta / q.theta);
+      HIKF_LAUNCH_CHECK("scale");
+    } else {
+      hikf::FmmParams f0;
+      f0.order = h->order;
+      f0.pow = p0.pow;
+      f0.theta = p0.theta;
+      f0.length = p0.length;
+      HIKF_TRY(hikf::h2_product<T>(h->tree, h->H, f0, C, ld, s));
+    }
+  }
+  // mean, variance
+  HIKF_TRY(hikf::arena_alloc(h->arena, &h->x, m));
+  HIKF_TRY(hikf::arena_alloc(h->arena, &h->var, m));
+  HIKF_TRY(hikf::arena_alloc(h->arena, &h->outbuf, m));
+  if (x0) {
+    HIKF_CUDA(cudaMemcpyAsync(h->outbuf, x0, sizeof(double) * m, cudaMemcpyHostToDevice, s));
+    hikf::vec_to_tree<<<hikf::nblk(m, 256), 256, 0, s>>>(h->outbuf, h->tree.perm, m, h->x);
+  } else {
+    hikf::vec_to_tree<<<hikf::nblk(m, 256), 256, 0, s>>>(nullptr, h->tree.perm, m, h->x);
+  }
+  HIKF_LAUNCH_CHECK("vec_to_tree");
+  hikf::fill_kernel<<<hikf::nblk(m, 256), 256, 0, s>>>(h->var, m, p0.theta);
+  HIKF_LAUNCH_CHECK("fill");
+  h->theta_q = q.theta;
+
+  // n x n state: S_1 = sym(H C_0 + H C_Q) + R, and sym(H C_Q) for the recurrence
+  HIKF_TRY(hikf::arena_alloc(h->arena, &h->rd, n));
+  HIKF_TRY(hikf::arena_alloc(h->arena, &h->hcq_sym, (size_t)n * n));
+  HIKF_TRY(hikf::arena_alloc(h->arena, &h->S, (size_t)n * n));
+  HIKF_CUDA(cudaMemcpyAsync(h->rd, r_diag, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+  double *hcq = nullptr, *a1 = nullptr, *zero = nullptr;
+  HIKF_CUDA(cudaMallocAsync((void**)&hcq, sizeof(double) * (size_t)n * n, s));
+  HIKF_CUDA(cudaMallocAsync((void**)&a1, sizeof(double) * (size_t)n * n, s));
+  HIKF_CUDA(cudaMallocAsync((void**)&zero, sizeof(double) * n, s));
+  HIKF_CUDA(cudaMemsetAsync(zero, 0, sizeof(double) * n, s));
+  HIKF_TRY(hikf::launch_gather_hc<T>(h->H, CQ, ld, hcq, 0, s));
+  HIKF_TRY(hikf::launch_form_s(hcq, zero, n, h->hcq_sym, s));
+  HIKF_TRY(hikf::launch_gather_hc<T>(h->H, C, ld, a1, 0, s));
+  HIKF_TRY(hikf::launch_gather_hc<T>(h->H, CQ, ld, a1, 1, s));
+  HIKF_TRY(hikf::launch_form_s(a1, h->rd, n, h->S, s));
+  HIKF_CUDA(cudaFreeAsync(hcq, s));
+  HIKF_CUDA(cudaFreeAsync(a1, s));
+  HIKF_CUDA(cudaFreeAsync(zero, s));
+
+  // chain scratch
+  hikf::ChainArgs& c = h->chain;
+  c.n = n;
+  c.ldm = n;
+  c.S = h->S;
+  const size_t nn = (size_t)n * n;
+  HIKF_TRY(hikf::arena_alloc(h->arena, &c.Shi, nn));
+  HIKF_TRY(hikf::arena_alloc(h->arena, &c.Slo, nn));
+  HIKF_TRY(hikf::arena_alloc(h->arena, &c.L32, nn));
+  HIKF_TRY(hikf::arena_alloc(h->arena, &c.X32, nn));
+  HIKF_TRY(hikf::arena_alloc(h->arena, &c.E, 2 * nn));
+  HIKF_TRY(hikf::arena_alloc(h->arena, &c.Mh, nn));
+  HIKF_TRY(hikf::arena_alloc(h->arena, &c.Ml, nn));
+  HIKF_TRY(hikf::arena_alloc(h->arena, &c.L64, nn));
+  HIKF_TRY(hikf::arena_alloc(h->arena, &c.X64, nn));
+  if (h->fp64()) HIKF_TRY(hikf::arena_alloc(h->arena, &c.M64, nn));
+  HIKF_TRY(hikf::arena_alloc(h->arena, &c.emax, 1));
+  HIKF_TRY(hikf::arena_alloc(h->arena, &h->flag, 2));
+  HIKF_TRY(hikf::arena_alloc(h->arena, &h->dstep, 1));
+  HIKF_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int) * 2, s));
+  HIKF_CUDA(cudaMemsetAsync(h->dstep, 0, sizeof(long long), s));
+  c.flag = h->flag;
+  c.fp64 = h->fp64() ? 1 : 0;
+  T* msw = nullptr;
+  HIKF_TRY(hikf::arena_alloc(h->arena, &msw, (size_t)h->nt * h->nt));
+  HIKF_CUDA(cudaMemsetAsync(msw, 0, sizeof(T) * (size_t)h->nt * h->nt, s));
+  h->Msw = msw;
+  HIKF_TRY(hikf::arena_alloc(h->arena, &h->e, n));
+  HIKF_TRY(hikf::arena_alloc(h->arena, &h->a, n));
+  HIKF_TRY(hikf::arena_alloc(h->arena, &h->ybuf, n));
+  return Status::Ok();
+}
+
+template <typename T>
+Status enqueue_step(hikf_t* h) {
+  cudaStream_t s = h->stream;
+  hikf::ChainArgs& c = h->chain;
+  int launches = 0;
+  HIKF_TRY(hikf::launch_chain(c, s));
+  launches += c.fp64 ? 1 : (2 + 3 * c.refine_iters + 3);
+  HIKF_TRY(hikf::launch_innovation(h->ybuf, h->H, h->x, h->e, h->flag, s));
+  HIKF_TRY(hikf::launch_gemv<T>(c.Mh, c.Ml, c.M64, h->n, c.ldm, h->e, h->a, (T*)h->Msw, h->nt, h->flag, s));
+  hikf::SweepArgs<T> sa;
+  sa.m = h->m;
+  sa.ld = h->ld;
+  sa.n = h->n;
+  sa.CQ = (const T*)h->CQ;
+  sa.C = (T*)h->C;
+  sa.Msw = (const T*)h->Msw;
+  sa.a = h->a;
+  sa.rd = h->rd;
+  sa.theta = h->theta_q;
+  sa.x = h->x;
+  sa.var = h->var;
+  sa.flag = h->flag;
+  const bool rec = h->prof && h->prof_count < (int)h->ev.size() / 2;
+  if (rec) HIKF_CUDA(cudaEventRecord(h->ev[2 * h->prof_count], s));
+  HIKF_TRY(hikf::launch_sweep<T>(sa, s, h->sms));
+  if (rec) {
+    HIKF_CUDA(cudaEventRecord(h->ev[2 * h->prof_count + 1], s));
+    ++h->prof_count;
+  }
+  hikf::count_step<<<1, 1, 0, s>>>(h->flag, h->dstep);
+  HIKF_LAUNCH_CHECK("count_step");
+  HIKF_TRY(hikf::launch_recur(h->hcq_sym, h->rd, c.Mh, c.Ml, c.M64, h->n, c.ldm, h->flag, h->S, s));
+  launches += 6;
+  h->launches = launches;
+  return Status::Ok();
+}
+
+Status enqueue(hikf_t* h) { return h->fp64() ? enqueue_step<double>(h) : enqueue_step<float>(h); }
+
+Status read_flag(hikf_t* h, int* out) {
+  int f[2] = {0, 0};
+  HIKF_CUDA(cudaMemcpyAsync(f, h->flag, sizeof(int) * 2, cudaMemcpyDeviceToHost, h->stream));
+  HIKF_CUDA(cudaStreamSynchronize(h->stream));
+  *out = f[0];
+  if (f[0]) HIKF_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int) * 2, h->stream));
+  return Status::Ok();
+}
+
+Status flag_status(int f) {
+  if (f & 1) return hikf::make_status(HIKF_EINVAL, "non-finite measurement y; step not applied");
+  if (f & 2) return hikf::make_status(HIKF_ENOTPD, "H C + R is not positive definite; step not applied");
+  return Status::Ok();
+}
+
+hikf_status create_impl(hikf_t** out, int dim, int64_t m, const double* points, hikf_kernel q, int n,
+                        const int64_t* rowptr, const int64_t* col, const double* val, const double* r_diag,
+                        const double* x0, hikf_kernel p0, const double* cq, const double* c0,
+                        const hikf_options* opt) {
+  auto t0 = std::chrono::steady_clock::now();
+  if (!out) return fail(nullptr, hikf::make_status(HIKF_EINVAL, "out is NULL"));
+  *out = nullptr;
+  hikf_options o;
+  hikf_options_default(&o);
+  if (opt) o = *opt;
+  Status st = validate_common(dim, m, points, n, rowptr, col, val, r_diag, x0, o);
+  if (!st.ok()) return fail(nullptr, st);
+  st = validate_kernel(q, cq != nullptr);
+  if (!st.ok()) return fail(nullptr, st);
+  st = validate_kernel(p0, true);
+  if (!st.ok()) return fail(nullptr, st);
+  if (cq && !c0) return fail(nullptr, hikf::make_status(HIKF_EINVAL, "c0 is NULL"));
+  if (o.precision == HIKF_PREC_MIXED)
+    return fail(nullptr, hikf::make_status(HIKF_EINVAL, "MIXED precision is not available in this build"));
+  hikf_t* h = new (std::nothrow) hikf_handle();
+  if (!h) return fail(nullptr, hikf::make_status(HIKF_ENOMEM, "host allocation failed"));
+  auto bail = [&](const Status& s) {
+    hikf::g_create_error = s.msg;
+    hikf_destroy(h);
+    return s.code;
+  };
+  h->dim = dim;
+  h->m = m;
+  h->n = n;
+  h->ld = hikf::padded_ld(n);
+  h->nt = hikf::sweep_nt(h->ld);
+  h->prec = o.precision;
+  h->order = o.cheb_order;
+  if (o.cuda_stream) {
+    h->stream = (cudaStream_t)o.cuda_stream;
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(hikf::cuda_status(e, "cudaStreamCreate", __FILE__, __LINE__));
+    h->own_stream = true;
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev);
+  h->tree.dim = dim;
+  h->tree.m = m;
+  h->tree.depth = o.max_depth >= 0 ? o.max_depth : hikf::auto_depth(m, dim, o.leaf_size);
+  const int dmax = dim == 2 ? hikf::kMaxDepth2D : hikf::kMaxDepth3D;
+  if (h->tree.depth > dmax) return bail(hikf::make_status(HIKF_EINVAL, "automatic depth too large; raise leaf_size"));
+  double* d_pts = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&d_pts, sizeof(double) * (size_t)m * dim, h->stream);
+  if (e != cudaSuccess) return bail(hikf::cuda_status(e, "cudaMallocAsync", __FILE__, __LINE__));
+  e = cudaMemcpyAsync(d_pts, points, sizeof(double) * (size_t)m * dim, cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess) return bail(hikf::cuda_status(e, "cudaMemcpyAsync", __FILE__, __LINE__));
+  st = hikf::build_tree(h->tree, h->arena, d_pts, h->stream);
+  cudaFreeAsync(d_pts, h->stream);
+  if (!st.ok()) return bail(st);
+  st = hikf::build_sparse(h->H, h->arena, h->tree, rowptr, col, val, n, h->stream);
+  if (!st.ok()) return bail(st);
+  st = h->fp64() ? setup_state<double>(h, q, p0, x0, cq, c0, r_diag) : setup_state<float>(h, q, p0, x0, cq, c0, r_diag);
+  if (!st.ok()) return bail(st);
+  e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return bail(hikf::cuda_status(e, "create", __FILE__, __LINE__));
+  h->create_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  *out = h;
+  return HIKF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hikf_status hikf_options_default(hikf_options* opt) {
+  if (!opt) return HIKF_EINVAL;
+  opt->cheb_order = 8;
+  opt->leaf_size = 64;
+  opt->max_depth = -1;
+  opt->precision = HIKF_PREC_FP32;
+  opt->cuda_stream = nullptr;
+  return HIKF_OK;
+}
+
+hikf_status hikf_create(hikf_t** out, int dim, int64_t m, const double* points, hikf_kernel q, int n,
+                        const int64_t* h_rowptr, const int64_t* h_col, const double* h_val, const double* r_diag,
+                        const double* x0, hikf_kernel p0, const hikf_options* opt) {
+  return create_impl(out, dim, m, points, q, n, h_rowptr, h_col, h_val, r_diag, x0, p0, nullptr, nullptr, opt);
+}
+
+hikf_status hikf_create_with_cq(hikf_t** out, int dim, int64_t m, const double* points, hikf_kernel q, int n,
+                                const int64_t* h_rowptr, const int64_t* h_col, const double* h_val,
+                                const double* r_diag, const double* x0, hikf_kernel p0, const double* cq,
+                                const double* c0, const hikf_options* opt) {
+  if (!cq) return fail(nullptr, hikf::make_status(HIKF_EINVAL, "cq is NULL"));
+  return create_impl(out, dim, m, points, q, n, h_rowptr, h_col, h_val, r_diag, x0, p0, cq, c0, opt);
+}
+
+hikf_status hikf_assimilate(hikf_t* h, const double* y) {
+  if (!h || !y) return h ? fail(h, hikf::make_status(HIKF_EINVAL, "y is NULL")) : HIKF_EINVAL;
+  for (int r = 0; r < h->n; ++r)
+    if (!std::isfinite(y[r])) return fail(h, hikf::make_status(HIKF_EINVAL, "non-finite measurement y"));
+  int f = 0;
+  Status st = read_flag(h, &f);
+  if (!st.ok()) return fail(h, st);
+  if (f) return fail(h, hikf::make_status(HIKF_ESTATE, "an earlier asynchronous step failed: " + flag_status(f).msg));
+  cudaError_t e = cudaMemcpyAsync(h->ybuf, y, sizeof(double) * h->n, cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess) return fail(h, hikf::cuda_status(e, "copy y", __FILE__, __LINE__));
+  st = enqueue(h);
+  if (!st.ok()) return fail(h, st);
+  st = read_flag(h, &f);
+  if (!st.ok()) return fail(h, st);
+  st = flag_status(f);
+  if (!st.ok()) return fail(h, st);
+  return HIKF_OK;
+}
+
+hikf_status hikf_assimilate_device(hikf_t* h, const double* d_y) {
+  if (!h || !d_y) return h ? fail(h, hikf::make_status(HIKF_EINVAL, "d_y is NULL")) : HIKF_EINVAL;
+  cudaError_t e = cudaMemcpyAsync(h->ybuf, d_y, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, h->stream);
+  if (e != cudaSuccess) return fail(h, hikf::cuda_status(e, "copy y", __FILE__, __LINE__));
+  Status st = enqueue(h);
+  if (!st.ok()) return fail(h, st);
+  return HIKF_OK;
+}
+
+hikf_status hikf_sync(hikf_t* h) {
+  if (!h) return HIKF_EINVAL;
+  int f = 0;
+  Status st = read_flag(h, &f);
+  if (!st.ok()) return fail(h, st);
+  st = flag_status(f);
+  if (!st.ok()) return fail(h, st);
+  return HIKF_OK;
+}
+
+static hikf_status get_vec(hikf_t* h, const double* src, double* out, bool device) {
+  if (!h || !out) return h ? fail(h, hikf::make_status(HIKF_EINVAL, "out is NULL")) : HIKF_EINVAL;
+  hikf::vec_to_caller<<<hikf::nblk(h->m, 256), 256, 0, h->stream>>>(src, h->tree.perm, h->m,
+                                                                     device ? out : h->outbuf);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(h, hikf::cuda_status(e, "vec_to_caller", __FILE__, __LINE__));
+  if (!device) {
+    e = cudaMemcpyAsync(out, h->outbuf, sizeof(double) * h->m, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return fail(h, hikf::cuda_status(e, "copy out", __FILE__, __LINE__));
+  }
+  return HIKF_OK;
+}
+
+hikf_status hikf_get_mean(hikf_t* h, double* out) { return get_vec(h, h ? h->x : nullptr, out, false); }
+hikf_status hikf_get_variance(hikf_t* h, double* out) { return get_vec(h, h ? h->var : nullptr, out, false); }
+hikf_status hikf_get_mean_device(hikf_t* h, double* d_out) { return get_vec(h, h ? h->x : nullptr, d_out, true); }
+hikf_status hikf_get_variance_device(hikf_t* h, double* d_out) {
+  return get_vec(h, h ? h->var : nullptr, d_out, true);
+}
+
+static hikf_status get_mat(hikf_t* h, const void* src, double* out) {
+  if (!h || !out) return h ? fail(h, hikf::make_status(HIKF_EINVAL, "out is NULL")) : HIKF_EINVAL;
+  double* d = nullptr;
+  const size_t bytes = sizeof(double) * (size_t)h->m * h->n;
+  cudaError_t e = cudaMallocAsync((void**)&d, bytes, h->stream);
+  if (e != cudaSuccess) return fail(h, hikf::cuda_status(e, "cudaMallocAsync", __FILE__, __LINE__));
+  if (h->fp64())
+    hikf::rows_to_caller<double><<<hikf::nblk(h->m * h->n, 256), 256, 0, h->stream>>>(
+        (const double*)src, h->tree.perm, h->m, h->n, h->ld, d);
+  else
+    hikf::rows_to_caller<float><<<hikf::nblk(h->m * h->n, 256), 256, 0, h->stream>>>(
+        (const float*)src, h->tree.perm, h->m, h->n, h->ld, d);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, bytes, cudaMemcpyDeviceToHost, h->stream);
+  cudaFreeAsync(d, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return fail(h, hikf::cuda_status(e, "get matrix", __FILE__, __LINE__));
+  return HIKF_OK;
+}
+
+hikf_status hikf_get_cq(hikf_t* h, double* out) { return get_mat(h, h ? h->CQ : nullptr, out); }
+hikf_status hikf_get_cross(hikf_t* h, double* out) { return get_mat(h, h ? h->C : nullptr, out); }
+
+hikf_status hikf_get_perm(hikf_t* h, int64_t* out) {
+  if (!h || !out) return HIKF_EINVAL;
+  cudaError_t e = cudaMemcpyAsync(out, h->tree.perm, sizeof(int64_t) * h->m, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return fail(h, hikf::cuda_status(e, "get perm", __FILE__, __LINE__));
+  return HIKF_OK;
+}
+
+hikf_status hikf_info(const hikf_t* h, hikf_info_t* info) {
+  if (!h || !info) return HIKF_EINVAL;
+  memset(info, 0, sizeof(*info));
+  info->m = h->m;
+  info->n = h->n;
+  info->dim = h->dim;
+  info->depth = h->tree.depth;
+  info->cheb_order = h->order;
+  info->precision = h->prec;
+  long long st = 0;
+  if (cudaMemcpyAsync(&st, h->dstep, sizeof(long long), cudaMemcpyDeviceToHost, h->stream) == cudaSuccess &&
+      cudaStreamSynchronize(h->stream) == cudaSuccess)
+    info->step = st;
+  info->device_bytes = h->arena.bytes;
+  info->create_ms = h->create_ms;
+  info->sweep_launches = h->launches;
+  return HIKF_OK;
+}
+
+hikf_status hikf_profile_enable(hikf_t* h, int enable) {
+  if (!h) return HIKF_EINVAL;
+  if (enable && h->ev.empty()) {
+    h->ev.resize(2 * 4096);
+    for (auto& e : h->ev) {
+      cudaError_t r = cudaEventCreate(&e);
+      if (r != cudaSuccess) return fail(h, hikf::cuda_status(r, "cudaEventCreate", __FILE__, __LINE__));
+    }
+  }
+  h->prof = enable != 0;
+  h->prof_count = 0;
+  return HIKF_OK;
+}
+
+hikf_status hikf_profile_read(hikf_t* h, double* sweep_ms, int64_t* sweep_launches) {
+  if (!h || !sweep_ms || !sweep_launches) return HIKF_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return fail(h, hikf::cuda_status(e, "sync", __FILE__, __LINE__));
+  double tot = 0.0;
+  for (int i = 0; i < h->prof_count; ++i) {
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, h->ev[2 * i], h->ev[2 * i + 1]);
+    if (e != cudaSuccess) return fail(h, hikf::cuda_status(e, "cudaEventElapsedTime", __FILE__, __LINE__));
+    tot += ms;
+  }
+  *sweep_ms = tot;
+  *sweep_launches = h->prof_count;
+  return HIKF_OK;
+}
+
+void* hikf_stream(const hikf_t* h) { return h ? (void*)h->stream : nullptr; }
+
+const char* hikf_last_error(const hikf_t* h) {
+  if (h) return h->err.c_str();
+  return hikf::g_create_error.c_str();
+}
+
+void hikf_destroy(hikf_t* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  h->arena.release();
+  for (auto& e : h->ev) cudaEventDestroy(e);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+hikf_status hikf_h2_qht(int dim, int64_t m, const double* points, hikf_kernel k, int n, const int64_t* h_rowptr,
+                        const int64_t* h_col, const double* h_val, const hikf_options* opt, double* out) {
+  if (!out) return fail(nullptr, hikf::make_status(HIKF_EINVAL, "out is NULL"));
+  std::vector<double> rd(std::max(n, 1), 1.0);
+  hikf_kernel zero = {k.pow, 0.0, 1.0};
+  hikf_t* h = nullptr;
+  hikf_status s = hikf_create(&h, dim, m, points, k, n, h_rowptr, h_col, h_val, rd.data(), nullptr, zero, opt);
+  if (s != HIKF_OK) return s;
+  s = hikf_get_cq(h, out);
+  if (s != HIKF_OK) hikf::g_create_error = h->err;
+  hikf_destroy(h);
+  return s;
+}
+
+}  // extern "C"

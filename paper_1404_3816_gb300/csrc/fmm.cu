@@ -1,0 +1,695 @@
+// H^2 product C_Q = Q H^T by a black-box FMM with tensor Chebyshev
+// interpolation (Sec. 3.2-3.3; Alg. 2 precomputation).
+//
+// Q H^T = [Q h^(1) ... Q h^(n)]: the n columns of H^T are n source vectors of
+// one FMM. Far-field kernel blocks between well-separated boxes B, B' are
+// replaced by their Chebyshev interpolant
+//     K(x, y) ~ sum_{a,c} S(x; B, a) K(xbar_a^B, ybar_c^B') S(y; B', c),
+// with first-kind nodes cos((2k-1)pi/(2p)) per axis and the 1-D weight
+// s_p(u, xi) = 1/p + (2/p) sum_{j=1}^{p-1} T_j(u) T_j(xi).
+// Passes: P2M (leaf anterpolation), M2M (upward, nested interpolation), M2L
+// (interaction lists), L2L (downward), L2P + P2P (near field, exact kernel).
+//
+// Layout in HBM: the boxes of all levels are concatenated (level l starts at
+// box_offset[l], boxes in Morton order); multipole W and local L arrays hold
+// [box][q][ld] with the n ray columns contiguous (ld = padded n), so every
+// pass streams whole 128-byte rows of n values.
+#include <math.h>
+
+#include <algorithm>
+
+#include "hikf_internal.cuh"
+
+namespace hikf {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kPMax = 12;
+constexpr int kPT = 64;   // points per chunk in P2M / L2P / P2P
+
+struct Geo {
+  double lo[3];
+  double side;
+  int dim, depth, p, q, ld, n;
+  int pow;
+  double theta, length;
+};
+
+__host__ __device__ inline int64_t cmin64(int64_t a, int64_t b) { return a < b ? a : b; }
+
+__host__ __device__ inline int ipow(int b, int e) {
+  int r = 1;
+  for (int i = 0; i < e; ++i) r *= b;
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// tables
+// ---------------------------------------------------------------------------
+// tab layout (double): [0, p*p): Tj(xi_k) at [j*p + k]; then T1[c][a'][a] (2*p*p)
+__global__ void cheb_tables(int p, double* __restrict__ tab) {
+  int t = threadIdx.x;
+  const double pi = 3.141592653589793238462643383279502884;
+  if (t < p * p) {
+    int j = t / p, k = t % p;
+    double xi = cos((2.0 * (k + 1) - 1.0) * pi / (2.0 * p));
+    tab[t] = cos(j * acos(xi));  // T_j(xi) = cos(j arccos xi)
+  }
+  __syncthreads();
+  if (t < 2 * p * p) {
+    int c = t / (p * p), ap = (t / p) % p, a = t % p;
+    double xi_ap = cos((2.0 * (ap + 1) - 1.0) * pi / (2.0 * p));
+    double u = 0.5 * (xi_ap + (c ? 1.0 : -1.0));  // child node in parent-local coordinates
+    // s_p(u, xi_a)
+    double s = 1.0 / p, tprev = 1.0, tcur = u;
+    for (int j = 1; j < p; ++j) {
+      s += (2.0 / p) * tcur * tab[j * p + a];
+      double tn = 2.0 * u * tcur - tprev;
+      tprev = tcur;
+      tcur = tn;
+    }
+    tab[p * p + t] = s;
+  }
+}
+
+__device__ __forceinline__ double kernel_value_d(double r2, int pow, double theta, double length) {
+  if (pow == 2) return theta * exp(-r2 / (length * length));
+  return theta * exp(-sqrt(r2) / length);
+}
+
+template <typename T>
+__device__ __forceinline__ T kernel_value(T r2, int pow, T theta, T inv_len, T inv_len2);
+
+template <>
+__device__ __forceinline__ float kernel_value<float>(float r2, int pow, float theta, float inv_len, float inv_len2) {
+  if (pow == 2) return theta * expf(-r2 * inv_len2);
+  return theta * expf(-sqrtf(r2) * inv_len);
+}
+template <>
+__device__ __forceinline__ double kernel_value<double>(double r2, int pow, double theta, double inv_len,
+                                                       double inv_len2) {
+  if (pow == 2) return theta * exp(-r2 * inv_len2);
+  return theta * exp(-sqrt(r2) * inv_len);
+}
+
+// M2L operator table: kop[(lev-2)][off][a][c] = K(xbar_a^B - ybar_c^{B+off})
+template <typename T>
+__global__ void m2l_table(Geo g, const double* __restrict__ tab, T* __restrict__ kop, int64_t total) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  const int q = g.q, p = g.p, dim = g.dim;
+  const int noff = ipow(7, dim);
+  int c = (int)(t % q);
+  int a = (int)((t / q) % q);
+  int off = (int)((t / ((int64_t)q * q)) % noff);
+  int lev = 2 + (int)(t / ((int64_t)q * q * noff));
+  const double pi = 3.141592653589793238462643383279502884;
+  double s = g.side / (double)(1 << lev);
+  double r2 = 0.0;
+  int aa = a, cc = c, oo = off;
+  for (int d = dim - 1; d >= 0; --d) {
+    int ad = aa % p, cd = cc % p, od = oo % 7 - 3;
+    aa /= p;
+    cc /= p;
+    oo /= 7;
+    double xa = cos((2.0 * (ad + 1) - 1.0) * pi / (2.0 * p));
+    double xc = cos((2.0 * (cd + 1) - 1.0) * pi / (2.0 * p));
+    double diff = 0.5 * s * (xa - xc) - s * od;
+    r2 += diff * diff;
+  }
+  kop[t] = (T)kernel_value_d(r2, g.pow, g.theta, g.length);
+}
+
+// per-box count of H^T nonzeros (sources) below the box
+__global__ void box_sources(const int64_t* __restrict__ leaf_start, const int64_t* __restrict__ trowptr,
+                            const int64_t* __restrict__ box_offset_d, int depth, int dim, int64_t nbox,
+                            int64_t* __restrict__ nsrc, int64_t* __restrict__ npts) {
+  int64_t gb = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gb >= nbox) return;
+  int lev = 0;
+  while (lev < depth && gb >= box_offset_d[lev + 1]) ++lev;
+  int64_t b = gb - box_offset_d[lev];
+  int64_t span = (int64_t)1 << (dim * (depth - lev));
+  int64_t p0 = leaf_start[b * span], p1 = leaf_start[(b + 1) * span];
+  nsrc[gb] = trowptr[p1] - trowptr[p0];
+  npts[gb] = p1 - p0;
+}
+
+// 1-D weights s_p(u, xi_k) for k < p, u in [-1, 1]
+template <typename T>
+__device__ __forceinline__ void weights_1d(T u, int p, const T* __restrict__ tj, T* __restrict__ w) {
+  // tj[j*p + k] = T_j(xi_k)
+  T tprev = (T)1, tcur = u;
+  const T inv = (T)1 / (T)p;
+  for (int k = 0; k < p; ++k) w[k] = inv;
+  for (int j = 1; j < p; ++j) {
+    const T f = (T)2 * inv * tcur;
+    for (int k = 0; k < p; ++k) w[k] += f * tj[j * p + k];
+    T tn = (T)2 * u * tcur - tprev;
+    tprev = tcur;
+    tcur = tn;
+  }
+}
+
+// S[i][a] for the points [ps, ps+cnt) in the leaf with Morton index b; smem out (kPT x q)
+template <typename T>
+__device__ void leaf_weights(const Geo& g, const double* __restrict__ pts, int64_t ps, int cnt, int64_t b,
+                             const T* __restrict__ tj, T* __restrict__ w1 /* kPT*3*kPMax */, T* __restrict__ S) {
+  const int p = g.p, dim = g.dim, q = g.q;
+  // leaf coordinates of box b from its Morton index
+  int64_t c[3] = {0, 0, 0};
+  for (int bit = 0; bit < g.depth; ++bit)
+    for (int d = 0; d < dim; ++d) c[d] |= ((b >> (bit * dim + (dim - 1 - d))) & 1) << bit;
+  const double wl = g.side / (double)((int64_t)1 << g.depth);
+  for (int t = threadIdx.x; t < cnt * dim; t += blockDim.x) {
+    int i = t / dim, d = t % dim;
+    double ctr = g.lo[d] + ((double)c[d] + 0.5) * wl;
+    T u = (T)((pts[(ps + i) * dim + d] - ctr) / (0.5 * wl));
+    weights_1d<T>(u, p, tj, w1 + (i * 3 + d) * kPMax);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < cnt * q; t += blockDim.x) {
+    int i = t / q, a = t % q;
+    T s = (T)1;
+    int aa = a;
+    for (int d = dim - 1; d >= 0; --d) {
+      s *= w1[(i * 3 + d) * kPMax + aa % p];
+      aa /= p;
+    }
+    S[i * q + a] = s;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// P2M: W_b = S_b^T H^T_b at the leaves
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) p2m_kernel(Geo g, const double* __restrict__ pts,
+                                                       const int64_t* __restrict__ leaf_start,
+                                                       const int64_t* __restrict__ trowptr,
+                                                       const int32_t* __restrict__ tcol,
+                                                       const double* __restrict__ tval,
+                                                       const double* __restrict__ tab,
+                                                       const int64_t* __restrict__ nsrc, int64_t leaf_box0, int nch,
+                                                       T* __restrict__ W) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* tj = reinterpret_cast<T*>(smem_raw);                // p*p
+  T* w1 = tj + kPMax * kPMax;                            // kPT*3*kPMax
+  T* S = w1 + kPT * 3 * kPMax;                           // kPT*q
+  T* Hd = S + kPT * g.q;                                 // kPT*nch
+  const int64_t b = blockIdx.x;
+  if (nsrc[leaf_box0 + b] == 0) return;
+  const int p = g.p, q = g.q, ld = g.ld;
+  for (int t = threadIdx.x; t < p * p; t += blockDim.x) tj[t] = (T)tab[t];
+  T* Wb = W + (leaf_box0 + b) * (int64_t)q * ld;
+  const int64_t p0 = leaf_start[b], p1 = leaf_start[b + 1];
+  __syncthreads();
+  for (int64_t ps = p0; ps < p1; ps += kPT) {
+    const int cnt = (int)cmin64(kPT, p1 - ps);
+    leaf_weights<T>(g, pts, ps, cnt, b, tj, w1, S);
+    for (int r0 = 0; r0 < ld; r0 += nch) {
+      for (int t = threadIdx.x; t < kPT * nch; t += blockDim.x) Hd[t] = (T)0;
+      __syncthreads();
+      for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+        for (int64_t e = trowptr[ps + i]; e < trowptr[ps + i + 1]; ++e) {
+          int r = tcol[e] - r0;
+          if (r >= 0 && r < nch) Hd[i * nch + r] += (T)tval[e];
+        }
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < q * nch; t += blockDim.x) {
+        int a = t / nch, r = t % nch;
+        if (r0 + r >= ld) continue;
+        T acc = (T)0;
+        for (int i = 0; i < cnt; ++i) acc += S[i * q + a] * Hd[i * nch + r];
+        Wb[(int64_t)a * ld + r0 + r] += acc;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// separable application of the 1-D transfer along one axis (smem -> smem)
+//   dst[a][r] = sum_k M[k][a_ax] src[a with a_ax := k][r]   (forward: M = T1[c] as [child][parent])
+//   transposed: dst[a][r] = sum_k M[a_ax][k] src[...k...][r]
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ void apply_axis(const T* __restrict__ src, T* __restrict__ dst, const T* __restrict__ M, int p, int q,
+                           int dim, int ax, int nch, bool transposed) {
+  const int stride = ipow(p, dim - 1 - ax);
+  for (int t = threadIdx.x; t < q * nch; t += blockDim.x) {
+    int a = t / nch, r = t % nch;
+    int aax = (a / stride) % p;
+    int base = a - aax * stride;
+    T acc = (T)0;
+    for (int k = 0; k < p; ++k) {
+      T mv = transposed ? M[aax * p + k] : M[k * p + aax];
+      acc += mv * src[(base + k * stride) * nch + r];
+    }
+    dst[t] = acc;
+  }
+  __syncthreads();
+}
+
+// M2M: W_parent = sum_children (T1[c_0] x ... x T1[c_{d-1}])^T W_child
+template <typename T>
+__global__ void __launch_bounds__(kThreads) m2m_kernel(Geo g, int lev, const double* __restrict__ tab,
+                                                       const int64_t* __restrict__ nsrc, int64_t box0,
+                                                       int64_t child0, int nch, T* __restrict__ W) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int p = g.p, q = g.q, ld = g.ld, dim = g.dim;
+  T* t1 = reinterpret_cast<T*>(smem_raw);  // 2*p*p
+  T* acc = t1 + 2 * kPMax * kPMax;         // q*nch
+  T* bufA = acc + q * nch;
+  T* bufB = bufA + q * nch;
+  const int64_t P = blockIdx.x;
+  if (nsrc[box0 + P] == 0) return;
+  for (int t = threadIdx.x; t < 2 * p * p; t += blockDim.x) t1[t] = (T)tab[p * p + t];
+  const int nchild = 1 << dim;
+  for (int r0 = 0; r0 < ld; r0 += nch) {
+    const int w = min(nch, ld - r0);
+    for (int t = threadIdx.x; t < q * nch; t += blockDim.x) acc[t] = (T)0;
+    __syncthreads();
+    for (int c = 0; c < nchild; ++c) {
+      const int64_t cb = child0 + P * nchild + c;
+      if (nsrc[cb] == 0) continue;
+      const T* Wc = W + cb * (int64_t)q * ld;
+      for (int t = threadIdx.x; t < q * nch; t += blockDim.x) {
+        int a = t / nch, r = t % nch;
+        bufA[t] = r < w ? Wc[(int64_t)a * ld + r0 + r] : (T)0;
+      }
+      __syncthreads();
+      T* s = bufA;
+      T* d = bufB;
+      for (int ax = 0; ax < dim; ++ax) {
+        int cax = (c >> (dim - 1 - ax)) & 1;
+        apply_axis<T>(s, d, t1 + cax * p * p, p, q, dim, ax, nch, false);
+        T* tmp = s;
+        s = d;
+        d = tmp;
+      }
+      for (int t = threadIdx.x; t < q * nch; t += blockDim.x) acc[t] += s[t];
+      __syncthreads();
+    }
+    T* Wp = W + (box0 + P) * (int64_t)q * ld;
+    for (int t = threadIdx.x; t < q * nch; t += blockDim.x) {
+      int a = t / nch, r = t % nch;
+      if (r < w) Wp[(int64_t)a * ld + r0 + r] = acc[t];
+    }
+    __syncthreads();
+  }
+}
+
+// L2L: L_child += (T1[c_0] x ... ) L_parent
+template <typename T>
+__global__ void __launch_bounds__(kThreads) l2l_kernel(Geo g, int lev, const double* __restrict__ tab,
+                                                       const int64_t* __restrict__ npts, int64_t box0,
+                                                       int64_t child0, int nch, T* __restrict__ Lx) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int p = g.p, q = g.q, ld = g.ld, dim = g.dim;
+  T* t1 = reinterpret_cast<T*>(smem_raw);
+  T* par = t1 + 2 * kPMax * kPMax;
+  T* bufA = par + q * nch;
+  T* bufB = bufA + q * nch;
+  const int64_t P = blockIdx.x;
+  if (npts[box0 + P] == 0) return;
+  for (int t = threadIdx.x; t < 2 * p * p; t += blockDim.x) t1[t] = (T)tab[p * p + t];
+  const int nchild = 1 << dim;
+  const T* Lp = Lx + (box0 + P) * (int64_t)q * ld;
+  for (int r0 = 0; r0 < ld; r0 += nch) {
+    const int w = min(nch, ld - r0);
+    for (int t = threadIdx.x; t < q * nch; t += blockDim.x) {
+      int a = t / nch, r = t % nch;
+      par[t] = r < w ? Lp[(int64_t)a * ld + r0 + r] : (T)0;
+    }
+    __syncthreads();
+    for (int c = 0; c < nchild; ++c) {
+      const int64_t cb = child0 + P * nchild + c;
+      if (npts[cb] == 0) continue;
+      const T* s = par;
+      T* d = bufA;
+      for (int ax = 0; ax < dim; ++ax) {
+        int cax = (c >> (dim - 1 - ax)) & 1;
+        apply_axis<T>(s, d, t1 + cax * p * p, p, q, dim, ax, nch, true);
+        s = d;
+        d = (d == bufA) ? bufB : bufA;
+      }
+      T* Lc = Lx + cb * (int64_t)q * ld;
+      for (int t = threadIdx.x; t < q * nch; t += blockDim.x) {
+        int a = t / nch, r = t % nch;
+        if (r < w) Lc[(int64_t)a * ld + r0 + r] += s[t];
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// M2L: L_B += sum_{B' in IL(B)} K_{lev, B'-B} W_B'   (tiled GEMM over the list)
+// ---------------------------------------------------------------------------
+constexpr int kM2L_BM = 64, kM2L_BN = 64, kM2L_BK = 16;
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) m2l_kernel(Geo g, int lev, const T* __restrict__ kop,
+                                                       const int64_t* __restrict__ nsrc,
+                                                       const int64_t* __restrict__ npts, int64_t box0,
+                                                       const T* __restrict__ W, T* __restrict__ Lx) {
+  __shared__ T As[kM2L_BK][kM2L_BM];
+  __shared__ T Bs[kM2L_BK][kM2L_BN];
+  __shared__ int il_box[216];
+  __shared__ int il_off[216];
+  __shared__ int il_n;
+  const int q = g.q, ld = g.ld, dim = g.dim;
+  const int64_t B = blockIdx.x;
+  if (npts[box0 + B] == 0) return;
+  const int a0 = blockIdx.y * kM2L_BM, r0 = blockIdx.z * kM2L_BN;
+  if (r0 >= ld) return;
+  // box coordinates from Morton index
+  int64_t cb[3] = {0, 0, 0};
+  for (int bit = 0; bit < lev; ++bit)
+    for (int d = 0; d < dim; ++d) cb[d] |= ((B >> (bit * dim + (dim - 1 - d))) & 1) << bit;
+  if (threadIdx.x == 0) il_n = 0;
+  __syncthreads();
+  // candidates: children of the parent's neighbours, offsets in [-3, 3]^dim relative to B
+  const int ncand = ipow(6, dim);
+  for (int t = threadIdx.x; t < ncand; t += blockDim.x) {
+    int tt = t;
+    int64_t cc[3] = {0, 0, 0};
+    int offs[3] = {0, 0, 0};
+    bool ok = true, sep = false;
+    for (int d = dim - 1; d >= 0; --d) {
+      int k = tt % 6;
+      tt /= 6;
+      cc[d] = 2 * (cb[d] >> 1) - 2 + k;
+      offs[d] = (int)(cc[d] - cb[d]);
+      if (cc[d] < 0 || cc[d] >= ((int64_t)1 << lev)) ok = false;
+      if (offs[d] > 1 || offs[d] < -1) sep = true;
+    }
+    if (!ok || !sep) continue;
+    int64_t key = 0;
+    for (int bit = lev - 1; bit >= 0; --bit)
+      for (int d = 0; d < dim; ++d) key = (key << 1) | ((cc[d] >> bit) & 1);
+    if (nsrc[box0 + key] == 0) continue;
+    int oi = 0;
+    for (int d = 0; d < dim; ++d) oi = oi * 7 + (offs[d] + 3);
+    int slot = atomicAdd(&il_n, 1);
+    il_box[slot] = (int)key;
+    il_off[slot] = oi;
+  }
+  __syncthreads();
+  const int nil = il_n;
+  if (nil == 0) return;
+  // deterministic order of the list
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < nil; ++i) {
+      int kb = il_box[i], ko = il_off[i], j = i - 1;
+      while (j >= 0 && il_box[j] > kb) {
+        il_box[j + 1] = il_box[j];
+        il_off[j + 1] = il_off[j];
+        --j;
+      }
+      il_box[j + 1] = kb;
+      il_off[j + 1] = ko;
+    }
+  }
+  __syncthreads();
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;  // 16 x 16 threads, 4 x 4 outputs each
+  T acc[4][4];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) acc[i][j] = (T)0;
+  const int noff = ipow(7, dim);
+  const T* kl = kop + (int64_t)(lev - 2) * noff * q * q;
+  const int kblocks = (q + kM2L_BK - 1) / kM2L_BK;
+  for (int e = 0; e < nil; ++e) {
+    const T* K = kl + (int64_t)il_off[e] * q * q;
+    const T* Ws = W + (box0 + il_box[e]) * (int64_t)q * ld;
+    for (int kb = 0; kb < kblocks; ++kb) {
+      const int c0 = kb * kM2L_BK;
+      for (int t = threadIdx.x; t < kM2L_BK * kM2L_BM; t += blockDim.x) {
+        int a = t / kM2L_BK, kk = t % kM2L_BK;
+        As[kk][a] = (a0 + a < q && c0 + kk < q) ? K[(int64_t)(a0 + a) * q + c0 + kk] : (T)0;
+      }
+      for (int t = threadIdx.x; t < kM2L_BK * kM2L_BN; t += blockDim.x) {
+        int kk = t / kM2L_BN, r = t % kM2L_BN;
+        Bs[kk][r] = (c0 + kk < q && r0 + r < ld) ? Ws[(int64_t)(c0 + kk) * ld + r0 + r] : (T)0;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < kM2L_BK; ++kk) {
+        T av[4], bv[4];
+        for (int i = 0; i < 4; ++i) av[i] = As[kk][ty * 4 + i];
+        for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+        for (int i = 0; i < 4; ++i)
+          for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
+      }
+      __syncthreads();
+    }
+  }
+  T* Lb = Lx + (box0 + B) * (int64_t)q * ld;
+  for (int i = 0; i < 4; ++i) {
+    int a = a0 + ty * 4 + i;
+    if (a >= q) continue;
+    for (int j = 0; j < 4; ++j) {
+      int r = r0 + tx + 16 * j;
+      if (r < ld) Lb[(int64_t)a * ld + r] += acc[i][j];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// L2P + P2P: C_Q rows of one leaf
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) l2p_p2p_kernel(Geo g, const double* __restrict__ pts,
+                                                           const int64_t* __restrict__ leaf_start,
+                                                           const int64_t* __restrict__ trowptr,
+                                                           const int32_t* __restrict__ tcol,
+                                                           const double* __restrict__ tval,
+                                                           const double* __restrict__ tab,
+                                                           const int64_t* __restrict__ nsrc, int64_t leaf_box0,
+                                                           int nch, const T* __restrict__ Lx, T* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int p = g.p, q = g.q, ld = g.ld, dim = g.dim, L = g.depth;
+  T* tj = reinterpret_cast<T*>(smem_raw);
+  T* w1 = tj + kPMax * kPMax;
+  T* S = w1 + kPT * 3 * kPMax;
+  T* Cs = S + kPT * q;                  // kPT x (nch + 1)
+  T* tx = Cs + kPT * (nch + 1);         // kPT x 3 target coords relative to the leaf centre
+  T* sx = tx + kPT * 3;                 // kPT x 3 staged source coords
+  int64_t* se = reinterpret_cast<int64_t*>(sx + kPT * 3 + 2);  // kPT x 2 H^T row ranges (8-byte aligned)
+  const int64_t b = blockIdx.x;
+  const int64_t p0 = leaf_start[b], p1 = leaf_start[b + 1];
+  if (p1 == p0) return;
+  for (int t = threadIdx.x; t < p * p; t += blockDim.x) tj[t] = (T)tab[t];
+  int64_t cb[3] = {0, 0, 0};
+  for (int bit = 0; bit < L; ++bit)
+    for (int d = 0; d < dim; ++d) cb[d] |= ((b >> (bit * dim + (dim - 1 - d))) & 1) << bit;
+  const double wl = g.side / (double)((int64_t)1 << L);
+  double ctr[3];
+  for (int d = 0; d < dim; ++d) ctr[d] = g.lo[d] + ((double)cb[d] + 0.5) * wl;
+  const T theta = (T)g.theta, inv_len = (T)(1.0 / g.length), inv_len2 = (T)(1.0 / (g.length * g.length));
+  const T* Lb = Lx + (leaf_box0 + b) * (int64_t)q * ld;
+  const int nnb = ipow(3, dim);
+  const int parts = kThreads / kPT;  // threads per target point
+  __syncthreads();
+  for (int64_t ps = p0; ps < p1; ps += kPT) {
+    const int cnt = (int)cmin64(kPT, p1 - ps);
+    if (L >= 2) leaf_weights<T>(g, pts, ps, cnt, b, tj, w1, S);
+    for (int t = threadIdx.x; t < cnt * dim; t += blockDim.x) {
+      int i = t / dim, d = t % dim;
+      tx[i * 3 + d] = (T)(pts[(ps + i) * dim + d] - ctr[d]);
+    }
+    __syncthreads();
+    for (int r0 = 0; r0 < ld; r0 += nch) {
+      const int w = min(nch, ld - r0);
+      // L2P
+      for (int t = threadIdx.x; t < kPT * nch; t += blockDim.x) {
+        int i = t / nch, r = t % nch;
+        T acc = (T)0;
+        if (L >= 2 && i < cnt && r < w) {
+          for (int a = 0; a < q; ++a) acc += S[i * q + a] * Lb[(int64_t)a * ld + r0 + r];
+        }
+        Cs[i * (nch + 1) + r] = acc;
+      }
+      __syncthreads();
+      // P2P over the touching leaves (exact kernel, sparse sources); the source
+      // coordinates relative to this leaf's centre are staged once per chunk
+      const int i = threadIdx.x % kPT, part = threadIdx.x / kPT;
+      const int cw = (nch + parts - 1) / parts;
+      const int rlo = part * cw, rhi = min(nch, rlo + cw);
+      T xi[3] = {(T)0, (T)0, (T)0};
+      if (i < cnt)
+        for (int d = 0; d < dim; ++d) xi[d] = tx[i * 3 + d];
+      for (int nb = 0; nb < nnb; ++nb) {
+        int64_t cn[3] = {0, 0, 0};
+        int tt = nb;
+        bool ok = true;
+        for (int d = dim - 1; d >= 0; --d) {
+          cn[d] = cb[d] + (tt % 3) - 1;
+          tt /= 3;
+          if (cn[d] < 0 || cn[d] >= ((int64_t)1 << L)) ok = false;
+        }
+        if (!ok) continue;
+        int64_t key = 0;
+        for (int bit = L - 1; bit >= 0; --bit)
+          for (int d = 0; d < dim; ++d) key = (key << 1) | ((cn[d] >> bit) & 1);
+        if (nsrc[leaf_box0 + key] == 0) continue;
+        for (int64_t js = leaf_start[key]; js < leaf_start[key + 1]; js += kPT) {
+          const int jc = (int)cmin64(kPT, leaf_start[key + 1] - js);
+          for (int t = threadIdx.x; t < jc; t += blockDim.x) {
+            se[2 * t] = trowptr[js + t];
+            se[2 * t + 1] = trowptr[js + t + 1];
+            for (int d = 0; d < dim; ++d) sx[t * 3 + d] = (T)(pts[(js + t) * dim + d] - ctr[d]);
+          }
+          __syncthreads();
+          if (i < cnt) {
+            for (int j = 0; j < jc; ++j) {
+              const int64_t e0 = se[2 * j], e1 = se[2 * j + 1];
+              if (e0 == e1) continue;
+              T r2 = (T)0;
+              for (int d = 0; d < dim; ++d) {
+                T dx = xi[d] - sx[j * 3 + d];
+                r2 += dx * dx;
+              }
+              const T kv = kernel_value<T>(r2, g.pow, theta, inv_len, inv_len2);
+              for (int64_t e = e0; e < e1; ++e) {
+                int r = tcol[e] - r0;
+                if (r >= rlo && r < rhi) Cs[i * (nch + 1) + r] += kv * (T)tval[e];
+              }
+            }
+          }
+          __syncthreads();
+        }
+      }
+      for (int t = threadIdx.x; t < cnt * nch; t += blockDim.x) {
+        int ii = t / nch, r = t % nch;
+        if (r < w) out[(ps + ii) * (int64_t)ld + r0 + r] = Cs[ii * (nch + 1) + r];
+      }
+      __syncthreads();
+    }
+  }
+}
+
+inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
+
+template <typename T>
+Status set_smem(const void* fn, size_t bytes) {
+  if (bytes > 48 * 1024) HIKF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  return Status::Ok();
+}
+
+}  // namespace
+
+template <typename T>
+Status h2_product(const Tree& t, const SparseH& h, const FmmParams& fp, T* out, int ldc, cudaStream_t s) {
+  Geo g;
+  for (int d = 0; d < 3; ++d) g.lo[d] = t.lo[d];
+  g.side = t.side;
+  g.dim = t.dim;
+  g.depth = t.depth;
+  g.p = fp.order;
+  g.q = ipow(fp.order, t.dim);
+  g.ld = ldc;
+  g.n = h.n;
+  g.pow = fp.pow;
+  g.theta = fp.theta;
+  g.length = fp.length;
+  const int p = g.p, q = g.q, L = t.depth, dim = t.dim;
+  const int64_t nbox = t.nbox_total;
+  const int64_t m = t.m;
+
+  HIKF_CUDA(cudaMemsetAsync(out, 0, sizeof(T) * (size_t)m * ldc, s));
+  // column chunk: keep q * nch * sizeof(T) * 3 within ~150 KB
+  int nch = 128;
+  while (nch > 32 && (size_t)q * nch * sizeof(T) * 3 > 150 * 1024) nch /= 2;
+  nch = std::min(nch, ldc);
+
+  double* tab = nullptr;
+  int64_t *nsrc = nullptr, *npts = nullptr, *boff = nullptr;
+  T *W = nullptr, *Lx = nullptr, *kop = nullptr;
+  const size_t boxbytes = sizeof(T) * (size_t)q * ldc;
+  HIKF_CUDA(cudaMallocAsync((void**)&tab, sizeof(double) * 3 * kPMax * kPMax, s));
+  HIKF_CUDA(cudaMallocAsync((void**)&nsrc, sizeof(int64_t) * nbox, s));
+  HIKF_CUDA(cudaMallocAsync((void**)&npts, sizeof(int64_t) * nbox, s));
+  HIKF_CUDA(cudaMallocAsync((void**)&boff, sizeof(int64_t) * (L + 2), s));
+  HIKF_CUDA(cudaMemcpyAsync(boff, t.box_offset, sizeof(int64_t) * (L + 2), cudaMemcpyHostToDevice, s));
+  cheb_tables<<<1, 512, 0, s>>>(p, tab);
+  HIKF_LAUNCH_CHECK("cheb_tables");
+  box_sources<<<nblk(nbox, kThreads), kThreads, 0, s>>>(t.leaf_start, h.trowptr, boff, L, dim, nbox, nsrc, npts);
+  HIKF_LAUNCH_CHECK("box_sources");
+
+  const int64_t leaf0 = t.box_offset[L];
+  const size_t smem_pts = sizeof(T) * (kPMax * kPMax + kPT * 3 * kPMax + (size_t)kPT * q);
+  if (L >= 2) {
+    HIKF_CUDA(cudaMallocAsync((void**)&W, boxbytes * nbox, s));
+    HIKF_CUDA(cudaMallocAsync((void**)&Lx, boxbytes * nbox, s));
+    HIKF_CUDA(cudaMemsetAsync(W, 0, boxbytes * nbox, s));
+    HIKF_CUDA(cudaMemsetAsync(Lx, 0, boxbytes * nbox, s));
+    const int noff = ipow(7, dim);
+    const int64_t ktotal = (int64_t)(L - 1) * noff * q * q;
+    HIKF_CUDA(cudaMallocAsync((void**)&kop, sizeof(T) * ktotal, s));
+    m2l_table<T><<<nblk(ktotal, kThreads), kThreads, 0, s>>>(g, tab, kop, ktotal);
+    HIKF_LAUNCH_CHECK("m2l_table");
+    // P2M
+    {
+      size_t sm = smem_pts + sizeof(T) * kPT * nch;
+      HIKF_TRY(set_smem<T>((const void*)p2m_kernel<T>, sm));
+      p2m_kernel<T><<<(unsigned)t.nleaf, kThreads, sm, s>>>(g, t.pts, t.leaf_start, h.trowptr, h.tcol, h.tval, tab,
+                                                             nsrc, leaf0, nch, W);
+      HIKF_LAUNCH_CHECK("p2m");
+    }
+    // M2M, levels L-1 .. 2
+    {
+      size_t sm = sizeof(T) * (2 * kPMax * kPMax + 3 * (size_t)q * nch);
+      HIKF_TRY(set_smem<T>((const void*)m2m_kernel<T>, sm));
+      for (int lev = L - 1; lev >= 2; --lev) {
+        m2m_kernel<T><<<(unsigned)((int64_t)1 << (dim * lev)), kThreads, sm, s>>>(
+            g, lev, tab, nsrc, t.box_offset[lev], t.box_offset[lev + 1], nch, W);
+        HIKF_LAUNCH_CHECK("m2m");
+      }
+    }
+    // M2L, all levels 2 .. L
+    for (int lev = 2; lev <= L; ++lev) {
+      dim3 grid((unsigned)((int64_t)1 << (dim * lev)), (unsigned)((q + kM2L_BM - 1) / kM2L_BM),
+                (unsigned)((ldc + kM2L_BN - 1) / kM2L_BN));
+      m2l_kernel<T><<<grid, kThreads, 0, s>>>(g, lev, kop, nsrc, npts, t.box_offset[lev], W, Lx);
+      HIKF_LAUNCH_CHECK("m2l");
+    }
+    // L2L, levels 2 .. L-1 (parent level)
+    {
+      size_t sm = sizeof(T) * (2 * kPMax * kPMax + 3 * (size_t)q * nch);
+      HIKF_TRY(set_smem<T>((const void*)l2l_kernel<T>, sm));
+      for (int lev = 2; lev <= L - 1; ++lev) {
+        l2l_kernel<T><<<(unsigned)((int64_t)1 << (dim * lev)), kThreads, sm, s>>>(
+            g, lev, tab, npts, t.box_offset[lev], t.box_offset[lev + 1], nch, Lx);
+        HIKF_LAUNCH_CHECK("l2l");
+      }
+    }
+  }
+  // L2P + P2P at the leaves
+  {
+    int nchp = ldc;
+    while (nchp > 32 && smem_pts + sizeof(T) * (size_t)kPT * (nchp + 1) > 160 * 1024) nchp /= 2;
+    size_t sm = smem_pts + sizeof(T) * ((size_t)kPT * (nchp + 1) + kPT * 6 + 4) + sizeof(int64_t) * 2 * kPT;
+    HIKF_TRY(set_smem<T>((const void*)l2p_p2p_kernel<T>, sm));
+    l2p_p2p_kernel<T><<<(unsigned)t.nleaf, kThreads, sm, s>>>(g, t.pts, t.leaf_start, h.trowptr, h.tcol, h.tval,
+                                                                tab, nsrc, leaf0, nchp, Lx, out);
+    HIKF_LAUNCH_CHECK("l2p_p2p");
+  }
+  HIKF_CUDA(cudaFreeAsync(tab, s));
+  HIKF_CUDA(cudaFreeAsync(nsrc, s));
+  HIKF_CUDA(cudaFreeAsync(npts, s));
+  HIKF_CUDA(cudaFreeAsync(boff, s));
+  if (W) HIKF_CUDA(cudaFreeAsync(W, s));
+  if (Lx) HIKF_CUDA(cudaFreeAsync(Lx, s));
+  if (kop) HIKF_CUDA(cudaFreeAsync(kop, s));
+  return Status::Ok();
+}
+
+template Status h2_product<float>(const Tree&, const SparseH&, const FmmParams&, float*, int, cudaStream_t);
+template Status h2_product<double>(const Tree&, const SparseH&, const FmmParams&, double*, int, cudaStream_t);
+
+}  // namespace hikf

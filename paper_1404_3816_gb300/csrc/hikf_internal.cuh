@@ -1,0 +1,120 @@
+// Internal declarations of the HiKF CUDA library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "hikf.h"
+
+namespace hikf {
+
+constexpr int kMaxN = 512;        // measurements (rays) per filter
+constexpr int kMaxOrder2D = 12;   // Chebyshev nodes per axis, 2D
+constexpr int kMaxOrder3D = 8;    // Chebyshev nodes per axis, 3D
+constexpr int kMaxDepth2D = 15;
+constexpr int kMaxDepth3D = 10;
+
+// Status carried inside the library: code + message.
+struct Status {
+  hikf_status code = HIKF_OK;
+  std::string msg;
+  bool ok() const { return code == HIKF_OK; }
+  static Status Ok() { return Status(); }
+};
+
+Status make_status(hikf_status c, const std::string& m);
+Status cuda_status(cudaError_t e, const char* what, const char* file, int line);
+
+#define HIKF_CUDA(call)                                                           \
+  do {                                                                            \
+    cudaError_t _e = (call);                                                      \
+    if (_e != cudaSuccess) return ::hikf::cuda_status(_e, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define HIKF_LAUNCH_CHECK(what)                                                   \
+  do {                                                                            \
+    cudaError_t _e = cudaGetLastError();                                          \
+    if (_e != cudaSuccess) return ::hikf::cuda_status(_e, what, __FILE__, __LINE__); \
+  } while (0)
+
+#define HIKF_TRY(expr)                 \
+  do {                                         \
+    ::hikf::Status _s = (expr);                \
+    if (!_s.ok()) return _s;                   \
+  } while (0)
+
+// Device memory arena of one handle: every buffer is cudaMalloc'ed at create
+// and released at destroy.
+struct Arena {
+  void* ptrs[64];
+  int count = 0;
+  int64_t bytes = 0;
+  Status alloc(void** p, size_t nbytes);
+  void release();
+};
+
+template <typename T>
+inline Status arena_alloc(Arena& a, T** p, size_t count) {
+  return a.alloc(reinterpret_cast<void**>(p), count * sizeof(T) + 0);
+}
+
+// ---------------------------------------------------------------------------
+// Tree (uniform 2^d-tree, Morton order)
+// ---------------------------------------------------------------------------
+struct Tree {
+  int dim = 2;
+  int depth = 0;          // L
+  int64_t m = 0;
+  int64_t nleaf = 0;      // 2^(dim L)
+  double lo[3] = {0, 0, 0};
+  double side = 1.0;
+  int64_t* perm = nullptr;      // [m] tree position -> caller index
+  int64_t* iperm = nullptr;     // [m] caller index -> tree position
+  int64_t* leaf_start = nullptr;  // [nleaf + 1]
+  double* pts = nullptr;        // [m * dim] points in tree order
+  int64_t box_offset[kMaxDepth2D + 2];  // first box of level l in the concatenated box arrays
+  int64_t nbox_total = 0;
+};
+
+// Sparse H in two layouts, columns in tree order.
+struct SparseH {
+  int n = 0;
+  int64_t nnz = 0;
+  int64_t* rowptr = nullptr;   // [n+1]   H rows (rays)
+  int32_t* col = nullptr;      // [nnz]   tree positions
+  double* val = nullptr;       // [nnz]
+  int64_t* trowptr = nullptr;  // [m+1]   H^T rows (points in tree order)
+  int32_t* tcol = nullptr;     // [nnz]   ray index
+  double* tval = nullptr;      // [nnz]
+};
+
+struct Workspace;  // scratch used by the build steps
+
+Status build_tree(Tree& t, Arena& arena, const double* d_points_caller, cudaStream_t s);
+Status build_sparse(SparseH& h, Arena& arena, const Tree& t, const int64_t* h_rowptr, const int64_t* h_col,
+                    const double* h_val, int n, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// H^2 product (black-box FMM)
+// ---------------------------------------------------------------------------
+struct FmmParams {
+  int order = 8;     // p
+  int pow = 1;
+  double theta = 1.0;
+  double length = 1.0;
+};
+
+// out: [m x ldc] in tree order (T = float or double); columns >= n are zero.
+template <typename T>
+Status h2_product(const Tree& t, const SparseH& h, const FmmParams& fp, T* out, int ldc, cudaStream_t s);
+
+int auto_depth(int64_t m, int dim, int leaf_size);
+
+// ---------------------------------------------------------------------------
+// Measurement update
+// ---------------------------------------------------------------------------
+int padded_ld(int n);  // leading dimension of the m x n matrices
+
+}  // namespace hikf

@@ -52,7 +52,7 @@ class Workload:
     x0: np.ndarray                   # (m,) initial mean
     steps: int
     seed: int
-    cheb_order: int = 6
+    cheb_order: int = 8
     leaf_size: int = 64
 
     @property
@@ -245,7 +245,7 @@ def measurements(w: Workload, steps: Optional[int] = None, seed_offset: int = 0)
 # --------------------------------------------------------------------------
 
 def make(grid: Sequence[int], n: int, q: KernelSpec, p0: KernelSpec, r: float, steps: int, seed: int,
-         name: str = "custom", cheb_order: int = 6, leaf_size: int = 64) -> Workload:
+         name: str = "custom", cheb_order: int = 8, leaf_size: int = 64) -> Workload:
     grid = tuple(int(g) for g in grid)
     rng = np.random.default_rng(seed)
     src_c, rec_c = _ray_split(n, len(grid))

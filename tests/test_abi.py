@@ -1,0 +1,65 @@
+"""The C ABI library loads and exports every entry point include/hikf.h declares."""
+import re
+from pathlib import Path
+
+import pytest
+
+ROOT = Path(__file__).resolve().parent.parent
+
+
+def _declared():
+    text = (ROOT / "include" / "hikf.h").read_text()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hikf_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1404_3816_gb300 import binding, build
+    if not binding.LIB_PATH.exists():
+        build.build()
+    return binding.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("hikf_create", "hikf_assimilate", "hikf_get_mean", "hikf_get_variance", "hikf_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [s for s in _declared() if not hasattr(lib, s)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_1404_3816_gb300 import binding
+    assert sorted(binding.EXPORTED) == _declared()
+
+
+def test_options_default_without_gpu(lib):
+    from paper_1404_3816_gb300 import binding
+    o = binding.options()
+    assert o.cheb_order == 8 and o.leaf_size == 64 and o.max_depth == -1 and o.precision == 0
+
+
+def test_invalid_arguments_are_rejected_before_any_device_work(lib):
+    import numpy as np
+    from paper_1404_3816_gb300 import binding, workload as W
+    w = W.small(grid=(10, 8), n=4, seed=1)
+    good = dict(points=w.points, q=w.q, h_rowptr=w.h_rowptr, h_col=w.h_col, h_val=w.h_val, r_diag=w.r_diag)
+    bad_cases = [
+        dict(r_diag=np.zeros(w.n)),
+        dict(h_col=np.where(np.arange(w.nnz) == 0, w.m + 5, w.h_col)),
+        dict(q=W.KernelSpec(3, 0.01, 8.0)),
+        dict(q=W.KernelSpec(1, -1.0, 8.0)),
+        dict(points=np.where(np.arange(w.m * 2).reshape(w.m, 2) == 3, np.nan, w.points)),
+    ]
+    for bad in bad_cases:
+        kw = dict(good)
+        kw.update(bad)
+        with pytest.raises(binding.HikfError) as e:
+            binding.Filter(**kw)
+        assert e.value.code == binding.HIKF_EINVAL
+    with pytest.raises(binding.HikfError):
+        binding.Filter(**good, cheb_order=40)

@@ -1,0 +1,207 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Sizes span several 64-row sweep tiles with a ragged tail, ray counts that are
+not multiples of the 32-column padding, all three sweep widths (128/256/512),
+2D and 3D trees, both kernels, and the degenerate cases (P0 = 0, depth 0).
+Tolerances: FP32 path 1e-5 relative L2 (the agreement target of the method,
+stated for the H^2 product and for mean/variance); FP64 path 1e-10.
+Integer/index work (the tree permutation) is compared bit-exactly.
+"""
+import numpy as np
+import pytest
+
+from oracle import h2, kf, qht
+from paper_1404_3816_gb300 import workload as W
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-5
+TOL64 = 1e-10
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_1404_3816_gb300 import binding, build
+    if not binding.LIB_PATH.exists():
+        build.build()
+    binding.load()
+    return binding
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def morton_perm(w, depth):
+    tree = h2.Tree(w.points, depth)
+    key = np.zeros(w.m, dtype=np.int64)
+    for bit in range(depth - 1, -1, -1):
+        for d in range(w.dim):
+            key = (key << 1) | ((tree.leaf[:, d] >> bit) & 1)
+    return np.argsort(key, kind="stable")
+
+
+CASES = {
+    "m1024_n16": lambda: W.config("crosswell2d_m1024_n16"),
+    "ragged_47x41_n24": lambda: W.small(grid=(47, 41), n=24, steps=6, seed=21),
+    "ragged_61x37_n100": lambda: W.small(grid=(61, 37), n=100, steps=4, seed=22),
+    "gauss_40x40_n32": lambda: W.small(grid=(40, 40), n=32, steps=4, seed=23,
+                                       q=W.KernelSpec(W.GAUSS, 0.01, 6.0), p0=W.KernelSpec(W.GAUSS, 1.0, 6.0)),
+    "n256_33x33": lambda: W.small(grid=(33, 33), n=256, steps=3, seed=24),
+    "n300_30x30": lambda: W.small(grid=(30, 30), n=300, steps=3, seed=25),
+    "3d_16x16x16_n16": lambda: W.make(grid=(16, 16, 16), n=16, q=W.KernelSpec(W.GAUSS, 0.01, 4.0),
+                                      p0=W.KernelSpec(W.GAUSS, 1.0, 4.0), r=1e-3, steps=3, seed=26, cheb_order=5),
+}
+
+
+def _oracle_h2(w, kspec, depth, p):
+    H = qht.h_csr(w.h_rowptr, w.h_col, w.h_val, w.m)
+    return h2.h2_qht(w.points, kf.gcf(kspec.theta, kspec.length, kspec.pow), H, p, depth)
+
+
+@pytest.mark.parametrize("name", ["m1024_n16", "ragged_47x41_n24", "3d_16x16x16_n16"])
+def test_tree_permutation_is_bit_exact(B, name):
+    w = CASES[name]()
+    with B.Filter.from_workload(w) as f:
+        depth = f.info()["depth"]
+        assert depth == h2.auto_depth(w.m, w.dim, w.leaf_size)
+        assert np.array_equal(f.perm(), morton_perm(w, depth))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("name", list(CASES))
+def test_h2_product_matches_oracle_definition(B, name, prec):
+    w = CASES[name]()
+    with B.Filter.from_workload(w, precision=prec) as f:
+        depth = f.info()["depth"]
+        got = f.cq()
+    ref = _oracle_h2(w, w.q, depth, w.cheb_order)
+    assert rel(got, ref) < (TOL32 if prec == "fp32" else TOL64)
+
+
+def test_h2_product_close_to_exact_sum(B):
+    w = CASES["m1024_n16"]()
+    H = qht.h_csr(w.h_rowptr, w.h_col, w.h_val, w.m)
+    exact = qht.qht(w.points, kf.gcf(w.q.theta, w.q.length, w.q.pow), H)
+    for p, bound in ((6, 1e-5), (8, 2e-7)):
+        got = B.h2_qht(w.points, w.q, w.h_rowptr, w.h_col, w.h_val, cheb_order=p)
+        assert rel(got, exact) < bound
+
+
+def test_depth_zero_is_direct_sum(B):
+    w = W.small(grid=(12, 9), n=5, seed=27)
+    H = qht.h_csr(w.h_rowptr, w.h_col, w.h_val, w.m)
+    exact = qht.qht(w.points, kf.gcf(w.q.theta, w.q.length, w.q.pow), H)
+    got = B.h2_qht(w.points, w.q, w.h_rowptr, w.h_col, w.h_val, max_depth=0)
+    assert rel(got, exact) < TOL32
+
+
+def _run(B, w, prec="fp32", **kw):
+    Y, _ = W.measurements(w)
+    with B.Filter.from_workload(w, precision=prec, **kw) as f:
+        depth = f.info()["depth"]
+        for y in Y:
+            f.assimilate(y)
+        return f.mean(), f.variance(), f.cross(), depth, Y
+
+
+def _oracle_run(w, depth, Y, p):
+    H = qht.h_csr(w.h_rowptr, w.h_col, w.h_val, w.m)
+    cq = _oracle_h2(w, w.q, depth, p)
+    if w.p0.theta == 0:
+        c0 = np.zeros_like(cq)
+    elif (w.p0.pow, w.p0.length) == (w.q.pow, w.q.length):
+        c0 = (w.p0.theta / w.q.theta) * cq
+    else:
+        c0 = _oracle_h2(w, w.p0, depth, p)
+    return kf.hikf_cross(cq, c0, np.full(w.m, w.p0.theta), w.q.theta, H, w.r_diag, w.x0, Y)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("name", list(CASES))
+def test_filter_matches_oracle(B, name, prec):
+    w = CASES[name]()
+    x, v, c, depth, Y = _run(B, w, prec)
+    ref = _oracle_run(w, depth, Y, w.cheb_order)
+    tol = TOL32 if prec == "fp32" else TOL64
+    assert rel(x, ref["x"]) < tol
+    assert rel(v, ref["var"]) < tol
+    assert rel(c, ref["C"]) < 10 * tol
+
+
+def test_filter_matches_full_kf_end_to_end(B):
+    """Against Alg. 1 with the dense m x m covariance (exact Q, no H^2 error)."""
+    w = CASES["m1024_n16"]()
+    x, v, _, _, Y = _run(B, w)
+    H = qht.h_csr(w.h_rowptr, w.h_col, w.h_val, w.m)
+    Q = kf.covariance_matrix(w.points, kf.gcf(w.q.theta, w.q.length, w.q.pow))
+    P0 = kf.covariance_matrix(w.points, kf.gcf(w.p0.theta, w.p0.length, w.p0.pow))
+    ref = kf.kf_full(P0, Q, H, w.r_diag, w.x0, Y)
+    assert rel(x, ref["x"]) < TOL32
+    assert rel(v, ref["var"]) < TOL32
+
+
+def test_p0_zero_and_distinct_p0_kernel(B):
+    for p0 in (W.KernelSpec(W.EXP, 0.0, 1.0), W.KernelSpec(W.GAUSS, 0.5, 5.0)):
+        w = W.small(grid=(36, 30), n=20, steps=4, seed=28, p0=p0)
+        x, v, _, depth, Y = _run(B, w)
+        ref = _oracle_run(w, depth, Y, w.cheb_order)
+        assert rel(x, ref["x"]) < TOL32
+        assert rel(v, ref["var"]) < TOL32
+
+
+def test_update_with_given_cq_matches_oracle(B):
+    """The measurement update alone, with C_Q and C_0 handed in (exact sums)."""
+    w = W.small(grid=(50, 44), n=40, steps=6, seed=29)
+    Y, _ = W.measurements(w)
+    H = qht.h_csr(w.h_rowptr, w.h_col, w.h_val, w.m)
+    cq = qht.qht(w.points, kf.gcf(w.q.theta, w.q.length, w.q.pow), H)
+    c0 = (w.p0.theta / w.q.theta) * cq
+    ref = kf.hikf_cross(cq, c0, np.full(w.m, w.p0.theta), w.q.theta, H, w.r_diag, w.x0, Y)
+    with B.Filter(w.points, w.q, w.h_rowptr, w.h_col, w.h_val, w.r_diag, w.x0, w.p0, cq=cq, c0=c0) as f:
+        for y in Y:
+            f.assimilate(y)
+        assert rel(f.mean(), ref["x"]) < TOL32
+        assert rel(f.variance(), ref["var"]) < TOL32
+        assert f.info()["step"] == Y.shape[0]
+
+
+def test_nonfinite_measurement_is_rejected_and_state_kept(B):
+    w = W.small(grid=(30, 28), n=12, steps=3, seed=30)
+    Y, _ = W.measurements(w)
+    with B.Filter.from_workload(w) as f:
+        f.assimilate(Y[0])
+        x0, v0, c0 = f.mean(), f.variance(), f.cross()
+        bad = Y[1].copy()
+        bad[3] = np.nan
+        with pytest.raises(B.HikfError) as e:
+            f.assimilate(bad)
+        assert e.value.code == B.HIKF_EINVAL
+        assert np.array_equal(f.mean(), x0) and np.array_equal(f.variance(), v0)
+        assert np.array_equal(f.cross(), c0)
+        f.assimilate(Y[1])
+        assert f.info()["step"] == 2
+
+
+def test_async_error_is_latched_then_cleared(B):
+    import torch
+    w = W.small(grid=(30, 28), n=12, steps=4, seed=31)
+    Y, _ = W.measurements(w)
+    ref = None
+    with B.Filter.from_workload(w) as g:
+        for y in Y[:2]:
+            g.assimilate(y)
+        ref = (g.mean(), g.variance())
+    with B.Filter.from_workload(w) as f:
+        dy = torch.tensor(Y, dtype=torch.float64, device="cuda")
+        bad = dy[2].clone()
+        bad[0] = float("inf")
+        f.assimilate_device(dy[0])
+        f.assimilate_device(dy[1])
+        f.assimilate_device(bad)       # rejected on the device
+        f.assimilate_device(dy[3])     # no-op: an error is latched
+        with pytest.raises(B.HikfError):
+            f.sync()
+        f.sync()                       # cleared
+        assert f.info()["step"] == 2
+        assert np.array_equal(f.mean(), ref[0]) and np.array_equal(f.variance(), ref[1])
