@@ -36,8 +36,8 @@ CONFIG_NAME = "crosswell2d_m1048576_n256"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="hikf", choices=["hikf", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed"])
     ap.add_argument("--order", type=int, default=8)
@@ -58,7 +58,7 @@ def dist_info():
 # clocks sampled while the timed region runs
 # ---------------------------------------------------------------------------
 class Clocks:
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -86,23 +86,30 @@ class Clocks:
                 self.proc.kill()
             self.f.close()
 
-    def summary(self):
+    def summary(self, t0=None, t1=None):
+        """Median SM clock and active throttle reasons of the samples taken in [t0, t1] (wall time)."""
         if self.proc is None or not self.path.exists():
             return None
-        sm, smax, reasons = [], 0.0, set()
+        import datetime
+        rows = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in self.path.read_text().splitlines():
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax = max(smax, float(parts[2]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(parts[1]), float(parts[2]),
+                             [nm for nm, val in zip(names, parts[5:9]) if val.lower() == "active"]))
             except ValueError:
                 continue
-            for nm, val in zip(names, parts[5:9]):
-                if val.lower() == "active":
-                    reasons.add(nm)
+        inside = [r for r in rows if t0 is None or (t0 - 0.1 <= r[0] <= t1 + 0.1)]
+        if not inside and rows and t0 is not None:      # region shorter than the sampling period
+            mid = 0.5 * (t0 + t1)
+            inside = sorted(rows, key=lambda r: abs(r[0] - mid))[:2]
+        sm = [r[1] for r in inside]
+        smax = max([r[2] for r in inside], default=0.0)
+        reasons = set(x for r in inside for x in r[3])
         try:
             self.path.unlink()
         except Exception:
@@ -110,7 +117,7 @@ class Clocks:
         if not sm:
             return None
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "all_samples": len(rows)}
 
 
 def peaks():
@@ -221,6 +228,7 @@ def main():
     info = f.info()
     stream = torch.cuda.ExternalStream(f.stream)
 
+    clk = Clocks(local).__enter__()
     for t in range(args.warmup):
         f.assimilate_device(dY[t])
     f.sync()
@@ -230,18 +238,21 @@ def main():
     f.profile(True)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    with Clocks(local) as clk:
-        ev0.record(stream)
-        for t in range(args.warmup, total):
-            f.assimilate_device(dY[t])
-        ev1.record(stream)
-        ev1.synchronize()
+    wall0 = time.time()
+    ev0.record(stream)
+    for t in range(args.warmup, total):
+        f.assimilate_device(dY[t])
+    ev1.record(stream)
+    ev1.synchronize()
+    wall1 = time.time()
+    clk.__exit__(None, None, None)
     f.sync()
     torch.cuda.synchronize()
     elapsed_ms = ev0.elapsed_time(ev1)
     sweep_ms, sweep_n = f.profile_read()
     f.profile(False)
-    clocks = clk.summary()
+    clocks = clk.summary(wall0, wall1)
+    info = f.info()
     if world > 1:
         t = torch.tensor([elapsed_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)

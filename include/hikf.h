@@ -74,7 +74,16 @@ typedef struct {
   int precision;     /* HIKF_PREC_*. Default HIKF_PREC_FP32. */
   void* cuda_stream; /* cudaStream_t the handle runs on; NULL = a stream the handle
                         creates and owns. Default NULL. */
+  int chain;         /* how S_t^{-1} = (H C_{t|t-1} + R)^{-1} is formed each step:
+                        HIKF_CHAIN_AUTO (default): spectral when P_0 = c Q (c >= 0,
+                        including P_0 = 0) and C_Q is computed, else factor;
+                        HIKF_CHAIN_FACTOR: a Cholesky factorisation every step;
+                        HIKF_CHAIN_SPECTRAL: one eigendecomposition of
+                        R^{-1/2} H C_Q R^{-1/2} at create, then an O(n) recurrence per
+                        step (HIKF_EINVAL when P_0 is not c Q). */
 } hikf_options;
+
+enum { HIKF_CHAIN_AUTO = 0, HIKF_CHAIN_FACTOR = 1, HIKF_CHAIN_SPECTRAL = 2 };
 
 /* Fill *opt with the defaults listed above. */
 hikf_status hikf_options_default(hikf_options* opt);
@@ -169,6 +178,7 @@ typedef struct {
   int64_t device_bytes; /* device memory held by the handle */
   double create_ms;   /* wall time of the precomputation */
   int sweep_launches; /* kernel launches of one measurement update */
+  int chain;          /* HIKF_CHAIN_FACTOR or HIKF_CHAIN_SPECTRAL: the form in use */
 } hikf_info_t;
 
 hikf_status hikf_info(const hikf_t* h, hikf_info_t* info);

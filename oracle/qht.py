@@ -43,3 +43,29 @@ def qht(points: np.ndarray, kern: KernelFn, H: sp.csr_matrix, rows: Optional[np.
         r = rows[a:a + chunk]
         out[a:a + r.shape[0]] = kern(points[r], ys) @ Hs
     return out
+
+
+def qht_gauss_grid(shape, theta: float, length: float, H: sp.csr_matrix) -> np.ndarray:
+    """Exact Q H^T for the Gaussian kernel on a full unit-cell grid (cell centres, C order).
+
+    theta exp(-|x - y|^2 / l^2) = theta prod_d exp(-(x_d - y_d)^2 / l^2), so on a tensor
+    grid Q is the Kronecker product of 1-D kernel matrices and each column
+    Q h^(k) (Sec. 3.2) is a sequence of 1-D products along the axes of the
+    reshaped h^(k). Used for full-size checks where the direct sum is too slow.
+    """
+    shape = tuple(int(s) for s in shape)
+    mats = []
+    for s in shape:
+        c = np.arange(s, dtype=np.float64) + 0.5
+        mats.append(np.exp(-((c[:, None] - c[None, :]) ** 2) / (length * length)))
+    H = sp.csr_matrix(H)
+    n = H.shape[0]
+    out = np.zeros((int(np.prod(shape)), n))
+    for k in range(n):
+        img = np.zeros(shape)
+        row = H.getrow(k)
+        img.reshape(-1)[row.indices] = row.data
+        for ax, mat in enumerate(mats):
+            img = np.moveaxis(np.tensordot(mat, img, axes=([1], [ax])), 0, ax)
+        out[:, k] = theta * img.reshape(-1)
+    return out

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "hikf_internal.cuh"
+#include "spectral.cuh"
 #include "step.cuh"
 
 namespace hikf {
@@ -131,6 +132,8 @@ struct hikf_handle {
   double* hcq_sym = nullptr;
   double* S = nullptr;
   hikf::ChainArgs chain;
+  bool spectral = false;
+  hikf::SpectralState sp;
   void* Msw = nullptr;
   double* e = nullptr;
   double* a = nullptr;
@@ -187,6 +190,7 @@ Status validate_common(int dim, int64_t m, const double* points, int n, const in
   if (o.max_depth > dmax) return make_status(HIKF_EINVAL, "max_depth too large");
   if (o.precision != HIKF_PREC_FP32 && o.precision != HIKF_PREC_FP64 && o.precision != HIKF_PREC_MIXED)
     return make_status(HIKF_EINVAL, "unknown precision");
+  if (o.chain < HIKF_CHAIN_AUTO || o.chain > HIKF_CHAIN_SPECTRAL) return make_status(HIKF_EINVAL, "unknown chain");
   return Status::Ok();
 }
 
@@ -202,7 +206,7 @@ Status validate_kernel(const hikf_kernel& k, bool allow_zero) {
 
 template <typename T>
 Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const double* x0, const double* cq,
-                   const double* c0, const double* r_diag) {
+                   const double* c0, const double* r_diag, int chain_opt) {
   cudaStream_t s = h->stream;
   const int64_t m = h->m;
   const int n = h->n, ld = h->ld;
@@ -307,6 +311,27 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
   HIKF_TRY(hikf::arena_alloc(h->arena, &h->e, n));
   HIKF_TRY(hikf::arena_alloc(h->arena, &h->a, n));
   HIKF_TRY(hikf::arena_alloc(h->arena, &h->ybuf, n));
+
+  // spectral chain when P_0 = c Q (c >= 0) and C_Q is our own H^2 product
+  const bool p0_is_cq = p0.theta == 0.0 || (p0.pow == q.pow && p0.length == q.length);
+  const bool can_spec = cq == nullptr && p0_is_cq;
+  if (chain_opt == HIKF_CHAIN_SPECTRAL && !can_spec)
+    return hikf::make_status(HIKF_EINVAL, "spectral chain needs P0 = c Q and a computed C_Q");
+  h->spectral = can_spec && chain_opt != HIKF_CHAIN_FACTOR;
+  if (h->spectral) {
+    hikf::SpectralState& sp = h->sp;
+    HIKF_TRY(hikf::arena_alloc(h->arena, &sp.lam, n));
+    HIKF_TRY(hikf::arena_alloc(h->arena, &sp.s, n));
+    HIKF_TRY(hikf::arena_alloc(h->arena, &sp.u, n));
+    HIKF_TRY(hikf::arena_alloc(h->arena, &sp.W64, nn));
+    HIKF_TRY(hikf::arena_alloc(h->arena, &sp.W32, nn));
+    const double cfac = p0.theta == 0.0 ? 0.0 : p0.theta / q.theta;
+    HIKF_TRY(hikf::spectral_setup(sp, h->hcq_sym, h->rd, n, cfac, h->flag, s));
+    int f[2] = {0, 0};
+    HIKF_CUDA(cudaMemcpyAsync(f, h->flag, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+    HIKF_CUDA(cudaStreamSynchronize(s));
+    if (f[0]) return hikf::make_status(HIKF_ENOTPD, "H C_1 + R is not positive definite");
+  }
   return Status::Ok();
 }
 
@@ -315,10 +340,17 @@ Status enqueue_step(hikf_t* h) {
   cudaStream_t s = h->stream;
   hikf::ChainArgs& c = h->chain;
   int launches = 0;
-  HIKF_TRY(hikf::launch_chain(c, s));
-  launches += c.fp64 ? 1 : (2 + 3 * c.refine_iters + 3);
-  HIKF_TRY(hikf::launch_innovation(h->ybuf, h->H, h->x, h->e, h->flag, s));
-  HIKF_TRY(hikf::launch_gemv<T>(c.Mh, c.Ml, c.M64, h->n, c.ldm, h->e, h->a, (T*)h->Msw, h->nt, h->flag, s));
+  if (h->spectral) {
+    HIKF_TRY(hikf::launch_innovation(h->ybuf, h->H, h->x, h->e, h->flag, s));
+    HIKF_TRY(hikf::spectral_gain<T>(h->sp, h->n, h->e, h->a, (T*)h->Msw, h->nt, h->flag, s));
+    launches += 4;
+  } else {
+    HIKF_TRY(hikf::launch_chain(c, s));
+    launches += c.fp64 ? 1 : (2 + 3 * c.refine_iters + 3);
+    HIKF_TRY(hikf::launch_innovation(h->ybuf, h->H, h->x, h->e, h->flag, s));
+    HIKF_TRY(hikf::launch_gemv<T>(c.Mh, c.Ml, c.M64, h->n, c.ldm, h->e, h->a, (T*)h->Msw, h->nt, h->flag, s));
+    launches += 2;
+  }
   hikf::SweepArgs<T> sa;
   sa.m = h->m;
   sa.ld = h->ld;
@@ -341,8 +373,11 @@ Status enqueue_step(hikf_t* h) {
   }
   hikf::count_step<<<1, 1, 0, s>>>(h->flag, h->dstep);
   HIKF_LAUNCH_CHECK("count_step");
-  HIKF_TRY(hikf::launch_recur(h->hcq_sym, h->rd, c.Mh, c.Ml, c.M64, h->n, c.ldm, h->flag, h->S, s));
-  launches += 6;
+  if (h->spectral)
+    HIKF_TRY(hikf::spectral_next(h->sp, h->n, h->flag, s));
+  else
+    HIKF_TRY(hikf::launch_recur(h->hcq_sym, h->rd, c.Mh, c.Ml, c.M64, h->n, c.ldm, h->flag, h->S, s));
+  launches += 3;
   h->launches = launches;
   return Status::Ok();
 }
@@ -422,7 +457,8 @@ hikf_status create_impl(hikf_t** out, int dim, int64_t m, const double* points, 
   if (!st.ok()) return bail(st);
   st = hikf::build_sparse(h->H, h->arena, h->tree, rowptr, col, val, n, h->stream);
   if (!st.ok()) return bail(st);
-  st = h->fp64() ? setup_state<double>(h, q, p0, x0, cq, c0, r_diag) : setup_state<float>(h, q, p0, x0, cq, c0, r_diag);
+  st = h->fp64() ? setup_state<double>(h, q, p0, x0, cq, c0, r_diag, o.chain)
+                 : setup_state<float>(h, q, p0, x0, cq, c0, r_diag, o.chain);
   if (!st.ok()) return bail(st);
   e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return bail(hikf::cuda_status(e, "create", __FILE__, __LINE__));
@@ -442,6 +478,7 @@ hikf_status hikf_options_default(hikf_options* opt) {
   opt->max_depth = -1;
   opt->precision = HIKF_PREC_FP32;
   opt->cuda_stream = nullptr;
+  opt->chain = HIKF_CHAIN_AUTO;
   return HIKF_OK;
 }
 
@@ -565,6 +602,7 @@ hikf_status hikf_info(const hikf_t* h, hikf_info_t* info) {
   info->device_bytes = h->arena.bytes;
   info->create_ms = h->create_ms;
   info->sweep_launches = h->launches;
+  info->chain = h->spectral ? HIKF_CHAIN_SPECTRAL : HIKF_CHAIN_FACTOR;
   return HIKF_OK;
 }
 

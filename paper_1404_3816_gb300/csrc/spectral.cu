@@ -1,0 +1,346 @@
+// Spectral form of the n x n chain of the measurement update.
+//
+// With stationary H, Q, R (Sec. 2.2) the random-walk filter's innovation
+// covariance obeys S_{t+1} = H C_Q + 2R - R S_t^{-1} R (because
+// H C_{t+1|t} = H C_{t|t} + H C_Q and H C_{t|t} = R - R S_t^{-1} R). Scaling by
+// D = R^{-1/2} gives  S~_{t+1} = B~ + 2I - S~_t^{-1}  with B~ = D sym(H C_Q) D.
+// When P_0 = c Q (c >= 0, which includes P_0 = 0), S~_1 = (1 + c) B~ + I, so every
+// S~_t is a function of B~: with B~ = V diag(lambda) V^T,
+//     s_1 = (1 + c) lambda + 1,   s_{t+1} = lambda + 2 - 1 / s_t     (per eigenvalue)
+//     M_t = S_t^{-1} = W diag(1 / s_t) W^T,   W = D V.
+// One FP64 eigendecomposition at create replaces a Cholesky factorisation per
+// step, whose FP64 cost and conditioning (cond(S) ~ 1e8 and more) would
+// otherwise dominate the update.
+//
+// Eigensolver: Householder reduction to tridiagonal form, explicit
+// accumulation of the orthogonal factor, then implicit symmetric QR steps with
+// Wilkinson shifts (Golub & Van Loan, Sec. 8.3), all on one CTA in FP64.
+#include <math.h>
+
+#include "hikf_internal.cuh"
+#include "spectral.cuh"
+
+namespace hikf {
+
+namespace {
+
+constexpr int kEigThreads = 1024;
+
+__device__ double block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int w = 0; w < nw; ++w) s += red[w];
+  return s;
+}
+
+// A (n x n, row-major, symmetric; destroyed), outputs lam (n) and V (n x n, columns = eigenvectors).
+// hv: n x n scratch for the Householder vectors. info = 1 when QR did not converge.
+__global__ void __launch_bounds__(kEigThreads) eig_sym_kernel(double* __restrict__ A, int n, double* __restrict__ lam,
+                                                              double* __restrict__ V, double* __restrict__ hv,
+                                                              int* __restrict__ info) {
+  __shared__ double red[32];
+  __shared__ double sv[kMaxN], sw[kMaxN], ssub[kMaxN];
+  __shared__ double rc[kMaxN], rs[kMaxN];
+  __shared__ int s_l, s_m, s_done;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  // ---- Householder tridiagonalisation -------------------------------------
+  for (int k = 0; k + 2 < n; ++k) {
+    double part = 0.0;
+    for (int i = k + 1 + tid; i < n; i += blockDim.x) {
+      double x = A[(int64_t)i * n + k];
+      part += x * x;
+    }
+    const double ss = block_sum(part, red);
+    const double x0 = A[(int64_t)(k + 1) * n + k];
+    const double tail = ss - x0 * x0;
+    double* vk = hv + (int64_t)k * n;
+    if (tail <= 0.0) {  // already tridiagonal in this column: H_k = I
+      for (int i = tid; i < n; i += blockDim.x) vk[i] = 0.0;
+      if (tid == 0) ssub[k] = x0;
+      __syncthreads();
+      continue;
+    }
+    const double alpha = x0 >= 0.0 ? -sqrt(ss) : sqrt(ss);
+    const double v0 = x0 - alpha;
+    const double vn = sqrt(tail + v0 * v0);
+    for (int i = tid; i < n; i += blockDim.x) {
+      double v = 0.0;
+      if (i == k + 1) v = v0 / vn;
+      else if (i > k + 1) v = A[(int64_t)i * n + k] / vn;
+      sv[i] = v;
+      vk[i] = v;
+    }
+    if (tid == 0) ssub[k] = alpha;
+    __syncthreads();
+    // w = A_sub v (rows k+1..n-1), warp per row
+    for (int i = k + 1 + warp; i < n; i += nw) {
+      double s = 0.0;
+      for (int j = k + 1 + lane; j < n; j += 32) s += A[(int64_t)i * n + j] * sv[j];
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) sw[i] = s;
+    }
+    __syncthreads();
+    double cp = 0.0;
+    for (int i = k + 1 + tid; i < n; i += blockDim.x) cp += sv[i] * sw[i];
+    const double cc = block_sum(cp, red);
+    for (int i = k + 1 + tid; i < n; i += blockDim.x) sw[i] = sw[i] - cc * sv[i];  // q = w - (v.w) v
+    __syncthreads();
+    const int len = n - k - 1;
+    for (int64_t t = tid; t < (int64_t)len * len; t += blockDim.x) {
+      int i = k + 1 + (int)(t / len), j = k + 1 + (int)(t % len);
+      A[(int64_t)i * n + j] -= 2.0 * (sv[i] * sw[j] + sw[i] * sv[j]);
+    }
+    __syncthreads();
+  }
+  // diagonal and sub-diagonal of T
+  double* d = lam;
+  for (int i = tid; i < n; i += blockDim.x) d[i] = A[(int64_t)i * n + i];
+  if (tid == 0 && n >= 2) ssub[n - 2] = A[(int64_t)(n - 1) * n + (n - 2)];
+  __syncthreads();
+  // ---- Q = H_0 H_1 ... H_{n-3}, accumulated backwards into V ---------------
+  for (int64_t t = tid; t < (int64_t)n * n; t += blockDim.x) V[t] = (t / n == t % n) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int k = n - 3; k >= 0; --k) {
+    const double* vk = hv + (int64_t)k * n;
+    for (int i = tid; i < n; i += blockDim.x) sv[i] = vk[i];
+    __syncthreads();
+    // y_j = sum_i v_i V[i][j], j > k (warp per column)
+    for (int j = k + 1 + warp; j < n; j += nw) {
+      double s = 0.0;
+      for (int i = k + 1 + lane; i < n; i += 32) s += sv[i] * V[(int64_t)i * n + j];
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) sw[j] = s;
+    }
+    __syncthreads();
+    const int len = n - k - 1;
+    for (int64_t t = tid; t < (int64_t)len * len; t += blockDim.x) {
+      int i = k + 1 + (int)(t / len), j = k + 1 + (int)(t % len);
+      V[(int64_t)i * n + j] -= 2.0 * sv[i] * sw[j];
+    }
+    __syncthreads();
+  }
+  // ---- implicit symmetric QR with Wilkinson shifts on (d, ssub) ------------
+  // thread 0 chases the bulge and records the rotations; every thread applies
+  // them to its own rows of V (V <- V G).
+  if (tid == 0) {
+    s_m = n - 1;
+    s_done = 0;
+    *info = 0;
+  }
+  __syncthreads();
+  const double eps = 2.220446049250313e-16;
+  int iters = 0;
+  const int max_iters = 40 * n + 100;
+  while (true) {
+    if (tid == 0) {
+      int m = s_m;
+      // deflate converged bottom entries
+      while (m > 0 && fabs(ssub[m - 1]) <= eps * (fabs(d[m - 1]) + fabs(d[m]))) {
+        ssub[m - 1] = 0.0;
+        --m;
+      }
+      s_m = m;
+      if (m == 0) {
+        s_done = 1;
+      } else {
+        int l = m - 1;
+        while (l > 0 && fabs(ssub[l - 1]) > eps * (fabs(d[l - 1]) + fabs(d[l]))) --l;
+        s_l = l;
+        // Wilkinson shift from the trailing 2 x 2 block
+        const double a = d[m - 1], b = ssub[m - 1], c2 = d[m];
+        const double delta = 0.5 * (a - c2);
+        const double sgn = delta >= 0.0 ? 1.0 : -1.0;
+        const double mu = c2 - b * b / (delta + sgn * hypot(delta, b));
+        double x = d[l] - mu, z = ssub[l];
+        for (int k = l; k < m; ++k) {
+          const double r = hypot(x, z);
+          double c = 1.0, s = 0.0;
+          if (r > 0.0) {
+            c = x / r;
+            s = z / r;
+          }
+          if (k > l) ssub[k - 1] = r;
+          const double ak = d[k], bk = ssub[k], ck = d[k + 1];
+          d[k] = ak * c * c + 2.0 * bk * c * s + ck * s * s;
+          d[k + 1] = ak * s * s - 2.0 * bk * c * s + ck * c * c;
+          ssub[k] = (ck - ak) * c * s + bk * (c * c - s * s);
+          if (k + 1 < m) {
+            const double f = ssub[k + 1];
+            z = f * s;
+            ssub[k + 1] = f * c;
+          }
+          x = ssub[k];
+          rc[k] = c;
+          rs[k] = s;
+        }
+      }
+    }
+    __syncthreads();
+    if (s_done) break;
+    const int l = s_l, m = s_m;
+    for (int row = tid; row < n; row += blockDim.x) {
+      double* vr = V + (int64_t)row * n;
+      double vk = vr[l];
+      for (int k = l; k < m; ++k) {
+        const double vk1 = vr[k + 1];
+        const double c = rc[k], s = rs[k];
+        vr[k] = c * vk + s * vk1;
+        vk = -s * vk + c * vk1;
+      }
+      vr[m] = vk;
+    }
+    __syncthreads();
+    if (++iters > max_iters) {
+      if (tid == 0) *info = 1;
+      break;
+    }
+  }
+}
+
+// B~ = D sym(HCQ) D with D = R^{-1/2}
+__global__ void scale_b_kernel(const double* __restrict__ hcq_sym, const double* __restrict__ rd, int n,
+                               double* __restrict__ out) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * n) return;
+  int i = (int)(t / n), j = (int)(t % n);
+  out[t] = hcq_sym[t] / sqrt(rd[i] * rd[j]);
+}
+
+// W = D V (FP64 and FP32 copies); s_1 = (1 + c) lambda + 1
+__global__ void spec_init_kernel(const double* __restrict__ V, const double* __restrict__ lam,
+                                 const double* __restrict__ rd, int n, double c, double* __restrict__ W64,
+                                 float* __restrict__ W32, double* __restrict__ s, int* __restrict__ flag) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < (int64_t)n * n) {
+    int i = (int)(t / n);
+    double w = V[t] / sqrt(rd[i]);
+    W64[t] = w;
+    W32[t] = (float)w;
+  }
+  if (t < n) {
+    double sv = (1.0 + c) * lam[t] + 1.0;
+    s[t] = sv;
+    if (!(sv > 0.0)) atomicOr(flag, 2);
+  }
+}
+
+// u = (1/s) o (W^T e), one warp per output
+__global__ void spec_u_kernel(const double* __restrict__ W64, const double* __restrict__ s,
+                              const double* __restrict__ e, int n, double* __restrict__ u,
+                              const int* __restrict__ flag) {
+  if (*flag) return;
+  const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (k >= n) return;
+  double acc = 0.0;
+  for (int i = lane; i < n; i += 32) acc += W64[(int64_t)i * n + k] * e[i];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) u[k] = acc / s[k];
+}
+
+// a = W u, one warp per output
+__global__ void spec_a_kernel(const double* __restrict__ W64, const double* __restrict__ u, int n,
+                              double* __restrict__ a, const int* __restrict__ flag) {
+  if (*flag) return;
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (i >= n) return;
+  double acc = 0.0;
+  for (int k = lane; k < n; k += 32) acc += W64[(int64_t)i * n + k] * u[k];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) a[i] = acc;
+}
+
+// Msw[i][j] = sum_k W_ik W_jk / s_k  (sweep operand, row stride nt), 16 x 16 output tiles
+template <typename T, typename WT>
+__global__ void spec_m_kernel(const WT* __restrict__ W, const double* __restrict__ s, int n, int nt,
+                              T* __restrict__ Msw, const int* __restrict__ flag) {
+  if (*flag) return;
+  __shared__ WT wi[16][33], wj[16][33], g[32];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int i0 = blockIdx.y * 16, j0 = blockIdx.x * 16;
+  WT acc = (WT)0;
+  for (int k0 = 0; k0 < n; k0 += 32) {
+    for (int t = threadIdx.x; t < 16 * 32; t += 256) {
+      int r = t / 32, kk = t % 32;
+      int k = k0 + kk;
+      wi[r][kk] = (i0 + r < n && k < n) ? W[(int64_t)(i0 + r) * n + k] : (WT)0;
+      wj[r][kk] = (j0 + r < n && k < n) ? W[(int64_t)(j0 + r) * n + k] : (WT)0;
+    }
+    if (threadIdx.x < 32) g[threadIdx.x] = k0 + threadIdx.x < n ? (WT)(1.0 / s[k0 + threadIdx.x]) : (WT)0;
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < 32; ++kk) acc += wi[ty][kk] * g[kk] * wj[tx][kk];
+    __syncthreads();
+  }
+  if (i0 + ty < n && j0 + tx < n) Msw[(int64_t)(i0 + ty) * nt + j0 + tx] = (T)acc;
+}
+
+// s <- lambda + 2 - 1/s   (after an applied step)
+__global__ void spec_next_kernel(const double* __restrict__ lam, int n, double* __restrict__ s,
+                                 int* __restrict__ flag) {
+  if (*flag) return;
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  s[k] = lam[k] + 2.0 - 1.0 / s[k];
+}
+
+inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
+
+}  // namespace
+
+Status spectral_setup(SpectralState& sp, const double* hcq_sym, const double* rd, int n, double c, int* flag,
+                      cudaStream_t s) {
+  const int64_t nn = (int64_t)n * n;
+  double *A = nullptr, *V = nullptr, *hv = nullptr;
+  int* info = nullptr;
+  HIKF_CUDA(cudaMallocAsync((void**)&A, sizeof(double) * nn, s));
+  HIKF_CUDA(cudaMallocAsync((void**)&V, sizeof(double) * nn, s));
+  HIKF_CUDA(cudaMallocAsync((void**)&hv, sizeof(double) * nn, s));
+  HIKF_CUDA(cudaMallocAsync((void**)&info, sizeof(int), s));
+  scale_b_kernel<<<nblk(nn, 256), 256, 0, s>>>(hcq_sym, rd, n, A);
+  HIKF_LAUNCH_CHECK("scale_b");
+  eig_sym_kernel<<<1, kEigThreads, 0, s>>>(A, n, sp.lam, V, hv, info);
+  HIKF_LAUNCH_CHECK("eig_sym");
+  spec_init_kernel<<<nblk(nn, 256), 256, 0, s>>>(V, sp.lam, rd, n, c, sp.W64, sp.W32, sp.s, flag);
+  HIKF_LAUNCH_CHECK("spec_init");
+  int hinfo = 0;
+  HIKF_CUDA(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, s));
+  HIKF_CUDA(cudaStreamSynchronize(s));
+  HIKF_CUDA(cudaFreeAsync(A, s));
+  HIKF_CUDA(cudaFreeAsync(V, s));
+  HIKF_CUDA(cudaFreeAsync(hv, s));
+  HIKF_CUDA(cudaFreeAsync(info, s));
+  if (hinfo) return make_status(HIKF_ECUDA, "eigensolver did not converge");
+  return Status::Ok();
+}
+
+template <typename T>
+Status spectral_gain(const SpectralState& sp, int n, const double* e, double* a, T* Msw, int nt, const int* flag,
+                     cudaStream_t s) {
+  spec_u_kernel<<<nblk((int64_t)n * 32, 256), 256, 0, s>>>(sp.W64, sp.s, e, n, sp.u, flag);
+  HIKF_LAUNCH_CHECK("spec_u");
+  spec_a_kernel<<<nblk((int64_t)n * 32, 256), 256, 0, s>>>(sp.W64, sp.u, n, a, flag);
+  HIKF_LAUNCH_CHECK("spec_a");
+  dim3 grid((unsigned)((n + 15) / 16), (unsigned)((n + 15) / 16));
+  if (sizeof(T) == 8)
+    spec_m_kernel<T, double><<<grid, 256, 0, s>>>(sp.W64, sp.s, n, nt, Msw, flag);
+  else
+    spec_m_kernel<T, float><<<grid, 256, 0, s>>>(sp.W32, sp.s, n, nt, Msw, flag);
+  HIKF_LAUNCH_CHECK("spec_m");
+  return Status::Ok();
+}
+template Status spectral_gain<float>(const SpectralState&, int, const double*, double*, float*, int, const int*,
+                                     cudaStream_t);
+template Status spectral_gain<double>(const SpectralState&, int, const double*, double*, double*, int, const int*,
+                                      cudaStream_t);
+
+Status spectral_next(const SpectralState& sp, int n, int* flag, cudaStream_t s) {
+  spec_next_kernel<<<nblk(n, 256), 256, 0, s>>>(sp.lam, n, sp.s, flag);
+  HIKF_LAUNCH_CHECK("spec_next");
+  return Status::Ok();
+}
+
+}  // namespace hikf

@@ -1,0 +1,26 @@
+// Spectral form of the n x n chain (internal).
+#pragma once
+
+#include "hikf_internal.cuh"
+
+namespace hikf {
+
+struct SpectralState {
+  double* lam = nullptr;  // n eigenvalues of D sym(H C_Q) D, D = R^{-1/2}
+  double* s = nullptr;    // n current s_t (eigenvalues of D S_t D)
+  double* W64 = nullptr;  // n x n, D V
+  float* W32 = nullptr;   // n x n, D V rounded to FP32
+  double* u = nullptr;    // n scratch
+};
+
+// Eigendecomposition of D sym(HCQ) D and s_1 = (1 + c) lambda + 1 (flag[0] |= 2 when some s_1 <= 0).
+Status spectral_setup(SpectralState& sp, const double* hcq_sym, const double* rd, int n, double c, int* flag,
+                      cudaStream_t s);
+// a = M_t e and the sweep operand Msw = M_t (row stride nt), M_t = W diag(1/s_t) W^T.
+template <typename T>
+Status spectral_gain(const SpectralState& sp, int n, const double* e, double* a, T* Msw, int nt, const int* flag,
+                     cudaStream_t s);
+// s_{t+1} = lambda + 2 - 1/s_t (skipped when the step failed).
+Status spectral_next(const SpectralState& sp, int n, int* flag, cudaStream_t s);
+
+}  // namespace hikf

@@ -1,0 +1,91 @@
+"""Full-size parity: the m = 2^20, n = 256 workload the benchmark times, and the
+m = 65536, n = 64 workload of 200 steps, checked against the FP64 oracle.
+
+* exponential kernel, m = 2^20: the exact direct sums are out of reach for all
+  rows, so sampled rows of C_Q are compared with the exact sum and with the H^2
+  definition (same Chebyshev order, same tree);
+* Gaussian kernel, m = 2^20: the exact C_Q follows from the Kronecker structure
+  of the Gaussian on the grid, so the whole pipeline (H^2 product + updates, in
+  the launch configuration of bench.py) is compared on every row;
+* exponential kernel, m = 65536: the whole 200-step run against O-cross with the
+  exact C_Q.
+"""
+import numpy as np
+import pytest
+
+from oracle import h2, kf, qht
+from paper_1404_3816_gb300 import workload as W
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_1404_3816_gb300 import binding, build
+    if not binding.LIB_PATH.exists():
+        build.build()
+    binding.load()
+    return binding
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def test_m2p20_h2_product_sampled_rows(B):
+    w = W.config("crosswell2d_m1048576_n256")
+    with B.Filter.from_workload(w) as f:
+        cq = f.cq()
+        depth = f.info()["depth"]
+    rows = np.sort(np.random.default_rng(3).choice(w.m, 48, replace=False))
+    H = qht.h_csr(w.h_rowptr, w.h_col, w.h_val, w.m)
+    k = kf.gcf(w.q.theta, w.q.length, w.q.pow)
+    ref_h2 = h2.h2_qht(w.points, k, H, w.cheb_order, depth, rows)
+    ref_exact = qht.qht(w.points, k, H, rows)
+    assert rel(cq[rows], ref_h2) < TOL                 # same approximation, FP32 vs FP64
+    assert rel(cq[rows], ref_exact) < 1e-6             # order 8 is well inside the 1e-5 target
+    assert np.all(np.isfinite(cq))
+
+
+def test_m2p20_order6_meets_h2_target(B):
+    w = W.config("crosswell2d_m1048576_n256")
+    cq = B.h2_qht(w.points, w.q, w.h_rowptr, w.h_col, w.h_val, cheb_order=6)
+    rows = np.sort(np.random.default_rng(4).choice(w.m, 48, replace=False))
+    H = qht.h_csr(w.h_rowptr, w.h_col, w.h_val, w.m)
+    ref_exact = qht.qht(w.points, kf.gcf(w.q.theta, w.q.length, w.q.pow), H, rows)
+    assert rel(cq[rows], ref_exact) < TOL
+
+
+def test_m2p20_gaussian_full_pipeline(B):
+    import torch
+    w = W.config("crosswell2d_m1048576_n256", q=W.KernelSpec(W.GAUSS, 0.01, 64.0),
+                 p0=W.KernelSpec(W.GAUSS, 1.0, 64.0))
+    T = 3
+    Y, _ = W.measurements(w, steps=T)
+    H = qht.h_csr(w.h_rowptr, w.h_col, w.h_val, w.m)
+    cq = qht.qht_gauss_grid(w.grid, w.q.theta, w.q.length, H)
+    ref = kf.hikf_cross(cq, 100.0 * cq, np.full(w.m, 1.0), w.q.theta, H, w.r_diag, w.x0, Y)
+    del cq
+    with B.Filter.from_workload(w) as f:           # the launch configuration of bench.py
+        dY = torch.tensor(Y, dtype=torch.float64, device="cuda")
+        for t in range(T):
+            f.assimilate_device(dY[t])
+        f.sync()
+        assert rel(f.mean(), ref["x"]) < TOL
+        assert rel(f.variance(), ref["var"]) < TOL
+
+
+def test_m65536_200_steps_end_to_end(B):
+    w = W.config("crosswell2d_m65536_n64")
+    Y, _ = W.measurements(w)
+    H = qht.h_csr(w.h_rowptr, w.h_col, w.h_val, w.m)
+    cq = qht.qht(w.points, kf.gcf(w.q.theta, w.q.length, w.q.pow), H)
+    ref = kf.hikf_cross(cq, (w.p0.theta / w.q.theta) * cq, np.full(w.m, w.p0.theta), w.q.theta, H, w.r_diag,
+                        w.x0, Y)
+    with B.Filter.from_workload(w) as f:
+        for y in Y:
+            f.assimilate(y)
+        assert rel(f.mean(), ref["x"]) < TOL
+        assert rel(f.variance(), ref["var"]) < TOL

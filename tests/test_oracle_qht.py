@@ -37,3 +37,12 @@ def test_sparse_sum_equals_dense_product():
     rows = np.array([0, 5, 77, w.m - 1])
     assert np.allclose(qht.qht(w.points, k, H), dense, rtol=1e-12, atol=1e-15)
     assert np.allclose(qht.qht(w.points, k, H, rows), dense[rows], rtol=1e-12, atol=1e-15)
+
+
+@pytest.mark.parametrize("grid", [(18, 14), (9, 7, 6)])
+def test_separable_gaussian_product_equals_direct_sum(grid):
+    w = W.make(grid=grid, n=6 if len(grid) == 2 else 16, q=W.KernelSpec(2, 0.3, 4.0),
+               p0=W.KernelSpec(2, 1.0, 4.0), r=1e-3, steps=1, seed=8)
+    H = qht.h_csr(w.h_rowptr, w.h_col, w.h_val, w.m)
+    direct = qht.qht(w.points, kf.gcf(0.3, 4.0, 2), H)
+    assert np.allclose(qht.qht_gauss_grid(grid, 0.3, 4.0, H), direct, rtol=1e-12, atol=1e-15)
