@@ -325,6 +325,8 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
     HIKF_TRY(hikf::arena_alloc(h->arena, &sp.u, n));
     HIKF_TRY(hikf::arena_alloc(h->arena, &sp.W64, nn));
     HIKF_TRY(hikf::arena_alloc(h->arena, &sp.W32, nn));
+    HIKF_TRY(hikf::arena_alloc(h->arena, &sp.Uhi, nn));
+    HIKF_TRY(hikf::arena_alloc(h->arena, &sp.Ulo, nn));
     const double cfac = p0.theta == 0.0 ? 0.0 : p0.theta / q.theta;
     HIKF_TRY(hikf::spectral_setup(sp, h->hcq_sym, h->rd, n, cfac, h->flag, s));
     int f[2] = {0, 0};
@@ -343,7 +345,7 @@ Status enqueue_step(hikf_t* h) {
   if (h->spectral) {
     HIKF_TRY(hikf::launch_innovation(h->ybuf, h->H, h->x, h->e, h->flag, s));
     HIKF_TRY(hikf::spectral_gain<T>(h->sp, h->n, h->e, h->a, (T*)h->Msw, h->nt, h->flag, s));
-    launches += 4;
+    launches += sizeof(T) == 4 ? 5 : 4;
   } else {
     HIKF_TRY(hikf::launch_chain(c, s));
     launches += c.fp64 ? 1 : (2 + 3 * c.refine_iters + 3);

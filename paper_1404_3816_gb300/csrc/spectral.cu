@@ -253,29 +253,81 @@ __global__ void spec_a_kernel(const double* __restrict__ W64, const double* __re
   if (lane == 0) a[i] = acc;
 }
 
-// Msw[i][j] = sum_k W_ik W_jk / s_k  (sweep operand, row stride nt), 16 x 16 output tiles
-template <typename T, typename WT>
-__global__ void spec_m_kernel(const WT* __restrict__ W, const double* __restrict__ s, int n, int nt,
-                              T* __restrict__ Msw, const int* __restrict__ flag) {
+// U = W diag(1/sqrt(s)) split into FP32 hi + lo, so that M = U U^T
+__global__ void spec_split_kernel(const double* __restrict__ W64, const double* __restrict__ s, int n,
+                                  float* __restrict__ Uhi, float* __restrict__ Ulo, const int* __restrict__ flag) {
   if (*flag) return;
-  __shared__ WT wi[16][33], wj[16][33], g[32];
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * n) return;
+  int k = (int)(t % n);
+  double u = W64[t] / sqrt(s[k]);
+  float hi = (float)u;
+  Uhi[t] = hi;
+  Ulo[t] = (float)(u - (double)hi);
+}
+
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// M = U U^T with U = Uhi + Ulo in compensated (double-float) FP32: the products
+// Uhi_ik Uhi_jk are split exactly (FMA) and summed with error-free additions; the
+// cross terms are ~2^-24 smaller and summed plainly. 16 x 16 output tiles.
+template <typename T>
+__global__ void spec_m_dd_kernel(const float* __restrict__ Uhi, const float* __restrict__ Ulo, int n, int nt,
+                                 T* __restrict__ Msw, const int* __restrict__ flag) {
+  if (*flag) return;
+  __shared__ float hi_i[16][33], lo_i[16][33], hi_j[16][33], lo_j[16][33];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int i0 = blockIdx.y * 16, j0 = blockIdx.x * 16;
-  WT acc = (WT)0;
+  float ps = 0.f, pc = 0.f;
   for (int k0 = 0; k0 < n; k0 += 32) {
     for (int t = threadIdx.x; t < 16 * 32; t += 256) {
-      int r = t / 32, kk = t % 32;
-      int k = k0 + kk;
-      wi[r][kk] = (i0 + r < n && k < n) ? W[(int64_t)(i0 + r) * n + k] : (WT)0;
-      wj[r][kk] = (j0 + r < n && k < n) ? W[(int64_t)(j0 + r) * n + k] : (WT)0;
+      int r = t / 32, kk = t % 32, k = k0 + kk;
+      bool oi = i0 + r < n && k < n, oj = j0 + r < n && k < n;
+      hi_i[r][kk] = oi ? Uhi[(int64_t)(i0 + r) * n + k] : 0.f;
+      lo_i[r][kk] = oi ? Ulo[(int64_t)(i0 + r) * n + k] : 0.f;
+      hi_j[r][kk] = oj ? Uhi[(int64_t)(j0 + r) * n + k] : 0.f;
+      lo_j[r][kk] = oj ? Ulo[(int64_t)(j0 + r) * n + k] : 0.f;
     }
-    if (threadIdx.x < 32) g[threadIdx.x] = k0 + threadIdx.x < n ? (WT)(1.0 / s[k0 + threadIdx.x]) : (WT)0;
     __syncthreads();
-#pragma unroll 8
+#pragma unroll 4
+    for (int kk = 0; kk < 32; ++kk) {
+      const float a = hi_i[ty][kk], b = hi_j[tx][kk];
+      const float p = __fmul_rn(a, b);
+      const float pe = __fmaf_rn(a, b, -p);
+      float s2, e2;
+      two_sum_f(ps, p, s2, e2);
+      ps = s2;
+      pc += e2 + pe + (a * lo_j[tx][kk] + lo_i[ty][kk] * b);
+    }
+    __syncthreads();
+  }
+  if (i0 + ty < n && j0 + tx < n) Msw[(int64_t)(i0 + ty) * nt + j0 + tx] = (T)((double)ps + (double)pc);
+}
+
+// FP64 operand (FP64 mode): M = W diag(1/s) W^T in FP64, 16 x 16 output tiles
+__global__ void spec_m64_kernel(const double* __restrict__ W, const double* __restrict__ s, int n, int nt,
+                                double* __restrict__ Msw, const int* __restrict__ flag) {
+  if (*flag) return;
+  __shared__ double wi[16][33], wj[16][33], g[32];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int i0 = blockIdx.y * 16, j0 = blockIdx.x * 16;
+  double acc = 0.0;
+  for (int k0 = 0; k0 < n; k0 += 32) {
+    for (int t = threadIdx.x; t < 16 * 32; t += 256) {
+      int r = t / 32, kk = t % 32, k = k0 + kk;
+      wi[r][kk] = (i0 + r < n && k < n) ? W[(int64_t)(i0 + r) * n + k] : 0.0;
+      wj[r][kk] = (j0 + r < n && k < n) ? W[(int64_t)(j0 + r) * n + k] : 0.0;
+    }
+    if (threadIdx.x < 32) g[threadIdx.x] = k0 + threadIdx.x < n ? 1.0 / s[k0 + threadIdx.x] : 0.0;
+    __syncthreads();
     for (int kk = 0; kk < 32; ++kk) acc += wi[ty][kk] * g[kk] * wj[tx][kk];
     __syncthreads();
   }
-  if (i0 + ty < n && j0 + tx < n) Msw[(int64_t)(i0 + ty) * nt + j0 + tx] = (T)acc;
+  if (i0 + ty < n && j0 + tx < n) Msw[(int64_t)(i0 + ty) * nt + j0 + tx] = acc;
 }
 
 // s <- lambda + 2 - 1/s   (after an applied step)
@@ -325,10 +377,13 @@ Status spectral_gain(const SpectralState& sp, int n, const double* e, double* a,
   spec_a_kernel<<<nblk((int64_t)n * 32, 256), 256, 0, s>>>(sp.W64, sp.u, n, a, flag);
   HIKF_LAUNCH_CHECK("spec_a");
   dim3 grid((unsigned)((n + 15) / 16), (unsigned)((n + 15) / 16));
-  if (sizeof(T) == 8)
-    spec_m_kernel<T, double><<<grid, 256, 0, s>>>(sp.W64, sp.s, n, nt, Msw, flag);
-  else
-    spec_m_kernel<T, float><<<grid, 256, 0, s>>>(sp.W32, sp.s, n, nt, Msw, flag);
+  if (sizeof(T) == 8) {
+    spec_m64_kernel<<<grid, 256, 0, s>>>(sp.W64, sp.s, n, nt, (double*)Msw, flag);
+  } else {
+    spec_split_kernel<<<nblk((int64_t)n * n, 256), 256, 0, s>>>(sp.W64, sp.s, n, sp.Uhi, sp.Ulo, flag);
+    HIKF_LAUNCH_CHECK("spec_split");
+    spec_m_dd_kernel<T><<<grid, 256, 0, s>>>(sp.Uhi, sp.Ulo, n, nt, Msw, flag);
+  }
   HIKF_LAUNCH_CHECK("spec_m");
   return Status::Ok();
 }

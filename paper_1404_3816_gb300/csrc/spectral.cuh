@@ -10,6 +10,8 @@ struct SpectralState {
   double* s = nullptr;    // n current s_t (eigenvalues of D S_t D)
   double* W64 = nullptr;  // n x n, D V
   float* W32 = nullptr;   // n x n, D V rounded to FP32
+  float* Uhi = nullptr;   // n x n, W diag(s)^{-1/2} as FP32 hi + lo (per step)
+  float* Ulo = nullptr;
   double* u = nullptr;    // n scratch
 };
 
