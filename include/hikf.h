@@ -81,9 +81,17 @@ typedef struct {
                         HIKF_CHAIN_SPECTRAL: one eigendecomposition of
                         R^{-1/2} H C_Q R^{-1/2} at create, then an O(n) recurrence per
                         step (HIKF_EINVAL when P_0 is not c Q). */
+  int form;          /* the state the update sweeps over each step:
+                        HIKF_FORM_CROSS (default): the cross-covariance C = P H^T of
+                        Alg. 2, one (m x n)(n x n) contraction per step, O(n^2 m);
+                        HIKF_FORM_EIGEN: the same filter carried as G = C R^{-1/2} V
+                        (V: eigenvectors of R^{-1/2} H C_Q R^{-1/2}); the update is
+                        then diagonal, O(n m) per step, and the variance a sum of
+                        squares. Needs the spectral chain (P_0 = c Q) and FP32/FP64. */
 } hikf_options;
 
 enum { HIKF_CHAIN_AUTO = 0, HIKF_CHAIN_FACTOR = 1, HIKF_CHAIN_SPECTRAL = 2 };
+enum { HIKF_FORM_CROSS = 0, HIKF_FORM_EIGEN = 1 };
 
 /* Fill *opt with the defaults listed above. */
 hikf_status hikf_options_default(hikf_options* opt);
@@ -179,6 +187,7 @@ typedef struct {
   double create_ms;   /* wall time of the precomputation */
   int sweep_launches; /* kernel launches of one measurement update */
   int chain;          /* HIKF_CHAIN_FACTOR or HIKF_CHAIN_SPECTRAL: the form in use */
+  int form;           /* HIKF_FORM_CROSS or HIKF_FORM_EIGEN */
 } hikf_info_t;
 
 hikf_status hikf_info(const hikf_t* h, hikf_info_t* info);

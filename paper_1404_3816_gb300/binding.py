@@ -24,6 +24,8 @@ PREC_FP32, PREC_MIXED, PREC_FP64 = 0, 1, 2
 PRECISIONS = {"fp32": PREC_FP32, "mixed": PREC_MIXED, "fp64": PREC_FP64}
 CHAIN_AUTO, CHAIN_FACTOR, CHAIN_SPECTRAL = 0, 1, 2
 CHAINS = {"auto": CHAIN_AUTO, "factor": CHAIN_FACTOR, "spectral": CHAIN_SPECTRAL}
+FORM_CROSS, FORM_EIGEN = 0, 1
+FORMS = {"cross": FORM_CROSS, "eigen": FORM_EIGEN}
 
 # every symbol include/hikf.h declares
 EXPORTED = ["hikf_options_default", "hikf_create", "hikf_create_with_cq", "hikf_assimilate",
@@ -45,14 +47,14 @@ class Kernel(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("cheb_order", C.c_int), ("leaf_size", C.c_int), ("max_depth", C.c_int),
-                ("precision", C.c_int), ("cuda_stream", C.c_void_p), ("chain", C.c_int)]
+                ("precision", C.c_int), ("cuda_stream", C.c_void_p), ("chain", C.c_int), ("form", C.c_int)]
 
 
 class Info(C.Structure):
     _fields_ = [("m", C.c_int64), ("n", C.c_int), ("dim", C.c_int), ("depth", C.c_int),
                 ("cheb_order", C.c_int), ("precision", C.c_int), ("step", C.c_int64),
                 ("device_bytes", C.c_int64), ("create_ms", C.c_double), ("sweep_launches", C.c_int),
-                ("chain", C.c_int)]
+                ("chain", C.c_int), ("form", C.c_int)]
 
 
 _lib = None
@@ -128,7 +130,7 @@ def kernel_struct(spec) -> Kernel:
 
 
 def options(cheb_order: int = 8, leaf_size: int = 64, max_depth: int = -1, precision="fp32",
-            stream=None, chain="auto") -> Options:
+            stream=None, chain="auto", form="cross") -> Options:
     o = Options()
     load().hikf_options_default(C.byref(o))
     o.cheb_order = int(cheb_order)
@@ -136,6 +138,7 @@ def options(cheb_order: int = 8, leaf_size: int = 64, max_depth: int = -1, preci
     o.max_depth = int(max_depth)
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     o.chain = CHAINS[chain] if isinstance(chain, str) else int(chain)
+    o.form = FORMS[form] if isinstance(form, str) else int(form)
     if stream is not None:
         o.cuda_stream = C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
     return o

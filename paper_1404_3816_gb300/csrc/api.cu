@@ -12,6 +12,7 @@
 #include "hikf_internal.cuh"
 #include "spectral.cuh"
 #include "step.cuh"
+#include "sweep_tc.cuh"
 
 namespace hikf {
 
@@ -134,6 +135,10 @@ struct hikf_handle {
   hikf::ChainArgs chain;
   bool spectral = false;
   hikf::SpectralState sp;
+  hikf::TcState tc;
+  bool eigen = false;
+  void* G = nullptr;   // eigenbasis state (HIKF_FORM_EIGEN), m x ld
+  void* Gq = nullptr;  // C_Q W
   void* Msw = nullptr;
   double* e = nullptr;
   double* a = nullptr;
@@ -150,6 +155,7 @@ struct hikf_handle {
   std::vector<cudaEvent_t> ev;
 
   bool fp64() const { return prec == HIKF_PREC_FP64; }
+  bool mixed() const { return prec == HIKF_PREC_MIXED; }
 };
 
 namespace {
@@ -191,6 +197,9 @@ Status validate_common(int dim, int64_t m, const double* points, int n, const in
   if (o.precision != HIKF_PREC_FP32 && o.precision != HIKF_PREC_FP64 && o.precision != HIKF_PREC_MIXED)
     return make_status(HIKF_EINVAL, "unknown precision");
   if (o.chain < HIKF_CHAIN_AUTO || o.chain > HIKF_CHAIN_SPECTRAL) return make_status(HIKF_EINVAL, "unknown chain");
+  if (o.form != HIKF_FORM_CROSS && o.form != HIKF_FORM_EIGEN) return make_status(HIKF_EINVAL, "unknown form");
+  if (o.form == HIKF_FORM_EIGEN && o.precision == HIKF_PREC_MIXED)
+    return make_status(HIKF_EINVAL, "the eigenbasis form runs on the CUDA cores (FP32 or FP64)");
   return Status::Ok();
 }
 
@@ -206,7 +215,7 @@ Status validate_kernel(const hikf_kernel& k, bool allow_zero) {
 
 template <typename T>
 Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const double* x0, const double* cq,
-                   const double* c0, const double* r_diag, int chain_opt) {
+                   const double* c0, const double* r_diag, int chain_opt, int form_opt) {
   cudaStream_t s = h->stream;
   const int64_t m = h->m;
   const int n = h->n, ld = h->ld;
@@ -298,9 +307,9 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
   HIKF_TRY(hikf::arena_alloc(h->arena, &c.X64, nn));
   if (h->fp64()) HIKF_TRY(hikf::arena_alloc(h->arena, &c.M64, nn));
   HIKF_TRY(hikf::arena_alloc(h->arena, &c.emax, 1));
-  HIKF_TRY(hikf::arena_alloc(h->arena, &h->flag, 2));
+  HIKF_TRY(hikf::arena_alloc(h->arena, &h->flag, 4));
   HIKF_TRY(hikf::arena_alloc(h->arena, &h->dstep, 1));
-  HIKF_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int) * 2, s));
+  HIKF_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int) * 4, s));
   HIKF_CUDA(cudaMemsetAsync(h->dstep, 0, sizeof(long long), s));
   c.flag = h->flag;
   c.fp64 = h->fp64() ? 1 : 0;
@@ -317,6 +326,8 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
   const bool can_spec = cq == nullptr && p0_is_cq;
   if (chain_opt == HIKF_CHAIN_SPECTRAL && !can_spec)
     return hikf::make_status(HIKF_EINVAL, "spectral chain needs P0 = c Q and a computed C_Q");
+  if (form_opt == HIKF_FORM_EIGEN && (!can_spec || chain_opt == HIKF_CHAIN_FACTOR))
+    return hikf::make_status(HIKF_EINVAL, "the eigenbasis form needs the spectral chain (P0 = c Q, computed C_Q)");
   h->spectral = can_spec && chain_opt != HIKF_CHAIN_FACTOR;
   if (h->spectral) {
     hikf::SpectralState& sp = h->sp;
@@ -333,6 +344,26 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
     HIKF_CUDA(cudaMemcpyAsync(f, h->flag, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
     HIKF_CUDA(cudaStreamSynchronize(s));
     if (f[0]) return hikf::make_status(HIKF_ENOTPD, "H C_1 + R is not positive definite");
+    if (form_opt == HIKF_FORM_EIGEN) {
+      T *G = nullptr, *Gq = nullptr;
+      HIKF_TRY(hikf::arena_alloc(h->arena, &G, (size_t)m * ld));
+      HIKF_TRY(hikf::arena_alloc(h->arena, &Gq, (size_t)m * ld));
+      HIKF_TRY(hikf::eigen_setup<T>(sp, CQ, m, ld, n, cfac, Gq, G, s));
+      h->G = G;
+      h->Gq = Gq;
+      h->eigen = true;
+    }
+  }
+  if (h->mixed()) {
+    hikf::TcState& tc = h->tc;
+    HIKF_TRY(hikf::tc_setup(tc, (const float*)C, (const float*)CQ, m, ld, n));
+    HIKF_TRY(hikf::arena_alloc(h->arena, &tc.bhi, (size_t)tc.nt * tc.nt));
+    HIKF_TRY(hikf::arena_alloc(h->arena, &tc.blo, (size_t)tc.nt * tc.nt));
+    HIKF_TRY(hikf::arena_alloc(h->arena, &tc.cmax, m));
+    HIKF_TRY(hikf::arena_alloc(h->arena, &tc.cqmax, m));
+    HIKF_TRY(hikf::arena_alloc(h->arena, &tc.mmax, 1));
+    HIKF_TRY(hikf::arena_alloc(h->arena, &tc.beta_exp, 1));
+    HIKF_TRY(hikf::tc_init_rows(tc, (const float*)C, (const float*)CQ, m, ld, s));
   }
   return Status::Ok();
 }
@@ -342,6 +373,23 @@ Status enqueue_step(hikf_t* h) {
   cudaStream_t s = h->stream;
   hikf::ChainArgs& c = h->chain;
   int launches = 0;
+  if (h->eigen) {
+    HIKF_TRY(hikf::launch_innovation(h->ybuf, h->H, h->x, h->e, h->flag, s));
+    HIKF_TRY(hikf::eigen_u(h->sp, h->n, h->e, h->flag, s));
+    const bool rec = h->prof && h->prof_count < (int)h->ev.size() / 2;
+    if (rec) HIKF_CUDA(cudaEventRecord(h->ev[2 * h->prof_count], s));
+    HIKF_TRY(hikf::eigen_step<T>(h->sp, h->m, h->ld, h->n, (T*)h->G, (const T*)h->Gq, h->theta_q, h->x, h->var,
+                                 h->flag, h->sms, s));
+    if (rec) {
+      HIKF_CUDA(cudaEventRecord(h->ev[2 * h->prof_count + 1], s));
+      ++h->prof_count;
+    }
+    hikf::count_step<<<1, 1, 0, s>>>(h->flag, h->dstep);
+    HIKF_LAUNCH_CHECK("count_step");
+    HIKF_TRY(hikf::spectral_next(h->sp, h->n, h->flag, s));
+    h->launches = 6;
+    return Status::Ok();
+  }
   if (h->spectral) {
     HIKF_TRY(hikf::launch_innovation(h->ybuf, h->H, h->x, h->e, h->flag, s));
     HIKF_TRY(hikf::spectral_gain<T>(h->sp, h->n, h->e, h->a, (T*)h->Msw, h->nt, h->flag, s));
@@ -366,9 +414,30 @@ Status enqueue_step(hikf_t* h) {
   sa.x = h->x;
   sa.var = h->var;
   sa.flag = h->flag;
+  if (h->mixed()) {
+    HIKF_TRY(hikf::tc_pack(h->tc, (const float*)h->Msw, h->nt, h->n, h->flag, s));
+    launches += 3;
+  }
   const bool rec = h->prof && h->prof_count < (int)h->ev.size() / 2;
   if (rec) HIKF_CUDA(cudaEventRecord(h->ev[2 * h->prof_count], s));
-  HIKF_TRY(hikf::launch_sweep<T>(sa, s, h->sms));
+  if (h->mixed()) {
+    hikf::TcArgs ta;
+    ta.m = h->m;
+    ta.ld = h->ld;
+    ta.n = h->n;
+    ta.C = (float*)h->C;
+    ta.a = h->a;
+    ta.rd = h->rd;
+    ta.theta = h->theta_q;
+    ta.x = h->x;
+    ta.var = h->var;
+    ta.flag = h->flag;
+    ta.err = h->flag + 2;
+    ta.beta_exp = h->tc.beta_exp;
+    HIKF_TRY(hikf::tc_sweep(h->tc, ta, h->sms, s));
+  } else {
+    HIKF_TRY(hikf::launch_sweep<T>(sa, s, h->sms));
+  }
   if (rec) {
     HIKF_CUDA(cudaEventRecord(h->ev[2 * h->prof_count + 1], s));
     ++h->prof_count;
@@ -387,15 +456,16 @@ Status enqueue_step(hikf_t* h) {
 Status enqueue(hikf_t* h) { return h->fp64() ? enqueue_step<double>(h) : enqueue_step<float>(h); }
 
 Status read_flag(hikf_t* h, int* out) {
-  int f[2] = {0, 0};
-  HIKF_CUDA(cudaMemcpyAsync(f, h->flag, sizeof(int) * 2, cudaMemcpyDeviceToHost, h->stream));
+  int f[4] = {0, 0, 0, 0};
+  HIKF_CUDA(cudaMemcpyAsync(f, h->flag, sizeof(int) * 4, cudaMemcpyDeviceToHost, h->stream));
   HIKF_CUDA(cudaStreamSynchronize(h->stream));
-  *out = f[0];
-  if (f[0]) HIKF_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int) * 2, h->stream));
+  *out = f[0] | (f[2] ? 8 : 0);
+  if (*out) HIKF_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int) * 4, h->stream));
   return Status::Ok();
 }
 
 Status flag_status(int f) {
+  if (f & 8) return hikf::make_status(HIKF_ETIMEOUT, "a bounded wait in the tensor-core sweep timed out");
   if (f & 1) return hikf::make_status(HIKF_EINVAL, "non-finite measurement y; step not applied");
   if (f & 2) return hikf::make_status(HIKF_ENOTPD, "H C + R is not positive definite; step not applied");
   return Status::Ok();
@@ -418,8 +488,8 @@ hikf_status create_impl(hikf_t** out, int dim, int64_t m, const double* points, 
   st = validate_kernel(p0, true);
   if (!st.ok()) return fail(nullptr, st);
   if (cq && !c0) return fail(nullptr, hikf::make_status(HIKF_EINVAL, "c0 is NULL"));
-  if (o.precision == HIKF_PREC_MIXED)
-    return fail(nullptr, hikf::make_status(HIKF_EINVAL, "MIXED precision is not available in this build"));
+  if (o.precision == HIKF_PREC_MIXED && hikf::padded_ld(n) > 256)
+    return fail(nullptr, hikf::make_status(HIKF_EINVAL, "MIXED precision supports n <= 256"));
   hikf_t* h = new (std::nothrow) hikf_handle();
   if (!h) return fail(nullptr, hikf::make_status(HIKF_ENOMEM, "host allocation failed"));
   auto bail = [&](const Status& s) {
@@ -459,8 +529,8 @@ hikf_status create_impl(hikf_t** out, int dim, int64_t m, const double* points, 
   if (!st.ok()) return bail(st);
   st = hikf::build_sparse(h->H, h->arena, h->tree, rowptr, col, val, n, h->stream);
   if (!st.ok()) return bail(st);
-  st = h->fp64() ? setup_state<double>(h, q, p0, x0, cq, c0, r_diag, o.chain)
-                 : setup_state<float>(h, q, p0, x0, cq, c0, r_diag, o.chain);
+  st = h->fp64() ? setup_state<double>(h, q, p0, x0, cq, c0, r_diag, o.chain, o.form)
+                 : setup_state<float>(h, q, p0, x0, cq, c0, r_diag, o.chain, o.form);
   if (!st.ok()) return bail(st);
   e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return bail(hikf::cuda_status(e, "create", __FILE__, __LINE__));
@@ -481,6 +551,7 @@ hikf_status hikf_options_default(hikf_options* opt) {
   opt->precision = HIKF_PREC_FP32;
   opt->cuda_stream = nullptr;
   opt->chain = HIKF_CHAIN_AUTO;
+  opt->form = HIKF_FORM_CROSS;
   return HIKF_OK;
 }
 
@@ -578,7 +649,17 @@ static hikf_status get_mat(hikf_t* h, const void* src, double* out) {
 }
 
 hikf_status hikf_get_cq(hikf_t* h, double* out) { return get_mat(h, h ? h->CQ : nullptr, out); }
-hikf_status hikf_get_cross(hikf_t* h, double* out) { return get_mat(h, h ? h->C : nullptr, out); }
+hikf_status hikf_get_cross(hikf_t* h, double* out) {
+  if (h && h->eigen) {
+    // C_{t|t} = (G - Gq) W^T R, formed on request into the C buffer (unused by this form)
+    Status st = h->fp64() ? hikf::eigen_cross<double>(h->sp, h->rd, h->m, h->ld, h->n, (const double*)h->G,
+                                                       (const double*)h->Gq, (double*)h->C, h->stream)
+                          : hikf::eigen_cross<float>(h->sp, h->rd, h->m, h->ld, h->n, (const float*)h->G,
+                                                      (const float*)h->Gq, (float*)h->C, h->stream);
+    if (!st.ok()) return fail(h, st);
+  }
+  return get_mat(h, h ? h->C : nullptr, out);
+}
 
 hikf_status hikf_get_perm(hikf_t* h, int64_t* out) {
   if (!h || !out) return HIKF_EINVAL;
@@ -605,6 +686,7 @@ hikf_status hikf_info(const hikf_t* h, hikf_info_t* info) {
   info->create_ms = h->create_ms;
   info->sweep_launches = h->launches;
   info->chain = h->spectral ? HIKF_CHAIN_SPECTRAL : HIKF_CHAIN_FACTOR;
+  info->form = h->eigen ? HIKF_FORM_EIGEN : HIKF_FORM_CROSS;
   return HIKF_OK;
 }
 

@@ -17,6 +17,8 @@
 // Wilkinson shifts (Golub & Van Loan, Sec. 8.3), all on one CTA in FP64.
 #include <math.h>
 
+#include <algorithm>
+
 #include "hikf_internal.cuh"
 #include "spectral.cuh"
 
@@ -397,5 +399,200 @@ Status spectral_next(const SpectralState& sp, int n, int* flag, cudaStream_t s) 
   HIKF_LAUNCH_CHECK("spec_next");
   return Status::Ok();
 }
+
+}  // namespace hikf
+
+// ---------------------------------------------------------------------------
+// Eigenbasis form of the state (rotated cross-covariance G = C_{t|t-1} W).
+// Because W^T R W = V^T V = I, the update C_{t|t} = C_{t|t-1} W diag(g) W^T R
+// becomes G_{t+1|t} = G_{t|t-1} diag(g) + C_Q W in the rotated basis, and
+//   sum_j K_ij (C_p)_ij = sum_k g_k G_ik^2,   (C_p a)_i = sum_k G_ik u_k,
+// with g = 1/s_t and u = g o (W^T e). One pass over G per step, O(m n).
+// ---------------------------------------------------------------------------
+namespace hikf {
+namespace {
+
+__device__ __forceinline__ void kahan_add(float v, float& s, float& c) {
+  const float y = v - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+// one warp per row; columns [0, ld) in float4 / double2 vectors
+template <typename T>
+__global__ void eigen_sweep_kernel(int64_t m, int ld, int n, T* __restrict__ G, const T* __restrict__ Gq,
+                                   const double* __restrict__ s, const double* __restrict__ u, double theta,
+                                   double* __restrict__ x, double* __restrict__ var, const int* __restrict__ flag) {
+  if (*flag) return;
+  __shared__ T sg[kMaxN], su[kMaxN];
+  for (int k = threadIdx.x; k < ld; k += blockDim.x) {
+    sg[k] = k < n ? (T)(1.0 / s[k]) : (T)0;
+    su[k] = k < n ? (T)u[k] : (T)0;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < m; row += warps) {
+    T* gr = G + row * ld;
+    const T* qr = Gq + row * ld;
+    float rs = 0.f, rc = 0.f, xs = 0.f, xc = 0.f;
+    double rd64 = 0.0, xd64 = 0.0;
+    if (sizeof(T) == 4) {
+      for (int k0 = lane * 4; k0 < ld; k0 += 128) {
+        float4 gv = *reinterpret_cast<const float4*>(gr + k0);
+        const float4 qv = *reinterpret_cast<const float4*>(qr + k0);
+        float* ga = reinterpret_cast<float*>(&gv);
+        const float* qa = reinterpret_cast<const float*>(&qv);
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          const float gk = (float)sg[k0 + w];
+          kahan_add(gk * ga[w] * ga[w], rs, rc);
+          kahan_add(ga[w] * (float)su[k0 + w], xs, xc);
+          ga[w] = ga[w] * gk + qa[w];
+        }
+        *reinterpret_cast<float4*>(gr + k0) = gv;
+      }
+      rd64 = (double)rs - (double)rc;
+      xd64 = (double)xs - (double)xc;
+    } else {
+      for (int k = lane; k < ld; k += 32) {
+        const double gv = (double)gr[k], gk = (double)sg[k];
+        rd64 += gk * gv * gv;
+        xd64 += gv * (double)su[k];
+        gr[k] = (T)(gv * gk + (double)qr[k]);
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      rd64 += __shfl_xor_sync(0xffffffffu, rd64, o);
+      xd64 += __shfl_xor_sync(0xffffffffu, xd64, o);
+    }
+    if (lane == 0) {
+      var[row] += theta - rd64;
+      x[row] += xd64;
+    }
+  }
+}
+
+// out (m x ldo) = A (m x lda, first kdim columns) * B (kdim x nout, row-major, ld ldb), 64 x 64 tiles
+template <typename T, typename BT>
+__global__ void gemm_tn_kernel(int64_t m, int kdim, int nout, const T* __restrict__ A, int lda,
+                               const BT* __restrict__ Bm, int ldb, T* __restrict__ out, int ldo, int subtract_q,
+                               const T* __restrict__ Aq) {
+  __shared__ T As[16][65];
+  __shared__ T Bs[16][64];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int64_t r0 = (int64_t)blockIdx.x * 64;
+  const int c0 = blockIdx.y * 64;
+  T acc[4][4];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) acc[i][j] = (T)0;
+  for (int k0 = 0; k0 < kdim; k0 += 16) {
+    for (int t = threadIdx.x; t < 64 * 16; t += 256) {
+      int r = t / 16, kk = t % 16;
+      int64_t gr = r0 + r;
+      T v = (T)0;
+      if (gr < m && k0 + kk < kdim) {
+        v = A[gr * lda + k0 + kk];
+        if (subtract_q) v -= Aq[gr * lda + k0 + kk];
+      }
+      As[kk][r] = v;
+    }
+    for (int t = threadIdx.x; t < 16 * 64; t += 256) {
+      int kk = t / 64, c = t % 64;
+      Bs[kk][c] = (k0 + kk < kdim && c0 + c < nout) ? (T)Bm[(int64_t)(k0 + kk) * ldb + c0 + c] : (T)0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      T a[4], b[4];
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+      for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+    }
+    __syncthreads();
+  }
+  for (int i = 0; i < 4; ++i) {
+    int64_t gr = r0 + ty * 4 + i;
+    if (gr >= m) continue;
+    for (int j = 0; j < 4; ++j) {
+      int c = c0 + tx + 16 * j;
+      if (c < ldo) out[gr * ldo + c] = c < nout ? acc[i][j] : (T)0;
+    }
+  }
+}
+
+// B = W^T R (n x n): B[k][j] = W[j][k] r_j
+__global__ void wtr_kernel(const double* __restrict__ W64, const double* __restrict__ rd, int n,
+                           double* __restrict__ out) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * n) return;
+  int k = (int)(t / n), j = (int)(t % n);
+  out[t] = W64[(int64_t)j * n + k] * rd[j];
+}
+
+template <typename T>
+__global__ void scale_copy_kernel(const T* __restrict__ src, T* __restrict__ dst, int64_t count, double f) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < count) dst[t] = (T)((double)src[t] * f);
+}
+
+inline int nb(int64_t n, int t) { return (int)((n + t - 1) / t); }
+
+}  // namespace
+
+template <typename T>
+Status eigen_setup(const SpectralState& sp, const T* CQ, int64_t m, int ld, int n, double c, T* Gq, T* G,
+                   cudaStream_t s) {
+  dim3 grid((unsigned)((m + 63) / 64), (unsigned)((ld + 63) / 64));
+  gemm_tn_kernel<T, double><<<grid, 256, 0, s>>>(m, n, n, CQ, ld, sp.W64, n, Gq, ld, 0, nullptr);
+  HIKF_LAUNCH_CHECK("gemm Gq");
+  scale_copy_kernel<T><<<nb(m * ld, 256), 256, 0, s>>>(Gq, G, m * ld, 1.0 + c);
+  HIKF_LAUNCH_CHECK("scale G");
+  return Status::Ok();
+}
+template Status eigen_setup<float>(const SpectralState&, const float*, int64_t, int, int, double, float*, float*,
+                                   cudaStream_t);
+template Status eigen_setup<double>(const SpectralState&, const double*, int64_t, int, int, double, double*,
+                                    double*, cudaStream_t);
+
+template <typename T>
+Status eigen_step(const SpectralState& sp, int64_t m, int ld, int n, T* G, const T* Gq, double theta, double* x,
+                  double* var, const int* flag, int sms, cudaStream_t s) {
+  const int64_t blocks = std::min<int64_t>((m + 7) / 8, (int64_t)sms * 8);
+  eigen_sweep_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(m, ld, n, G, Gq, sp.s, sp.u, theta, x, var, flag);
+  HIKF_LAUNCH_CHECK("eigen_sweep");
+  return Status::Ok();
+}
+template Status eigen_step<float>(const SpectralState&, int64_t, int, int, float*, const float*, double, double*,
+                                  double*, const int*, int, cudaStream_t);
+template Status eigen_step<double>(const SpectralState&, int64_t, int, int, double*, const double*, double, double*,
+                                   double*, const int*, int, cudaStream_t);
+
+Status eigen_u(const SpectralState& sp, int n, const double* e, const int* flag, cudaStream_t s) {
+  spec_u_kernel<<<nb((int64_t)n * 32, 256), 256, 0, s>>>(sp.W64, sp.s, e, n, sp.u, flag);
+  HIKF_LAUNCH_CHECK("spec_u");
+  return Status::Ok();
+}
+
+// C_{t|t} = (G - Gq) W^T R  (output in the caller's T, m x ld)
+template <typename T>
+Status eigen_cross(const SpectralState& sp, const double* rd, int64_t m, int ld, int n, const T* G, const T* Gq,
+                   T* out, cudaStream_t s) {
+  double* B = nullptr;
+  HIKF_CUDA(cudaMallocAsync((void**)&B, sizeof(double) * (size_t)n * n, s));
+  wtr_kernel<<<nb((int64_t)n * n, 256), 256, 0, s>>>(sp.W64, rd, n, B);
+  HIKF_LAUNCH_CHECK("wtr");
+  dim3 grid((unsigned)((m + 63) / 64), (unsigned)((ld + 63) / 64));
+  gemm_tn_kernel<T, double><<<grid, 256, 0, s>>>(m, n, n, G, ld, B, n, out, ld, 1, Gq);
+  HIKF_LAUNCH_CHECK("gemm cross");
+  HIKF_CUDA(cudaFreeAsync(B, s));
+  return Status::Ok();
+}
+template Status eigen_cross<float>(const SpectralState&, const double*, int64_t, int, int, const float*, const float*,
+                                   float*, cudaStream_t);
+template Status eigen_cross<double>(const SpectralState&, const double*, int64_t, int, int, const double*,
+                                    const double*, double*, cudaStream_t);
 
 }  // namespace hikf

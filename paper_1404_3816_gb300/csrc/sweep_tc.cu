@@ -1,0 +1,579 @@
+// The measurement-update sweep (S4) on the 5th-generation tensor cores.
+//
+// Per 128-row tile of the m x n cross-covariance (Alg. 2):
+//   C_p = C + C_Q,  K = C_p M,  delta^2 += diag(Q) - sum_j K_ij C_p,ij,
+//   x += C_p a,  C <- K R  (= C_p - K H C_p, Eq. KF_pred_new, since H C_p = S - R).
+//
+// K = C_p M is a dense (m x n) x (n x n) contraction. To keep FP32-level accuracy
+// on FP16 tensor cores each operand is split into two FP16 pieces after a
+// power-of-two scaling (row scale alpha_i for C_p, one scale beta for M):
+//   alpha C_p = A1 + A2,  beta M = B1 + B2,  K = (A1 B1 + A1 B2 + A2 B1) / (alpha beta),
+// 22 significant bits per operand; products are exact in the FP32 accumulator.
+// The row scale comes from a bound carried from the previous step:
+// |C_p,ij| <= max_j |C_{t|t}| + max_j |C_Q|.
+//
+// Data path (one persistent CTA per SM, warp-specialised):
+//   warp 0      TMA: raw FP32 tiles of C and C_Q (128 rows x 32 columns, 128B
+//               swizzle) and the pre-laid-out FP16 images of M (bulk copies)
+//   warps 4-7   one thread per row: C_p = C + C_Q, x increment, split into FP16
+//               pieces in the canonical no-swizzle K-major layout, C_p into TMEM;
+//               after the MMAs: epilogue from TMEM (rowdot, C <- K R, row max)
+//   warp 1      TMEM allocation and the single-thread tcgen05.mma issue
+// TMEM (512 columns): accumulator K in columns [0, 256), C_p in [256, 512).
+// Every wait is bounded (about two seconds); a timeout sets an error code,
+// drains the copies and MMAs in flight, frees TMEM and returns.
+#include <cuda.h>
+#include <cuda_fp16.h>
+#include <math.h>
+
+#include <algorithm>
+
+#include "hikf_internal.cuh"
+#include "sweep_tc.cuh"
+
+namespace hikf {
+
+namespace {
+
+constexpr int kBM = 128;                 // rows per tile (MMA M)
+constexpr int kKC = 32;                  // K per stage
+constexpr int kRawStages = 3;
+constexpr int kAStages = 2;
+constexpr int kBStages = 2;
+constexpr int kRawBytes = kBM * kKC * 4;          // one FP32 raw tile (C or C_Q): 16 KB
+constexpr int kAPieceBytes = kBM * kKC * 2;       // one FP16 A piece: 8 KB
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
+
+template <int NT>
+struct TcLayout {
+  static constexpr int BPiece = NT * kKC * 2;                        // one FP16 B piece per stage
+  static constexpr int RawOff = 0;
+  static constexpr int AOff = RawOff + kRawStages * 2 * kRawBytes;
+  static constexpr int BOff = AOff + kAStages * 2 * kAPieceBytes;
+  static constexpr int VecOff = BOff + kBStages * 2 * BPiece;      // a (NT floats), r (NT floats)
+  static constexpr int BarOff = VecOff + 2 * NT * 4;
+  static constexpr int NumBars = 2 * kRawStages + 2 * kAStages + 2 * kBStages + 3;
+  static constexpr int Total = BarOff + NumBars * 8 + 16;
+  static constexpr int Smem = Total + 1024;                          // slack for 1024-B alignment
+};
+
+// ---- PTX wrappers ----------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(bar),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// bounded wait: false (and *err set) after ~2 s
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, const volatile int* abort_flag) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = now_ns();
+  while (true) {
+    if (mbar_try(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (now_ns() - t0 > kWaitNs) {
+      atomicExch(err, 1);
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ void fence_barrier_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols));
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tc_mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                           uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+#define TC_REG32(a) \
+  a[0], a[1], a[2], a[3], a[4], a[5], a[6], a[7], a[8], a[9], a[10], a[11], a[12], a[13], a[14], a[15], a[16], a[17], \
+      a[18], a[19], a[20], a[21], a[22], a[23], a[24], a[25], a[26], a[27], a[28], a[29], a[30], a[31]
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]),
+      "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]),
+      "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor, canonical K-major layout without swizzle:
+// core matrices of 8 rows x 16 bytes; lbo = byte step between core matrices
+// along K, sbo = byte step between 8-row groups; version 1 (tcgen05).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;  // base offset 0, layout type 0 (no swizzle)
+}
+
+// byte offset of element (row, k), k < 32, in a K-major core-matrix piece (32 K = 4 core matrices per row group)
+__host__ __device__ __forceinline__ uint32_t core_off(int row, int k) {
+  return (uint32_t)((row >> 3) * 512 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ int pow2_exp(float bound) {
+  // e with bound < 2^e (bound > 0)
+  int e;
+  frexpf(bound, &e);
+  return e;
+}
+
+template <int NT>
+__global__ void __launch_bounds__(256, 1) sweep_tc_kernel(const __grid_constant__ CUtensorMap tmC,
+                                                          const __grid_constant__ CUtensorMap tmCQ, TcArgs args) {
+  using Lay = TcLayout<NT>;
+  constexpr int NK = NT / kKC;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (*args.flag) return;  // a rejected step is a no-op
+
+  float* s_a = reinterpret_cast<float*>(smem + Lay::VecOff);
+  float* s_r = s_a + NT;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Lay::BarOff);
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + Lay::BarOff + Lay::NumBars * 8);
+  volatile int* s_abort = reinterpret_cast<volatile int*>(s_tmem + 1);
+  const uint32_t bar0 = smem_u32(bars);
+  auto raw_full = [&](int s) { return bar0 + 8u * s; };
+  auto raw_empty = [&](int s) { return bar0 + 8u * (kRawStages + s); };
+  auto a_full = [&](int s) { return bar0 + 8u * (2 * kRawStages + s); };
+  auto a_empty = [&](int s) { return bar0 + 8u * (2 * kRawStages + kAStages + s); };
+  auto b_full = [&](int s) { return bar0 + 8u * (2 * kRawStages + 2 * kAStages + s); };
+  auto b_empty = [&](int s) { return bar0 + 8u * (2 * kRawStages + 2 * kAStages + kBStages + s); };
+  const uint32_t acc_full = bar0 + 8u * (2 * kRawStages + 2 * kAStages + 2 * kBStages);
+  const uint32_t acc_empty = acc_full + 8u;
+  const uint32_t drain = acc_full + 16u;
+
+  for (int j = threadIdx.x; j < NT; j += blockDim.x) {
+    s_a[j] = j < args.n ? (float)args.a[j] : 0.f;
+    s_r[j] = j < args.n ? (float)args.rd[j] : 0.f;
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kRawStages; ++s) {
+      mbar_init(raw_full(s), 1);
+      mbar_init(raw_empty(s), 4);
+    }
+    for (int s = 0; s < kAStages; ++s) {
+      mbar_init(a_full(s), 4);
+      mbar_init(a_empty(s), 1);
+    }
+    for (int s = 0; s < kBStages; ++s) {
+      mbar_init(b_full(s), 1);
+      mbar_init(b_empty(s), 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, 4);
+    mbar_init(drain, 1);
+    *s_abort = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(smem_u32(s_tmem), 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *s_tmem;
+  const int64_t ntiles = (args.m + kBM - 1) / kBM;
+  const int beta_exp = *args.beta_exp;
+
+  if (warp == 0) {
+    // ---------------- producer ----------------
+    if (lane == 0) {
+      int rs = 0, bs = 0;
+      uint32_t rph = 0, bph = 0;
+      bool ok = true;
+      for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        for (int kc = 0; kc < NK && ok; ++kc) {
+          ok = mbar_wait(raw_empty(rs), rph ^ 1u, args.err, s_abort);
+          if (!ok) break;
+          const uint32_t rbase = smem_u32(smem + Lay::RawOff + rs * 2 * kRawBytes);
+          mbar_expect_tx(raw_full(rs), 2 * kRawBytes);
+          tma_load_2d(rbase, &tmC, kc * kKC, (int)(tile * kBM), raw_full(rs));
+          tma_load_2d(rbase + kRawBytes, &tmCQ, kc * kKC, (int)(tile * kBM), raw_full(rs));
+          if (++rs == kRawStages) {
+            rs = 0;
+            rph ^= 1u;
+          }
+          ok = mbar_wait(b_empty(bs), bph ^ 1u, args.err, s_abort);
+          if (!ok) break;
+          const uint32_t bbase = smem_u32(smem + Lay::BOff + bs * 2 * Lay::BPiece);
+          mbar_expect_tx(b_full(bs), 2 * Lay::BPiece);
+          bulk_load(bbase, args.bimg_hi + (size_t)kc * Lay::BPiece / 2, Lay::BPiece, b_full(bs));
+          bulk_load(bbase + Lay::BPiece, args.bimg_lo + (size_t)kc * Lay::BPiece / 2, Lay::BPiece, b_full(bs));
+          if (++bs == kBStages) {
+            bs = 0;
+            bph ^= 1u;
+          }
+        }
+      }
+      if (!ok) {
+        *s_abort = 1;
+        // copies already issued land within microseconds; give them 5 ms before the CTA exits
+        const unsigned long long t0 = now_ns();
+        while (now_ns() - t0 < 5000000ull) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const uint32_t idesc = (1u << 4) | ((uint32_t)(NT >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+      int as = 0, bs = 0;
+      uint32_t aph = 0, bph = 0, eph = 0;
+      bool ok = true;
+      for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        ok = mbar_wait(acc_empty, eph ^ 1u, args.err, s_abort);
+        eph ^= 1u;
+        if (!ok) break;
+        tc_fence_after();
+        for (int kc = 0; kc < NK && ok; ++kc) {
+          ok = mbar_wait(a_full(as), aph, args.err, s_abort) && mbar_wait(b_full(bs), bph, args.err, s_abort);
+          if (!ok) break;
+          tc_fence_after();
+          const uint32_t abase = smem_u32(smem + Lay::AOff + as * 2 * kAPieceBytes);
+          const uint32_t bbase = smem_u32(smem + Lay::BOff + bs * 2 * Lay::BPiece);
+          for (int ks = 0; ks < kKC / 16; ++ks) {
+            const uint64_t a1 = smem_desc(abase + ks * 256, 128, 512);
+            const uint64_t a2 = smem_desc(abase + kAPieceBytes + ks * 256, 128, 512);
+            const uint64_t b1 = smem_desc(bbase + ks * 256, 128, 512);
+            const uint64_t b2 = smem_desc(bbase + Lay::BPiece + ks * 256, 128, 512);
+            tc_mma_f16(tmem, a1, b1, idesc, (kc > 0 || ks > 0) ? 1u : 0u);
+            tc_mma_f16(tmem, a1, b2, idesc, 1u);
+            tc_mma_f16(tmem, a2, b1, idesc, 1u);
+          }
+          tc_commit(a_empty(as));
+          tc_commit(b_empty(bs));
+          if (++as == kAStages) {
+            as = 0;
+            aph ^= 1u;
+          }
+          if (++bs == kBStages) {
+            bs = 0;
+            bph ^= 1u;
+          }
+        }
+        if (!ok) break;
+        tc_commit(acc_full);
+      }
+      // all issued MMAs complete before TMEM is released
+      tc_commit(drain);
+      mbar_wait(drain, 0, args.err, s_abort);
+      if (!ok) *s_abort = 1;
+    }
+  } else if (warp >= 4) {
+    // ---------------- converter + epilogue (thread = row) ----------------
+    const int q = warp - 4;  // TMEM lane quarter
+    const int r = q * 32 + lane;
+    const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16);
+    int rs = 0, as = 0;
+    uint32_t rph = 0, aph = 0, fph = 0;
+    bool ok = true;
+    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+      const int64_t row = tile * kBM + r;
+      const bool valid = row < args.m;
+      float bound = valid ? args.cmax[row] + args.cqmax[row] : 0.f;
+      const int ea = bound > 0.f ? max(-100, min(100, pow2_exp(bound))) : 0;
+      const float alpha = ldexpf(1.f, 14 - ea);
+      float xs = 0.f, xc = 0.f;
+      for (int kc = 0; kc < NK; ++kc) {
+        ok = __all_sync(0xffffffffu, mbar_wait(raw_full(rs), rph, args.err, s_abort));
+        if (!ok) break;
+        const unsigned char* rc = smem + Lay::RawOff + rs * 2 * kRawBytes;
+        float cp[kKC];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int phys = c ^ (r & 7);  // 128B swizzle of the TMA tile
+          const float4 u = *reinterpret_cast<const float4*>(rc + r * 128 + phys * 16);
+          const float4 v = *reinterpret_cast<const float4*>(rc + kRawBytes + r * 128 + phys * 16);
+          cp[4 * c + 0] = u.x + v.x;
+          cp[4 * c + 1] = u.y + v.y;
+          cp[4 * c + 2] = u.z + v.z;
+          cp[4 * c + 3] = u.w + v.w;
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(raw_empty(rs));
+        if (++rs == kRawStages) {
+          rs = 0;
+          rph ^= 1u;
+        }
+#pragma unroll
+        for (int k = 0; k < kKC; ++k) {
+          const float y = cp[k] * s_a[kc * kKC + k] - xc;
+          const float t = xs + y;
+          xc = (t - xs) - y;
+          xs = t;
+        }
+        // C_p chunk into TMEM columns 256 + 32 kc
+        tmem_st32(tq + 256 + kc * kKC, reinterpret_cast<const uint32_t*>(cp));
+        ok = __all_sync(0xffffffffu, mbar_wait(a_empty(as), aph ^ 1u, args.err, s_abort));
+        if (!ok) break;
+        unsigned char* ab = smem + Lay::AOff + as * 2 * kAPieceBytes;
+#pragma unroll
+        for (int g = 0; g < kKC / 8; ++g) {
+          __align__(16) __half hi[8], lo[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const float sv = cp[8 * g + u] * alpha;
+            const __half h = __float2half_rn(sv);
+            hi[u] = h;
+            lo[u] = __float2half_rn(sv - __half2float(h));
+          }
+          *reinterpret_cast<uint4*>(ab + core_off(r, 8 * g)) = *reinterpret_cast<const uint4*>(hi);
+          *reinterpret_cast<uint4*>(ab + kAPieceBytes + core_off(r, 8 * g)) = *reinterpret_cast<const uint4*>(lo);
+        }
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(a_full(as));
+        if (++as == kAStages) {
+          as = 0;
+          aph ^= 1u;
+        }
+      }
+      if (!ok) break;
+      tmem_wait_st();
+      // ---- epilogue ----
+      ok = __all_sync(0xffffffffu, mbar_wait(acc_full, fph, args.err, s_abort));
+      fph ^= 1u;
+      if (!ok) break;
+      tc_fence_after();
+      const float inv = ldexpf(1.f, ea - 14 - beta_exp);  // 1 / (alpha beta)
+      float rs_ = 0.f, rc_ = 0.f, rmax = 0.f;
+      for (int j = 0; j < NK; ++j) {
+        uint32_t kv[32], cv[32];
+        tmem_ld32(tq + j * kKC, kv);
+        tmem_ld32(tq + 256 + j * kKC, cv);
+        tmem_wait_ld();
+        float out[32];
+#pragma unroll
+        for (int u = 0; u < 32; ++u) {
+          const float k = __uint_as_float(kv[u]) * inv;
+          const float c = __uint_as_float(cv[u]);
+          const float y = k * c - rc_;
+          const float t = rs_ + y;
+          rc_ = (t - rs_) - y;
+          rs_ = t;
+          out[u] = k * s_r[j * kKC + u];
+          rmax = fmaxf(rmax, fabsf(out[u]));
+        }
+        const int col0 = j * kKC;
+        if (valid && col0 < args.ld) {
+          float4* dst = reinterpret_cast<float4*>(args.C + row * args.ld + col0);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) dst[u] = make_float4(out[4 * u], out[4 * u + 1], out[4 * u + 2], out[4 * u + 3]);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acc_empty);
+      if (valid) {
+        args.var[row] += args.theta - ((double)rs_ - (double)rc_);
+        args.x[row] += (double)xs - (double)xc;
+        args.cmax[row] = rmax;
+      }
+    }
+    if (!ok) *s_abort = 1;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    __syncwarp();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+// B images: beta M split into FP16 hi / lo, K-major core-matrix layout per 32-K stage (see pack_b_dyn_kernel)
+__global__ void absmax_kernel(const float* __restrict__ M, int nt, int n, unsigned* __restrict__ out) {
+  float mx = 0.f;
+  for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += blockDim.x) {
+    int i = (int)(t / n), j = (int)(t % n);
+    mx = fmaxf(mx, fabsf(M[(int64_t)i * nt + j]));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  __shared__ float red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmaxf(mx, red[w]);
+    *out = __float_as_uint(fmaxf(red[0], mx));
+  }
+}
+
+// beta exponent from max|M| (written where pack_b_kernel and the sweep read it)
+__global__ void beta_kernel(const unsigned* __restrict__ mx, int* __restrict__ beta_exp) {
+  const float v = __uint_as_float(*mx);
+  int e = 0;
+  if (v > 0.f) frexpf(v, &e);
+  *beta_exp = 14 - e;
+}
+
+template <int NT>
+__global__ void pack_b_dyn_kernel(const float* __restrict__ Msw, int nt_src, int n, const int* __restrict__ beta_exp,
+                                  __half* __restrict__ hi, __half* __restrict__ lo, const int* __restrict__ flag) {
+  if (*flag) return;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)NT * NT) return;
+  const int nidx = (int)(t / NT), k = (int)(t % NT);
+  const float v = (nidx < n && k < n) ? Msw[(int64_t)nidx * nt_src + k] * ldexpf(1.f, *beta_exp) : 0.f;
+  const __half h = __float2half_rn(v);
+  const __half l = __float2half_rn(v - __half2float(h));
+  const int kc = k / kKC, kk = k % kKC;
+  const size_t off = (size_t)kc * (NT * kKC) + core_off(nidx, kk) / 2;
+  hi[off] = h;
+  lo[off] = l;
+}
+
+// per-row max |value| of an m x ld FP32 matrix (row scale bounds)
+__global__ void rowmax_kernel(const float* __restrict__ A, int64_t m, int ld, float* __restrict__ out) {
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= m) return;
+  float mx = 0.f;
+  for (int j = lane; j < ld; j += 32) mx = fmaxf(mx, fabsf(A[row * ld + j]));
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) out[row] = mx;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+Status encode_map(CUtensorMap* map, const float* base, int64_t m, int ld) {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    HIKF_CUDA(cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !p) return make_status(HIKF_ECUDA, "cuTensorMapEncodeTiled unavailable");
+    fn = (EncodeTiledFn)p;
+  }
+  cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)m};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+  cuuint32_t box[2] = {(cuuint32_t)kKC, (cuuint32_t)kBM};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return make_status(HIKF_ECUDA, "cuTensorMapEncodeTiled failed");
+  return Status::Ok();
+}
+
+inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
+
+}  // namespace
+
+Status tc_setup(TcState& tc, const float* C, const float* CQ, int64_t m, int ld, int n) {
+  if (ld > 256) return make_status(HIKF_EINVAL, "MIXED precision supports n <= 256");
+  tc.nt = ld <= 128 ? 128 : 256;
+  HIKF_TRY(encode_map(&tc.mapC, C, m, ld));
+  HIKF_TRY(encode_map(&tc.mapCQ, CQ, m, ld));
+  tc.smem = tc.nt == 128 ? TcLayout<128>::Smem : TcLayout<256>::Smem;
+  const void* fn = tc.nt == 128 ? (const void*)sweep_tc_kernel<128> : (const void*)sweep_tc_kernel<256>;
+  HIKF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, tc.smem));
+  return Status::Ok();
+}
+
+Status tc_init_rows(const TcState& tc, const float* C, const float* CQ, int64_t m, int ld, cudaStream_t s) {
+  rowmax_kernel<<<nblk(m, 8), 256, 0, s>>>(C, m, ld, tc.cmax);
+  HIKF_LAUNCH_CHECK("rowmax");
+  rowmax_kernel<<<nblk(m, 8), 256, 0, s>>>(CQ, m, ld, tc.cqmax);
+  HIKF_LAUNCH_CHECK("rowmax");
+  return Status::Ok();
+}
+
+Status tc_pack(const TcState& tc, const float* Msw, int nt_src, int n, const int* flag, cudaStream_t s) {
+  absmax_kernel<<<1, 1024, 0, s>>>(Msw, nt_src, n, tc.mmax);
+  HIKF_LAUNCH_CHECK("absmax");
+  beta_kernel<<<1, 1, 0, s>>>(tc.mmax, tc.beta_exp);
+  HIKF_LAUNCH_CHECK("beta");
+  const int64_t cnt = (int64_t)tc.nt * tc.nt;
+  if (tc.nt == 128)
+    pack_b_dyn_kernel<128><<<nblk(cnt, 256), 256, 0, s>>>(Msw, nt_src, n, tc.beta_exp, tc.bhi, tc.blo, flag);
+  else
+    pack_b_dyn_kernel<256><<<nblk(cnt, 256), 256, 0, s>>>(Msw, nt_src, n, tc.beta_exp, tc.bhi, tc.blo, flag);
+  HIKF_LAUNCH_CHECK("pack_b");
+  return Status::Ok();
+}
+
+Status tc_sweep(const TcState& tc, TcArgs args, int sms, cudaStream_t s) {
+  const int64_t ntiles = (args.m + kBM - 1) / kBM;
+  const int grid = (int)std::min<int64_t>(ntiles, sms);
+  args.bimg_hi = tc.bhi;
+  args.bimg_lo = tc.blo;
+  args.cmax = tc.cmax;
+  args.cqmax = tc.cqmax;
+  if (tc.nt == 128)
+    sweep_tc_kernel<128><<<grid, 256, tc.smem, s>>>(tc.mapC, tc.mapCQ, args);
+  else
+    sweep_tc_kernel<256><<<grid, 256, tc.smem, s>>>(tc.mapC, tc.mapCQ, args);
+  HIKF_LAUNCH_CHECK("sweep_tc");
+  return Status::Ok();
+}
+
+}  // namespace hikf

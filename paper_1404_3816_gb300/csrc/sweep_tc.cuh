@@ -1,0 +1,47 @@
+// Tensor-core sweep of the measurement update (internal).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_fp16.h>
+
+#include "hikf_internal.cuh"
+
+namespace hikf {
+
+struct TcArgs {
+  int64_t m = 0;
+  int ld = 0;
+  int n = 0;
+  float* C = nullptr;           // m x ld, updated in place (written as K R)
+  const double* a = nullptr;    // n
+  const double* rd = nullptr;   // n, diag R
+  double theta = 0.0;           // diag Q
+  double* x = nullptr;          // m
+  double* var = nullptr;        // m
+  const int* flag = nullptr;    // step error flag: nonzero -> no-op
+  int* err = nullptr;           // set to 1 when a bounded wait times out
+  const int* beta_exp = nullptr;  // scale exponent of M (device)
+  const __half* bimg_hi = nullptr;
+  const __half* bimg_lo = nullptr;
+  float* cmax = nullptr;        // m: max_j |C_ij| of the current C (row-scale bound)
+  const float* cqmax = nullptr; // m: max_j |C_Q,ij|
+};
+
+struct TcState {
+  int nt = 256;                 // MMA N (128 or 256)
+  int smem = 0;
+  CUtensorMap mapC, mapCQ;
+  __half* bhi = nullptr;        // nt x nt images of beta M (FP16 hi / lo)
+  __half* blo = nullptr;
+  float* cmax = nullptr;
+  float* cqmax = nullptr;
+  unsigned* mmax = nullptr;
+  int* beta_exp = nullptr;
+};
+
+Status tc_setup(TcState& tc, const float* C, const float* CQ, int64_t m, int ld, int n);
+Status tc_init_rows(const TcState& tc, const float* C, const float* CQ, int64_t m, int ld, cudaStream_t s);
+Status tc_pack(const TcState& tc, const float* Msw, int nt_src, int n, const int* flag, cudaStream_t s);
+Status tc_sweep(const TcState& tc, TcArgs args, int sms, cudaStream_t s);
+
+}  // namespace hikf
