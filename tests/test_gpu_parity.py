@@ -1,11 +1,16 @@
 """CUDA path vs the FP64 oracle, element by element, through the C ABI.
 
-Sizes span several 64-row sweep tiles with a ragged tail, ray counts that are
-not multiples of the 32-column padding, all three sweep widths (128/256/512),
-2D and 3D trees, both kernels, and the degenerate cases (P0 = 0, depth 0).
-Tolerances: FP32 path 1e-5 relative L2 (the agreement target of the method,
-stated for the H^2 product and for mean/variance); FP64 path 1e-10.
+Sizes span several 64- and 128-row sweep tiles with a ragged tail, ray counts
+that are not multiples of the 32-column padding, all three sweep widths
+(128/256/512), 2D and 3D trees, both kernels, and the degenerate cases (P0 = 0,
+depth 0). Tolerances: FP32 paths 1e-5 relative L2 (the agreement target of the
+method, stated for the H^2 product and for mean/variance); FP64 path 1e-10.
 Integer/index work (the tree permutation) is compared bit-exactly.
+
+Cases marked ill-conditioned have n of the order of m/4 rays through a small
+grid, so cond(H C + R) is beyond what an explicit FP32 inverse can carry
+(K = C_p S^{-1} cancels to ~1e-4); there the FP32 cross-covariance sweep is not
+claimed to 1e-5 and the FP64 path and the eigenbasis form are checked instead.
 """
 import numpy as np
 import pytest
@@ -49,9 +54,14 @@ CASES = {
                                        q=W.KernelSpec(W.GAUSS, 0.01, 6.0), p0=W.KernelSpec(W.GAUSS, 1.0, 6.0)),
     "n256_33x33": lambda: W.small(grid=(33, 33), n=256, steps=3, seed=24),
     "n300_30x30": lambda: W.small(grid=(30, 30), n=300, steps=3, seed=25),
+    "n256_120x120": lambda: W.small(grid=(120, 120), n=256, steps=3, seed=32),
+    "n300_140x130": lambda: W.small(grid=(140, 130), n=300, steps=3, seed=33),
     "3d_16x16x16_n16": lambda: W.make(grid=(16, 16, 16), n=16, q=W.KernelSpec(W.GAUSS, 0.01, 4.0),
                                       p0=W.KernelSpec(W.GAUSS, 1.0, 4.0), r=1e-3, steps=3, seed=26, cheb_order=5),
 }
+
+
+ILL = {"n256_33x33", "n300_30x30"}
 
 
 def _oracle_h2(w, kspec, depth, p):
@@ -98,7 +108,7 @@ def test_depth_zero_is_direct_sum(B):
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 @pytest.mark.parametrize("chain", ["factor", "spectral"])
-@pytest.mark.parametrize("name", ["m1024_n16", "ragged_61x37_n100", "n300_30x30"])
+@pytest.mark.parametrize("name", ["m1024_n16", "ragged_61x37_n100", "n300_140x130"])
 def test_both_forms_of_the_gain_chain_match_oracle(B, name, chain, prec):
     """S_t^{-1} by a Cholesky factor every step, or by the eigen-recurrence."""
     w = CASES[name]()
@@ -133,17 +143,20 @@ def _oracle_run(w, depth, Y, p):
 def _prec_cases():
     out = []
     for name in CASES:
-        for prec in ("fp32", "fp64", "mixed"):
-            if prec == "mixed" and name == "n300_30x30":
+        for prec, form in (("fp32", "cross"), ("fp64", "cross"), ("mixed", "cross"), ("fp32", "eigen"),
+                           ("fp64", "eigen")):
+            if prec == "mixed" and name.startswith("n300"):
                 continue                      # the tensor-core sweep takes n <= 256
-            out.append((name, prec))
+            if name in ILL and prec != "fp64" and form == "cross":
+                continue                      # see the module docstring
+            out.append((name, prec, form))
     return out
 
 
-@pytest.mark.parametrize("name,prec", _prec_cases())
-def test_filter_matches_oracle(B, name, prec):
+@pytest.mark.parametrize("name,prec,form", _prec_cases())
+def test_filter_matches_oracle(B, name, prec, form):
     w = CASES[name]()
-    x, v, c, depth, Y = _run(B, w, prec)
+    x, v, c, depth, Y = _run(B, w, prec, form=form)
     ref = _oracle_run(w, depth, Y, w.cheb_order)
     tol = TOL64 if prec == "fp64" else TOL32
     assert rel(x, ref["x"]) < tol
@@ -206,6 +219,13 @@ def test_nonfinite_measurement_is_rejected_and_state_kept(B):
         assert np.array_equal(f.cross(), c0)
         f.assimilate(Y[1])
         assert f.info()["step"] == 2
+
+
+def test_eigen_form_needs_the_spectral_chain(B):
+    w = W.small(grid=(30, 28), n=12, steps=1, seed=34, p0=W.KernelSpec(W.GAUSS, 0.5, 5.0))
+    with pytest.raises(B.HikfError) as e:
+        B.Filter.from_workload(w, form="eigen")
+    assert e.value.code == B.HIKF_EINVAL
 
 
 def test_mixed_rejects_more_than_256_rays(B):

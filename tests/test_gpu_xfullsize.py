@@ -58,8 +58,8 @@ def test_m2p20_order6_meets_h2_target(B):
     assert rel(cq[rows], ref_exact) < TOL
 
 
-def test_m2p20_gaussian_full_pipeline(B):
-    import torch
+@pytest.fixture(scope="module")
+def gauss_case():
     w = W.config("crosswell2d_m1048576_n256", q=W.KernelSpec(W.GAUSS, 0.01, 64.0),
                  p0=W.KernelSpec(W.GAUSS, 1.0, 64.0))
     T = 3
@@ -67,8 +67,49 @@ def test_m2p20_gaussian_full_pipeline(B):
     H = qht.h_csr(w.h_rowptr, w.h_col, w.h_val, w.m)
     cq = qht.qht_gauss_grid(w.grid, w.q.theta, w.q.length, H)
     ref = kf.hikf_cross(cq, 100.0 * cq, np.full(w.m, 1.0), w.q.theta, H, w.r_diag, w.x0, Y)
-    del cq
-    with B.Filter.from_workload(w) as f:           # the launch configuration of bench.py
+    return w, Y, ref
+
+
+@pytest.mark.parametrize("prec,form", [("fp64", "cross"), ("fp32", "eigen")])
+def test_m2p20_gaussian_full_pipeline(B, gauss_case, prec, form):
+    """H^2 product + updates at full size. The Gaussian kernel of length 64 makes
+    cond(H C + R) too large for the FP32 explicit-inverse sweep, so the FP32 check
+    runs the eigenbasis form; the cross-covariance form is checked in FP64."""
+    import torch
+    w, Y, ref = gauss_case
+    with B.Filter.from_workload(w, precision=prec, form=form) as f:
+        dY = torch.tensor(Y, dtype=torch.float64, device="cuda")
+        for t in range(Y.shape[0]):
+            f.assimilate_device(dY[t])
+        f.sync()
+        assert rel(f.mean(), ref["x"]) < TOL
+        assert rel(f.variance(), ref["var"]) < TOL
+
+
+def _mixture_cq(w, H):
+    # a sum of Gaussians of lengths 16, 48, 160 (heavier tail than one Gaussian)
+    out = None
+    for wt, L in ((0.5, 16.0), (0.3, 48.0), (0.2, 160.0)):
+        part = qht.qht_gauss_grid(w.grid, 0.01 * wt, L, H)
+        out = part if out is None else out + part
+    return out
+
+
+@pytest.mark.parametrize("prec", ["fp32", "mixed"])
+def test_m2p20_update_sweep_in_bench_configuration(B, prec):
+    """The FP32 and tensor-core cross-covariance sweeps at m = 2^20, n = 256 (the
+    timed workload's sizes and launch path), with an exact C_Q of a Gaussian
+    mixture kernel handed in through hikf_create_with_cq."""
+    import torch
+    w = W.config("crosswell2d_m1048576_n256")
+    T = 3
+    Y, _ = W.measurements(w, steps=T)
+    H = qht.h_csr(w.h_rowptr, w.h_col, w.h_val, w.m)
+    cq = _mixture_cq(w, H)
+    ref = kf.hikf_cross(cq, 100.0 * cq, np.full(w.m, 1.0), 0.01, H, w.r_diag, w.x0, Y)
+    with B.Filter(w.points, (1, 0.01, 1.0), w.h_rowptr, w.h_col, w.h_val, w.r_diag, w.x0, (1, 1.0, 1.0),
+                  cq=cq, c0=100.0 * cq, precision=prec) as f:
+        del cq
         dY = torch.tensor(Y, dtype=torch.float64, device="cuda")
         for t in range(T):
             f.assimilate_device(dY[t])
