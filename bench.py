@@ -39,7 +39,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="hikf", choices=["hikf", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp32", "mixed"])
+    ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--order", type=int, default=8)
     ap.add_argument("--config", default=CONFIG_NAME)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -131,7 +132,7 @@ def peaks():
 
 def source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("step.cu", "sweep_tc.cu"):
+    for f in ("step.cu", "sweep_tc.cu", "spectral.cu"):
         p = ROOT / "paper_1404_3816_gb300" / "csrc" / f
         if p.exists():
             h.update(p.read_bytes())
@@ -223,43 +224,54 @@ def main():
     total = args.warmup + args.steps
     Y, _ = W.measurements(w, steps=total)
     dY = torch.tensor(Y, dtype=torch.float64, device="cuda")
+    m, n = w.m, w.n
+    pk, pk_kind = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12     # FP32 FMA lanes x 2 flop x max SM clock
+    bytes_alg = 12.0 * m * n + 24.0 * m                 # read C, C_Q, write C (FP32); x, var r/w (FP64)
+    flops_alg = 2.0 * m * n * n + 6.0 * m * n
 
-    f = binding.Filter.from_workload(w, cheb_order=args.order, precision=args.precision)
-    info = f.info()
-    stream = torch.cuda.ExternalStream(f.stream)
+    def timed(prec, form, clocks=False, barrier=False):
+        """warmup + timed steps on a fresh filter; the filter is returned open."""
+        f = binding.Filter.from_workload(w, cheb_order=args.order, precision=prec, form=form)
+        stream = torch.cuda.ExternalStream(f.stream)
+        clk = Clocks(local).__enter__() if clocks else None
+        for t in range(args.warmup):
+            f.assimilate_device(dY[t])
+        f.sync()
+        if barrier and world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        f.profile(True)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        wall0 = time.time()
+        ev0.record(stream)
+        for t in range(args.warmup, total):
+            f.assimilate_device(dY[t])
+        ev1.record(stream)
+        ev1.synchronize()
+        wall1 = time.time()
+        if clk:
+            clk.__exit__(None, None, None)
+        f.sync()
+        torch.cuda.synchronize()
+        sweep_ms, sweep_n = f.profile_read()
+        f.profile(False)
+        return {"f": f, "elapsed_ms": ev0.elapsed_time(ev1), "sweep_ms": sweep_ms / max(1, sweep_n),
+                "clocks": clk.summary(wall0, wall1) if clk else None, "info": f.info(),
+                "mean": f.mean(), "var": f.variance()}
 
-    clk = Clocks(local).__enter__()
-    for t in range(args.warmup):
-        f.assimilate_device(dY[t])
-    f.sync()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    f.profile(True)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    wall0 = time.time()
-    ev0.record(stream)
-    for t in range(args.warmup, total):
-        f.assimilate_device(dY[t])
-    ev1.record(stream)
-    ev1.synchronize()
-    wall1 = time.time()
-    clk.__exit__(None, None, None)
-    f.sync()
-    torch.cuda.synchronize()
-    elapsed_ms = ev0.elapsed_time(ev1)
-    sweep_ms, sweep_n = f.profile_read()
-    f.profile(False)
-    clocks = clk.summary(wall0, wall1)
-    info = f.info()
+    head = timed(args.precision, "cross", clocks=True, barrier=True)
+    f = head["f"]
+    info = head["info"]
+    elapsed_ms = head["elapsed_ms"]
     if world > 1:
         t = torch.tensor([elapsed_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         elapsed_ms = float(t.item())
         dist.barrier()
-    steps_total = args.steps * world
-    value = steps_total / (elapsed_ms / 1000.0)
+    value = args.steps * world / (elapsed_ms / 1000.0)
 
     # e2e through the C ABI with host buffers: y in, mean and variance out, every step
     ne2e = max(1, args.e2e_steps)
@@ -280,45 +292,58 @@ def main():
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_s = float(tt.item())
     e2e_value = ne2e * world / e2e_s
+    f.close()
 
-    # roofline of the sweep (dominant kernel)
-    pk, pk_kind = peaks()
-    m, n = w.m, w.n
-    per_launch_ms = sweep_ms / max(1, sweep_n)
-    bytes_alg = 12.0 * m * n + 24.0 * m          # read C, C_Q, write C (FP32); x, var r/w (FP64)
-    flops_alg = 2.0 * m * n * n + 6.0 * m * n
-    if args.precision == "fp32":
-        sm_max = float(pk.get("sm_max_mhz", 2070.0))
-        peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12   # FP32 FMA lanes x 2 flop x max SM clock
-        achieved = flops_alg / (per_launch_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": ncu_traffic(args.precision, n),
-                "kernel": "sweep (FP32 CUDA cores)",
-                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (MEASURED_PEAKS sm_max_mhz)"}
-    else:
-        peak = float(pk["hbm_gbs"])
-        achieved = bytes_alg / (per_launch_ms / 1e3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": ncu_traffic(args.precision, n), "kernel": "sweep (tcgen05)",
-                "peak_source": f"hbm_gbs of {pk_kind}"}
-    roof["ms_per_launch"] = per_launch_ms
-    roof["alg_bytes_per_launch"] = bytes_alg
-    roof["alg_flops_per_launch"] = flops_alg
+    def roofline(prec, form, ms):
+        if form == "eigen" or prec == "mixed":
+            achieved = bytes_alg / (ms / 1e3) / 1e9
+            return {"bound": "hbm", "achieved": achieved, "peak": float(pk["hbm_gbs"]), "unit": "GB/s",
+                    "frac": achieved / float(pk["hbm_gbs"]), "traffic": ncu_traffic(prec if form == "cross" else
+                                                                                     "eigen", n),
+                    "kernel": "sweep_tc_kernel (tcgen05)" if form == "cross" else "eigen_sweep_f32_kernel",
+                    "peak_source": f"hbm_gbs, {pk_kind} (MEASURED_PEAKS.json)", "ms_per_launch": ms,
+                    "alg_bytes_per_launch": bytes_alg}
+        achieved = flops_alg / (ms / 1e3) / 1e12
+        return {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
+                "traffic": ncu_traffic(prec, n), "kernel": "sweep_kernel (FP32 CUDA cores)",
+                "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz", "ms_per_launch": ms,
+                "alg_flops_per_launch": flops_alg}
 
     line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "tf32x3",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f16 split hi/lo, f32 accumulate" if args.precision == "mixed" else "f32",
             "data": "synthetic",
             "config": {"workload": args.config, "m": m, "n": n, "dim": 2, "kernel": "exp, L=64, theta=0.01",
                        "p0": "exp, L=64, theta=1", "R": "1e-3 I", "cheb_order": args.order,
-                       "tree_depth": info["depth"], "precision": args.precision,
+                       "tree_depth": info["depth"], "precision": args.precision, "form": "cross (Alg. 2)",
+                       "chain": "spectral" if info["chain"] == 2 else "factor",
                        "create_ms": info["create_ms"], "device_bytes": info["device_bytes"],
                        "l2": "no flush: every step streams C and C_Q (2 GB FP32) > L2",
                        "parallelism": f"replicas x{world}"},
             "gpu_launches": int(info["sweep_launches"]) * args.steps,
             "e2e": {"value": e2e_value, "unit": "steps/s", "h2d_bytes_per_step": 8 * n,
                     "d2h_bytes_per_step": 16 * m, "steps": ne2e},
-            "roofline": roof, "clocks": clocks}
+            "roofline": roofline(args.precision, "cross", head["sweep_ms"]), "clocks": head["clocks"]}
+
+    if world == 1 and not args.no_compare:
+        # the other arithmetic of the same update, and the eigenbasis form; accuracy against
+        # the FP64 eigenbasis form (exact reformulation, checked against the oracle in tests)
+        ref = timed("fp64", "eigen")
+        ref["f"].close()
+        def err(r):
+            return {"mean": float(np.linalg.norm(r["mean"] - ref["mean"]) / np.linalg.norm(ref["mean"])),
+                    "var": float(np.linalg.norm(r["var"] - ref["var"]) / np.linalg.norm(ref["var"]))}
+        line["err_vs_fp64"] = {args.precision: err(head)}
+        comps = {}
+        for prec, form in (("fp32" if args.precision == "mixed" else "mixed", "cross"), ("fp32", "eigen")):
+            r = timed(prec, form)
+            r["f"].close()
+            key = f"{prec}_{form}"
+            comps[key] = {"value": args.steps / (r["elapsed_ms"] / 1000.0), "unit": "steps/s",
+                          "ms_per_step": r["elapsed_ms"] / args.steps, "roofline": roofline(prec, form, r["sweep_ms"]),
+                          "err_vs_fp64": err(r)}
+        line["compare"] = comps
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         steps = 3
@@ -326,7 +351,6 @@ def main():
         line["cpu_baseline"] = {"value": steps / dt, "unit": "steps/s", "cores": cpu_threads(), "kind": "oracle",
                                 "sample": f"{steps} FP64 O-cross updates at m={m}, n={n} (numpy, PSD stand-in C_Q);"
                                           " H^2 precompute not included"}
-    f.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -419,49 +419,116 @@ __device__ __forceinline__ void kahan_add(float v, float& s, float& c) {
   s = t;
 }
 
-// one warp per row; columns [0, ld) in float4 / double2 vectors
-template <typename T>
-__global__ void eigen_sweep_kernel(int64_t m, int ld, int n, T* __restrict__ G, const T* __restrict__ Gq,
-                                   const double* __restrict__ s, const double* __restrict__ u, double theta,
-                                   double* __restrict__ x, double* __restrict__ var, const int* __restrict__ flag) {
+// FP32: one warp per group of kRows rows; every load of the group is issued before
+// any store (the rows' G, Gq, x and delta^2), so each warp keeps ~kRows x 2 KB in flight.
+template <int VPL, int kRows>
+__global__ void __launch_bounds__(256) eigen_sweep_f32_kernel(int64_t m, int ld, int n, float* __restrict__ G,
+                                                              const float* __restrict__ Gq,
+                                                              const double* __restrict__ s,
+                                                              const double* __restrict__ u, double theta,
+                                                              double* __restrict__ x, double* __restrict__ var,
+                                                              const int* __restrict__ flag) {
   if (*flag) return;
-  __shared__ T sg[kMaxN], su[kMaxN];
+  __shared__ __align__(16) float sg[kMaxN], su[kMaxN];
   for (int k = threadIdx.x; k < ld; k += blockDim.x) {
-    sg[k] = k < n ? (T)(1.0 / s[k]) : (T)0;
-    su[k] = k < n ? (T)u[k] : (T)0;
+    sg[k] = k < n ? (float)(1.0 / s[k]) : 0.f;
+    su[k] = k < n ? (float)u[k] : 0.f;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int nv = ld / 128 + ((ld % 128) > lane * 4 ? 1 : 0);  // float4 vectors of this lane (ld % 32 == 0)
+  const int64_t groups = (m + kRows - 1) / kRows;
+  const int64_t gstride = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t grp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); grp < groups; grp += gstride) {
+    const int64_t row0 = grp * kRows;
+    float4 gv[kRows][VPL], qv[kRows][VPL];
+    double vr = 0.0, xr = 0.0;
+    const int64_t myrow = row0 + lane;
+    if (lane < kRows && myrow < m) {
+      vr = var[myrow];
+      xr = x[myrow];
+    }
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+      const int64_t row = row0 + r;
+#pragma unroll
+      for (int v = 0; v < VPL; ++v) {
+        if (v < nv && row < m) {
+          gv[r][v] = *reinterpret_cast<const float4*>(G + row * ld + v * 128 + lane * 4);
+          qv[r][v] = *reinterpret_cast<const float4*>(Gq + row * ld + v * 128 + lane * 4);
+        }
+      }
+    }
+    double rdv[kRows], xiv[kRows];
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+      const int64_t row = row0 + r;
+      float rp = 0.f, xp = 0.f;  // at most 16 terms per lane: plain FMA partials
+#pragma unroll
+      for (int v = 0; v < VPL; ++v) {
+        if (v < nv && row < m) {
+          float* ga = reinterpret_cast<float*>(&gv[r][v]);
+          const float* qa = reinterpret_cast<const float*>(&qv[r][v]);
+          const float4 g4 = *reinterpret_cast<const float4*>(sg + v * 128 + lane * 4);
+          const float4 u4 = *reinterpret_cast<const float4*>(su + v * 128 + lane * 4);
+          const float gk[4] = {g4.x, g4.y, g4.z, g4.w};
+          const float uk[4] = {u4.x, u4.y, u4.z, u4.w};
+#pragma unroll
+          for (int w = 0; w < 4; ++w) {
+            rp = fmaf(gk[w] * ga[w], ga[w], rp);
+            xp = fmaf(ga[w], uk[w], xp);
+            ga[w] = fmaf(ga[w], gk[w], qa[w]);
+          }
+          *reinterpret_cast<float4*>(G + row * ld + v * 128 + lane * 4) = gv[r][v];
+        }
+      }
+      rdv[r] = (double)rp;
+      xiv[r] = (double)xp;
+    }
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+      for (int o = 16; o > 0; o >>= 1) {
+        rdv[r] += __shfl_xor_sync(0xffffffffu, rdv[r], o);
+        xiv[r] += __shfl_xor_sync(0xffffffffu, xiv[r], o);
+      }
+    }
+    if (lane < kRows && myrow < m) {
+      double rd_mine = rdv[0], xi_mine = xiv[0];
+#pragma unroll
+      for (int r = 1; r < kRows; ++r)
+        if (lane == r) {
+          rd_mine = rdv[r];
+          xi_mine = xiv[r];
+        }
+      var[myrow] = vr + theta - rd_mine;
+      x[myrow] = xr + xi_mine;
+    }
+  }
+}
+
+// FP64 (oracle-grade mode): one warp per row
+__global__ void eigen_sweep_f64_kernel(int64_t m, int ld, int n, double* __restrict__ G,
+                                       const double* __restrict__ Gq, const double* __restrict__ s,
+                                       const double* __restrict__ u, double theta, double* __restrict__ x,
+                                       double* __restrict__ var, const int* __restrict__ flag) {
+  if (*flag) return;
+  __shared__ double sg[kMaxN], su[kMaxN];
+  for (int k = threadIdx.x; k < ld; k += blockDim.x) {
+    sg[k] = k < n ? 1.0 / s[k] : 0.0;
+    su[k] = k < n ? u[k] : 0.0;
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < m; row += warps) {
-    T* gr = G + row * ld;
-    const T* qr = Gq + row * ld;
-    float rs = 0.f, rc = 0.f, xs = 0.f, xc = 0.f;
+    double* gr = G + row * ld;
+    const double* qr = Gq + row * ld;
     double rd64 = 0.0, xd64 = 0.0;
-    if (sizeof(T) == 4) {
-      for (int k0 = lane * 4; k0 < ld; k0 += 128) {
-        float4 gv = *reinterpret_cast<const float4*>(gr + k0);
-        const float4 qv = *reinterpret_cast<const float4*>(qr + k0);
-        float* ga = reinterpret_cast<float*>(&gv);
-        const float* qa = reinterpret_cast<const float*>(&qv);
-#pragma unroll
-        for (int w = 0; w < 4; ++w) {
-          const float gk = (float)sg[k0 + w];
-          kahan_add(gk * ga[w] * ga[w], rs, rc);
-          kahan_add(ga[w] * (float)su[k0 + w], xs, xc);
-          ga[w] = ga[w] * gk + qa[w];
-        }
-        *reinterpret_cast<float4*>(gr + k0) = gv;
-      }
-      rd64 = (double)rs - (double)rc;
-      xd64 = (double)xs - (double)xc;
-    } else {
-      for (int k = lane; k < ld; k += 32) {
-        const double gv = (double)gr[k], gk = (double)sg[k];
-        rd64 += gk * gv * gv;
-        xd64 += gv * (double)su[k];
-        gr[k] = (T)(gv * gk + (double)qr[k]);
-      }
+    for (int k = lane; k < ld; k += 32) {
+      const double gv = gr[k], gk = sg[k];
+      rd64 += gk * gv * gv;
+      xd64 += gv * su[k];
+      gr[k] = gv * gk + qr[k];
     }
     for (int o = 16; o > 0; o >>= 1) {
       rd64 += __shfl_xor_sync(0xffffffffu, rd64, o);
@@ -560,8 +627,20 @@ template Status eigen_setup<double>(const SpectralState&, const double*, int64_t
 template <typename T>
 Status eigen_step(const SpectralState& sp, int64_t m, int ld, int n, T* G, const T* Gq, double theta, double* x,
                   double* var, const int* flag, int sms, cudaStream_t s) {
-  const int64_t blocks = std::min<int64_t>((m + 7) / 8, (int64_t)sms * 8);
-  eigen_sweep_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(m, ld, n, G, Gq, sp.s, sp.u, theta, x, var, flag);
+  if (sizeof(T) == 4) {
+    auto launch = [&](auto kern, int rows) {
+      const int64_t groups = (m + rows - 1) / rows;
+      const int64_t blocks = std::min<int64_t>((groups + 7) / 8, (int64_t)sms * 8);
+      kern<<<(unsigned)blocks, 256, 0, s>>>(m, ld, n, (float*)G, (const float*)Gq, sp.s, sp.u, theta, x, var, flag);
+    };
+    if (ld <= 128) launch(eigen_sweep_f32_kernel<1, 4>, 4);
+    else if (ld <= 256) launch(eigen_sweep_f32_kernel<2, 4>, 4);
+    else launch(eigen_sweep_f32_kernel<4, 2>, 2);
+  } else {
+    const int64_t blocks = std::min<int64_t>((m + 7) / 8, (int64_t)sms * 8);
+    eigen_sweep_f64_kernel<<<(unsigned)blocks, 256, 0, s>>>(m, ld, n, (double*)G, (const double*)Gq, sp.s, sp.u,
+                                                            theta, x, var, flag);
+  }
   HIKF_LAUNCH_CHECK("eigen_sweep");
   return Status::Ok();
 }

@@ -37,9 +37,11 @@ namespace {
 
 constexpr int kBM = 128;                 // rows per tile (MMA M)
 constexpr int kKC = 32;                  // K per stage
-constexpr int kRawStages = 3;
-constexpr int kAStages = 2;
+constexpr int kGroups = 2;               // converter/epilogue warp groups (4 warps each, one per TMEM lane quarter)
+constexpr int kRawStages = 3;            // chunk j -> raw stage j % 3, consumed by group j % 2
+constexpr int kAStages = 2;              // chunk j -> A stage j % 2 (= its group)
 constexpr int kBStages = 2;
+constexpr int kThreadsTc = 128 + 128 * kGroups;
 constexpr int kRawBytes = kBM * kKC * 4;          // one FP32 raw tile (C or C_Q): 16 KB
 constexpr int kAPieceBytes = kBM * kKC * 2;       // one FP16 A piece: 8 KB
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
@@ -51,8 +53,9 @@ struct TcLayout {
   static constexpr int AOff = RawOff + kRawStages * 2 * kRawBytes;
   static constexpr int BOff = AOff + kAStages * 2 * kAPieceBytes;
   static constexpr int VecOff = BOff + kBStages * 2 * BPiece;      // a (NT floats), r (NT floats)
-  static constexpr int BarOff = VecOff + 2 * NT * 4;
-  static constexpr int NumBars = 2 * kRawStages + 2 * kAStages + 2 * kBStages + 3;
+  static constexpr int RedOff = VecOff + 2 * NT * 4;                 // group-1 partials: 128 x {rd hi, rd lo, x hi, x lo, max}
+  static constexpr int BarOff = RedOff + 128 * 5 * 4;
+  static constexpr int NumBars = 2 * kRawStages + 2 * kAStages + 2 * kBStages + 5;
   static constexpr int Total = BarOff + NumBars * 8 + 16;
   static constexpr int Smem = Total + 1024;                          // slack for 1024-B alignment
 };
@@ -186,7 +189,7 @@ __device__ __forceinline__ int pow2_exp(float bound) {
 }
 
 template <int NT>
-__global__ void __launch_bounds__(256, 1) sweep_tc_kernel(const __grid_constant__ CUtensorMap tmC,
+__global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_constant__ CUtensorMap tmC,
                                                           const __grid_constant__ CUtensorMap tmCQ, TcArgs args) {
   using Lay = TcLayout<NT>;
   constexpr int NK = NT / kKC;
@@ -210,6 +213,8 @@ __global__ void __launch_bounds__(256, 1) sweep_tc_kernel(const __grid_constant_
   const uint32_t acc_full = bar0 + 8u * (2 * kRawStages + 2 * kAStages + 2 * kBStages);
   const uint32_t acc_empty = acc_full + 8u;
   const uint32_t drain = acc_full + 16u;
+  const uint32_t red_full = acc_full + 24u;   // group 1's row partials written (4 warp arrivals)
+  const uint32_t red_empty = acc_full + 32u;  // group 0 has read them (4 warp arrivals)
 
   for (int j = threadIdx.x; j < NT; j += blockDim.x) {
     s_a[j] = j < args.n ? (float)args.a[j] : 0.f;
@@ -218,7 +223,7 @@ __global__ void __launch_bounds__(256, 1) sweep_tc_kernel(const __grid_constant_
   if (threadIdx.x == 0) {
     for (int s = 0; s < kRawStages; ++s) {
       mbar_init(raw_full(s), 1);
-      mbar_init(raw_empty(s), 4);
+      mbar_init(raw_empty(s), 4);  // the 4 warps of the consuming group
     }
     for (int s = 0; s < kAStages; ++s) {
       mbar_init(a_full(s), 4);
@@ -229,8 +234,10 @@ __global__ void __launch_bounds__(256, 1) sweep_tc_kernel(const __grid_constant_
       mbar_init(b_empty(s), 1);
     }
     mbar_init(acc_full, 1);
-    mbar_init(acc_empty, 4);
+    mbar_init(acc_empty, 4 * kGroups);
     mbar_init(drain, 1);
+    mbar_init(red_full, 4);
+    mbar_init(red_empty, 4);
     *s_abort = 0;
     fence_barrier_init();
   }
@@ -245,21 +252,20 @@ __global__ void __launch_bounds__(256, 1) sweep_tc_kernel(const __grid_constant_
   if (warp == 0) {
     // ---------------- producer ----------------
     if (lane == 0) {
-      int rs = 0, bs = 0;
-      uint32_t rph = 0, bph = 0;
+      int bs = 0;
+      uint32_t bph = 0;
+      int64_t j = 0;
       bool ok = true;
       for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        for (int kc = 0; kc < NK && ok; ++kc) {
+        for (int kc = 0; kc < NK && ok; ++kc, ++j) {
+          const int rs = (int)(j % kRawStages);
+          const uint32_t rph = (uint32_t)((j / kRawStages) & 1);
           ok = mbar_wait(raw_empty(rs), rph ^ 1u, args.err, s_abort);
           if (!ok) break;
           const uint32_t rbase = smem_u32(smem + Lay::RawOff + rs * 2 * kRawBytes);
           mbar_expect_tx(raw_full(rs), 2 * kRawBytes);
           tma_load_2d(rbase, &tmC, kc * kKC, (int)(tile * kBM), raw_full(rs));
           tma_load_2d(rbase + kRawBytes, &tmCQ, kc * kKC, (int)(tile * kBM), raw_full(rs));
-          if (++rs == kRawStages) {
-            rs = 0;
-            rph ^= 1u;
-          }
           ok = mbar_wait(b_empty(bs), bph ^ 1u, args.err, s_abort);
           if (!ok) break;
           const uint32_t bbase = smem_u32(smem + Lay::BOff + bs * 2 * Lay::BPiece);
@@ -328,20 +334,26 @@ __global__ void __launch_bounds__(256, 1) sweep_tc_kernel(const __grid_constant_
     }
   } else if (warp >= 4) {
     // ---------------- converter + epilogue (thread = row) ----------------
-    const int q = warp - 4;  // TMEM lane quarter
+    // group g converts the K-chunks kc with kc % 2 == g and writes the output column
+    // chunks [g NK/2, (g+1) NK/2); the two groups' row partials meet in shared memory.
+    const int g = (warp - 4) / 4;
+    const int q = warp & 3;  // TMEM lane quarter of this warp
     const int r = q * 32 + lane;
     const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16);
-    int rs = 0, as = 0;
-    uint32_t rph = 0, aph = 0, fph = 0;
+    float* red = reinterpret_cast<float*>(smem + Lay::RedOff);
+    uint32_t fph = 0, redph = 0;
+    int64_t j = g;  // global chunk counter of this group (stride kGroups)
     bool ok = true;
     for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
       const int64_t row = tile * kBM + r;
       const bool valid = row < args.m;
-      float bound = valid ? args.cmax[row] + args.cqmax[row] : 0.f;
+      const float bound = valid ? args.cmax[row] + args.cqmax[row] : 0.f;
       const int ea = bound > 0.f ? max(-100, min(100, pow2_exp(bound))) : 0;
       const float alpha = ldexpf(1.f, 14 - ea);
       float xs = 0.f, xc = 0.f;
-      for (int kc = 0; kc < NK; ++kc) {
+      for (int kc = g; kc < NK; kc += kGroups, j += kGroups) {
+        const int rs = (int)(j % kRawStages);
+        const uint32_t rph = (uint32_t)((j / kRawStages) & 1);
         ok = __all_sync(0xffffffffu, mbar_wait(raw_full(rs), rph, args.err, s_abort));
         if (!ok) break;
         const unsigned char* rc = smem + Lay::RawOff + rs * 2 * kRawBytes;
@@ -358,70 +370,82 @@ __global__ void __launch_bounds__(256, 1) sweep_tc_kernel(const __grid_constant_
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(raw_empty(rs));
-        if (++rs == kRawStages) {
-          rs = 0;
-          rph ^= 1u;
-        }
+        // x increment: chunk partial by FMA, chunks combined with compensation
+        {
+          const float4* a4 = reinterpret_cast<const float4*>(s_a + kc * kKC);
+          float part = 0.f;
 #pragma unroll
-        for (int k = 0; k < kKC; ++k) {
-          const float y = cp[k] * s_a[kc * kKC + k] - xc;
+          for (int c = 0; c < 8; ++c) {
+            const float4 av = a4[c];
+            part = fmaf(cp[4 * c + 0], av.x, part);
+            part = fmaf(cp[4 * c + 1], av.y, part);
+            part = fmaf(cp[4 * c + 2], av.z, part);
+            part = fmaf(cp[4 * c + 3], av.w, part);
+          }
+          const float y = part - xc;
           const float t = xs + y;
           xc = (t - xs) - y;
           xs = t;
         }
-        // C_p chunk into TMEM columns 256 + 32 kc
         tmem_st32(tq + 256 + kc * kKC, reinterpret_cast<const uint32_t*>(cp));
+        const int as = (int)(j % kAStages);
+        const uint32_t aph = (uint32_t)((j / kAStages) & 1);
         ok = __all_sync(0xffffffffu, mbar_wait(a_empty(as), aph ^ 1u, args.err, s_abort));
         if (!ok) break;
         unsigned char* ab = smem + Lay::AOff + as * 2 * kAPieceBytes;
 #pragma unroll
-        for (int g = 0; g < kKC / 8; ++g) {
-          __align__(16) __half hi[8], lo[8];
+        for (int gg = 0; gg < kKC / 8; ++gg) {
+          __align__(16) __half2 hi[4], lo[4];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const float sv = cp[8 * g + u] * alpha;
-            const __half h = __float2half_rn(sv);
+          for (int u = 0; u < 4; ++u) {
+            const float2 sv = make_float2(cp[8 * gg + 2 * u] * alpha, cp[8 * gg + 2 * u + 1] * alpha);
+            const __half2 h = __float22half2_rn(sv);
+            const float2 hf = __half22float2(h);
             hi[u] = h;
-            lo[u] = __float2half_rn(sv - __half2float(h));
+            lo[u] = __float22half2_rn(make_float2(sv.x - hf.x, sv.y - hf.y));
           }
-          *reinterpret_cast<uint4*>(ab + core_off(r, 8 * g)) = *reinterpret_cast<const uint4*>(hi);
-          *reinterpret_cast<uint4*>(ab + kAPieceBytes + core_off(r, 8 * g)) = *reinterpret_cast<const uint4*>(lo);
+          *reinterpret_cast<uint4*>(ab + core_off(r, 8 * gg)) = *reinterpret_cast<const uint4*>(hi);
+          *reinterpret_cast<uint4*>(ab + kAPieceBytes + core_off(r, 8 * gg)) = *reinterpret_cast<const uint4*>(lo);
         }
         fence_proxy_async();
         __syncwarp();
         if (lane == 0) mbar_arrive(a_full(as));
-        if (++as == kAStages) {
-          as = 0;
-          aph ^= 1u;
-        }
       }
       if (!ok) break;
       tmem_wait_st();
-      // ---- epilogue ----
+      // ---- epilogue: output column chunks [g NK/2, (g+1) NK/2) ----
       ok = __all_sync(0xffffffffu, mbar_wait(acc_full, fph, args.err, s_abort));
       fph ^= 1u;
       if (!ok) break;
       tc_fence_after();
       const float inv = ldexpf(1.f, ea - 14 - beta_exp);  // 1 / (alpha beta)
       float rs_ = 0.f, rc_ = 0.f, rmax = 0.f;
-      for (int j = 0; j < NK; ++j) {
+      for (int jc = g * (NK / kGroups); jc < (g + 1) * (NK / kGroups); ++jc) {
         uint32_t kv[32], cv[32];
-        tmem_ld32(tq + j * kKC, kv);
-        tmem_ld32(tq + 256 + j * kKC, cv);
+        tmem_ld32(tq + jc * kKC, kv);
+        tmem_ld32(tq + 256 + jc * kKC, cv);
         tmem_wait_ld();
         float out[32];
+        float part = 0.f;
+        const float4* r4 = reinterpret_cast<const float4*>(s_r + jc * kKC);
 #pragma unroll
-        for (int u = 0; u < 32; ++u) {
-          const float k = __uint_as_float(kv[u]) * inv;
-          const float c = __uint_as_float(cv[u]);
-          const float y = k * c - rc_;
-          const float t = rs_ + y;
-          rc_ = (t - rs_) - y;
-          rs_ = t;
-          out[u] = k * s_r[j * kKC + u];
-          rmax = fmaxf(rmax, fabsf(out[u]));
+        for (int c = 0; c < 8; ++c) {
+          const float4 rv = r4[c];
+          const float rr[4] = {rv.x, rv.y, rv.z, rv.w};
+#pragma unroll
+          for (int w = 0; w < 4; ++w) {
+            const int u = 4 * c + w;
+            const float k = __uint_as_float(kv[u]) * inv;
+            part = fmaf(k, __uint_as_float(cv[u]), part);
+            out[u] = k * rr[w];
+            rmax = fmaxf(rmax, fabsf(out[u]));
+          }
         }
-        const int col0 = j * kKC;
+        const float y = part - rc_;
+        const float t = rs_ + y;
+        rc_ = (t - rs_) - y;
+        rs_ = t;
+        const int col0 = jc * kKC;
         if (valid && col0 < args.ld) {
           float4* dst = reinterpret_cast<float4*>(args.C + row * args.ld + col0);
 #pragma unroll
@@ -431,11 +455,31 @@ __global__ void __launch_bounds__(256, 1) sweep_tc_kernel(const __grid_constant_
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(acc_empty);
-      if (valid) {
-        args.var[row] += args.theta - ((double)rs_ - (double)rc_);
-        args.x[row] += (double)xs - (double)xc;
-        args.cmax[row] = rmax;
+      // combine the two groups' row partials through shared memory (bounded mbarrier handoff)
+      if (g == 1) {
+        ok = __all_sync(0xffffffffu, mbar_wait(red_empty, redph ^ 1u, args.err, s_abort));
+        if (!ok) break;
+        red[r * 5 + 0] = rs_;
+        red[r * 5 + 1] = rc_;
+        red[r * 5 + 2] = xs;
+        red[r * 5 + 3] = xc;
+        red[r * 5 + 4] = rmax;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(red_full);
+      } else {
+        ok = __all_sync(0xffffffffu, mbar_wait(red_full, redph, args.err, s_abort));
+        if (!ok) break;
+        if (valid) {
+          const double rd = ((double)rs_ - (double)rc_) + ((double)red[r * 5 + 0] - (double)red[r * 5 + 1]);
+          const double xi = ((double)xs - (double)xc) + ((double)red[r * 5 + 2] - (double)red[r * 5 + 3]);
+          args.var[row] += args.theta - rd;
+          args.x[row] += xi;
+          args.cmax[row] = fmaxf(rmax, red[r * 5 + 4]);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(red_empty);
       }
+      redph ^= 1u;
     }
     if (!ok) *s_abort = 1;
   }
@@ -569,9 +613,9 @@ Status tc_sweep(const TcState& tc, TcArgs args, int sms, cudaStream_t s) {
   args.cmax = tc.cmax;
   args.cqmax = tc.cqmax;
   if (tc.nt == 128)
-    sweep_tc_kernel<128><<<grid, 256, tc.smem, s>>>(tc.mapC, tc.mapCQ, args);
+    sweep_tc_kernel<128><<<grid, kThreadsTc, tc.smem, s>>>(tc.mapC, tc.mapCQ, args);
   else
-    sweep_tc_kernel<256><<<grid, 256, tc.smem, s>>>(tc.mapC, tc.mapCQ, args);
+    sweep_tc_kernel<256><<<grid, kThreadsTc, tc.smem, s>>>(tc.mapC, tc.mapCQ, args);
   HIKF_LAUNCH_CHECK("sweep_tc");
   return Status::Ok();
 }
