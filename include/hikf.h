@@ -84,10 +84,11 @@ typedef struct {
   int form;          /* the state the update sweeps over each step:
                         HIKF_FORM_CROSS (default): the cross-covariance C = P H^T of
                         Alg. 2, one (m x n)(n x n) contraction per step, O(n^2 m);
-                        HIKF_FORM_EIGEN: the same filter carried as G = C R^{-1/2} V
+                        HIKF_FORM_EIGEN: the same filter carried as G = C_{t|t} R^{-1/2} V
                         (V: eigenvectors of R^{-1/2} H C_Q R^{-1/2}); the update is
-                        then diagonal, O(n m) per step, and the variance a sum of
-                        squares. Needs the spectral chain (P_0 = c Q) and FP32/FP64. */
+                        then diagonal, O(n m) per step, and the variance reduction a
+                        sum of squares. Needs the spectral chain (P_0 = c Q) and
+                        FP32/FP64. hikf_get_cross forms C_{t|t} = G V^T R^{1/2} on request. */
 } hikf_options;
 
 enum { HIKF_CHAIN_AUTO = 0, HIKF_CHAIN_FACTOR = 1, HIKF_CHAIN_SPECTRAL = 2 };
@@ -220,6 +221,21 @@ void hikf_destroy(hikf_t* h);
 hikf_status hikf_h2_qht(int dim, int64_t m, const double* points, hikf_kernel k, int n,
                         const int64_t* h_rowptr, const int64_t* h_col, const double* h_val,
                         const hikf_options* opt, double* out);
+
+/*
+ * hikf_spd_inverse — M = S^{-1} for a symmetric positive-definite n x n matrix
+ * by an FP64 Cholesky factorisation S = L L^T and the inverse of L: the
+ * (H C_{t+1|t} + R)^{-1} of the gain (Eq. kalmangin_new), the factor path of
+ * the update used when P_0 is not a multiple of Q.
+ *   d_S     device, n x n FP64 row-major (only the lower triangle is read).
+ *   n       1 <= n <= 512.
+ *   d_M     device, n x n FP64 row-major output (full symmetric matrix).
+ *   stream  cudaStream_t, NULL = the default stream.
+ * Allocates n x n FP64 of device scratch for the call (stream-ordered) and
+ * frees it before returning. Synchronous. HIKF_ENOTPD when a pivot is not
+ * positive (d_M is then unspecified), HIKF_EINVAL for bad sizes or pointers.
+ */
+hikf_status hikf_spd_inverse(const double* d_S, int n, double* d_M, void* stream);
 
 #ifdef __cplusplus
 }

@@ -357,8 +357,7 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
   if (h->mixed()) {
     hikf::TcState& tc = h->tc;
     HIKF_TRY(hikf::tc_setup(tc, (const float*)C, (const float*)CQ, m, ld, n));
-    HIKF_TRY(hikf::arena_alloc(h->arena, &tc.bhi, (size_t)tc.nt * tc.nt));
-    HIKF_TRY(hikf::arena_alloc(h->arena, &tc.blo, (size_t)tc.nt * tc.nt));
+    HIKF_TRY(hikf::arena_alloc(h->arena, &tc.bimg, (size_t)3 * tc.nt * tc.nt));
     HIKF_TRY(hikf::arena_alloc(h->arena, &tc.cmax, m));
     HIKF_TRY(hikf::arena_alloc(h->arena, &tc.cqmax, m));
     HIKF_TRY(hikf::arena_alloc(h->arena, &tc.mmax, 1));
@@ -734,6 +733,29 @@ void hikf_destroy(hikf_t* h) {
   for (auto& e : h->ev) cudaEventDestroy(e);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
+}
+
+hikf_status hikf_spd_inverse(const double* d_S, int n, double* d_M, void* stream) {
+  if (!d_S || !d_M) return fail(nullptr, hikf::make_status(HIKF_EINVAL, "null matrix pointer"));
+  if (n < 1 || n > hikf::kMaxN) return fail(nullptr, hikf::make_status(HIKF_EINVAL, "n out of range [1, 512]"));
+  cudaStream_t s = (cudaStream_t)stream;
+  double* scratch = nullptr;
+  int* flag = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&scratch, sizeof(double) * (size_t)n * n, s);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&flag, sizeof(int) * 2, s);
+  if (e != cudaSuccess) return fail(nullptr, hikf::cuda_status(e, "cudaMallocAsync", __FILE__, __LINE__));
+  Status st = hikf::spd_inverse_f64(d_S, n, d_M, scratch, flag, s);
+  int f[2] = {0, 0};
+  if (st.ok()) {
+    e = cudaMemcpyAsync(f, flag, sizeof(int) * 2, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = hikf::cuda_status(e, "spd_inverse", __FILE__, __LINE__);
+  }
+  cudaFreeAsync(scratch, s);
+  cudaFreeAsync(flag, s);
+  if (!st.ok()) return fail(nullptr, st);
+  if (f[0] & 2) return fail(nullptr, hikf::make_status(HIKF_ENOTPD, "matrix is not positive definite"));
+  return HIKF_OK;
 }
 
 hikf_status hikf_h2_qht(int dim, int64_t m, const double* points, hikf_kernel k, int n, const int64_t* h_rowptr,

@@ -403,11 +403,12 @@ Status spectral_next(const SpectralState& sp, int n, int* flag, cudaStream_t s) 
 }  // namespace hikf
 
 // ---------------------------------------------------------------------------
-// Eigenbasis form of the state (rotated cross-covariance G = C_{t|t-1} W).
-// Because W^T R W = V^T V = I, the update C_{t|t} = C_{t|t-1} W diag(g) W^T R
-// becomes G_{t+1|t} = G_{t|t-1} diag(g) + C_Q W in the rotated basis, and
-//   sum_j K_ij (C_p)_ij = sum_k g_k G_ik^2,   (C_p a)_i = sum_k G_ik u_k,
-// with g = 1/s_t and u = g o (W^T e). One pass over G per step, O(m n).
+// Eigenbasis form of the state (rotated cross-covariance G = C_{t|t} W, W = D V).
+// Because W^T R W = V^T V = I, the update C_{t|t} = C_p W diag(g) W^T R becomes, with
+// G_p = G + C_Q W the rotated prior,  G <- G_p diag(g), and
+//   sum_j K_ij (C_p)_ij = sum_k g_k G_p,ik^2,   (C_p a)_i = sum_k G_p,ik u_k,
+// with g = 1/s_t and u = g o (W^T e). One pass over G per step, O(m n);
+// C_{t|t} = G W^T R is formed only on request.
 // ---------------------------------------------------------------------------
 namespace hikf {
 namespace {
@@ -475,9 +476,10 @@ __global__ void __launch_bounds__(256) eigen_sweep_f32_kernel(int64_t m, int ld,
           const float uk[4] = {u4.x, u4.y, u4.z, u4.w};
 #pragma unroll
           for (int w = 0; w < 4; ++w) {
-            rp = fmaf(gk[w] * ga[w], ga[w], rp);
-            xp = fmaf(ga[w], uk[w], xp);
-            ga[w] = fmaf(ga[w], gk[w], qa[w]);
+            const float gp = ga[w] + qa[w];  // rotated prior
+            rp = fmaf(gk[w] * gp, gp, rp);
+            xp = fmaf(gp, uk[w], xp);
+            ga[w] = gp * gk[w];
           }
           *reinterpret_cast<float4*>(G + row * ld + v * 128 + lane * 4) = gv[r][v];
         }
@@ -525,10 +527,10 @@ __global__ void eigen_sweep_f64_kernel(int64_t m, int ld, int n, double* __restr
     const double* qr = Gq + row * ld;
     double rd64 = 0.0, xd64 = 0.0;
     for (int k = lane; k < ld; k += 32) {
-      const double gv = gr[k], gk = sg[k];
-      rd64 += gk * gv * gv;
-      xd64 += gv * su[k];
-      gr[k] = gv * gk + qr[k];
+      const double gp = gr[k] + qr[k], gk = sg[k];
+      rd64 += gk * gp * gp;
+      xd64 += gp * su[k];
+      gr[k] = gp * gk;
     }
     for (int o = 16; o > 0; o >>= 1) {
       rd64 += __shfl_xor_sync(0xffffffffu, rd64, o);
@@ -615,7 +617,7 @@ Status eigen_setup(const SpectralState& sp, const T* CQ, int64_t m, int ld, int 
   dim3 grid((unsigned)((m + 63) / 64), (unsigned)((ld + 63) / 64));
   gemm_tn_kernel<T, double><<<grid, 256, 0, s>>>(m, n, n, CQ, ld, sp.W64, n, Gq, ld, 0, nullptr);
   HIKF_LAUNCH_CHECK("gemm Gq");
-  scale_copy_kernel<T><<<nb(m * ld, 256), 256, 0, s>>>(Gq, G, m * ld, 1.0 + c);
+  scale_copy_kernel<T><<<nb(m * ld, 256), 256, 0, s>>>(Gq, G, m * ld, c);  // C_0 W = c C_Q W
   HIKF_LAUNCH_CHECK("scale G");
   return Status::Ok();
 }
@@ -655,7 +657,7 @@ Status eigen_u(const SpectralState& sp, int n, const double* e, const int* flag,
   return Status::Ok();
 }
 
-// C_{t|t} = (G - Gq) W^T R  (output in the caller's T, m x ld)
+// C_{t|t} = G W^T R  (output in the caller's T, m x ld)
 template <typename T>
 Status eigen_cross(const SpectralState& sp, const double* rd, int64_t m, int ld, int n, const T* G, const T* Gq,
                    T* out, cudaStream_t s) {
@@ -664,7 +666,7 @@ Status eigen_cross(const SpectralState& sp, const double* rd, int64_t m, int ld,
   wtr_kernel<<<nb((int64_t)n * n, 256), 256, 0, s>>>(sp.W64, rd, n, B);
   HIKF_LAUNCH_CHECK("wtr");
   dim3 grid((unsigned)((m + 63) / 64), (unsigned)((ld + 63) / 64));
-  gemm_tn_kernel<T, double><<<grid, 256, 0, s>>>(m, n, n, G, ld, B, n, out, ld, 1, Gq);
+  gemm_tn_kernel<T, double><<<grid, 256, 0, s>>>(m, n, n, G, ld, B, n, out, ld, 0, nullptr);
   HIKF_LAUNCH_CHECK("gemm cross");
   HIKF_CUDA(cudaFreeAsync(B, s));
   return Status::Ok();

@@ -25,8 +25,8 @@ Status spectral_gain(const SpectralState& sp, int n, const double* e, double* a,
 // s_{t+1} = lambda + 2 - 1/s_t (skipped when the step failed).
 Status spectral_next(const SpectralState& sp, int n, int* flag, cudaStream_t s);
 
-// Eigenbasis form of the state: Gq = C_Q W, G = (1 + c) Gq at create; per step
-// u = (W^T e) / s, then one pass G <- G diag(1/s) + Gq with the variance and mean updates.
+// Eigenbasis form of the state: Gq = C_Q W, G = C_0 W = c Gq at create; per step
+// u = (W^T e) / s, then one pass G <- (G + Gq) diag(1/s) with the variance and mean updates.
 template <typename T>
 Status eigen_setup(const SpectralState& sp, const T* CQ, int64_t m, int ld, int n, double c, T* Gq, T* G,
                    cudaStream_t s);
@@ -34,7 +34,7 @@ Status eigen_u(const SpectralState& sp, int n, const double* e, const int* flag,
 template <typename T>
 Status eigen_step(const SpectralState& sp, int64_t m, int ld, int n, T* G, const T* Gq, double theta, double* x,
                   double* var, const int* flag, int sms, cudaStream_t s);
-// the current C_{t|t} = (G - Gq) W^T R
+// the current C_{t|t} = G W^T R
 template <typename T>
 Status eigen_cross(const SpectralState& sp, const double* rd, int64_t m, int ld, int n, const T* G, const T* Gq,
                    T* out, cudaStream_t s);

@@ -652,3 +652,15 @@ Status launch_recur(const double* hcq_sym, const double* rd, const float* Mh, co
 }
 
 }  // namespace hikf
+
+namespace hikf {
+
+Status spd_inverse_f64(const double* S, int n, double* M, double* scratch, int* flag, cudaStream_t s) {
+  HIKF_CUDA(cudaMemsetAsync(flag, 0, sizeof(int) * 2, s));
+  // force = 1: factor S itself; the inverse goes to M (ldm = n)
+  chol64_kernel<<<1, 1024, 0, s>>>(S, n, scratch, nullptr, M, n, nullptr, nullptr, flag, 1);
+  HIKF_LAUNCH_CHECK("chol64");
+  return Status::Ok();
+}
+
+}  // namespace hikf

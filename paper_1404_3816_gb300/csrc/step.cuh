@@ -62,4 +62,7 @@ Status launch_gemv(const float* Mh, const float* Ml, const double* M64, int n, i
 Status launch_recur(const double* hcq_sym, const double* rd, const float* Mh, const float* Ml, const double* M64,
                     int n, int ldm, const int* flag, double* S, cudaStream_t s);
 
+// Standalone S^{-1} (FP64 Cholesky on one CTA): scratch n x n FP64, flag 2 ints (flag[0] & 2: not PD).
+Status spd_inverse_f64(const double* S, int n, double* M, double* scratch, int* flag, cudaStream_t s);
+
 }  // namespace hikf

@@ -5,10 +5,12 @@
 //   x += C_p a,  C <- K R  (= C_p - K H C_p, Eq. KF_pred_new, since H C_p = S - R).
 //
 // K = C_p M is a dense (m x n) x (n x n) contraction. To keep FP32-level accuracy
-// on FP16 tensor cores each operand is split into two FP16 pieces after a
+// on FP16 tensor cores each operand is split into three FP16 pieces after a
 // power-of-two scaling (row scale alpha_i for C_p, one scale beta for M):
-//   alpha C_p = A1 + A2,  beta M = B1 + B2,  K = (A1 B1 + A1 B2 + A2 B1) / (alpha beta),
-// 22 significant bits per operand; products are exact in the FP32 accumulator.
+//   alpha C_p = A1 + A2 + A3,  beta M = B1 + B2 + B3  (about 33 significant bits),
+//   K = (A1 B1 + A1 B2 + A2 B1 + A1 B3 + A2 B2 + A3 B1) / (alpha beta),
+// i.e. every product down to 2^-22 of the leading one; products are exact in the
+// FP32 accumulator. (Two pieces, 22 bits, lose ~3 bits against FP32 over long runs.)
 // The row scale comes from a bound carried from the previous step:
 // |C_p,ij| <= max_j |C_{t|t}| + max_j |C_Q|.
 //
@@ -38,7 +40,8 @@ namespace {
 constexpr int kBM = 128;                 // rows per tile (MMA M)
 constexpr int kKC = 32;                  // K per stage
 constexpr int kGroups = 2;               // converter/epilogue warp groups (4 warps each, one per TMEM lane quarter)
-constexpr int kRawStages = 3;            // chunk j -> raw stage j % 3, consumed by group j % 2
+constexpr int kRawStages = 2;            // chunk j -> raw stage j % 2 (= its group)
+constexpr int kPieces = 3;               // FP16 pieces per operand (3 x 11 bits)
 constexpr int kAStages = 2;              // chunk j -> A stage j % 2 (= its group)
 constexpr int kBStages = 2;
 constexpr int kThreadsTc = 128 + 128 * kGroups;
@@ -51,8 +54,8 @@ struct TcLayout {
   static constexpr int BPiece = NT * kKC * 2;                        // one FP16 B piece per stage
   static constexpr int RawOff = 0;
   static constexpr int AOff = RawOff + kRawStages * 2 * kRawBytes;
-  static constexpr int BOff = AOff + kAStages * 2 * kAPieceBytes;
-  static constexpr int VecOff = BOff + kBStages * 2 * BPiece;      // a (NT floats), r (NT floats)
+  static constexpr int BOff = AOff + kAStages * kPieces * kAPieceBytes;
+  static constexpr int VecOff = BOff + kBStages * kPieces * BPiece;  // a (NT floats), r (NT floats)
   static constexpr int RedOff = VecOff + 2 * NT * 4;                 // group-1 partials: 128 x {rd hi, rd lo, x hi, x lo, max}
   static constexpr int BarOff = RedOff + 128 * 5 * 4;
   static constexpr int NumBars = 2 * kRawStages + 2 * kAStages + 2 * kBStages + 5;
@@ -268,10 +271,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
           tma_load_2d(rbase + kRawBytes, &tmCQ, kc * kKC, (int)(tile * kBM), raw_full(rs));
           ok = mbar_wait(b_empty(bs), bph ^ 1u, args.err, s_abort);
           if (!ok) break;
-          const uint32_t bbase = smem_u32(smem + Lay::BOff + bs * 2 * Lay::BPiece);
-          mbar_expect_tx(b_full(bs), 2 * Lay::BPiece);
-          bulk_load(bbase, args.bimg_hi + (size_t)kc * Lay::BPiece / 2, Lay::BPiece, b_full(bs));
-          bulk_load(bbase + Lay::BPiece, args.bimg_lo + (size_t)kc * Lay::BPiece / 2, Lay::BPiece, b_full(bs));
+          const uint32_t bbase = smem_u32(smem + Lay::BOff + bs * kPieces * Lay::BPiece);
+          mbar_expect_tx(b_full(bs), kPieces * Lay::BPiece);
+          for (int pc = 0; pc < kPieces; ++pc)
+            bulk_load(bbase + pc * Lay::BPiece, args.bimg + ((size_t)pc * NK + kc) * (Lay::BPiece / 2), Lay::BPiece,
+                      b_full(bs));
           if (++bs == kBStages) {
             bs = 0;
             bph ^= 1u;
@@ -302,16 +306,22 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
           ok = mbar_wait(a_full(as), aph, args.err, s_abort) && mbar_wait(b_full(bs), bph, args.err, s_abort);
           if (!ok) break;
           tc_fence_after();
-          const uint32_t abase = smem_u32(smem + Lay::AOff + as * 2 * kAPieceBytes);
-          const uint32_t bbase = smem_u32(smem + Lay::BOff + bs * 2 * Lay::BPiece);
+          const uint32_t abase = smem_u32(smem + Lay::AOff + as * kPieces * kAPieceBytes);
+          const uint32_t bbase = smem_u32(smem + Lay::BOff + bs * kPieces * Lay::BPiece);
           for (int ks = 0; ks < kKC / 16; ++ks) {
             const uint64_t a1 = smem_desc(abase + ks * 256, 128, 512);
             const uint64_t a2 = smem_desc(abase + kAPieceBytes + ks * 256, 128, 512);
+            const uint64_t a3 = smem_desc(abase + 2 * kAPieceBytes + ks * 256, 128, 512);
             const uint64_t b1 = smem_desc(bbase + ks * 256, 128, 512);
             const uint64_t b2 = smem_desc(bbase + Lay::BPiece + ks * 256, 128, 512);
-            tc_mma_f16(tmem, a1, b1, idesc, (kc > 0 || ks > 0) ? 1u : 0u);
-            tc_mma_f16(tmem, a1, b2, idesc, 1u);
+            const uint64_t b3 = smem_desc(bbase + 2 * Lay::BPiece + ks * 256, 128, 512);
+            // smallest terms first
+            tc_mma_f16(tmem, a3, b1, idesc, (kc > 0 || ks > 0) ? 1u : 0u);
+            tc_mma_f16(tmem, a2, b2, idesc, 1u);
+            tc_mma_f16(tmem, a1, b3, idesc, 1u);
             tc_mma_f16(tmem, a2, b1, idesc, 1u);
+            tc_mma_f16(tmem, a1, b2, idesc, 1u);
+            tc_mma_f16(tmem, a1, b1, idesc, 1u);
           }
           tc_commit(a_empty(as));
           tc_commit(b_empty(bs));
@@ -344,10 +354,36 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
     uint32_t fph = 0, redph = 0;
     int64_t j = g;  // global chunk counter of this group (stride kGroups)
     bool ok = true;
+    // row scalars of the next tile are loaded one tile ahead (hides their latency)
+    float nb_c = 0.f, nb_q = 0.f;
+    double nv = 0.0, nx = 0.0;
+    {
+      const int64_t row = (int64_t)blockIdx.x * kBM + r;
+      if (blockIdx.x < ntiles && row < args.m) {
+        nb_c = args.cmax[row];
+        nb_q = args.cqmax[row];
+        if (g == 0) {
+          nv = args.var[row];
+          nx = args.x[row];
+        }
+      }
+    }
     for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
       const int64_t row = tile * kBM + r;
       const bool valid = row < args.m;
-      const float bound = valid ? args.cmax[row] + args.cqmax[row] : 0.f;
+      const float bound = valid ? nb_c + nb_q : 0.f;
+      const double cur_v = nv, cur_x = nx;
+      {
+        const int64_t nrow = (tile + gridDim.x) * kBM + r;
+        if (tile + gridDim.x < ntiles && nrow < args.m) {
+          nb_c = args.cmax[nrow];
+          nb_q = args.cqmax[nrow];
+          if (g == 0) {
+            nv = args.var[nrow];
+            nx = args.x[nrow];
+          }
+        }
+      }
       const int ea = bound > 0.f ? max(-100, min(100, pow2_exp(bound))) : 0;
       const float alpha = ldexpf(1.f, 14 - ea);
       float xs = 0.f, xc = 0.f;
@@ -392,20 +428,26 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
         const uint32_t aph = (uint32_t)((j / kAStages) & 1);
         ok = __all_sync(0xffffffffu, mbar_wait(a_empty(as), aph ^ 1u, args.err, s_abort));
         if (!ok) break;
-        unsigned char* ab = smem + Lay::AOff + as * 2 * kAPieceBytes;
+        unsigned char* ab = smem + Lay::AOff + as * kPieces * kAPieceBytes;
 #pragma unroll
         for (int gg = 0; gg < kKC / 8; ++gg) {
-          __align__(16) __half2 hi[4], lo[4];
+          __align__(16) __half2 p1[4], p2[4], p3[4];
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const float2 sv = make_float2(cp[8 * gg + 2 * u] * alpha, cp[8 * gg + 2 * u + 1] * alpha);
-            const __half2 h = __float22half2_rn(sv);
-            const float2 hf = __half22float2(h);
-            hi[u] = h;
-            lo[u] = __float22half2_rn(make_float2(sv.x - hf.x, sv.y - hf.y));
+            const __half2 h1 = __float22half2_rn(sv);
+            const float2 f1 = __half22float2(h1);
+            const float2 r1 = make_float2(sv.x - f1.x, sv.y - f1.y);  // exact in FP32
+            const __half2 h2 = __float22half2_rn(r1);
+            const float2 f2 = __half22float2(h2);
+            p1[u] = h1;
+            p2[u] = h2;
+            p3[u] = __float22half2_rn(make_float2(r1.x - f2.x, r1.y - f2.y));
           }
-          *reinterpret_cast<uint4*>(ab + core_off(r, 8 * gg)) = *reinterpret_cast<const uint4*>(hi);
-          *reinterpret_cast<uint4*>(ab + kAPieceBytes + core_off(r, 8 * gg)) = *reinterpret_cast<const uint4*>(lo);
+          const uint32_t off = core_off(r, 8 * gg);
+          *reinterpret_cast<uint4*>(ab + off) = *reinterpret_cast<const uint4*>(p1);
+          *reinterpret_cast<uint4*>(ab + kAPieceBytes + off) = *reinterpret_cast<const uint4*>(p2);
+          *reinterpret_cast<uint4*>(ab + 2 * kAPieceBytes + off) = *reinterpret_cast<const uint4*>(p3);
         }
         fence_proxy_async();
         __syncwarp();
@@ -472,8 +514,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
         if (valid) {
           const double rd = ((double)rs_ - (double)rc_) + ((double)red[r * 5 + 0] - (double)red[r * 5 + 1]);
           const double xi = ((double)xs - (double)xc) + ((double)red[r * 5 + 2] - (double)red[r * 5 + 3]);
-          args.var[row] += args.theta - rd;
-          args.x[row] += xi;
+          args.var[row] = cur_v + args.theta - rd;
+          args.x[row] = cur_x + xi;
           args.cmax[row] = fmaxf(rmax, red[r * 5 + 4]);
         }
         __syncwarp();
@@ -519,18 +561,23 @@ __global__ void beta_kernel(const unsigned* __restrict__ mx, int* __restrict__ b
 
 template <int NT>
 __global__ void pack_b_dyn_kernel(const float* __restrict__ Msw, int nt_src, int n, const int* __restrict__ beta_exp,
-                                  __half* __restrict__ hi, __half* __restrict__ lo, const int* __restrict__ flag) {
+                                  __half* __restrict__ img, const int* __restrict__ flag) {
   if (*flag) return;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)NT * NT) return;
   const int nidx = (int)(t / NT), k = (int)(t % NT);
   const float v = (nidx < n && k < n) ? Msw[(int64_t)nidx * nt_src + k] * ldexpf(1.f, *beta_exp) : 0.f;
-  const __half h = __float2half_rn(v);
-  const __half l = __float2half_rn(v - __half2float(h));
+  const __half h1 = __float2half_rn(v);
+  const float r1 = v - __half2float(h1);
+  const __half h2 = __float2half_rn(r1);
+  const __half h3 = __float2half_rn(r1 - __half2float(h2));
   const int kc = k / kKC, kk = k % kKC;
-  const size_t off = (size_t)kc * (NT * kKC) + core_off(nidx, kk) / 2;
-  hi[off] = h;
-  lo[off] = l;
+  const size_t chunk = (size_t)NT * kKC;                   // halves per piece per chunk
+  const size_t off = (size_t)kc * chunk + core_off(nidx, kk) / 2;
+  const size_t piece = (size_t)(NT / kKC) * chunk;         // halves per piece (all chunks)
+  img[off] = h1;
+  img[piece + off] = h2;
+  img[2 * piece + off] = h3;
 }
 
 // per-row max |value| of an m x ld FP32 matrix (row scale bounds)
@@ -598,9 +645,9 @@ Status tc_pack(const TcState& tc, const float* Msw, int nt_src, int n, const int
   HIKF_LAUNCH_CHECK("beta");
   const int64_t cnt = (int64_t)tc.nt * tc.nt;
   if (tc.nt == 128)
-    pack_b_dyn_kernel<128><<<nblk(cnt, 256), 256, 0, s>>>(Msw, nt_src, n, tc.beta_exp, tc.bhi, tc.blo, flag);
+    pack_b_dyn_kernel<128><<<nblk(cnt, 256), 256, 0, s>>>(Msw, nt_src, n, tc.beta_exp, tc.bimg, flag);
   else
-    pack_b_dyn_kernel<256><<<nblk(cnt, 256), 256, 0, s>>>(Msw, nt_src, n, tc.beta_exp, tc.bhi, tc.blo, flag);
+    pack_b_dyn_kernel<256><<<nblk(cnt, 256), 256, 0, s>>>(Msw, nt_src, n, tc.beta_exp, tc.bimg, flag);
   HIKF_LAUNCH_CHECK("pack_b");
   return Status::Ok();
 }
@@ -608,8 +655,7 @@ Status tc_pack(const TcState& tc, const float* Msw, int nt_src, int n, const int
 Status tc_sweep(const TcState& tc, TcArgs args, int sms, cudaStream_t s) {
   const int64_t ntiles = (args.m + kBM - 1) / kBM;
   const int grid = (int)std::min<int64_t>(ntiles, sms);
-  args.bimg_hi = tc.bhi;
-  args.bimg_lo = tc.blo;
+  args.bimg = tc.bimg;
   args.cmax = tc.cmax;
   args.cqmax = tc.cqmax;
   if (tc.nt == 128)

@@ -21,8 +21,7 @@ struct TcArgs {
   const int* flag = nullptr;    // step error flag: nonzero -> no-op
   int* err = nullptr;           // set to 1 when a bounded wait times out
   const int* beta_exp = nullptr;  // scale exponent of M (device)
-  const __half* bimg_hi = nullptr;
-  const __half* bimg_lo = nullptr;
+  const __half* bimg = nullptr;   // 3 pieces x (n_t / 32) chunks of n_t x 32 FP16 images of beta M
   float* cmax = nullptr;        // m: max_j |C_ij| of the current C (row-scale bound)
   const float* cqmax = nullptr; // m: max_j |C_Q,ij|
 };
@@ -31,8 +30,7 @@ struct TcState {
   int nt = 256;                 // MMA N (128 or 256)
   int smem = 0;
   CUtensorMap mapC, mapCQ;
-  __half* bhi = nullptr;        // nt x nt images of beta M (FP16 hi / lo)
-  __half* blo = nullptr;
+  __half* bimg = nullptr;       // 3 x nt x nt FP16 images of beta M (three pieces)
   float* cmax = nullptr;
   float* cqmax = nullptr;
   unsigned* mmax = nullptr;

@@ -63,3 +63,16 @@ def test_invalid_arguments_are_rejected_before_any_device_work(lib):
         assert e.value.code == binding.HIKF_EINVAL
     with pytest.raises(binding.HikfError):
         binding.Filter(**good, cheb_order=40)
+
+
+def test_serving_schedule_and_footprint_without_gpu():
+    from paper_1404_3816_gb300 import serve
+    streams = serve.serving_streams(count=64)
+    sides = [w.grid[0] for w in streams]
+    assert min(sides) >= 64 and max(sides) <= 1024
+    assert {w.n for w in streams} <= {16, 32, 64, 128, 256}
+    sched = serve.poisson_schedule(streams, rate=500.0, seconds=2.0)
+    assert 800 < len(sched) < 1200                     # ~ rate x seconds
+    assert all(0 <= s < 64 for _, s in sched)
+    big = max(streams, key=lambda w: w.m)
+    assert serve.footprint_bytes(big) > 2 * big.m * 4 * ((big.n + 31) // 32 * 32)

@@ -257,3 +257,32 @@ def test_async_error_is_latched_then_cleared(B):
         f.sync()                       # cleared
         assert f.info()["step"] == 2
         assert np.array_equal(f.mean(), ref[0]) and np.array_equal(f.variance(), ref[1])
+
+
+@pytest.mark.parametrize("n", [1, 17, 100, 256, 512])
+def test_spd_inverse_entry_point(B, n):
+    """The factor path's S^{-1} (hikf_spd_inverse) on random SPD matrices with
+    a spread of eigenvalues like H C + R (cond ~ 1e6)."""
+    import torch
+    rng = np.random.default_rng(n)
+    Qm, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    ev = np.logspace(-3, 3, n)
+    S = (Qm * ev) @ Qm.T
+    S = 0.5 * (S + S.T)
+    dS = torch.tensor(S, device="cuda")
+    dM = torch.empty_like(dS)
+    B.spd_inverse(dS, dM)
+    M = dM.cpu().numpy()
+    ref = np.linalg.inv(S)
+    assert rel(M, ref) < 1e-9
+    assert np.allclose(M, M.T, rtol=0, atol=1e-12 * np.abs(M).max())
+
+
+def test_spd_inverse_rejects_indefinite(B):
+    import torch
+    S = np.diag([1.0, -2.0, 3.0])
+    dS = torch.tensor(S, device="cuda")
+    dM = torch.empty_like(dS)
+    with pytest.raises(B.HikfError) as e:
+        B.spd_inverse(dS, dM)
+    assert e.value.code == B.HIKF_ENOTPD
