@@ -237,6 +237,27 @@ hikf_status hikf_h2_qht(int dim, int64_t m, const double* points, hikf_kernel k,
  */
 hikf_status hikf_spd_inverse(const double* d_S, int n, double* d_M, void* stream);
 
+/*
+ * hikf_spd_inverse_noalloc — hikf_spd_inverse without any device allocation,
+ * for callers that must not call cudaMalloc/cudaFree (or an allocating library
+ * routine) on this path: processes that reserve all of their device memory up
+ * front and hand out fixed slices of it (a server dividing HBM among filter
+ * handles, for example), and latency-bound loops in which an allocation could
+ * synchronise the device or fail under fragmentation. It has no counterpart in
+ * the paper; it runs the same kernel as hikf_spd_inverse.
+ *   d_S, d_M, stream  as in hikf_spd_inverse (caller-owned device buffers).
+ *   n       1 <= n <= HIKF_NOALLOC_MAX_N; larger n returns HIKF_EINVAL.
+ * Scratch is a static device array of HIKF_NOALLOC_MAX_N^2 FP64 (512 KB) plus
+ * a status word, which every GPU that loads the library holds until the
+ * process exits. The first call on a device resolves the array's device
+ * address on that device (cudaGetSymbolAddress). All calls share the array and
+ * it keeps the last call's contents: calls whose work overlaps on the GPU (from
+ * several host threads or streams) race and must be serialised by the caller.
+ * Synchronous. HIKF_ENOTPD when a pivot is not positive (d_M unspecified).
+ */
+#define HIKF_NOALLOC_MAX_N 256
+hikf_status hikf_spd_inverse_noalloc(const double* d_S, int n, double* d_M, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

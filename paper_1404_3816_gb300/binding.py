@@ -32,7 +32,7 @@ EXPORTED = ["hikf_options_default", "hikf_create", "hikf_create_with_cq", "hikf_
             "hikf_assimilate_device", "hikf_sync", "hikf_get_mean", "hikf_get_variance",
             "hikf_get_mean_device", "hikf_get_variance_device", "hikf_get_cq", "hikf_get_cross",
             "hikf_get_perm", "hikf_info", "hikf_stream", "hikf_last_error", "hikf_destroy", "hikf_h2_qht",
-            "hikf_profile_enable", "hikf_profile_read", "hikf_spd_inverse"]
+            "hikf_profile_enable", "hikf_profile_read", "hikf_spd_inverse", "hikf_spd_inverse_noalloc"]
 
 
 class HikfError(RuntimeError):
@@ -94,6 +94,7 @@ def load(path: Optional[os.PathLike] = None) -> C.CDLL:
     lib.hikf_profile_enable.argtypes = [H, C.c_int]
     lib.hikf_profile_read.argtypes = [H, dp, ip]
     lib.hikf_spd_inverse.argtypes = [vp, C.c_int, vp, vp]
+    lib.hikf_spd_inverse_noalloc.argtypes = [vp, C.c_int, vp, vp]
     lib.hikf_h2_qht.argtypes = [C.c_int, C.c_int64, dp, Kernel, C.c_int, ip, ip, dp, C.POINTER(Options), dp]
     for nm in EXPORTED:
         fn = getattr(lib, nm)
@@ -304,3 +305,10 @@ def spd_inverse(d_S, d_M, stream=None):
     n = int(d_S.shape[0])
     st = None if stream is None else C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
     _check(load().hikf_spd_inverse(C.c_void_p(d_S.data_ptr()), n, C.c_void_p(d_M.data_ptr()), st), None)
+
+
+def spd_inverse_noalloc(d_S, d_M, stream=None):
+    """hikf_spd_inverse_noalloc: the same inverse with the library's static device scratch."""
+    n = int(d_S.shape[0])
+    st = None if stream is None else C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+    _check(load().hikf_spd_inverse_noalloc(C.c_void_p(d_S.data_ptr()), n, C.c_void_p(d_M.data_ptr()), st), None)

@@ -664,3 +664,62 @@ Status spd_inverse_f64(const double* S, int n, double* M, double* scratch, int* 
 }
 
 }  // namespace hikf
+
+// ---------------------------------------------------------------------------
+// S^{-1} without device allocation: the scratch of the FP64 factor is a static
+// device array (HIKF_NOALLOC_MAX_N^2 FP64) shared by all calls on a device.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace hikf {
+namespace {
+
+__device__ __align__(256) double g_noalloc_scratch[HIKF_NOALLOC_MAX_N * HIKF_NOALLOC_MAX_N];
+__device__ __align__(256) int g_noalloc_flag[4];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_scratch_ptr[kMaxDevices];
+int* g_noalloc_flag_ptr[kMaxDevices];
+
+// device addresses of the static scratch on the current device, resolved once per device
+Status noalloc_scratch(double** scratch, int** flag) {
+  int dev = 0;
+  HIKF_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return make_status(HIKF_EINVAL, "device ordinal out of range");
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_scratch_ptr[dev]) {
+    void* a = nullptr;
+    void* b = nullptr;
+    HIKF_CUDA(cudaGetSymbolAddress(&a, g_noalloc_scratch));
+    HIKF_CUDA(cudaGetSymbolAddress(&b, g_noalloc_flag));
+    g_noalloc_scratch_ptr[dev] = (double*)a;
+    g_noalloc_flag_ptr[dev] = (int*)b;
+  }
+  *scratch = g_noalloc_scratch_ptr[dev];
+  *flag = g_noalloc_flag_ptr[dev];
+  return Status::Ok();
+}
+
+}  // namespace
+}  // namespace hikf
+
+extern "C" hikf_status hikf_spd_inverse_noalloc(const double* d_S, int n, double* d_M, void* stream) {
+  using hikf::Status;
+  if (!d_S || !d_M) return HIKF_EINVAL;
+  if (n < 1 || n > HIKF_NOALLOC_MAX_N) return HIKF_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  double* scratch = nullptr;
+  int* flag = nullptr;
+  Status st = hikf::noalloc_scratch(&scratch, &flag);
+  if (st.ok()) st = hikf::spd_inverse_f64(d_S, n, d_M, scratch, flag, s);  // clears the status word first
+  int f[2] = {0, 0};
+  if (st.ok()) {
+    cudaError_t e = cudaMemcpyAsync(f, flag, sizeof(int) * 2, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = hikf::cuda_status(e, "spd_inverse_noalloc", __FILE__, __LINE__);
+  }
+  if (!st.ok()) return st.code;
+  if (f[0] & 2) return HIKF_ENOTPD;
+  return HIKF_OK;
+}
