@@ -36,7 +36,7 @@ CONFIG_NAME = "crosswell2d_m1048576_n256"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="hikf", choices=["hikf", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp32", "mixed"])
@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--config", default=CONFIG_NAME)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--serve-seconds", type=float, default=20.0,
+                    help="length of the served-latency run (64 streams, Poisson arrivals); 0 skips it")
     return ap.parse_args()
 
 
@@ -72,8 +74,11 @@ class Clocks:
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
+            t_end = time.time() + 10.0           # nvidia-smi takes a moment to start sampling
+            while time.time() < t_end and self.proc.poll() is None and self.path.stat().st_size == 0:
+                time.sleep(0.02)
         except Exception:
             self.proc = None
         return self
@@ -153,21 +158,27 @@ def ncu_traffic(precision: str, n: int):
 # ---------------------------------------------------------------------------
 # CPU oracle leg (FP64 numpy, Alg. 2) on a bounded sample of the same workload
 # ---------------------------------------------------------------------------
-def oracle_steps(w, steps: int, rng_seed: int = 0):
-    """Time `steps` O-cross updates at the full m, n of the workload.
+def oracle_steps(w, steps: int, rng_seed: int = 0, rows: int = 0):
+    """Time `steps` O-cross updates of the workload (all m rows, or the first `rows` points).
 
     The exact C_Q of this size is out of reach on a CPU (m * nnz kernel sums), so
     the sample feeds a PSD stand-in C_Q = G (H G)^T (G: m x 8, seeded); the update
-    arithmetic timed here does not depend on the values of C_Q.
+    arithmetic timed here does not depend on the values of C_Q. With `rows` < m the
+    update runs on those points only (H restricted to their columns): every term of
+    one update but the O(n^3) inverse is proportional to the row count.
     """
     from oracle import kf, qht
     H = qht.h_csr(w.h_rowptr, w.h_col, w.h_val, w.m)
-    g = np.random.default_rng(rng_seed).standard_normal((w.m, 8)) * 0.01
+    m = w.m
+    if 0 < rows < w.m:
+        H = H[:, :rows]
+        m = rows
+    g = np.random.default_rng(rng_seed).standard_normal((m, 8)) * 0.01
     cq = g @ np.asarray(H @ g).T
     c0 = 100.0 * cq
     Y = np.random.default_rng(rng_seed + 1).standard_normal((steps, w.n)) * 1e-2
     t0 = time.perf_counter()
-    kf.hikf_cross(cq, c0, np.full(w.m, 1.0), 0.01, H, w.r_diag, w.x0, Y)
+    kf.hikf_cross(cq, c0, np.full(m, 1.0), 0.01, H, w.r_diag, w.x0[:m], Y)
     dt = time.perf_counter() - t0
     return dt
 
@@ -180,23 +191,34 @@ def cpu_threads() -> int:
 
 
 def run_reference(args, rank, world):
+    """The oracle timed on the host cores. Each step is a bounded sample: the O-cross
+    update on the first `rows` points (rows = m / 2^k, chosen from one probe step so that
+    the whole run stays within about two minutes); the step time is scaled to all m rows."""
     if rank != 0:
         return 0
     from paper_1404_3816_gb300 import workload as W
     w = W.config(args.config)
-    for _ in range(max(0, args.warmup)):
-        oracle_steps(w, 1)
     steps = max(1, args.steps)
-    dt = oracle_steps(w, steps)
-    value = steps / dt
+    rows = w.m // 16
+    probe = oracle_steps(w, 1, rows=rows)
+    budget_s = 120.0
+    while rows > w.m // 1024 and probe * (steps + args.warmup) > budget_s:
+        rows //= 2
+        probe /= 2.0
+    for _ in range(max(0, args.warmup)):
+        oracle_steps(w, 1, rows=rows)
+    dt = oracle_steps(w, steps, rows=rows)
+    dt_full = dt * (w.m / rows)
+    value = steps / dt_full
     line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus, "steps": steps,
-            "warmup": args.warmup, "ms_per_step": 1000.0 * dt / steps, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * dt_full / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
             "config": {"workload": args.config, "m": w.m, "n": w.n, "kernel": "exp L=64",
                        "note": "FP64 numpy oracle of Alg. 2 on the host cores"},
             "cpu_baseline": {"value": value, "unit": "steps/s", "cores": cpu_threads(), "kind": "oracle",
-                             "sample": f"{steps} O-cross updates at m={w.m}, n={w.n} with a PSD stand-in C_Q"},
+                             "sample": f"{steps} O-cross updates on {rows} of the m={w.m} points (n={w.n}, PSD "
+                                       f"stand-in C_Q), time scaled by m/{rows}"},
             "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -222,7 +244,7 @@ def main():
 
     w = W.config(args.config, seed=W._cfg_table()[args.config]["seed"] + rank)
     total = args.warmup + args.steps
-    Y, _ = W.measurements(w, steps=total)
+    Y, _ = W.measurements(w, steps=max(total, w.steps))
     dY = torch.tensor(Y, dtype=torch.float64, device="cuda")
     m, n = w.m, w.n
     pk, pk_kind = peaks()
@@ -328,13 +350,28 @@ def main():
 
     if world == 1 and not args.no_compare:
         # the other arithmetic of the same update, and the eigenbasis form; accuracy against
-        # the FP64 eigenbasis form (exact reformulation, checked against the oracle in tests)
+        # the FP64 eigenbasis form (exact reformulation, checked against the oracle in tests),
+        # at the timed horizon (warm-up + timed steps) and at the workload's own horizon
         ref = timed("fp64", "eigen")
         ref["f"].close()
-        def err(r):
-            return {"mean": float(np.linalg.norm(r["mean"] - ref["mean"]) / np.linalg.norm(ref["mean"])),
-                    "var": float(np.linalg.norm(r["var"] - ref["var"]) / np.linalg.norm(ref["var"]))}
-        line["err_vs_fp64"] = {args.precision: err(head)}
+
+        def err(r, rf):
+            return {"mean": float(np.linalg.norm(r["mean"] - rf["mean"]) / np.linalg.norm(rf["mean"])),
+                    "var": float(np.linalg.norm(r["var"] - rf["var"]) / np.linalg.norm(rf["var"]))}
+
+        hz = w.steps
+
+        def final(prec, form):
+            with binding.Filter.from_workload(w, cheb_order=args.order, precision=prec, form=form) as g:
+                for t in range(hz):
+                    g.assimilate_device(dY[t])
+                g.sync()
+                return {"mean": g.mean(), "var": g.variance()}
+
+        ref_hz = final("fp64", "eigen")
+        line["err_vs_fp64"] = {"steps": total, args.precision: err(head, ref)}
+        line["err_vs_fp64_at_workload_horizon"] = {"steps": hz, args.precision: err(final(args.precision, "cross"),
+                                                                                      ref_hz)}
         comps = {}
         for prec, form in (("fp32" if args.precision == "mixed" else "mixed", "cross"), ("fp32", "eigen")):
             r = timed(prec, form)
@@ -342,8 +379,23 @@ def main():
             key = f"{prec}_{form}"
             comps[key] = {"value": args.steps / (r["elapsed_ms"] / 1000.0), "unit": "steps/s",
                           "ms_per_step": r["elapsed_ms"] / args.steps, "roofline": roofline(prec, form, r["sweep_ms"]),
-                          "err_vs_fp64": err(r)}
+                          "err_vs_fp64": err(r, ref)}
+            line["err_vs_fp64_at_workload_horizon"][key] = err(final(prec, form), ref_hz)
         line["compare"] = comps
+
+    if rank == 0 and world == 1 and args.serve_seconds > 0:
+        # served step latency: 64 monitoring streams (log-uniform m from 4096 to 2^20, n in
+        # {16..256}), Poisson arrivals at 500/s in total, HBM budget 150 GB
+        from paper_1404_3816_gb300 import serve
+        sv = serve.run_serving(serve.serving_streams(64), rate=500.0, seconds=args.serve_seconds,
+                               budget_bytes=150 * 10**9, precision=args.precision, form="cross")
+        line["serving"] = {"p50_ms": sv["p50_ms"], "p99_ms": sv["p99_ms"], "mean_ms": sv["mean_ms"],
+                           "steps": sv["steps"], "steps_per_s": sv["steps_per_s"], "seconds": sv["seconds"],
+                           "rate_per_s": sv["rate_per_s"], "streams": sv["streams"], "admitted": sv["admitted"],
+                           "rejected": sv["rejected"], "hbm_reserved_gb": sv["hbm_reserved_gb"],
+                           "create_s_all": sv["create_s_all"],
+                           "workload": "64 streams, side log-uniform 64..1024, n in {16,32,64,128,256}, "
+                                       "exp L=side/16, R=1e-3 I, Poisson 500/s, budget 150 GB"}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         steps = 3

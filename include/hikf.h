@@ -89,6 +89,8 @@ typedef struct {
                         then diagonal, O(n m) per step, and the variance reduction a
                         sum of squares. Needs the spectral chain (P_0 = c Q) and
                         FP32/FP64. hikf_get_cross forms C_{t|t} = G V^T R^{1/2} on request. */
+  int graph;         /* 1 (default): each update is replayed as one CUDA graph, captured on
+                        the first update; 0: kernels are launched one by one. */
 } hikf_options;
 
 enum { HIKF_CHAIN_AUTO = 0, HIKF_CHAIN_FACTOR = 1, HIKF_CHAIN_SPECTRAL = 2 };

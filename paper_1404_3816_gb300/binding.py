@@ -47,7 +47,8 @@ class Kernel(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("cheb_order", C.c_int), ("leaf_size", C.c_int), ("max_depth", C.c_int),
-                ("precision", C.c_int), ("cuda_stream", C.c_void_p), ("chain", C.c_int), ("form", C.c_int)]
+                ("precision", C.c_int), ("cuda_stream", C.c_void_p), ("chain", C.c_int), ("form", C.c_int),
+                ("graph", C.c_int)]
 
 
 class Info(C.Structure):
@@ -132,7 +133,7 @@ def kernel_struct(spec) -> Kernel:
 
 
 def options(cheb_order: int = 8, leaf_size: int = 64, max_depth: int = -1, precision="fp32",
-            stream=None, chain="auto", form="cross") -> Options:
+            stream=None, chain="auto", form="cross", graph=True) -> Options:
     o = Options()
     load().hikf_options_default(C.byref(o))
     o.cheb_order = int(cheb_order)
@@ -141,6 +142,7 @@ def options(cheb_order: int = 8, leaf_size: int = 64, max_depth: int = -1, preci
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     o.chain = CHAINS[chain] if isinstance(chain, str) else int(chain)
     o.form = FORMS[form] if isinstance(form, str) else int(form)
+    o.graph = 1 if graph else 0
     if stream is not None:
         o.cuda_stream = C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
     return o

@@ -149,6 +149,13 @@ struct hikf_handle {
   std::string err;
   double create_ms = 0.0;
   int launches = 0;
+  // the update as a CUDA graph (HIKF options.graph)
+  bool use_graph = true;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  cudaEvent_t gev[2] = {nullptr, nullptr};
+  cudaGraphNode_t gnode[2] = {nullptr, nullptr};
+  bool capturing = false;  // event records become graph event-record nodes
   // sweep timing (hikf_profile_enable)
   bool prof = false;
   int prof_count = 0;
@@ -237,6 +244,8 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
   } else {
     hikf::FmmParams fp;
     fp.order = h->order;
+    fp.tensor_m2l = h->mixed();
+    fp.sms = h->sms;
     fp.pow = q.pow;
     fp.theta = q.theta;
     fp.length = q.length;
@@ -250,6 +259,8 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
     } else {
       hikf::FmmParams f0;
       f0.order = h->order;
+      f0.tensor_m2l = h->mixed();
+      f0.sms = h->sms;
       f0.pow = p0.pow;
       f0.theta = p0.theta;
       f0.length = p0.length;
@@ -320,6 +331,8 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
   HIKF_TRY(hikf::arena_alloc(h->arena, &h->e, n));
   HIKF_TRY(hikf::arena_alloc(h->arena, &h->a, n));
   HIKF_TRY(hikf::arena_alloc(h->arena, &h->ybuf, n));
+  HIKF_TRY(hikf::prepare_sweep<T>(ld));
+  HIKF_TRY(hikf::prepare_chain());
 
   // spectral chain when P_0 = c Q (c >= 0) and C_Q is our own H^2 product
   const bool p0_is_cq = p0.theta == 0.0 || (p0.pow == q.pow && p0.length == q.length);
@@ -360,29 +373,26 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
     HIKF_TRY(hikf::arena_alloc(h->arena, &tc.bimg, (size_t)3 * tc.nt * tc.nt));
     HIKF_TRY(hikf::arena_alloc(h->arena, &tc.cmax, m));
     HIKF_TRY(hikf::arena_alloc(h->arena, &tc.cqmax, m));
-    HIKF_TRY(hikf::arena_alloc(h->arena, &tc.mmax, 1));
+    HIKF_TRY(hikf::arena_alloc(h->arena, &tc.mmax, hikf::kAbsBlocks));
     HIKF_TRY(hikf::arena_alloc(h->arena, &tc.beta_exp, 1));
     HIKF_TRY(hikf::tc_init_rows(tc, (const float*)C, (const float*)CQ, m, ld, s));
   }
   return Status::Ok();
 }
 
+// One measurement update on the handle's stream. ev0/ev1 (may be null) bracket the sweep.
 template <typename T>
-Status enqueue_step(hikf_t* h) {
+Status enqueue_step(hikf_t* h, cudaEvent_t ev0, cudaEvent_t ev1) {
   cudaStream_t s = h->stream;
   hikf::ChainArgs& c = h->chain;
   int launches = 0;
   if (h->eigen) {
     HIKF_TRY(hikf::launch_innovation(h->ybuf, h->H, h->x, h->e, h->flag, s));
     HIKF_TRY(hikf::eigen_u(h->sp, h->n, h->e, h->flag, s));
-    const bool rec = h->prof && h->prof_count < (int)h->ev.size() / 2;
-    if (rec) HIKF_CUDA(cudaEventRecord(h->ev[2 * h->prof_count], s));
+    if (ev0) HIKF_CUDA(cudaEventRecordWithFlags(ev0, s, h->capturing ? cudaEventRecordExternal : 0));
     HIKF_TRY(hikf::eigen_step<T>(h->sp, h->m, h->ld, h->n, (T*)h->G, (const T*)h->Gq, h->theta_q, h->x, h->var,
                                  h->flag, h->sms, s));
-    if (rec) {
-      HIKF_CUDA(cudaEventRecord(h->ev[2 * h->prof_count + 1], s));
-      ++h->prof_count;
-    }
+    if (ev1) HIKF_CUDA(cudaEventRecordWithFlags(ev1, s, h->capturing ? cudaEventRecordExternal : 0));
     hikf::count_step<<<1, 1, 0, s>>>(h->flag, h->dstep);
     HIKF_LAUNCH_CHECK("count_step");
     HIKF_TRY(hikf::spectral_next(h->sp, h->n, h->flag, s));
@@ -417,14 +427,14 @@ Status enqueue_step(hikf_t* h) {
     HIKF_TRY(hikf::tc_pack(h->tc, (const float*)h->Msw, h->nt, h->n, h->flag, s));
     launches += 3;
   }
-  const bool rec = h->prof && h->prof_count < (int)h->ev.size() / 2;
-  if (rec) HIKF_CUDA(cudaEventRecord(h->ev[2 * h->prof_count], s));
+  if (ev0) HIKF_CUDA(cudaEventRecordWithFlags(ev0, s, h->capturing ? cudaEventRecordExternal : 0));
   if (h->mixed()) {
     hikf::TcArgs ta;
     ta.m = h->m;
     ta.ld = h->ld;
     ta.n = h->n;
     ta.C = (float*)h->C;
+    ta.CQ = (const float*)h->CQ;
     ta.a = h->a;
     ta.rd = h->rd;
     ta.theta = h->theta_q;
@@ -437,10 +447,7 @@ Status enqueue_step(hikf_t* h) {
   } else {
     HIKF_TRY(hikf::launch_sweep<T>(sa, s, h->sms));
   }
-  if (rec) {
-    HIKF_CUDA(cudaEventRecord(h->ev[2 * h->prof_count + 1], s));
-    ++h->prof_count;
-  }
+  if (ev1) HIKF_CUDA(cudaEventRecordWithFlags(ev1, s, h->capturing ? cudaEventRecordExternal : 0));
   hikf::count_step<<<1, 1, 0, s>>>(h->flag, h->dstep);
   HIKF_LAUNCH_CHECK("count_step");
   if (h->spectral)
@@ -452,7 +459,61 @@ Status enqueue_step(hikf_t* h) {
   return Status::Ok();
 }
 
-Status enqueue(hikf_t* h) { return h->fp64() ? enqueue_step<double>(h) : enqueue_step<float>(h); }
+Status enqueue_direct(hikf_t* h, cudaEvent_t ev0, cudaEvent_t ev1) {
+  return h->fp64() ? enqueue_step<double>(h, ev0, ev1) : enqueue_step<float>(h, ev0, ev1);
+}
+
+// The update as one CUDA graph, captured on first use (thread-local capture mode, so
+// other threads' allocations are not affected). Two event-record nodes bracket the
+// sweep; they record placeholder events unless profiling points them at the record.
+Status build_graph(hikf_t* h) {
+  HIKF_CUDA(cudaEventCreate(&h->gev[0]));
+  HIKF_CUDA(cudaEventCreate(&h->gev[1]));
+  HIKF_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  h->capturing = true;
+  Status st = enqueue_direct(h, h->gev[0], h->gev[1]);
+  h->capturing = false;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+  if (!st.ok()) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return hikf::cuda_status(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+  h->graph = g;
+  HIKF_CUDA(cudaGraphInstantiate(&h->graph_exec, g, 0));
+  size_t cnt = 0;
+  HIKF_CUDA(cudaGraphGetNodes(g, nullptr, &cnt));
+  std::vector<cudaGraphNode_t> nodes(cnt);
+  HIKF_CUDA(cudaGraphGetNodes(g, nodes.data(), &cnt));
+  for (auto nd : nodes) {
+    cudaGraphNodeType ty;
+    HIKF_CUDA(cudaGraphNodeGetType(nd, &ty));
+    if (ty != cudaGraphNodeTypeEventRecord) continue;
+    cudaEvent_t ev = nullptr;
+    HIKF_CUDA(cudaGraphEventRecordNodeGetEvent(nd, &ev));
+    if (ev == h->gev[0]) h->gnode[0] = nd;
+    if (ev == h->gev[1]) h->gnode[1] = nd;
+  }
+  if (!h->gnode[0] || !h->gnode[1]) return hikf::make_status(HIKF_ECUDA, "graph event nodes not found");
+  return Status::Ok();
+}
+
+Status enqueue(hikf_t* h) {
+  const bool rec = h->prof && h->prof_count < (int)h->ev.size() / 2;
+  cudaEvent_t ev0 = rec ? h->ev[2 * h->prof_count] : nullptr;
+  cudaEvent_t ev1 = rec ? h->ev[2 * h->prof_count + 1] : nullptr;
+  if (!h->use_graph) {
+    HIKF_TRY(enqueue_direct(h, ev0, ev1));
+  } else {
+    if (!h->graph_exec) HIKF_TRY(build_graph(h));
+    HIKF_CUDA(cudaGraphExecEventRecordNodeSetEvent(h->graph_exec, h->gnode[0], rec ? ev0 : h->gev[0]));
+    HIKF_CUDA(cudaGraphExecEventRecordNodeSetEvent(h->graph_exec, h->gnode[1], rec ? ev1 : h->gev[1]));
+    HIKF_CUDA(cudaGraphLaunch(h->graph_exec, h->stream));
+  }
+  if (rec) ++h->prof_count;
+  return Status::Ok();
+}
 
 Status read_flag(hikf_t* h, int* out) {
   int f[4] = {0, 0, 0, 0};
@@ -503,8 +564,10 @@ hikf_status create_impl(hikf_t** out, int dim, int64_t m, const double* points, 
   h->nt = hikf::sweep_nt(h->ld);
   h->prec = o.precision;
   h->order = o.cheb_order;
+  h->use_graph = o.graph != 0;
   if (o.cuda_stream) {
     h->stream = (cudaStream_t)o.cuda_stream;
+    if (h->stream == cudaStreamLegacy) h->use_graph = false;  // the legacy stream cannot be captured
   } else {
     cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return bail(hikf::cuda_status(e, "cudaStreamCreate", __FILE__, __LINE__));
@@ -551,6 +614,7 @@ hikf_status hikf_options_default(hikf_options* opt) {
   opt->cuda_stream = nullptr;
   opt->chain = HIKF_CHAIN_AUTO;
   opt->form = HIKF_FORM_CROSS;
+  opt->graph = 1;
   return HIKF_OK;
 }
 
@@ -729,6 +793,10 @@ const char* hikf_last_error(const hikf_t* h) {
 void hikf_destroy(hikf_t* h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  for (auto& e : h->gev)
+    if (e) cudaEventDestroy(e);
   h->arena.release();
   for (auto& e : h->ev) cudaEventDestroy(e);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);

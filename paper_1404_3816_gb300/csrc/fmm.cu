@@ -19,6 +19,7 @@
 #include <algorithm>
 
 #include "hikf_internal.cuh"
+#include "m2l_tc.cuh"
 
 namespace hikf {
 
@@ -652,11 +653,42 @@ Status h2_product(const Tree& t, const SparseH& h, const FmmParams& fp, T* out, 
       }
     }
     // M2L, all levels 2 .. L
+    const bool tc = fp.tensor_m2l && sizeof(T) == 4 && m2l_tc_supported(q, ldc);
+    int* err = nullptr;
+    if (tc) {
+      HIKF_CUDA(cudaMallocAsync((void**)&err, sizeof(int), s));
+      HIKF_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    }
     for (int lev = 2; lev <= L; ++lev) {
+      if (tc) {
+        M2lTcArgs ma;
+        ma.lev = lev;
+        ma.dim = dim;
+        ma.q = q;
+        ma.ld = ldc;
+        ma.sms = fp.sms;
+        ma.box0 = t.box_offset[lev];
+        ma.nbox = (int64_t)1 << (dim * lev);
+        ma.W = (const float*)W;
+        ma.L = (float*)Lx;
+        ma.kop_level = (const float*)kop + (int64_t)(lev - 2) * ipow(7, dim) * q * q;
+        ma.nsrc = nsrc;
+        ma.npts = npts;
+        ma.err = err;
+        HIKF_TRY(m2l_tc_level(ma, s));
+        continue;
+      }
       dim3 grid((unsigned)((int64_t)1 << (dim * lev)), (unsigned)((q + kM2L_BM - 1) / kM2L_BM),
                 (unsigned)((ldc + kM2L_BN - 1) / kM2L_BN));
       m2l_kernel<T><<<grid, kThreads, 0, s>>>(g, lev, kop, nsrc, npts, t.box_offset[lev], W, Lx);
       HIKF_LAUNCH_CHECK("m2l");
+    }
+    if (tc) {
+      int herr = 0;
+      HIKF_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+      HIKF_CUDA(cudaStreamSynchronize(s));
+      HIKF_CUDA(cudaFreeAsync(err, s));
+      if (herr) return make_status(HIKF_ETIMEOUT, "a bounded wait in the tensor-core M2L timed out");
     }
     // L2L, levels 2 .. L-1 (parent level)
     {

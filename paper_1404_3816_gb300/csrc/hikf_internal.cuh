@@ -104,6 +104,8 @@ struct FmmParams {
   int pow = 1;
   double theta = 1.0;
   double length = 1.0;
+  bool tensor_m2l = false;  // M2L on the tensor cores (FP32 storage only)
+  int sms = 1;
 };
 
 // out: [m x ldc] in tree order (T = float or double); columns >= n are zero.

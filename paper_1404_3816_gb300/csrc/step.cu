@@ -529,13 +529,26 @@ __global__ void __launch_bounds__(256) sweep_kernel(int64_t m, int ld, int n, co
 }
 
 template <typename T, int NT, int TM>
+Status sweep_config(int* per_sm_out) {
+  using Cfg = SweepCfg<T, NT, TM>;
+  auto fn = sweep_kernel<T, NT, TM>;
+  static int per_sm = 0;  // resolved once per instantiation, at create (outside any graph capture)
+  if (per_sm == 0) {
+    HIKF_CUDA(cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM));
+    int v = 1;
+    HIKF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, fn, 256, Cfg::SMEM));
+    per_sm = std::max(v, 1);
+  }
+  *per_sm_out = per_sm;
+  return Status::Ok();
+}
+
+template <typename T, int NT, int TM>
 Status launch_sweep_t(const SweepArgs<T>& s, cudaStream_t st, int sms) {
   using Cfg = SweepCfg<T, NT, TM>;
   auto fn = sweep_kernel<T, NT, TM>;
-  HIKF_CUDA(cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM));
   int per_sm = 1;
-  HIKF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, Cfg::SMEM));
-  per_sm = std::max(per_sm, 1);
+  HIKF_TRY((sweep_config<T, NT, TM>(&per_sm)));
   int64_t ntiles = (s.m + Cfg::BM - 1) / Cfg::BM;
   int grid = (int)std::min<int64_t>(ntiles, (int64_t)sms * per_sm);
   grid = std::max(grid, 1);
@@ -567,6 +580,28 @@ Status launch_sweep(const SweepArgs<T>& s, cudaStream_t st, int sms) {
 }
 
 template Status launch_sweep<float>(const SweepArgs<float>&, cudaStream_t, int);
+
+template <typename T>
+Status prepare_sweep(int ld) {
+  const int nt = sweep_nt(ld);
+  int v = 0;
+  if (sizeof(T) == 4) {
+    if (nt == 128) return sweep_config<T, 128, 8>(&v);
+    if (nt == 256) return sweep_config<T, 256, 8>(&v);
+    return sweep_config<T, 512, 4>(&v);
+  }
+  if (nt == 128) return sweep_config<T, 128, 8>(&v);
+  if (nt == 256) return sweep_config<T, 256, 4>(&v);
+  return sweep_config<T, 512, 2>(&v);
+}
+template Status prepare_sweep<float>(int);
+template Status prepare_sweep<double>(int);
+
+Status prepare_chain() {
+  HIKF_CUDA(cudaFuncSetAttribute((const void*)chol32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(float) * (512 + (size_t)kSmemN * (kSmemN + 1) / 2))));
+  return Status::Ok();
+}
 template Status launch_sweep<double>(const SweepArgs<double>&, cudaStream_t, int);
 
 template <typename T>
@@ -595,7 +630,6 @@ Status launch_chain(const ChainArgs& c, cudaStream_t s) {
   }
   {
     size_t sm = n <= kSmemN ? sizeof(float) * (512 + (size_t)n * (n + 1) / 2) : sizeof(float) * 512;
-    HIKF_CUDA(cudaFuncSetAttribute((const void*)chol32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     chol32_kernel<<<1, 1024, sm, s>>>(c.S, n, c.Shi, c.Slo, c.L32, c.X32, c.flag);
   }
   HIKF_LAUNCH_CHECK("chol32");

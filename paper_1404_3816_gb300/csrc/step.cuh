@@ -49,6 +49,10 @@ int sweep_nt(int ld);
 
 template <typename T>
 Status launch_sweep(const SweepArgs<T>& s, cudaStream_t st, int sms);
+// launch attributes resolved at create (so that the update can be captured as a graph)
+template <typename T>
+Status prepare_sweep(int ld);
+Status prepare_chain();
 
 template <typename T>
 Status launch_gather_hc(const SparseH& h, const T* C, int ld, double* out, int accumulate, cudaStream_t s);

@@ -32,6 +32,7 @@
 
 #include "hikf_internal.cuh"
 #include "sweep_tc.cuh"
+#include "tc_ptx.cuh"
 
 namespace hikf {
 
@@ -47,7 +48,6 @@ constexpr int kBStages = 2;
 constexpr int kThreadsTc = 128 + 128 * kGroups;
 constexpr int kRawBytes = kBM * kKC * 4;          // one FP32 raw tile (C or C_Q): 16 KB
 constexpr int kAPieceBytes = kBM * kKC * 2;       // one FP16 A piece: 8 KB
-constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
 
 template <int NT>
 struct TcLayout {
@@ -63,126 +63,7 @@ struct TcLayout {
   static constexpr int Smem = Total + 1024;                          // slack for 1024-B alignment
 };
 
-// ---- PTX wrappers ----------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(bar),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ unsigned long long now_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-// bounded wait: false (and *err set) after ~2 s
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, const volatile int* abort_flag) {
-  if (mbar_try(bar, parity)) return true;
-  const unsigned long long t0 = now_ns();
-  while (true) {
-    if (mbar_try(bar, parity)) return true;
-    if (*abort_flag) return false;
-    if (now_ns() - t0 > kWaitNs) {
-      atomicExch(err, 1);
-      return false;
-    }
-  }
-}
-__device__ __forceinline__ void fence_barrier_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          dst),
-      "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
-      : "memory");
-}
-__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(bar)
-               : "memory");
-}
-
-__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols));
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void tc_mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                           uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
-}
-
-#define TC_REG32(a) \
-  a[0], a[1], a[2], a[3], a[4], a[5], a[6], a[7], a[8], a[9], a[10], a[11], a[12], a[13], a[14], a[15], a[16], a[17], \
-      a[18], a[19], a[20], a[21], a[22], a[23], a[24], a[25], a[26], a[27], a[28], a[29], a[30], a[31]
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
-        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
-        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
-        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-      : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t* v) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
-      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
-      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]),
-      "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]),
-      "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
-      : "memory");
-}
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-
-// Shared-memory matrix descriptor, canonical K-major layout without swizzle:
-// core matrices of 8 rows x 16 bytes; lbo = byte step between core matrices
-// along K, sbo = byte step between 8-row groups; version 1 (tcgen05).
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((addr >> 4) & 0x3FFFu);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1 << 46;
-  return d;  // base offset 0, layout type 0 (no swizzle)
-}
-
-// byte offset of element (row, k), k < 32, in a K-major core-matrix piece (32 K = 4 core matrices per row group)
-__host__ __device__ __forceinline__ uint32_t core_off(int row, int k) {
-  return (uint32_t)((row >> 3) * 512 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
-}
+using namespace tc;
 
 __device__ __forceinline__ int pow2_exp(float bound) {
   // e with bound < 2^e (bound > 0)
@@ -339,7 +220,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
       }
       // all issued MMAs complete before TMEM is released
       tc_commit(drain);
-      mbar_wait(drain, 0, args.err, s_abort);
+      mbar_wait_drain(drain, 0, args.err);
       if (!ok) *s_abort = 1;
     }
   } else if (warp >= 4) {
@@ -535,28 +416,34 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
 }
 
 // B images: beta M split into FP16 hi / lo, K-major core-matrix layout per 32-K stage (see pack_b_dyn_kernel)
+// max|M| over the n x n block: block b reduces rows b, b + kAbsBlocks, ... into out[b]
 __global__ void absmax_kernel(const float* __restrict__ M, int nt, int n, unsigned* __restrict__ out) {
   float mx = 0.f;
-  for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += blockDim.x) {
-    int i = (int)(t / n), j = (int)(t % n);
-    mx = fmaxf(mx, fabsf(M[(int64_t)i * nt + j]));
-  }
+  for (int i = blockIdx.x; i < n; i += gridDim.x)
+    for (int j = threadIdx.x; j < n; j += blockDim.x) mx = fmaxf(mx, fabsf(M[(int64_t)i * nt + j]));
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   __shared__ float red[32];
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmaxf(mx, red[w]);
-    *out = __float_as_uint(fmaxf(red[0], mx));
+    out[blockIdx.x] = __float_as_uint(fmaxf(red[0], mx));
   }
 }
 
-// beta exponent from max|M| (written where pack_b_kernel and the sweep read it)
+// beta exponent from the kAbsBlocks partial maxima of |M| (written where pack_b_kernel and the sweep read it)
 __global__ void beta_kernel(const unsigned* __restrict__ mx, int* __restrict__ beta_exp) {
-  const float v = __uint_as_float(*mx);
-  int e = 0;
-  if (v > 0.f) frexpf(v, &e);
-  *beta_exp = 14 - e;
+  float v = __uint_as_float(mx[threadIdx.x]);
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __shared__ float red[kAbsBlocks / 32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 0; w < kAbsBlocks / 32; ++w) v = fmaxf(v, red[w]);
+    int e = 0;
+    if (v > 0.f) frexpf(v, &e);
+    *beta_exp = 14 - e;
+  }
 }
 
 template <int NT>
@@ -639,9 +526,9 @@ Status tc_init_rows(const TcState& tc, const float* C, const float* CQ, int64_t 
 }
 
 Status tc_pack(const TcState& tc, const float* Msw, int nt_src, int n, const int* flag, cudaStream_t s) {
-  absmax_kernel<<<1, 1024, 0, s>>>(Msw, nt_src, n, tc.mmax);
+  absmax_kernel<<<kAbsBlocks, 256, 0, s>>>(Msw, nt_src, n, tc.mmax);
   HIKF_LAUNCH_CHECK("absmax");
-  beta_kernel<<<1, 1, 0, s>>>(tc.mmax, tc.beta_exp);
+  beta_kernel<<<1, kAbsBlocks, 0, s>>>(tc.mmax, tc.beta_exp);
   HIKF_LAUNCH_CHECK("beta");
   const int64_t cnt = (int64_t)tc.nt * tc.nt;
   if (tc.nt == 128)

@@ -13,6 +13,7 @@ struct TcArgs {
   int ld = 0;
   int n = 0;
   float* C = nullptr;           // m x ld, updated in place (written as K R)
+  const float* CQ = nullptr;    // m x ld (read by the epilogue; the converter reads it by TMA)
   const double* a = nullptr;    // n
   const double* rd = nullptr;   // n, diag R
   double theta = 0.0;           // diag Q
@@ -33,9 +34,11 @@ struct TcState {
   __half* bimg = nullptr;       // 3 x nt x nt FP16 images of beta M (three pieces)
   float* cmax = nullptr;
   float* cqmax = nullptr;
-  unsigned* mmax = nullptr;
+  unsigned* mmax = nullptr;     // kAbsBlocks partial maxima of |M|
   int* beta_exp = nullptr;
 };
+
+constexpr int kAbsBlocks = 64;
 
 Status tc_setup(TcState& tc, const float* C, const float* CQ, int64_t m, int ld, int n);
 Status tc_init_rows(const TcState& tc, const float* C, const float* CQ, int64_t m, int ld, cudaStream_t s);

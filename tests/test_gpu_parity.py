@@ -78,15 +78,29 @@ def test_tree_permutation_is_bit_exact(B, name):
         assert np.array_equal(f.perm(), morton_perm(w, depth))
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("prec", ["fp32", "fp64", "mixed"])
 @pytest.mark.parametrize("name", list(CASES))
 def test_h2_product_matches_oracle_definition(B, name, prec):
+    """mixed: M2L on the tensor cores (split TF32); fp32/fp64: CUDA-core M2L."""
     w = CASES[name]()
+    if prec == "mixed" and w.n > 256:
+        pytest.skip("the tensor-core paths take n <= 256")
     with B.Filter.from_workload(w, precision=prec) as f:
         depth = f.info()["depth"]
         got = f.cq()
     ref = _oracle_h2(w, w.q, depth, w.cheb_order)
-    assert rel(got, ref) < (TOL32 if prec == "fp32" else TOL64)
+    assert rel(got, ref) < (TOL64 if prec == "fp64" else TOL32)
+
+
+@pytest.mark.parametrize("p", [4, 6, 7, 10])
+def test_tensor_core_m2l_across_orders(B, p):
+    """q = p^2 from 16 to 100 (MMA N 32 / 64 / 128), ragged grid, n = 40 (one M half)."""
+    w = W.small(grid=(75, 61), n=40, steps=1, seed=50 + p)
+    with B.Filter.from_workload(w, precision="mixed", cheb_order=p) as f:
+        depth = f.info()["depth"]
+        got = f.cq()
+    ref = _oracle_h2(w, w.q, depth, p)
+    assert rel(got, ref) < TOL32
 
 
 def test_h2_product_close_to_exact_sum(B):
@@ -289,3 +303,17 @@ def test_spd_inverse_rejects_indefinite(B):
     with pytest.raises(B.HikfError) as e:
         B.spd_inverse(dS, dM)
     assert e.value.code == B.HIKF_ENOTPD
+
+
+@pytest.mark.parametrize("prec,form,chain", [("fp32", "cross", "factor"), ("fp32", "cross", "spectral"),
+                                             ("mixed", "cross", "auto"), ("fp32", "eigen", "auto"),
+                                             ("fp64", "cross", "factor")])
+def test_graph_replay_equals_direct_launches(B, prec, form, chain):
+    """The update replayed as a captured CUDA graph gives bit-identical state to the same
+    kernels launched one by one (every kernel on the path is deterministic)."""
+    w = CASES["ragged_61x37_n100"]()
+    out = []
+    for graph in (True, False):
+        out.append(_run(B, w, prec, form=form, chain=chain, graph=graph))
+    for a, b in zip(out[0][:3], out[1][:3]):
+        assert np.array_equal(a, b)
