@@ -190,6 +190,19 @@ def cpu_threads() -> int:
         return os.cpu_count() or 1
 
 
+def job_rate(units_per_rank: int, seconds: float, world: int, device=None):
+    """Whole-job rate of independent replicas: every rank processed `units_per_rank`
+    units in `seconds` (its own clock); the job took the slowest rank's time.
+    Returns (units of all ranks / max seconds, max seconds). Collective: all ranks call it."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        seconds = float(t.item())
+    return units_per_rank * world / seconds, seconds
+
+
 def run_reference(args, rank, world):
     """The oracle timed on the host cores. Each step is a bounded sample: the O-cross
     update on the first `rows` points (rows = m / 2^k, chosen from one probe step so that
@@ -287,13 +300,10 @@ def main():
     head = timed(args.precision, "cross", clocks=True, barrier=True)
     f = head["f"]
     info = head["info"]
-    elapsed_ms = head["elapsed_ms"]
+    value, elapsed_s = job_rate(args.steps, head["elapsed_ms"] / 1000.0, world, device="cuda")
+    elapsed_ms = elapsed_s * 1000.0
     if world > 1:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
         dist.barrier()
-    value = args.steps * world / (elapsed_ms / 1000.0)
 
     # e2e through the C ABI with host buffers: y in, mean and variance out, every step
     ne2e = max(1, args.e2e_steps)
@@ -308,12 +318,7 @@ def main():
         f.assimilate(y_np[t])
         f.mean_into(out_x)
         f.variance_into(out_v)
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        tt = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e_value = ne2e * world / e2e_s
+    e2e_value, _ = job_rate(ne2e, time.perf_counter() - t0, world, device="cuda")
     f.close()
 
     def roofline(prec, form, ms):
@@ -381,6 +386,47 @@ def main():
                           "ms_per_step": r["elapsed_ms"] / args.steps, "roofline": roofline(prec, form, r["sweep_ms"]),
                           "err_vs_fp64": err(r, ref)}
             line["err_vs_fp64_at_workload_horizon"][key] = err(final(prec, form), ref_hz)
+
+        # n-space form: O(n^2) per step; x and delta^2 formed in one pass over Gq = C_Q W,
+        # either on request (steps only) or after every step (the same outputs as the other forms)
+        r = timed("fp32", "nspace")
+        r["f"].close()
+        fo = binding.Filter.from_workload(w, cheb_order=args.order, precision="fp32", form="nspace")
+        so = torch.cuda.ExternalStream(fo.stream)
+        dx = torch.empty(m, dtype=torch.float64, device="cuda")
+        dv = torch.empty_like(dx)
+        for t in range(args.warmup):
+            fo.assimilate_device(dY[t])
+            fo.mean_into(dx)
+            fo.variance_into(dv)
+        fo.sync()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(so)
+        for t in range(args.warmup, total):
+            fo.assimilate_device(dY[t])
+            fo.mean_into(dx)
+            fo.variance_into(dv)
+        e1.record(so)
+        e1.synchronize()
+        ms_out = e0.elapsed_time(e1) / args.steps
+        fo.close()
+        ms_step = r["elapsed_ms"] / args.steps
+        out_ms = max(ms_out - ms_step, 1e-6)
+        out_bytes = 4.0 * m * ((n + 31) // 32 * 32) + 8.0 * m + 16.0 * m   # Gq read, x_0 read, x and delta^2 written
+        achieved = out_bytes / (out_ms / 1e3) / 1e9
+        comps["fp32_nspace"] = {
+            "value": args.steps / (r["elapsed_ms"] / 1000.0), "unit": "steps/s", "ms_per_step": ms_step,
+            "note": "x and delta^2 not formed per step (on request)",
+            "with_outputs_every_step": {"value": 1000.0 / ms_out, "unit": "steps/s", "ms_per_step": ms_out},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": float(pk["hbm_gbs"]), "unit": "GB/s",
+                         "frac": achieved / float(pk["hbm_gbs"]), "traffic": None,
+                         "kernel": "nspace_outputs_kernel (x, delta^2 from Gq)",
+                         "ms_per_launch": out_ms, "alg_bytes_per_launch": out_bytes,
+                         "method": "per-step time with outputs minus per-step time without"},
+            "err_vs_fp64": err(r, ref)}
+        line["err_vs_fp64_at_workload_horizon"]["fp32_nspace"] = err(final("fp32", "nspace"), ref_hz)
         line["compare"] = comps
 
     if rank == 0 and world == 1 and args.serve_seconds > 0:

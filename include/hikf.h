@@ -62,7 +62,9 @@ typedef struct {
  *   FP32:  C, C_Q and the H^2 product in FP32 on the CUDA cores; the n x n
  *          solve refined to FP64-level accuracy; diag(P) and the state in FP64.
  *   MIXED: as FP32, with the per-step O(n^2 m) product on the tensor cores
- *          (tcgen05, split TF32 operands, FP32 accumulation).
+ *          (tcgen05; each FP32 operand split into three FP16 pieces, FP32
+ *          accumulation) and the M2L translations of the H^2 product on the
+ *          tensor cores (tcgen05, FP32 operands split into two TF32 pieces).
  *   FP64:  everything in FP64 (small problems; the FP64 rate of this part is low). */
 enum { HIKF_PREC_FP32 = 0, HIKF_PREC_MIXED = 1, HIKF_PREC_FP64 = 2 };
 
@@ -88,13 +90,21 @@ typedef struct {
                         (V: eigenvectors of R^{-1/2} H C_Q R^{-1/2}); the update is
                         then diagonal, O(n m) per step, and the variance reduction a
                         sum of squares. Needs the spectral chain (P_0 = c Q) and
-                        FP32/FP64. hikf_get_cross forms C_{t|t} = G V^T R^{1/2} on request. */
+                        FP32/FP64. hikf_get_cross forms C_{t|t} = G V^T R^{1/2} on request;
+                        HIKF_FORM_NSPACE: with P_0 = c Q the eigenbasis state stays
+                        G_{t|t} = C_Q R^{-1/2} V diag(gamma_t), so the filter is carried by
+                        three n-vectors (x_t = x_0 + G_Q b_t, delta^2_t = delta^2_0 +
+                        t theta - G_Q^2 h_t, G_Q = C_Q R^{-1/2} V) and one step costs O(n^2)
+                        with no pass over the m rows. hikf_get_mean / hikf_get_variance
+                        (and the _device forms) form x and delta^2 in one pass over G_Q
+                        when the state has changed since the last call; hikf_get_cross
+                        forms C_{t|t}. Same conditions as HIKF_FORM_EIGEN. */
   int graph;         /* 1 (default): each update is replayed as one CUDA graph, captured on
                         the first update; 0: kernels are launched one by one. */
 } hikf_options;
 
 enum { HIKF_CHAIN_AUTO = 0, HIKF_CHAIN_FACTOR = 1, HIKF_CHAIN_SPECTRAL = 2 };
-enum { HIKF_FORM_CROSS = 0, HIKF_FORM_EIGEN = 1 };
+enum { HIKF_FORM_CROSS = 0, HIKF_FORM_EIGEN = 1, HIKF_FORM_NSPACE = 2 };
 
 /* Fill *opt with the defaults listed above. */
 hikf_status hikf_options_default(hikf_options* opt);
@@ -190,7 +200,7 @@ typedef struct {
   double create_ms;   /* wall time of the precomputation */
   int sweep_launches; /* kernel launches of one measurement update */
   int chain;          /* HIKF_CHAIN_FACTOR or HIKF_CHAIN_SPECTRAL: the form in use */
-  int form;           /* HIKF_FORM_CROSS or HIKF_FORM_EIGEN */
+  int form;           /* HIKF_FORM_CROSS, HIKF_FORM_EIGEN or HIKF_FORM_NSPACE */
 } hikf_info_t;
 
 hikf_status hikf_info(const hikf_t* h, hikf_info_t* info);

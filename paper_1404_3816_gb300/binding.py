@@ -24,8 +24,8 @@ PREC_FP32, PREC_MIXED, PREC_FP64 = 0, 1, 2
 PRECISIONS = {"fp32": PREC_FP32, "mixed": PREC_MIXED, "fp64": PREC_FP64}
 CHAIN_AUTO, CHAIN_FACTOR, CHAIN_SPECTRAL = 0, 1, 2
 CHAINS = {"auto": CHAIN_AUTO, "factor": CHAIN_FACTOR, "spectral": CHAIN_SPECTRAL}
-FORM_CROSS, FORM_EIGEN = 0, 1
-FORMS = {"cross": FORM_CROSS, "eigen": FORM_EIGEN}
+FORM_CROSS, FORM_EIGEN, FORM_NSPACE = 0, 1, 2
+FORMS = {"cross": FORM_CROSS, "eigen": FORM_EIGEN, "nspace": FORM_NSPACE}
 
 # every symbol include/hikf.h declares
 EXPORTED = ["hikf_options_default", "hikf_create", "hikf_create_with_cq", "hikf_assimilate",

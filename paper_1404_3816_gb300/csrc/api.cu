@@ -137,6 +137,12 @@ struct hikf_handle {
   hikf::SpectralState sp;
   hikf::TcState tc;
   bool eigen = false;
+  bool nspace = false;       // n-space form (HIKF_FORM_NSPACE): G = Gq diag(gamma)
+  hikf::NspaceState ns;
+  double* x0t = nullptr;     // x_0 in tree order (n-space form)
+  double var0 = 0.0;         // delta^2_0 = theta_0
+  long long enq = 0;         // updates enqueued (host count)
+  long long outs_at = -1;    // value of enq when x, delta^2 were last formed (n-space form)
   void* G = nullptr;   // eigenbasis state (HIKF_FORM_EIGEN), m x ld
   void* Gq = nullptr;  // C_Q W
   void* Msw = nullptr;
@@ -204,9 +210,10 @@ Status validate_common(int dim, int64_t m, const double* points, int n, const in
   if (o.precision != HIKF_PREC_FP32 && o.precision != HIKF_PREC_FP64 && o.precision != HIKF_PREC_MIXED)
     return make_status(HIKF_EINVAL, "unknown precision");
   if (o.chain < HIKF_CHAIN_AUTO || o.chain > HIKF_CHAIN_SPECTRAL) return make_status(HIKF_EINVAL, "unknown chain");
-  if (o.form != HIKF_FORM_CROSS && o.form != HIKF_FORM_EIGEN) return make_status(HIKF_EINVAL, "unknown form");
-  if (o.form == HIKF_FORM_EIGEN && o.precision == HIKF_PREC_MIXED)
-    return make_status(HIKF_EINVAL, "the eigenbasis form runs on the CUDA cores (FP32 or FP64)");
+  if (o.form != HIKF_FORM_CROSS && o.form != HIKF_FORM_EIGEN && o.form != HIKF_FORM_NSPACE)
+    return make_status(HIKF_EINVAL, "unknown form");
+  if (o.form != HIKF_FORM_CROSS && o.precision == HIKF_PREC_MIXED)
+    return make_status(HIKF_EINVAL, "the eigenbasis and n-space forms run on the CUDA cores (FP32 or FP64)");
   return Status::Ok();
 }
 
@@ -339,8 +346,9 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
   const bool can_spec = cq == nullptr && p0_is_cq;
   if (chain_opt == HIKF_CHAIN_SPECTRAL && !can_spec)
     return hikf::make_status(HIKF_EINVAL, "spectral chain needs P0 = c Q and a computed C_Q");
-  if (form_opt == HIKF_FORM_EIGEN && (!can_spec || chain_opt == HIKF_CHAIN_FACTOR))
-    return hikf::make_status(HIKF_EINVAL, "the eigenbasis form needs the spectral chain (P0 = c Q, computed C_Q)");
+  if (form_opt != HIKF_FORM_CROSS && (!can_spec || chain_opt == HIKF_CHAIN_FACTOR))
+    return hikf::make_status(HIKF_EINVAL,
+                             "the eigenbasis and n-space forms need the spectral chain (P0 = c Q, computed C_Q)");
   h->spectral = can_spec && chain_opt != HIKF_CHAIN_FACTOR;
   if (h->spectral) {
     hikf::SpectralState& sp = h->sp;
@@ -365,6 +373,31 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
       h->G = G;
       h->Gq = Gq;
       h->eigen = true;
+    } else if (form_opt == HIKF_FORM_NSPACE) {
+      T* Gq = nullptr;
+      HIKF_TRY(hikf::arena_alloc(h->arena, &Gq, (size_t)m * ld));
+      HIKF_TRY(hikf::eigen_setup<T>(sp, CQ, m, ld, n, cfac, Gq, (T*)nullptr, s));
+      h->Gq = Gq;
+      hikf::NspaceState& ns = h->ns;
+      HIKF_TRY(hikf::arena_alloc(h->arena, &ns.gam, n));
+      HIKF_TRY(hikf::arena_alloc(h->arena, &ns.b, n));
+      HIKF_TRY(hikf::arena_alloc(h->arena, &ns.h, n));
+      HIKF_TRY(hikf::arena_alloc(h->arena, &ns.P, nn));
+      HIKF_TRY(hikf::arena_alloc(h->arena, &ns.hx0, n));
+      HIKF_TRY(hikf::arena_alloc(h->arena, &h->x0t, m));
+      hikf::fill_kernel<<<hikf::nblk(n, 256), 256, 0, s>>>(ns.gam, n, cfac);
+      HIKF_LAUNCH_CHECK("fill");
+      HIKF_CUDA(cudaMemsetAsync(ns.b, 0, sizeof(double) * n, s));
+      HIKF_CUDA(cudaMemsetAsync(ns.h, 0, sizeof(double) * n, s));
+      HIKF_TRY(hikf::launch_gather_hc<T>(h->H, Gq, ld, ns.P, 0, s));
+      HIKF_CUDA(cudaMemcpyAsync(h->x0t, h->x, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+      // H x_0 = -(0 - H x_0)
+      HIKF_CUDA(cudaMemsetAsync(h->ybuf, 0, sizeof(double) * n, s));
+      HIKF_TRY(hikf::launch_innovation(h->ybuf, h->H, h->x, ns.hx0, h->flag, s));
+      hikf::scale_kernel<double><<<hikf::nblk(n, 256), 256, 0, s>>>(ns.hx0, ns.hx0, n, -1.0);
+      HIKF_LAUNCH_CHECK("scale");
+      h->var0 = p0.theta;
+      h->nspace = true;
     }
   }
   if (h->mixed()) {
@@ -386,6 +419,13 @@ Status enqueue_step(hikf_t* h, cudaEvent_t ev0, cudaEvent_t ev1) {
   cudaStream_t s = h->stream;
   hikf::ChainArgs& c = h->chain;
   int launches = 0;
+  if (h->nspace) {
+    if (ev0) HIKF_CUDA(cudaEventRecordWithFlags(ev0, s, h->capturing ? cudaEventRecordExternal : 0));
+    HIKF_TRY(hikf::nspace_step(h->sp, h->ns, h->n, h->ybuf, h->e, h->flag, h->dstep, s));
+    if (ev1) HIKF_CUDA(cudaEventRecordWithFlags(ev1, s, h->capturing ? cudaEventRecordExternal : 0));
+    h->launches = 3;
+    return Status::Ok();
+  }
   if (h->eigen) {
     HIKF_TRY(hikf::launch_innovation(h->ybuf, h->H, h->x, h->e, h->flag, s));
     HIKF_TRY(hikf::eigen_u(h->sp, h->n, h->e, h->flag, s));
@@ -434,7 +474,6 @@ Status enqueue_step(hikf_t* h, cudaEvent_t ev0, cudaEvent_t ev1) {
     ta.ld = h->ld;
     ta.n = h->n;
     ta.C = (float*)h->C;
-    ta.CQ = (const float*)h->CQ;
     ta.a = h->a;
     ta.rd = h->rd;
     ta.theta = h->theta_q;
@@ -512,6 +551,18 @@ Status enqueue(hikf_t* h) {
     HIKF_CUDA(cudaGraphLaunch(h->graph_exec, h->stream));
   }
   if (rec) ++h->prof_count;
+  ++h->enq;
+  return Status::Ok();
+}
+
+// n-space form: form x and delta^2 of the current state (once per state)
+Status form_outputs(hikf_t* h) {
+  if (!h->nspace || h->outs_at == h->enq) return Status::Ok();
+  HIKF_TRY(h->fp64() ? hikf::nspace_outputs<double>(h->ns, (const double*)h->Gq, h->m, h->ld, h->n, h->x0t,
+                                                     h->var0, h->theta_q, h->dstep, h->x, h->var, h->sms, h->stream)
+                     : hikf::nspace_outputs<float>(h->ns, (const float*)h->Gq, h->m, h->ld, h->n, h->x0t, h->var0,
+                                                    h->theta_q, h->dstep, h->x, h->var, h->sms, h->stream));
+  h->outs_at = h->enq;
   return Status::Ok();
 }
 
@@ -672,6 +723,8 @@ hikf_status hikf_sync(hikf_t* h) {
 
 static hikf_status get_vec(hikf_t* h, const double* src, double* out, bool device) {
   if (!h || !out) return h ? fail(h, hikf::make_status(HIKF_EINVAL, "out is NULL")) : HIKF_EINVAL;
+  Status fs = form_outputs(h);
+  if (!fs.ok()) return fail(h, fs);
   hikf::vec_to_caller<<<hikf::nblk(h->m, 256), 256, 0, h->stream>>>(src, h->tree.perm, h->m,
                                                                      device ? out : h->outbuf);
   cudaError_t e = cudaGetLastError();
@@ -721,6 +774,14 @@ hikf_status hikf_get_cross(hikf_t* h, double* out) {
                                                       (const float*)h->Gq, (float*)h->C, h->stream);
     if (!st.ok()) return fail(h, st);
   }
+  if (h && h->nspace) {
+    // C_{t|t} = Gq diag(gamma) W^T R, formed on request into the C buffer (unused by this form)
+    Status st = h->fp64() ? hikf::nspace_cross<double>(h->sp, h->ns, h->rd, h->m, h->ld, h->n, (const double*)h->Gq,
+                                                        (double*)h->C, h->stream)
+                          : hikf::nspace_cross<float>(h->sp, h->ns, h->rd, h->m, h->ld, h->n, (const float*)h->Gq,
+                                                       (float*)h->C, h->stream);
+    if (!st.ok()) return fail(h, st);
+  }
   return get_mat(h, h ? h->C : nullptr, out);
 }
 
@@ -749,7 +810,7 @@ hikf_status hikf_info(const hikf_t* h, hikf_info_t* info) {
   info->create_ms = h->create_ms;
   info->sweep_launches = h->launches;
   info->chain = h->spectral ? HIKF_CHAIN_SPECTRAL : HIKF_CHAIN_FACTOR;
-  info->form = h->eigen ? HIKF_FORM_EIGEN : HIKF_FORM_CROSS;
+  info->form = h->nspace ? HIKF_FORM_NSPACE : (h->eigen ? HIKF_FORM_EIGEN : HIKF_FORM_CROSS);
   return HIKF_OK;
 }
 

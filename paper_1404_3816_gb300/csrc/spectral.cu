@@ -12,9 +12,12 @@
 // step, whose FP64 cost and conditioning (cond(S) ~ 1e8 and more) would
 // otherwise dominate the update.
 //
-// Eigensolver: Householder reduction to tridiagonal form, explicit
-// accumulation of the orthogonal factor, then implicit symmetric QR steps with
-// Wilkinson shifts (Golub & Van Loan, Sec. 8.3), all on one CTA in FP64.
+// Eigensolver (FP64): Householder reduction to tridiagonal form on one CTA;
+// implicit symmetric QR steps with Wilkinson shifts (Golub & Van Loan, Sec. 8.3)
+// chased by one thread, which only records the rotations; then the eigenvectors
+// V = Q G_1 G_2 ... row by row over many CTAs (rows are independent). The FP64
+// rate per SM is low on this part, so the O(n^3) work is spread over SMs and
+// the serial chase does O(n^2) work only.
 #include <math.h>
 
 #include <algorithm>
@@ -39,17 +42,16 @@ __device__ double block_sum(double v, double* red) {
   return s;
 }
 
-// A (n x n, row-major, symmetric; destroyed), outputs lam (n) and V (n x n, columns = eigenvectors).
-// hv: n x n scratch for the Householder vectors. info = 1 when QR did not converge.
-__global__ void __launch_bounds__(kEigThreads) eig_sym_kernel(double* __restrict__ A, int n, double* __restrict__ lam,
-                                                              double* __restrict__ V, double* __restrict__ hv,
-                                                              int* __restrict__ info) {
+// ---- 1. Householder tridiagonalisation (one CTA) --------------------------
+// A (n x n, row-major, symmetric; destroyed) -> T = Q^T A Q with diagonal d and
+// sub-diagonal e; Q = H_0 H_1 ... H_{n-3}, H_k = I - 2 v_k v_k^T with v_k (unit,
+// zero at indices <= k) stored as row k of hv.
+__global__ void __launch_bounds__(kEigThreads) eig_tridiag_kernel(double* __restrict__ A, int n,
+                                                                 double* __restrict__ d, double* __restrict__ e,
+                                                                 double* __restrict__ hv) {
   __shared__ double red[32];
-  __shared__ double sv[kMaxN], sw[kMaxN], ssub[kMaxN];
-  __shared__ double rc[kMaxN], rs[kMaxN];
-  __shared__ int s_l, s_m, s_done;
+  __shared__ double sv[kMaxN], sw[kMaxN];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  // ---- Householder tridiagonalisation -------------------------------------
   for (int k = 0; k + 2 < n; ++k) {
     double part = 0.0;
     for (int i = k + 1 + tid; i < n; i += blockDim.x) {
@@ -62,7 +64,7 @@ __global__ void __launch_bounds__(kEigThreads) eig_sym_kernel(double* __restrict
     double* vk = hv + (int64_t)k * n;
     if (tail <= 0.0) {  // already tridiagonal in this column: H_k = I
       for (int i = tid; i < n; i += blockDim.x) vk[i] = 0.0;
-      if (tid == 0) ssub[k] = x0;
+      if (tid == 0) e[k] = x0;
       __syncthreads();
       continue;
     }
@@ -76,7 +78,7 @@ __global__ void __launch_bounds__(kEigThreads) eig_sym_kernel(double* __restrict
       sv[i] = v;
       vk[i] = v;
     }
-    if (tid == 0) ssub[k] = alpha;
+    if (tid == 0) e[k] = alpha;
     __syncthreads();
     // w = A_sub v (rows k+1..n-1), warp per row
     for (int i = k + 1 + warp; i < n; i += nw) {
@@ -98,109 +100,118 @@ __global__ void __launch_bounds__(kEigThreads) eig_sym_kernel(double* __restrict
     }
     __syncthreads();
   }
-  // diagonal and sub-diagonal of T
-  double* d = lam;
   for (int i = tid; i < n; i += blockDim.x) d[i] = A[(int64_t)i * n + i];
-  if (tid == 0 && n >= 2) ssub[n - 2] = A[(int64_t)(n - 1) * n + (n - 2)];
-  __syncthreads();
-  // ---- Q = H_0 H_1 ... H_{n-3}, accumulated backwards into V ---------------
-  for (int64_t t = tid; t < (int64_t)n * n; t += blockDim.x) V[t] = (t / n == t % n) ? 1.0 : 0.0;
-  __syncthreads();
-  for (int k = n - 3; k >= 0; --k) {
-    const double* vk = hv + (int64_t)k * n;
-    for (int i = tid; i < n; i += blockDim.x) sv[i] = vk[i];
-    __syncthreads();
-    // y_j = sum_i v_i V[i][j], j > k (warp per column)
-    for (int j = k + 1 + warp; j < n; j += nw) {
-      double s = 0.0;
-      for (int i = k + 1 + lane; i < n; i += 32) s += sv[i] * V[(int64_t)i * n + j];
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) sw[j] = s;
-    }
-    __syncthreads();
-    const int len = n - k - 1;
-    for (int64_t t = tid; t < (int64_t)len * len; t += blockDim.x) {
-      int i = k + 1 + (int)(t / len), j = k + 1 + (int)(t % len);
-      V[(int64_t)i * n + j] -= 2.0 * sv[i] * sw[j];
-    }
-    __syncthreads();
-  }
-  // ---- implicit symmetric QR with Wilkinson shifts on (d, ssub) ------------
-  // thread 0 chases the bulge and records the rotations; every thread applies
-  // them to its own rows of V (V <- V G).
-  if (tid == 0) {
-    s_m = n - 1;
-    s_done = 0;
-    *info = 0;
-  }
-  __syncthreads();
+  if (tid == 0 && n >= 2) e[n - 2] = A[(int64_t)(n - 1) * n + (n - 2)];
+}
+
+// ---- 2. implicit symmetric QR with Wilkinson shifts on (d, e), one thread ----
+// (Golub & Van Loan, Alg. 8.3.2 with deflation.) The chase does not need the
+// eigenvectors: it records every Givens rotation (c, s) in order, and the active
+// block [l, m] of every sweep, for the row-parallel back-transformation.
+// Capacity: at most max_sweeps sweeps of at most n - 1 rotations each.
+__global__ void eig_qr_chase_kernel(double* __restrict__ d, double* __restrict__ e, int n, int max_sweeps,
+                                    double2* __restrict__ rot, int2* __restrict__ sweep_lm,
+                                    int* __restrict__ nsweeps, int* __restrict__ info) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const double eps = 2.220446049250313e-16;
-  int iters = 0;
-  const int max_iters = 40 * n + 100;
+  int m = n - 1, ns = 0;
+  int64_t nr = 0;
+  *info = 0;
   while (true) {
-    if (tid == 0) {
-      int m = s_m;
-      // deflate converged bottom entries
-      while (m > 0 && fabs(ssub[m - 1]) <= eps * (fabs(d[m - 1]) + fabs(d[m]))) {
-        ssub[m - 1] = 0.0;
-        --m;
-      }
-      s_m = m;
-      if (m == 0) {
-        s_done = 1;
-      } else {
-        int l = m - 1;
-        while (l > 0 && fabs(ssub[l - 1]) > eps * (fabs(d[l - 1]) + fabs(d[l]))) --l;
-        s_l = l;
-        // Wilkinson shift from the trailing 2 x 2 block
-        const double a = d[m - 1], b = ssub[m - 1], c2 = d[m];
-        const double delta = 0.5 * (a - c2);
-        const double sgn = delta >= 0.0 ? 1.0 : -1.0;
-        const double mu = c2 - b * b / (delta + sgn * hypot(delta, b));
-        double x = d[l] - mu, z = ssub[l];
-        for (int k = l; k < m; ++k) {
-          const double r = hypot(x, z);
-          double c = 1.0, s = 0.0;
-          if (r > 0.0) {
-            c = x / r;
-            s = z / r;
-          }
-          if (k > l) ssub[k - 1] = r;
-          const double ak = d[k], bk = ssub[k], ck = d[k + 1];
-          d[k] = ak * c * c + 2.0 * bk * c * s + ck * s * s;
-          d[k + 1] = ak * s * s - 2.0 * bk * c * s + ck * c * c;
-          ssub[k] = (ck - ak) * c * s + bk * (c * c - s * s);
-          if (k + 1 < m) {
-            const double f = ssub[k + 1];
-            z = f * s;
-            ssub[k + 1] = f * c;
-          }
-          x = ssub[k];
-          rc[k] = c;
-          rs[k] = s;
-        }
-      }
+    while (m > 0 && fabs(e[m - 1]) <= eps * (fabs(d[m - 1]) + fabs(d[m]))) {
+      e[m - 1] = 0.0;
+      --m;
     }
-    __syncthreads();
-    if (s_done) break;
-    const int l = s_l, m = s_m;
-    for (int row = tid; row < n; row += blockDim.x) {
-      double* vr = V + (int64_t)row * n;
-      double vk = vr[l];
-      for (int k = l; k < m; ++k) {
-        const double vk1 = vr[k + 1];
-        const double c = rc[k], s = rs[k];
-        vr[k] = c * vk + s * vk1;
-        vk = -s * vk + c * vk1;
-      }
-      vr[m] = vk;
-    }
-    __syncthreads();
-    if (++iters > max_iters) {
-      if (tid == 0) *info = 1;
+    if (m == 0) break;
+    if (ns >= max_sweeps) {
+      *info = 1;
       break;
     }
+    int l = m - 1;
+    while (l > 0 && fabs(e[l - 1]) > eps * (fabs(d[l - 1]) + fabs(d[l]))) --l;
+    // Wilkinson shift from the trailing 2 x 2 block
+    const double a = d[m - 1], b = e[m - 1], c2 = d[m];
+    const double delta = 0.5 * (a - c2);
+    const double sgn = delta >= 0.0 ? 1.0 : -1.0;
+    const double mu = c2 - b * b / (delta + sgn * hypot(delta, b));
+    double x = d[l] - mu, z = e[l];
+    for (int k = l; k < m; ++k) {
+      // r = |(x, z)|, c = x / r, s = z / r: one reciprocal square root where x^2 + z^2
+      // is safely inside the normal range (always, for the matrices of this library),
+      // hypot and a division otherwise
+      const double t2 = fma(x, x, z * z);
+      double r, c = 1.0, s = 0.0;
+      if (t2 > 1e-290 && t2 < 1e290) {
+        const double ir = rsqrt(t2);
+        r = t2 * ir;
+        c = x * ir;
+        s = z * ir;
+      } else {
+        r = hypot(x, z);
+        if (r > 0.0) {
+          c = x / r;
+          s = z / r;
+        }
+      }
+      if (k > l) e[k - 1] = r;
+      const double ak = d[k], bk = e[k], ck = d[k + 1];
+      d[k] = ak * c * c + 2.0 * bk * c * s + ck * s * s;
+      d[k + 1] = ak * s * s - 2.0 * bk * c * s + ck * c * c;
+      e[k] = (ck - ak) * c * s + bk * (c * c - s * s);
+      if (k + 1 < m) {
+        const double f = e[k + 1];
+        z = f * s;
+        e[k + 1] = f * c;
+      }
+      x = e[k];
+      rot[nr++] = make_double2(c, s);
+    }
+    sweep_lm[ns++] = make_int2(l, m);
   }
+  *nsweeps = ns;
+}
+
+// ---- 3. eigenvectors V = H_0 ... H_{n-3} G_1 G_2 ... , one thread per row ----
+// Row i of V is e_i^T times the product; each factor acts on a row independently,
+// so the rows are spread over many CTAs (each row held in shared memory).
+constexpr int kVecRows = 8;  // rows (threads) per CTA
+__global__ void __launch_bounds__(kVecRows) eig_vectors_kernel(const double* __restrict__ hv,
+                                                               const double2* __restrict__ rot,
+                                                               const int2* __restrict__ sweep_lm,
+                                                               const int* __restrict__ nsweeps,
+                                                               const int* __restrict__ info, int n,
+                                                               double* __restrict__ V) {
+  extern __shared__ double srow[];  // kVecRows x (n + 1)
+  const int i = blockIdx.x * kVecRows + threadIdx.x;
+  if (*info || i >= n) return;
+  double* vr = srow + threadIdx.x * (n + 1);
+  for (int j = 0; j < n; ++j) vr[j] = j == i ? 1.0 : 0.0;
+  // row <- row (I - 2 v_k v_k^T), k = 0 .. n-3
+  for (int k = 0; k + 2 < n; ++k) {
+    const double* vk = hv + (int64_t)k * n;
+    double dot = 0.0;
+    for (int j = k + 1; j < n; ++j) dot += vr[j] * vk[j];
+    const double t = 2.0 * dot;
+    if (t != 0.0)
+      for (int j = k + 1; j < n; ++j) vr[j] -= t * vk[j];
+  }
+  // row <- row G, sweep by sweep, rotations in recorded order
+  const int ns = *nsweeps;
+  int64_t off = 0;
+  for (int sw = 0; sw < ns; ++sw) {
+    const int2 lm = sweep_lm[sw];
+    double vk = vr[lm.x];
+#pragma unroll 4
+    for (int k = lm.x; k < lm.y; ++k) {
+      const double2 cs = rot[off + (k - lm.x)];
+      const double vk1 = vr[k + 1];
+      vr[k] = cs.x * vk + cs.y * vk1;
+      vk = -cs.y * vk + cs.x * vk1;
+    }
+    vr[lm.y] = vk;
+    off += lm.y - lm.x;
+  }
+  for (int j = 0; j < n; ++j) V[(int64_t)i * n + j] = vr[j];
 }
 
 // B~ = D sym(HCQ) D with D = R^{-1/2}
@@ -348,25 +359,41 @@ inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
 Status spectral_setup(SpectralState& sp, const double* hcq_sym, const double* rd, int n, double c, int* flag,
                       cudaStream_t s) {
   const int64_t nn = (int64_t)n * n;
-  double *A = nullptr, *V = nullptr, *hv = nullptr;
-  int* info = nullptr;
+  const int max_sweeps = 40 * n + 100;
+  const int64_t max_rot = (int64_t)max_sweeps * std::max(1, n - 1);
+  double *A = nullptr, *V = nullptr, *hv = nullptr, *e = nullptr;
+  double2* rot = nullptr;
+  int2* lm = nullptr;
+  int* ints = nullptr;  // info, nsweeps
   HIKF_CUDA(cudaMallocAsync((void**)&A, sizeof(double) * nn, s));
   HIKF_CUDA(cudaMallocAsync((void**)&V, sizeof(double) * nn, s));
   HIKF_CUDA(cudaMallocAsync((void**)&hv, sizeof(double) * nn, s));
-  HIKF_CUDA(cudaMallocAsync((void**)&info, sizeof(int), s));
+  HIKF_CUDA(cudaMallocAsync((void**)&e, sizeof(double) * n, s));
+  HIKF_CUDA(cudaMallocAsync((void**)&rot, sizeof(double2) * max_rot, s));
+  HIKF_CUDA(cudaMallocAsync((void**)&lm, sizeof(int2) * max_sweeps, s));
+  HIKF_CUDA(cudaMallocAsync((void**)&ints, 2 * sizeof(int), s));
+  HIKF_CUDA(cudaMemsetAsync(e, 0, sizeof(double) * n, s));
   scale_b_kernel<<<nblk(nn, 256), 256, 0, s>>>(hcq_sym, rd, n, A);
   HIKF_LAUNCH_CHECK("scale_b");
-  eig_sym_kernel<<<1, kEigThreads, 0, s>>>(A, n, sp.lam, V, hv, info);
-  HIKF_LAUNCH_CHECK("eig_sym");
+  eig_tridiag_kernel<<<1, kEigThreads, 0, s>>>(A, n, sp.lam, e, hv);
+  HIKF_LAUNCH_CHECK("eig_tridiag");
+  eig_qr_chase_kernel<<<1, 32, 0, s>>>(sp.lam, e, n, max_sweeps, rot, lm, ints + 1, ints);
+  HIKF_LAUNCH_CHECK("eig_qr_chase");
+  const size_t vsmem = sizeof(double) * kVecRows * (size_t)(n + 1);
+  eig_vectors_kernel<<<nblk(n, kVecRows), kVecRows, vsmem, s>>>(hv, rot, lm, ints + 1, ints, n, V);
+  HIKF_LAUNCH_CHECK("eig_vectors");
   spec_init_kernel<<<nblk(nn, 256), 256, 0, s>>>(V, sp.lam, rd, n, c, sp.W64, sp.W32, sp.s, flag);
   HIKF_LAUNCH_CHECK("spec_init");
   int hinfo = 0;
-  HIKF_CUDA(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, s));
+  HIKF_CUDA(cudaMemcpyAsync(&hinfo, ints, sizeof(int), cudaMemcpyDeviceToHost, s));
   HIKF_CUDA(cudaStreamSynchronize(s));
   HIKF_CUDA(cudaFreeAsync(A, s));
   HIKF_CUDA(cudaFreeAsync(V, s));
   HIKF_CUDA(cudaFreeAsync(hv, s));
-  HIKF_CUDA(cudaFreeAsync(info, s));
+  HIKF_CUDA(cudaFreeAsync(e, s));
+  HIKF_CUDA(cudaFreeAsync(rot, s));
+  HIKF_CUDA(cudaFreeAsync(lm, s));
+  HIKF_CUDA(cudaFreeAsync(ints, s));
   if (hinfo) return make_status(HIKF_ECUDA, "eigensolver did not converge");
   return Status::Ok();
 }
@@ -617,8 +644,10 @@ Status eigen_setup(const SpectralState& sp, const T* CQ, int64_t m, int ld, int 
   dim3 grid((unsigned)((m + 63) / 64), (unsigned)((ld + 63) / 64));
   gemm_tn_kernel<T, double><<<grid, 256, 0, s>>>(m, n, n, CQ, ld, sp.W64, n, Gq, ld, 0, nullptr);
   HIKF_LAUNCH_CHECK("gemm Gq");
-  scale_copy_kernel<T><<<nb(m * ld, 256), 256, 0, s>>>(Gq, G, m * ld, c);  // C_0 W = c C_Q W
-  HIKF_LAUNCH_CHECK("scale G");
+  if (G) {
+    scale_copy_kernel<T><<<nb(m * ld, 256), 256, 0, s>>>(Gq, G, m * ld, c);  // C_0 W = c C_Q W
+    HIKF_LAUNCH_CHECK("scale G");
+  }
   return Status::Ok();
 }
 template Status eigen_setup<float>(const SpectralState&, const float*, int64_t, int, int, double, float*, float*,
@@ -675,5 +704,187 @@ template Status eigen_cross<float>(const SpectralState&, const double*, int64_t,
                                    float*, cudaStream_t);
 template Status eigen_cross<double>(const SpectralState&, const double*, int64_t, int, int, const double*,
                                     const double*, double*, cudaStream_t);
+
+}  // namespace hikf
+
+// ---------------------------------------------------------------------------
+// n-space form. Under the spectral condition with P_0 = c Q the rotated state is
+// G_{t|t} = Gq diag(gamma_t) with Gq = C_Q W fixed: G_0 = c Gq, and one step maps
+// G_p = G + Gq = Gq diag(gamma + 1) to G_p diag(g_t), so gamma_{t} = (gamma_{t-1} + 1) g_t.
+// The mean and the variance then stay linear in Gq:
+//   x_t = x_0 + Gq b_t,              b_t = b_{t-1} + (gamma_{t-1} + 1) o u_t,
+//   delta^2_t = delta^2_0 + t theta - sum_k h_k,t Gq_ik^2,   h_t = h_{t-1} + g_t o (gamma_{t-1} + 1)^2,
+// and the innovation needs only H x_t = H x_0 + (H Gq) b_t. A step is O(n^2) (two n x n
+// products, no pass over the m rows); x and delta^2 are formed on request in one pass
+// over Gq, and C_{t|t} = Gq diag(gamma) W^T R likewise.
+// ---------------------------------------------------------------------------
+namespace hikf {
+namespace {
+
+// e = y - H x_0 - P b  (P = H Gq, n x n), one warp per row; non-finite y -> flag bit 1
+__global__ void nspace_innovation_kernel(const double* __restrict__ y, const double* __restrict__ hx0,
+                                         const double* __restrict__ P, const double* __restrict__ b, int n,
+                                         double* __restrict__ e, int* __restrict__ flag) {
+  const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (r >= n) return;
+  double acc = 0.0;
+  for (int c = lane; c < n; c += 32) acc += P[(int64_t)r * n + c] * b[c];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) {
+    const double yv = y[r];
+    if (!isfinite(yv)) atomicOr(flag, 1);
+    e[r] = yv - hx0[r] - acc;
+  }
+}
+
+// per eigen-direction: b += (gamma + 1) u, h += g (gamma + 1)^2, gamma <- (gamma + 1) g,
+// s <- lambda + 2 - g (u = g W^T e is already formed); counts the applied step
+__global__ void nspace_update_kernel(const double* __restrict__ lam, double* __restrict__ s,
+                                     const double* __restrict__ u, double* __restrict__ gam, double* __restrict__ b,
+                                     double* __restrict__ h, int n, const int* __restrict__ flag,
+                                     long long* __restrict__ step) {
+  if (*flag) return;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k == 0) *step += 1;
+  if (k >= n) return;
+  const double g = 1.0 / s[k];
+  const double gp = gam[k] + 1.0;
+  b[k] += gp * u[k];
+  h[k] += g * gp * gp;
+  gam[k] = gp * g;
+  s[k] = lam[k] + 2.0 - g;
+}
+
+// double-float helpers (FP32 pairs): error-free sum and product
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void dd_add(float& sh, float& sl, float ph, float pl) {
+  float s, e;
+  two_sum(sh, ph, s, e);
+  e += sl + pl;
+  sh = s + e;
+  sl = e - (sh - s);
+}
+
+// x = x_0 + Gq b, delta^2 = delta^2_0 + t theta - sum_k h_k Gq_ik^2 (FP32 Gq, double-float
+// products and sums, FP64 result). One warp per row, lanes over the columns.
+template <typename T>
+__global__ void __launch_bounds__(256) nspace_outputs_kernel(const T* __restrict__ Gq, int64_t m, int ld, int n,
+                                                             const double* __restrict__ x0, double var0,
+                                                             double theta, const long long* __restrict__ step,
+                                                             const double* __restrict__ b,
+                                                             const double* __restrict__ h, double* __restrict__ x,
+                                                             double* __restrict__ var) {
+  __shared__ float sbh[kMaxN], sbl[kMaxN], shh[kMaxN], shl[kMaxN];
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    sbh[k] = (float)b[k];
+    sbl[k] = (float)(b[k] - (double)sbh[k]);
+    shh[k] = (float)h[k];
+    shl[k] = (float)(h[k] - (double)shh[k]);
+  }
+  __syncthreads();
+  const double tq = (double)*step * theta;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < m; i += warps) {
+    const T* gr = Gq + i * ld;
+    double xs, vs;
+    if (sizeof(T) == 8) {
+      double ax = 0.0, av = 0.0;
+      for (int k = lane; k < n; k += 32) {
+        const double gv = (double)gr[k];
+        ax = fma(gv, b[k], ax);
+        av = fma(gv * gv, h[k], av);
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        ax += __shfl_xor_sync(0xffffffffu, ax, o);
+        av += __shfl_xor_sync(0xffffffffu, av, o);
+      }
+      xs = ax;
+      vs = av;
+    } else {
+      float xh = 0.f, xl = 0.f, vh = 0.f, vl = 0.f;
+      for (int k = lane; k < n; k += 32) {
+        const float gv = (float)gr[k];
+        // Gq b: exact product with the high part, plain product with the low part
+        const float p = gv * sbh[k];
+        dd_add(xh, xl, p, fmaf(gv, sbh[k], -p) + gv * sbl[k]);
+        // h Gq^2: Gq^2 exactly as (qh, ql), times (hh, hl)
+        const float qh = gv * gv;
+        const float ql = fmaf(gv, gv, -qh);
+        const float r = qh * shh[k];
+        dd_add(vh, vl, r, fmaf(qh, shh[k], -r) + (qh * shl[k] + ql * shh[k]));
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const float oxh = __shfl_xor_sync(0xffffffffu, xh, o), oxl = __shfl_xor_sync(0xffffffffu, xl, o);
+        const float ovh = __shfl_xor_sync(0xffffffffu, vh, o), ovl = __shfl_xor_sync(0xffffffffu, vl, o);
+        dd_add(xh, xl, oxh, oxl);
+        dd_add(vh, vl, ovh, ovl);
+      }
+      xs = (double)xh + (double)xl;
+      vs = (double)vh + (double)vl;
+    }
+    if (lane == 0) {
+      x[i] = x0[i] + xs;
+      var[i] = (var0 + tq) - vs;
+    }
+  }
+}
+
+// B = diag(gamma) W^T R (n x n): B[k][j] = gamma_k W[j][k] r_j
+__global__ void nspace_wtr_kernel(const double* __restrict__ W64, const double* __restrict__ rd,
+                                  const double* __restrict__ gam, int n, double* __restrict__ out) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * n) return;
+  int k = (int)(t / n), j = (int)(t % n);
+  out[t] = gam[k] * W64[(int64_t)j * n + k] * rd[j];
+}
+
+}  // namespace
+
+Status nspace_step(const SpectralState& sp, const NspaceState& ns, int n, const double* y, double* e, int* flag,
+                   long long* step, cudaStream_t s) {
+  nspace_innovation_kernel<<<nb((int64_t)n * 32, 256), 256, 0, s>>>(y, ns.hx0, ns.P, ns.b, n, e, flag);
+  HIKF_LAUNCH_CHECK("nspace_innovation");
+  spec_u_kernel<<<nb((int64_t)n * 32, 256), 256, 0, s>>>(sp.W64, sp.s, e, n, sp.u, flag);
+  HIKF_LAUNCH_CHECK("spec_u");
+  nspace_update_kernel<<<nb(n, 256), 256, 0, s>>>(sp.lam, sp.s, sp.u, ns.gam, ns.b, ns.h, n, flag, step);
+  HIKF_LAUNCH_CHECK("nspace_update");
+  return Status::Ok();
+}
+
+template <typename T>
+Status nspace_outputs(const NspaceState& ns, const T* Gq, int64_t m, int ld, int n, const double* x0, double var0,
+                      double theta, const long long* step, double* x, double* var, int sms, cudaStream_t s) {
+  const int64_t blocks = std::min<int64_t>((m + 7) / 8, (int64_t)sms * 8);
+  nspace_outputs_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(Gq, m, ld, n, x0, var0, theta, step, ns.b, ns.h, x, var);
+  HIKF_LAUNCH_CHECK("nspace_outputs");
+  return Status::Ok();
+}
+template Status nspace_outputs<float>(const NspaceState&, const float*, int64_t, int, int, const double*, double,
+                                      double, const long long*, double*, double*, int, cudaStream_t);
+template Status nspace_outputs<double>(const NspaceState&, const double*, int64_t, int, int, const double*, double,
+                                       double, const long long*, double*, double*, int, cudaStream_t);
+
+template <typename T>
+Status nspace_cross(const SpectralState& sp, const NspaceState& ns, const double* rd, int64_t m, int ld, int n,
+                    const T* Gq, T* out, cudaStream_t s) {
+  double* B = nullptr;
+  HIKF_CUDA(cudaMallocAsync((void**)&B, sizeof(double) * (size_t)n * n, s));
+  nspace_wtr_kernel<<<nb((int64_t)n * n, 256), 256, 0, s>>>(sp.W64, rd, ns.gam, n, B);
+  HIKF_LAUNCH_CHECK("nspace_wtr");
+  dim3 grid((unsigned)((m + 63) / 64), (unsigned)((ld + 63) / 64));
+  gemm_tn_kernel<T, double><<<grid, 256, 0, s>>>(m, n, n, Gq, ld, B, n, out, ld, 0, nullptr);
+  HIKF_LAUNCH_CHECK("gemm nspace cross");
+  HIKF_CUDA(cudaFreeAsync(B, s));
+  return Status::Ok();
+}
+template Status nspace_cross<float>(const SpectralState&, const NspaceState&, const double*, int64_t, int, int,
+                                    const float*, float*, cudaStream_t);
+template Status nspace_cross<double>(const SpectralState&, const NspaceState&, const double*, int64_t, int, int,
+                                     const double*, double*, cudaStream_t);
 
 }  // namespace hikf

@@ -34,6 +34,26 @@ Status eigen_u(const SpectralState& sp, int n, const double* e, const int* flag,
 template <typename T>
 Status eigen_step(const SpectralState& sp, int64_t m, int ld, int n, T* G, const T* Gq, double theta, double* x,
                   double* var, const int* flag, int sms, cudaStream_t s);
+// n-space form: G_{t|t} = Gq diag(gamma), x = x_0 + Gq b, delta^2 = delta^2_0 + t theta - Gq^2 h
+struct NspaceState {
+  double* gam = nullptr;  // n, gamma_t (gamma_0 = c)
+  double* b = nullptr;    // n, mean coefficients
+  double* h = nullptr;    // n, variance coefficients
+  double* P = nullptr;    // n x n, H Gq
+  double* hx0 = nullptr;  // n, H x_0
+};
+// one step: e = y - H x_0 - P b, u = (W^T e) / s, the coefficient updates and s_{t+1}
+Status nspace_step(const SpectralState& sp, const NspaceState& ns, int n, const double* y, double* e, int* flag,
+                   long long* step, cudaStream_t s);
+// x and delta^2 of the current state, one pass over Gq
+template <typename T>
+Status nspace_outputs(const NspaceState& ns, const T* Gq, int64_t m, int ld, int n, const double* x0, double var0,
+                      double theta, const long long* step, double* x, double* var, int sms, cudaStream_t s);
+// C_{t|t} = Gq diag(gamma) W^T R
+template <typename T>
+Status nspace_cross(const SpectralState& sp, const NspaceState& ns, const double* rd, int64_t m, int ld, int n,
+                    const T* Gq, T* out, cudaStream_t s);
+
 // the current C_{t|t} = G W^T R
 template <typename T>
 Status eigen_cross(const SpectralState& sp, const double* rd, int64_t m, int ld, int n, const T* G, const T* Gq,

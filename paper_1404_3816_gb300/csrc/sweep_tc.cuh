@@ -13,7 +13,6 @@ struct TcArgs {
   int ld = 0;
   int n = 0;
   float* C = nullptr;           // m x ld, updated in place (written as K R)
-  const float* CQ = nullptr;    // m x ld (read by the epilogue; the converter reads it by TMA)
   const double* a = nullptr;    // n
   const double* rd = nullptr;   // n, diag R
   double theta = 0.0;           // diag Q

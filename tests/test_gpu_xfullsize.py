@@ -70,11 +70,11 @@ def gauss_case():
     return w, Y, ref
 
 
-@pytest.mark.parametrize("prec,form", [("fp64", "cross"), ("fp32", "eigen")])
+@pytest.mark.parametrize("prec,form", [("fp64", "cross"), ("fp32", "eigen"), ("fp32", "nspace")])
 def test_m2p20_gaussian_full_pipeline(B, gauss_case, prec, form):
     """H^2 product + updates at full size. The Gaussian kernel of length 64 makes
     cond(H C + R) too large for the FP32 explicit-inverse sweep, so the FP32 check
-    runs the eigenbasis form; the cross-covariance form is checked in FP64."""
+    runs the eigenbasis and n-space forms; the cross-covariance form is checked in FP64."""
     import torch
     w, Y, ref = gauss_case
     with B.Filter.from_workload(w, precision=prec, form=form) as f:
