@@ -135,22 +135,28 @@ def peaks():
         "fallback"
 
 
-def source_hash() -> str:
+# source files of each timed kernel: a committed traffic figure counts only while they are unchanged
+KERNEL_SOURCES = {"mixed": ("sweep_tc.cu", "tc_ptx.cuh"), "fp32": ("step.cu",), "eigen": ("spectral.cu",),
+                  "nspace": ("spectral.cu",)}
+
+
+def source_hash(kind: str) -> str:
     h = hashlib.sha256()
-    for f in ("step.cu", "sweep_tc.cu", "spectral.cu"):
+    for f in KERNEL_SOURCES[kind]:
         p = ROOT / "paper_1404_3816_gb300" / "csrc" / f
         if p.exists():
             h.update(p.read_bytes())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(precision: str, n: int):
-    """DRAM bytes per sweep launch from the committed ncu summary, if the source is unchanged."""
-    p = ROOT / "profiles" / f"sweep_{precision}_m1048576_n{n}.json"
+def ncu_traffic(kind: str, n: int):
+    """DRAM bytes per launch of the timed kernel from the committed ncu summary
+    (profiles/traffic_<kind>_m1048576_n<n>.json), if its source is unchanged."""
+    p = ROOT / "profiles" / f"traffic_{kind}_m1048576_n{n}.json"
     if not p.exists():
         return None
     d = json.loads(p.read_text())
-    if d.get("source_hash") != source_hash():
+    if d.get("source_hash") != source_hash(kind):
         return None
     return d.get("dram_bytes_per_launch")
 

@@ -769,67 +769,100 @@ __device__ __forceinline__ void dd_add(float& sh, float& sl, float ph, float pl)
   sl = e - (sh - s);
 }
 
-// x = x_0 + Gq b, delta^2 = delta^2_0 + t theta - sum_k h_k Gq_ik^2 (FP32 Gq, double-float
-// products and sums, FP64 result). One warp per row, lanes over the columns.
-template <typename T>
-__global__ void __launch_bounds__(256) nspace_outputs_kernel(const T* __restrict__ Gq, int64_t m, int ld, int n,
-                                                             const double* __restrict__ x0, double var0,
-                                                             double theta, const long long* __restrict__ step,
-                                                             const double* __restrict__ b,
-                                                             const double* __restrict__ h, double* __restrict__ x,
-                                                             double* __restrict__ var) {
-  __shared__ float sbh[kMaxN], sbl[kMaxN], shh[kMaxN], shl[kMaxN];
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    sbh[k] = (float)b[k];
-    sbl[k] = (float)(b[k] - (double)sbh[k]);
-    shh[k] = (float)h[k];
-    shl[k] = (float)(h[k] - (double)shh[k]);
+// x = x_0 + Gq b, delta^2 = delta^2_0 + t theta - sum_k h_k Gq_ik^2.
+// FP32 Gq: four lanes per row, each lane takes float4 column groups 4 (lane & 3) + 16 j
+// (so a warp reads 64 contiguous bytes of each of 8 rows per load); Gq b by FP32 products
+// with a compensated sum (b as an FP32 pair), h Gq^2 with the square exact (TwoProd) and a
+// double-float sum, since delta^2_t is a small difference of large terms; FP64 result.
+// FP64 Gq: one warp per row in FP64.
+__global__ void __launch_bounds__(256) nspace_outputs_f32_kernel(const float* __restrict__ Gq, int64_t m, int ld,
+                                                                 int n, const double* __restrict__ x0, double var0,
+                                                                 double theta, const long long* __restrict__ step,
+                                                                 const double* __restrict__ b,
+                                                                 const double* __restrict__ h,
+                                                                 double* __restrict__ x, double* __restrict__ var) {
+  __shared__ __align__(16) float sbh[kMaxN], sbl[kMaxN], shh[kMaxN], shl[kMaxN];
+  for (int k = threadIdx.x; k < kMaxN; k += blockDim.x) {
+    const double bv = k < n ? b[k] : 0.0, hv = k < n ? h[k] : 0.0;
+    sbh[k] = (float)bv;
+    sbl[k] = (float)(bv - (double)sbh[k]);
+    shh[k] = (float)hv;
+    shl[k] = (float)(hv - (double)shh[k]);
   }
   __syncthreads();
+  const double tq = (double)*step * theta;
+  const int lane = threadIdx.x & 31, sub = lane & 3;
+  const int64_t groups = (int64_t)gridDim.x * (blockDim.x >> 2);
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 2; i - (lane >> 2) < m; i += groups) {
+    const bool live = i < m;
+    float xs = 0.f, xc = 0.f, vh = 0.f, vl = 0.f;
+    if (live) {
+      const float4* gr = reinterpret_cast<const float4*>(Gq + i * ld);
+      for (int c = 4 * sub; c < n; c += 16) {
+        const float4 g4 = __ldcs(gr + (c >> 2));
+        const float4 bh = *reinterpret_cast<const float4*>(sbh + c);
+        const float4 bl = *reinterpret_cast<const float4*>(sbl + c);
+        const float4 hh = *reinterpret_cast<const float4*>(shh + c);
+        const float4 hl = *reinterpret_cast<const float4*>(shl + c);
+        const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
+        const float bhv[4] = {bh.x, bh.y, bh.z, bh.w}, blv[4] = {bl.x, bl.y, bl.z, bl.w};
+        const float hhv[4] = {hh.x, hh.y, hh.z, hh.w}, hlv[4] = {hl.x, hl.y, hl.z, hl.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          // x: FMA product, Kahan-compensated sum
+          const float p = fmaf(gv[u], bhv[u], gv[u] * blv[u]);
+          const float y = p - xc;
+          const float t = xs + y;
+          xc = (t - xs) - y;
+          xs = t;
+          // delta^2: (qh + ql) = Gq^2 exactly, times (hh + hl), double-float sum
+          const float qh = gv[u] * gv[u];
+          const float ql = fmaf(gv[u], gv[u], -qh);
+          const float r = qh * hhv[u];
+          dd_add(vh, vl, r, fmaf(qh, hhv[u], -r) + (qh * hlv[u] + ql * hhv[u]));
+        }
+      }
+    }
+    // combine the four lanes of the row (the Kahan pair (xs, xc) holds xs - xc)
+    float xl = -xc;
+#pragma unroll
+    for (int o = 1; o < 4; o <<= 1) {
+      const float oxs = __shfl_xor_sync(0xffffffffu, xs, o), oxl = __shfl_xor_sync(0xffffffffu, xl, o);
+      const float ovh = __shfl_xor_sync(0xffffffffu, vh, o), ovl = __shfl_xor_sync(0xffffffffu, vl, o);
+      dd_add(xs, xl, oxs, oxl);
+      dd_add(vh, vl, ovh, ovl);
+    }
+    if (live && sub == 0) {
+      x[i] = x0[i] + ((double)xs + (double)xl);
+      var[i] = (var0 + tq) - ((double)vh + (double)vl);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) nspace_outputs_f64_kernel(const double* __restrict__ Gq, int64_t m, int ld,
+                                                                 int n, const double* __restrict__ x0, double var0,
+                                                                 double theta, const long long* __restrict__ step,
+                                                                 const double* __restrict__ b,
+                                                                 const double* __restrict__ h,
+                                                                 double* __restrict__ x, double* __restrict__ var) {
   const double tq = (double)*step * theta;
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < m; i += warps) {
-    const T* gr = Gq + i * ld;
-    double xs, vs;
-    if (sizeof(T) == 8) {
-      double ax = 0.0, av = 0.0;
-      for (int k = lane; k < n; k += 32) {
-        const double gv = (double)gr[k];
-        ax = fma(gv, b[k], ax);
-        av = fma(gv * gv, h[k], av);
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        ax += __shfl_xor_sync(0xffffffffu, ax, o);
-        av += __shfl_xor_sync(0xffffffffu, av, o);
-      }
-      xs = ax;
-      vs = av;
-    } else {
-      float xh = 0.f, xl = 0.f, vh = 0.f, vl = 0.f;
-      for (int k = lane; k < n; k += 32) {
-        const float gv = (float)gr[k];
-        // Gq b: exact product with the high part, plain product with the low part
-        const float p = gv * sbh[k];
-        dd_add(xh, xl, p, fmaf(gv, sbh[k], -p) + gv * sbl[k]);
-        // h Gq^2: Gq^2 exactly as (qh, ql), times (hh, hl)
-        const float qh = gv * gv;
-        const float ql = fmaf(gv, gv, -qh);
-        const float r = qh * shh[k];
-        dd_add(vh, vl, r, fmaf(qh, shh[k], -r) + (qh * shl[k] + ql * shh[k]));
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        const float oxh = __shfl_xor_sync(0xffffffffu, xh, o), oxl = __shfl_xor_sync(0xffffffffu, xl, o);
-        const float ovh = __shfl_xor_sync(0xffffffffu, vh, o), ovl = __shfl_xor_sync(0xffffffffu, vl, o);
-        dd_add(xh, xl, oxh, oxl);
-        dd_add(vh, vl, ovh, ovl);
-      }
-      xs = (double)xh + (double)xl;
-      vs = (double)vh + (double)vl;
+    const double* gr = Gq + i * ld;
+    double ax = 0.0, av = 0.0;
+    for (int k = lane; k < n; k += 32) {
+      const double gv = gr[k];
+      ax = fma(gv, b[k], ax);
+      av = fma(gv * gv, h[k], av);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      ax += __shfl_xor_sync(0xffffffffu, ax, o);
+      av += __shfl_xor_sync(0xffffffffu, av, o);
     }
     if (lane == 0) {
-      x[i] = x0[i] + xs;
-      var[i] = (var0 + tq) - vs;
+      x[i] = x0[i] + ax;
+      var[i] = (var0 + tq) - av;
     }
   }
 }
@@ -859,8 +892,15 @@ Status nspace_step(const SpectralState& sp, const NspaceState& ns, int n, const 
 template <typename T>
 Status nspace_outputs(const NspaceState& ns, const T* Gq, int64_t m, int ld, int n, const double* x0, double var0,
                       double theta, const long long* step, double* x, double* var, int sms, cudaStream_t s) {
-  const int64_t blocks = std::min<int64_t>((m + 7) / 8, (int64_t)sms * 8);
-  nspace_outputs_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(Gq, m, ld, n, x0, var0, theta, step, ns.b, ns.h, x, var);
+  if (sizeof(T) == 4) {
+    const int64_t blocks = std::min<int64_t>((m + 63) / 64, (int64_t)sms * 8);
+    nspace_outputs_f32_kernel<<<(unsigned)blocks, 256, 0, s>>>((const float*)Gq, m, ld, n, x0, var0, theta, step,
+                                                              ns.b, ns.h, x, var);
+  } else {
+    const int64_t blocks = std::min<int64_t>((m + 7) / 8, (int64_t)sms * 8);
+    nspace_outputs_f64_kernel<<<(unsigned)blocks, 256, 0, s>>>((const double*)Gq, m, ld, n, x0, var0, theta, step,
+                                                              ns.b, ns.h, x, var);
+  }
   HIKF_LAUNCH_CHECK("nspace_outputs");
   return Status::Ok();
 }
