@@ -56,7 +56,7 @@ struct TcLayout {
   static constexpr int AOff = RawOff + kRawStages * 2 * kRawBytes;
   static constexpr int BOff = AOff + kAStages * kPieces * kAPieceBytes;
   static constexpr int VecOff = BOff + kBStages * kPieces * BPiece;  // a (NT floats), r (NT floats)
-  static constexpr int RedOff = VecOff + 2 * NT * 4;                 // group-1 partials: 128 x {rd hi, rd lo, x hi, x lo, max}
+  static constexpr int RedOff = VecOff + 2 * NT * 4;                 // group-0 partials: 128 x {rd hi, rd lo, x hi, x lo, max}
   static constexpr int BarOff = RedOff + 128 * 5 * 4;
   static constexpr int NumBars = 2 * kRawStages + 2 * kAStages + 2 * kBStages + 5;
   static constexpr int Total = BarOff + NumBars * 8 + 16;
@@ -74,7 +74,8 @@ __device__ __forceinline__ int pow2_exp(float bound) {
 
 template <int NT>
 __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_constant__ CUtensorMap tmC,
-                                                          const __grid_constant__ CUtensorMap tmCQ, TcArgs args) {
+                                                          const __grid_constant__ CUtensorMap tmCQ,
+                                                          const __grid_constant__ CUtensorMap tmCst, TcArgs args) {
   using Lay = TcLayout<NT>;
   constexpr int NK = NT / kKC;
   extern __shared__ unsigned char smem_raw[];
@@ -243,7 +244,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
       if (blockIdx.x < ntiles && row < args.m) {
         nb_c = args.cmax[row];
         nb_q = args.cqmax[row];
-        if (g == 0) {
+        if (g == 1) {
           nv = args.var[row];
           nx = args.x[row];
         }
@@ -259,7 +260,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
         if (tile + gridDim.x < ntiles && nrow < args.m) {
           nb_c = args.cmax[nrow];
           nb_q = args.cqmax[nrow];
-          if (g == 0) {
+          if (g == 1) {
             nv = args.var[nrow];
             nx = args.x[nrow];
           }
@@ -343,6 +344,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
       tc_fence_after();
       const float inv = ldexpf(1.f, ea - 14 - beta_exp);  // 1 / (alpha beta)
       float rs_ = 0.f, rc_ = 0.f, rmax = 0.f;
+      // output staging: this warp's 32 rows x 32 columns as two 16-row boxes (2 KB each,
+      // 128B-swizzled like the C tensor map) in the bytes its own rows occupy in A pieces
+      // 0 and 1 of the group's A stage; no MMA reads that stage during the epilogue, and
+      // only this warp writes those bytes (its converter rows), so no other warp waits
+      unsigned char* stg = smem + Lay::AOff + g * kPieces * kAPieceBytes + (lane >> 4) * kAPieceBytes + q * 2048;
       for (int jc = g * (NK / kGroups); jc < (g + 1) * (NK / kGroups); ++jc) {
         uint32_t kv[32], cv[32];
         tmem_ld32(tq + jc * kKC, kv);
@@ -369,17 +375,35 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
         rc_ = (t - rs_) - y;
         rs_ = t;
         const int col0 = jc * kKC;
-        if (valid && col0 < args.ld) {
-          float4* dst = reinterpret_cast<float4*>(args.C + row * args.ld + col0);
+        if (col0 < args.ld) {
+          // the previous store from this buffer has been read out of shared memory
+          if (lane == 0) bulk_wait_read0();
+          __syncwarp();
 #pragma unroll
-          for (int u = 0; u < 8; ++u) dst[u] = make_float4(out[4 * u], out[4 * u + 1], out[4 * u + 2], out[4 * u + 3]);
+          for (int u = 0; u < 8; ++u)
+            *reinterpret_cast<float4*>(stg + (lane & 15) * 128 + ((u ^ (lane & 7)) * 16)) =
+                make_float4(out[4 * u], out[4 * u + 1], out[4 * u + 2], out[4 * u + 3]);
+          fence_proxy_async();
+          __syncwarp();
+          // rows past m are clipped by the tensor map
+          if (lane == 0) {
+            unsigned char* s0 = smem + Lay::AOff + g * kPieces * kAPieceBytes + q * 2048;
+            tma_store_2d(&tmCst, smem_u32(s0), col0, (int)(tile * kBM + q * 32));
+            tma_store_2d(&tmCst, smem_u32(s0 + kAPieceBytes), col0, (int)(tile * kBM + q * 32 + 16));
+            bulk_commit();
+          }
         }
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(acc_empty);
-      // combine the two groups' row partials through shared memory (bounded mbarrier handoff)
-      if (g == 1) {
+      // this warp's converter rows overwrite the staging bytes next
+      if (lane == 0) bulk_wait_read0();
+      __syncwarp();
+      // combine the two groups' row partials through shared memory (bounded mbarrier handoff);
+      // group 1 finishes the rows, so group 0 can start converting the next tile's first
+      // chunk (the first the next MMAs need) at once
+      if (g == 0) {
         ok = __all_sync(0xffffffffu, mbar_wait(red_empty, redph ^ 1u, args.err, s_abort));
         if (!ok) break;
         red[r * 5 + 0] = rs_;
@@ -405,6 +429,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
       redph ^= 1u;
     }
     if (!ok) *s_abort = 1;
+    if (lane == 0) bulk_wait0();
   }
   tc_fence_before();
   __syncthreads();
@@ -482,7 +507,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-Status encode_map(CUtensorMap* map, const float* base, int64_t m, int ld) {
+Status encode_map(CUtensorMap* map, const float* base, int64_t m, int ld, int box_rows = kBM) {
   static EncodeTiledFn fn = nullptr;
   if (!fn) {
     cudaDriverEntryPointQueryResult q;
@@ -493,7 +518,7 @@ Status encode_map(CUtensorMap* map, const float* base, int64_t m, int ld) {
   }
   cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)m};
   cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
-  cuuint32_t box[2] = {(cuuint32_t)kKC, (cuuint32_t)kBM};
+  cuuint32_t box[2] = {(cuuint32_t)kKC, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -510,6 +535,7 @@ Status tc_setup(TcState& tc, const float* C, const float* CQ, int64_t m, int ld,
   if (ld > 256) return make_status(HIKF_EINVAL, "MIXED precision supports n <= 256");
   tc.nt = ld <= 128 ? 128 : 256;
   HIKF_TRY(encode_map(&tc.mapC, C, m, ld));
+  HIKF_TRY(encode_map(&tc.mapCst, C, m, ld, 16));
   HIKF_TRY(encode_map(&tc.mapCQ, CQ, m, ld));
   tc.smem = tc.nt == 128 ? TcLayout<128>::Smem : TcLayout<256>::Smem;
   const void* fn = tc.nt == 128 ? (const void*)sweep_tc_kernel<128> : (const void*)sweep_tc_kernel<256>;
@@ -546,9 +572,9 @@ Status tc_sweep(const TcState& tc, TcArgs args, int sms, cudaStream_t s) {
   args.cmax = tc.cmax;
   args.cqmax = tc.cqmax;
   if (tc.nt == 128)
-    sweep_tc_kernel<128><<<grid, kThreadsTc, tc.smem, s>>>(tc.mapC, tc.mapCQ, args);
+    sweep_tc_kernel<128><<<grid, kThreadsTc, tc.smem, s>>>(tc.mapC, tc.mapCQ, tc.mapCst, args);
   else
-    sweep_tc_kernel<256><<<grid, kThreadsTc, tc.smem, s>>>(tc.mapC, tc.mapCQ, args);
+    sweep_tc_kernel<256><<<grid, kThreadsTc, tc.smem, s>>>(tc.mapC, tc.mapCQ, tc.mapCst, args);
   HIKF_LAUNCH_CHECK("sweep_tc");
   return Status::Ok();
 }

@@ -30,6 +30,7 @@ struct TcState {
   int nt = 256;                 // MMA N (128 or 256)
   int smem = 0;
   CUtensorMap mapC, mapCQ;
+  CUtensorMap mapCst;           // C, 32-column x 16-row boxes: the epilogue's tile stores
   __half* bimg = nullptr;       // 3 x nt x nt FP16 images of beta M (three pieces)
   float* cmax = nullptr;
   float* cqmax = nullptr;
