@@ -135,15 +135,46 @@ def peaks():
         "fallback"
 
 
-# source files of each timed kernel: a committed traffic figure counts only while they are unchanged
-KERNEL_SOURCES = {"mixed": ("sweep_tc.cu", "tc_ptx.cuh"), "fp32": ("step.cu",), "eigen": ("spectral.cu",),
-                  "nspace": ("spectral.cu",)}
+# the source of each timed kernel (its definition and the device helpers it calls, plus
+# whole headers): a committed traffic figure counts only while this text is unchanged
+KERNEL_SOURCES = {
+    "mixed": ("sweep_tc.cu", ("sweep_tc_kernel", "pow2_exp"), ("tc_ptx.cuh",)),
+    "fp32": ("step.cu", ("sweep_kernel",), ()),
+    "eigen": ("spectral.cu", ("eigen_sweep_f32_kernel", "kahan_add"), ()),
+    "nspace": ("nspace.cu", ("nspace_outputs_f32_kernel", "dd_add", "two_sum"), ()),
+}
+
+
+def _definition(text: str, name: str) -> str:
+    """The text of the first definition of function `name` (signature to matching brace)."""
+    import re
+    for mt in re.finditer(r"\b" + re.escape(name) + r"\s*\(", text):
+        i, depth = mt.end(), 1
+        while i < len(text) and depth:          # skip the parameter list
+            depth += {"(": 1, ")": -1}.get(text[i], 0)
+            i += 1
+        j = i
+        while j < len(text) and text[j] not in "{;":
+            j += 1
+        if j >= len(text) or text[j] == ";":
+            continue                            # a declaration or a call
+        depth, k = 1, j + 1
+        while k < len(text) and depth:
+            depth += {"{": 1, "}": -1}.get(text[k], 0)
+            k += 1
+        return text[mt.start():k]
+    return ""
 
 
 def source_hash(kind: str) -> str:
+    f, names, headers = KERNEL_SOURCES[kind]
+    csrc = ROOT / "paper_1404_3816_gb300" / "csrc"
+    text = (csrc / f).read_text() if (csrc / f).exists() else ""
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES[kind]:
-        p = ROOT / "paper_1404_3816_gb300" / "csrc" / f
+    for nm in names:
+        h.update(_definition(text, nm).encode())
+    for hd in headers:
+        p = csrc / hd
         if p.exists():
             h.update(p.read_bytes())
     return h.hexdigest()[:16]
@@ -427,7 +458,7 @@ def main():
             "note": "x and delta^2 not formed per step (on request)",
             "with_outputs_every_step": {"value": 1000.0 / ms_out, "unit": "steps/s", "ms_per_step": ms_out},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": float(pk["hbm_gbs"]), "unit": "GB/s",
-                         "frac": achieved / float(pk["hbm_gbs"]), "traffic": None,
+                         "frac": achieved / float(pk["hbm_gbs"]), "traffic": ncu_traffic("nspace", n),
                          "kernel": "nspace_outputs_kernel (x, delta^2 from Gq)",
                          "ms_per_launch": out_ms, "alg_bytes_per_launch": out_bytes,
                          "method": "per-step time with outputs minus per-step time without"},

@@ -101,10 +101,18 @@ typedef struct {
                         forms C_{t|t}. Same conditions as HIKF_FORM_EIGEN. */
   int graph;         /* 1 (default): each update is replayed as one CUDA graph, captured on
                         the first update; 0: kernels are launched one by one. */
+  int m2l;           /* where the M2L translations of the H^2 product run:
+                        HIKF_M2L_AUTO (default): on the tensor cores for MIXED, on the
+                        CUDA cores otherwise; HIKF_M2L_TENSOR: on the tensor cores
+                        (tcgen05, FP32 operands split into two TF32 pieces, all levels in
+                        one launch per pass of 256 rays x 128 operator rows, launch
+                        variant autotuned once per shape) for FP32 and MIXED
+                        (HIKF_EINVAL for FP64); HIKF_M2L_SIMT: on the CUDA cores. */
 } hikf_options;
 
 enum { HIKF_CHAIN_AUTO = 0, HIKF_CHAIN_FACTOR = 1, HIKF_CHAIN_SPECTRAL = 2 };
 enum { HIKF_FORM_CROSS = 0, HIKF_FORM_EIGEN = 1, HIKF_FORM_NSPACE = 2 };
+enum { HIKF_M2L_AUTO = 0, HIKF_M2L_TENSOR = 1, HIKF_M2L_SIMT = 2 };
 
 /* Fill *opt with the defaults listed above. */
 hikf_status hikf_options_default(hikf_options* opt);

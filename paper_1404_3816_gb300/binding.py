@@ -26,6 +26,8 @@ CHAIN_AUTO, CHAIN_FACTOR, CHAIN_SPECTRAL = 0, 1, 2
 CHAINS = {"auto": CHAIN_AUTO, "factor": CHAIN_FACTOR, "spectral": CHAIN_SPECTRAL}
 FORM_CROSS, FORM_EIGEN, FORM_NSPACE = 0, 1, 2
 FORMS = {"cross": FORM_CROSS, "eigen": FORM_EIGEN, "nspace": FORM_NSPACE}
+M2L_AUTO, M2L_TENSOR, M2L_SIMT = 0, 1, 2
+M2LS = {"auto": M2L_AUTO, "tensor": M2L_TENSOR, "simt": M2L_SIMT}
 
 # every symbol include/hikf.h declares
 EXPORTED = ["hikf_options_default", "hikf_create", "hikf_create_with_cq", "hikf_assimilate",
@@ -48,7 +50,7 @@ class Kernel(C.Structure):
 class Options(C.Structure):
     _fields_ = [("cheb_order", C.c_int), ("leaf_size", C.c_int), ("max_depth", C.c_int),
                 ("precision", C.c_int), ("cuda_stream", C.c_void_p), ("chain", C.c_int), ("form", C.c_int),
-                ("graph", C.c_int)]
+                ("graph", C.c_int), ("m2l", C.c_int)]
 
 
 class Info(C.Structure):
@@ -133,7 +135,7 @@ def kernel_struct(spec) -> Kernel:
 
 
 def options(cheb_order: int = 8, leaf_size: int = 64, max_depth: int = -1, precision="fp32",
-            stream=None, chain="auto", form="cross", graph=True) -> Options:
+            stream=None, chain="auto", form="cross", graph=True, m2l="auto") -> Options:
     o = Options()
     load().hikf_options_default(C.byref(o))
     o.cheb_order = int(cheb_order)
@@ -143,6 +145,7 @@ def options(cheb_order: int = 8, leaf_size: int = 64, max_depth: int = -1, preci
     o.chain = CHAINS[chain] if isinstance(chain, str) else int(chain)
     o.form = FORMS[form] if isinstance(form, str) else int(form)
     o.graph = 1 if graph else 0
+    o.m2l = M2LS[m2l] if isinstance(m2l, str) else int(m2l)
     if stream is not None:
         o.cuda_stream = C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
     return o

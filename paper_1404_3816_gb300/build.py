@@ -19,7 +19,7 @@ BUILD = PKG / "_build"
 LIBDIR = PKG / "_lib"
 LIB = LIBDIR / "libhikf.so"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["tree.cu", "fmm.cu", "m2l_tc.cu", "step.cu", "spectral.cu", "sweep_tc.cu", "api.cu"]
+SOURCES = ["tree.cu", "fmm.cu", "m2l_tc.cu", "step.cu", "spectral.cu", "nspace.cu", "sweep_tc.cu", "api.cu"]
 
 
 def nvcc() -> str:

@@ -167,8 +167,10 @@ struct hikf_handle {
   int prof_count = 0;
   std::vector<cudaEvent_t> ev;
 
+  int m2l = HIKF_M2L_AUTO;
   bool fp64() const { return prec == HIKF_PREC_FP64; }
   bool mixed() const { return prec == HIKF_PREC_MIXED; }
+  bool tensor_m2l() const { return m2l == HIKF_M2L_TENSOR ? !fp64() : (m2l == HIKF_M2L_AUTO && mixed()); }
 };
 
 namespace {
@@ -212,6 +214,9 @@ Status validate_common(int dim, int64_t m, const double* points, int n, const in
   if (o.chain < HIKF_CHAIN_AUTO || o.chain > HIKF_CHAIN_SPECTRAL) return make_status(HIKF_EINVAL, "unknown chain");
   if (o.form != HIKF_FORM_CROSS && o.form != HIKF_FORM_EIGEN && o.form != HIKF_FORM_NSPACE)
     return make_status(HIKF_EINVAL, "unknown form");
+  if (o.m2l < HIKF_M2L_AUTO || o.m2l > HIKF_M2L_SIMT) return make_status(HIKF_EINVAL, "unknown m2l");
+  if (o.m2l == HIKF_M2L_TENSOR && o.precision == HIKF_PREC_FP64)
+    return make_status(HIKF_EINVAL, "the tensor-core M2L takes FP32 storage (FP32 or MIXED)");
   if (o.form != HIKF_FORM_CROSS && o.precision == HIKF_PREC_MIXED)
     return make_status(HIKF_EINVAL, "the eigenbasis and n-space forms run on the CUDA cores (FP32 or FP64)");
   return Status::Ok();
@@ -251,7 +256,7 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
   } else {
     hikf::FmmParams fp;
     fp.order = h->order;
-    fp.tensor_m2l = h->mixed();
+    fp.tensor_m2l = h->tensor_m2l();
     fp.sms = h->sms;
     fp.pow = q.pow;
     fp.theta = q.theta;
@@ -266,7 +271,7 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
     } else {
       hikf::FmmParams f0;
       f0.order = h->order;
-      f0.tensor_m2l = h->mixed();
+      f0.tensor_m2l = h->tensor_m2l();
       f0.sms = h->sms;
       f0.pow = p0.pow;
       f0.theta = p0.theta;
@@ -616,6 +621,7 @@ hikf_status create_impl(hikf_t** out, int dim, int64_t m, const double* points, 
   h->prec = o.precision;
   h->order = o.cheb_order;
   h->use_graph = o.graph != 0;
+  h->m2l = o.m2l;
   if (o.cuda_stream) {
     h->stream = (cudaStream_t)o.cuda_stream;
     if (h->stream == cudaStreamLegacy) h->use_graph = false;  // the legacy stream cannot be captured
@@ -666,6 +672,7 @@ hikf_status hikf_options_default(hikf_options* opt) {
   opt->chain = HIKF_CHAIN_AUTO;
   opt->form = HIKF_FORM_CROSS;
   opt->graph = 1;
+  opt->m2l = HIKF_M2L_AUTO;
   return HIKF_OK;
 }
 

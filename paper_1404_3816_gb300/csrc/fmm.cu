@@ -653,42 +653,43 @@ Status h2_product(const Tree& t, const SparseH& h, const FmmParams& fp, T* out, 
       }
     }
     // M2L, all levels 2 .. L
-    const bool tc = fp.tensor_m2l && sizeof(T) == 4 && m2l_tc_supported(q, ldc);
-    int* err = nullptr;
+    const bool tc = fp.tensor_m2l && sizeof(T) == 4 && m2l_tc_supported(q, ldc) && L - 1 <= 16;
     if (tc) {
+      int* err = nullptr;
       HIKF_CUDA(cudaMallocAsync((void**)&err, sizeof(int), s));
       HIKF_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
-    }
-    for (int lev = 2; lev <= L; ++lev) {
-      if (tc) {
-        M2lTcArgs ma;
-        ma.lev = lev;
-        ma.dim = dim;
-        ma.q = q;
-        ma.ld = ldc;
-        ma.sms = fp.sms;
-        ma.box0 = t.box_offset[lev];
-        ma.nbox = (int64_t)1 << (dim * lev);
-        ma.W = (const float*)W;
-        ma.L = (float*)Lx;
-        ma.kop_level = (const float*)kop + (int64_t)(lev - 2) * ipow(7, dim) * q * q;
-        ma.nsrc = nsrc;
-        ma.npts = npts;
-        ma.err = err;
-        HIKF_TRY(m2l_tc_level(ma, s));
-        continue;
+      M2lTcAll ma;
+      ma.dim = dim;
+      ma.q = q;
+      ma.ld = ldc;
+      ma.sms = fp.sms;
+      ma.nlev = L - 1;
+      for (int lev = 2; lev <= L; ++lev) {
+        ma.lev[lev - 2] = lev;
+        ma.box0[lev - 2] = t.box_offset[lev];
+        ma.nbox[lev - 2] = (int64_t)1 << (dim * lev);
       }
-      dim3 grid((unsigned)((int64_t)1 << (dim * lev)), (unsigned)((q + kM2L_BM - 1) / kM2L_BM),
-                (unsigned)((ldc + kM2L_BN - 1) / kM2L_BN));
-      m2l_kernel<T><<<grid, kThreads, 0, s>>>(g, lev, kop, nsrc, npts, t.box_offset[lev], W, Lx);
-      HIKF_LAUNCH_CHECK("m2l");
-    }
-    if (tc) {
+      ma.W = (const float*)W;
+      ma.L = (float*)Lx;
+      ma.kop = (const float*)kop;
+      ma.nsrc = nsrc;
+      ma.npts = npts;
+      ma.err = err;
+      ma.autotune = fp.autotune;
+      Status st = m2l_tc_all(ma, s);
       int herr = 0;
       HIKF_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
       HIKF_CUDA(cudaStreamSynchronize(s));
       HIKF_CUDA(cudaFreeAsync(err, s));
+      HIKF_TRY(st);
       if (herr) return make_status(HIKF_ETIMEOUT, "a bounded wait in the tensor-core M2L timed out");
+    } else {
+      for (int lev = 2; lev <= L; ++lev) {
+        dim3 grid((unsigned)((int64_t)1 << (dim * lev)), (unsigned)((q + kM2L_BM - 1) / kM2L_BM),
+                  (unsigned)((ldc + kM2L_BN - 1) / kM2L_BN));
+        m2l_kernel<T><<<grid, kThreads, 0, s>>>(g, lev, kop, nsrc, npts, t.box_offset[lev], W, Lx);
+        HIKF_LAUNCH_CHECK("m2l");
+      }
     }
     // L2L, levels 2 .. L-1 (parent level)
     {

@@ -105,6 +105,7 @@ struct FmmParams {
   double theta = 1.0;
   double length = 1.0;
   bool tensor_m2l = false;  // M2L on the tensor cores (FP32 storage only)
+  bool autotune = true;     // tensor-core M2L: time the launch variants once per shape
   int sms = 1;
 };
 

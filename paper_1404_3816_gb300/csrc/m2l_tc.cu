@@ -3,18 +3,28 @@
 // At level l every target box B receives L_B = sum_{B' in IL(B)} K_{l, B'-B} W_{B'}
 // (q x n, q = p^d Chebyshev nodes, n rays). Per target box this runs as the
 // transposed product  L_B^T (n x q) = sum_{B'} W_{B'}^T (n x q) K^T (q x q)  with the
-// rays as the MMA M dimension (128 per half, up to two halves), the operator rows as N
-// and the source nodes as K. Operands are TF32 split into two pieces (rounded hi +
-// exact remainder) and three products are accumulated in FP32 in TMEM:
+// rays as the MMA M dimension (128 per half, up to two halves per pass, passes of 256
+// rays), the operator rows as N (passes of up to 128 rows) and the source nodes as K. Operands are TF32 split
+// into two pieces (rounded hi + exact remainder) and three products are accumulated
+// in FP32 in TMEM:
 //   A1 B1 + A1 B2 + A2 B1  (~2^-21 relative), no scaling needed (TF32 keeps FP32's range).
-// W_{B'} is packed once per level into K-major core-matrix images, operators once per
-// level; both are fed to shared memory by bulk copies (TMA engine) through a two-stage
-// mbarrier pipeline. Warp 0 copies, warp 1 issues tcgen05.mma, warps 4-7 drain TMEM and
-// write L (coalesced over the rays); two TMEM accumulators let the drain of one box
-// overlap the MMAs of the next. Bounded waits as in the sweep kernel.
+// All levels go out in one persistent launch per pass: the work items are the
+// (level, box) pairs of every level, W of all levels is packed once into K-major
+// core-matrix images and the operators of all levels likewise; both are fed to shared
+// memory by bulk copies (TMA engine) through a multi-stage mbarrier pipeline. Warp 0
+// copies, warp 1 issues tcgen05.mma, warps 4-7 drain TMEM and write L (coalesced over
+// the rays); two TMEM accumulators let the drain of one box overlap the MMAs of the
+// next. The number of pipeline stages and of CTAs per SM are chosen by a small
+// autotuner that times each feasible variant once per problem shape (the outputs of
+// all variants are identical) and remembers the fastest for the process. Bounded
+// waits as in the sweep kernel.
 #include <math.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
 
 #include "hikf_internal.cuh"
 #include "m2l_tc.cuh"
@@ -27,7 +37,6 @@ namespace {
 using namespace tc;
 
 constexpr int kKC = 32;       // K (source nodes) per chunk: 128-byte rows of FP32
-constexpr int kStages = 2;
 constexpr int kThreads = 256;
 
 // byte offset of (row, k), k < 32, in a K-major FP32 core-matrix chunk (8 rows x 16 B cores)
@@ -43,6 +52,8 @@ __device__ __forceinline__ void tf32_split(float v, float& hi, float& lo) {
 
 struct Dims {
   int q, npad, nkc, ld, halves, ldp;  // ldp = 128 * halves
+  int r0, rw;                         // rays [r0, r0 + rw) of this pass (rw <= ldp)
+  int a0, aw;                         // operator rows (target nodes) [a0, a0 + aw) of this pass (aw <= npad)
   int64_t a_box_bytes;                // one box: 2 pieces x nkc chunks x ldp x 128 B
   int64_t a_chunk_bytes;              // ldp x 128 B
   int64_t b_chunk_bytes;              // npad x 128 B
@@ -59,7 +70,7 @@ __global__ void pack_w_kernel(const float* __restrict__ W, int64_t box0, int64_t
   if (nsrc[box0 + b] == 0) return;
   const int rem = (int)(t % per_box);
   const int c = rem / d.ldp, r = rem % d.ldp;
-  const float v = (c < d.q && r < d.ld) ? W[(box0 + b) * (int64_t)d.q * d.ld + (int64_t)c * d.ld + r] : 0.f;
+  const float v = (c < d.q && r < d.rw) ? W[(box0 + b) * (int64_t)d.q * d.ld + (int64_t)c * d.ld + d.r0 + r] : 0.f;
   float hi, lo;
   tf32_split(v, hi, lo);
   const int kc = c / kKC, kk = c % kKC;
@@ -76,13 +87,28 @@ __global__ void pack_k_kernel(const float* __restrict__ kop_level, int noff, Dim
   const int off = (int)(t / per_off);
   const int rem = (int)(t % per_off);
   const int a = rem / (d.nkc * kKC), c = rem % (d.nkc * kKC);
-  const float v = (a < d.q && c < d.q) ? kop_level[((int64_t)off * d.q + a) * d.q + c] : 0.f;
+  const float v = (a < d.aw && c < d.q) ? kop_level[((int64_t)off * d.q + d.a0 + a) * d.q + c] : 0.f;
   float hi, lo;
   tf32_split(v, hi, lo);
   const int kc = c / kKC, kk = c % kKC;
   unsigned char* base = img + off * d.b_off_bytes + (int64_t)kc * d.b_chunk_bytes + off32(a, kk);
   *reinterpret_cast<float*>(base) = hi;
   *reinterpret_cast<float*>(base + (int64_t)d.nkc * d.b_chunk_bytes) = lo;
+}
+
+// the work items of one launch: the boxes of levels lev[0] < lev[1] < ..., in order
+constexpr int kMaxLevels = 16;
+struct LevelTab {
+  int nlev = 0;
+  int lev[kMaxLevels];
+  int64_t box0[kMaxLevels];        // first box of the level in the all-level arrays
+  int64_t item0[kMaxLevels + 1];   // first work item of the level
+};
+
+__device__ __forceinline__ int item_level(const LevelTab& lt, int64_t it) {
+  int li = 0;
+  while (li + 1 < lt.nlev && it >= lt.item0[li + 1]) ++li;
+  return li;
 }
 
 // interaction list of box B (Morton index at `lev`), deterministic order; returns count
@@ -146,35 +172,46 @@ __device__ bool has_interactions(int64_t B, int lev, int dim, const int64_t* __r
   return false;
 }
 
-template <int NPAD, int HALVES>
-__global__ void __launch_bounds__(kThreads, 1) m2l_tc_kernel(Dims d, int lev, int dim, int64_t box0, int64_t nbox,
+template <int NPAD, int HALVES, int STAGES>
+struct TcM2lCfg {
+  static constexpr int LDP = 128 * HALVES;
+  static constexpr int A_CHUNK = LDP * 128;   // bytes of one A piece chunk
+  static constexpr int B_CHUNK = NPAD * 128;  // bytes of one B piece chunk
+  static constexpr int STAGE = 2 * A_CHUNK + 2 * B_CHUNK;
+  static constexpr int ACC_COLS = HALVES * NPAD;  // TMEM columns per accumulator buffer
+  static constexpr int TMEM_COLS = 2 * ACC_COLS <= 32 ? 32 : (2 * ACC_COLS <= 64 ? 64 : (2 * ACC_COLS <= 128 ? 128
+                                                         : (2 * ACC_COLS <= 256 ? 256 : 512)));
+  static constexpr int NBARS = 2 * STAGES + 5;
+  static constexpr int SMEM = STAGES * STAGE + NBARS * 8 + 64 + 1024;
+};
+
+template <int NPAD, int HALVES, int STAGES>
+__global__ void __launch_bounds__(kThreads, 1) m2l_tc_kernel(Dims d, LevelTab lt, int dim, int64_t wbox0,
                                                              const int64_t* __restrict__ nsrc,
                                                              const int64_t* __restrict__ npts,
                                                              const unsigned char* __restrict__ wimg,
                                                              const unsigned char* __restrict__ kimg,
                                                              float* __restrict__ Lx, int* __restrict__ err) {
-  constexpr int LDP = 128 * HALVES;
-  constexpr int A_CHUNK = LDP * 128;   // bytes of one A piece chunk
-  constexpr int B_CHUNK = NPAD * 128;  // bytes of one B piece chunk
-  constexpr int STAGE = 2 * A_CHUNK + 2 * B_CHUNK;
-  constexpr int ACC_COLS = HALVES * NPAD;  // TMEM columns per accumulator buffer
-  constexpr int TMEM_COLS = 2 * ACC_COLS <= 32 ? 32 : (2 * ACC_COLS <= 64 ? 64 : (2 * ACC_COLS <= 128 ? 128
-                                                        : (2 * ACC_COLS <= 256 ? 256 : 512)));
+  using Cfg = TcM2lCfg<NPAD, HALVES, STAGES>;
+  constexpr int A_CHUNK = Cfg::A_CHUNK, B_CHUNK = Cfg::B_CHUNK, STAGE = Cfg::STAGE;
+  constexpr int ACC_COLS = Cfg::ACC_COLS, TMEM_COLS = Cfg::TMEM_COLS;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * STAGE);
-  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 5);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE);
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bars + Cfg::NBARS);
   volatile int* s_abort = reinterpret_cast<volatile int*>(s_tmem + 1);
   const uint32_t bar0 = smem_u32(bars);
   auto full = [&](int s) { return bar0 + 8u * s; };
-  auto empty = [&](int s) { return bar0 + 8u * (kStages + s); };
-  const uint32_t acc_full0 = bar0 + 8u * (2 * kStages);
+  auto empty = [&](int s) { return bar0 + 8u * (STAGES + s); };
+  const uint32_t acc_full0 = bar0 + 8u * (2 * STAGES);
   const uint32_t acc_empty0 = acc_full0 + 16u;
   const uint32_t drain = acc_full0 + 32u;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int noff = dim == 2 ? 49 : 343;
+  const int64_t nitems = lt.item0[lt.nlev];
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < STAGES; ++s) {
       mbar_init(full(s), 1);
       mbar_init(empty(s), 1);
     }
@@ -197,20 +234,25 @@ __global__ void __launch_bounds__(kThreads, 1) m2l_tc_kernel(Dims d, int lev, in
     if (lane == 0) {
       int64_t j = 0;  // chunk counter across boxes
       bool ok = true;
-      for (int64_t B = blockIdx.x; B < nbox && ok; B += gridDim.x) {
+      for (int64_t it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
+        const int li = item_level(lt, it);
+        const int lev = lt.lev[li];
+        const int64_t B = it - lt.item0[li], box0 = lt.box0[li];
         if (npts[box0 + B] == 0) continue;
         const int nil = interaction_list(B, lev, dim, nsrc, box0, il_src, il_off);
+        const unsigned char* wl = wimg + (box0 - wbox0) * d.a_box_bytes;
+        const unsigned char* kl = kimg + (int64_t)(lev - 2) * noff * d.b_off_bytes;
         for (int e = 0; e < nil && ok; ++e) {
           for (int kc = 0; kc < d.nkc && ok; ++kc, ++j) {
-            const int s = (int)(j % kStages);
-            ok = mbar_wait(empty(s), (uint32_t)(((j / kStages) & 1) ^ 1), err, s_abort);
+            const int s = (int)(j % STAGES);
+            ok = mbar_wait(empty(s), (uint32_t)(((j / STAGES) & 1) ^ 1), err, s_abort);
             if (!ok) break;
             const uint32_t dst = smem_u32(smem + s * STAGE);
             mbar_expect_tx(full(s), STAGE);
-            const unsigned char* a = wimg + (int64_t)il_src[e] * d.a_box_bytes + (int64_t)kc * d.a_chunk_bytes;
+            const unsigned char* a = wl + (int64_t)il_src[e] * d.a_box_bytes + (int64_t)kc * d.a_chunk_bytes;
             bulk_load(dst, a, A_CHUNK, full(s));
             bulk_load(dst + A_CHUNK, a + (int64_t)d.nkc * d.a_chunk_bytes, A_CHUNK, full(s));
-            const unsigned char* bsrc = kimg + (int64_t)il_off[e] * d.b_off_bytes + (int64_t)kc * d.b_chunk_bytes;
+            const unsigned char* bsrc = kl + (int64_t)il_off[e] * d.b_off_bytes + (int64_t)kc * d.b_chunk_bytes;
             bulk_load(dst + 2 * A_CHUNK, bsrc, B_CHUNK, full(s));
             bulk_load(dst + 2 * A_CHUNK + B_CHUNK, bsrc + (int64_t)d.nkc * d.b_chunk_bytes, B_CHUNK, full(s));
           }
@@ -230,7 +272,10 @@ __global__ void __launch_bounds__(kThreads, 1) m2l_tc_kernel(Dims d, int lev, in
       const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NPAD >> 3) << 17) | (8u << 24);
       int64_t j = 0, nb = 0;
       bool ok = true;
-      for (int64_t B = blockIdx.x; B < nbox && ok; B += gridDim.x) {
+      for (int64_t it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
+        const int li = item_level(lt, it);
+        const int lev = lt.lev[li];
+        const int64_t B = it - lt.item0[li], box0 = lt.box0[li];
         if (npts[box0 + B] == 0) continue;
         const int nil = interaction_list(B, lev, dim, nsrc, box0, il_src, il_off);
         if (nil == 0) continue;
@@ -241,8 +286,8 @@ __global__ void __launch_bounds__(kThreads, 1) m2l_tc_kernel(Dims d, int lev, in
         const uint32_t dacc = tmem + (uint32_t)(buf * ACC_COLS);
         for (int e = 0; e < nil && ok; ++e) {
           for (int kc = 0; kc < d.nkc && ok; ++kc, ++j) {
-            const int s = (int)(j % kStages);
-            ok = mbar_wait(full(s), (uint32_t)((j / kStages) & 1), err, s_abort);
+            const int s = (int)(j % STAGES);
+            ok = mbar_wait(full(s), (uint32_t)((j / STAGES) & 1), err, s_abort);
             if (!ok) break;
             tc_fence_after();
             const uint32_t base = smem_u32(smem + s * STAGE);
@@ -271,28 +316,31 @@ __global__ void __launch_bounds__(kThreads, 1) m2l_tc_kernel(Dims d, int lev, in
       if (!ok) *s_abort = 1;
     }
   } else if (warp >= 4) {
-    // drain TMEM: thread = ray row (lane quarter q), writes L[B][a][r] coalesced over r
+    // drain TMEM: thread = ray row (lane quarter q), writes L[B][a][r0 + r] coalesced over r
     const int q4 = warp & 3;
     int64_t nb = 0;
     bool ok = true;
-    for (int64_t B = blockIdx.x; B < nbox && ok; B += gridDim.x) {
+    for (int64_t it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
+      const int li = item_level(lt, it);
+      const int lev = lt.lev[li];
+      const int64_t B = it - lt.item0[li], box0 = lt.box0[li];
       if (npts[box0 + B] == 0) continue;
       if (!has_interactions(B, lev, dim, nsrc, box0)) continue;
       const int buf = (int)(nb & 1);
       ok = __all_sync(0xffffffffu, mbar_wait(acc_full0 + 8u * buf, (uint32_t)((nb >> 1) & 1), err, s_abort));
       if (!ok) break;
       tc_fence_after();
-      float* Lb = Lx + (box0 + B) * (int64_t)d.q * d.ld;
+      float* Lb = Lx + (box0 + B) * (int64_t)d.q * d.ld + (int64_t)d.a0 * d.ld + d.r0;
       for (int h = 0; h < HALVES; ++h) {
         const int r = h * 128 + q4 * 32 + lane;
         for (int c0 = 0; c0 < NPAD; c0 += 32) {
           uint32_t v[32];
           tmem_ld32(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(buf * ACC_COLS + h * NPAD + c0), v);
           tmem_wait_ld();
-          if (r < d.ld) {
+          if (r < d.rw) {
 #pragma unroll
             for (int u = 0; u < 32; ++u)
-              if (c0 + u < d.q) Lb[(int64_t)(c0 + u) * d.ld + r] = __uint_as_float(v[u]);
+              if (c0 + u < d.aw) Lb[(int64_t)(c0 + u) * d.ld + r] = __uint_as_float(v[u]);
           }
         }
       }
@@ -314,59 +362,169 @@ __global__ void __launch_bounds__(kThreads, 1) m2l_tc_kernel(Dims d, int lev, in
 
 inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
-template <int NPAD, int HALVES>
-Status launch_m2l_tc(const Dims& d, int lev, int dim, int64_t box0, int64_t nbox, const int64_t* nsrc,
-                     const int64_t* npts, const unsigned char* wimg, const unsigned char* kimg, float* Lx, int* err,
-                     int sms, cudaStream_t s) {
-  constexpr int STAGE = 2 * (128 * HALVES) * 128 + 2 * NPAD * 128;
-  const int smem = kStages * STAGE + (2 * kStages + 5) * 8 + 64 + 1024;
-  auto fn = m2l_tc_kernel<NPAD, HALVES>;
-  HIKF_CUDA(cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  const int grid = (int)std::min<int64_t>(nbox, sms);
-  fn<<<grid, kThreads, smem, s>>>(d, lev, dim, box0, nbox, nsrc, npts, wimg, kimg, Lx, err);
+// one launch variant: pipeline stages and CTAs per SM
+struct Variant {
+  int stages = 2, per_sm = 1;
+};
+
+template <int NPAD, int HALVES, int STAGES>
+Status launch_variant(const Dims& d, const LevelTab& lt, int dim, int64_t wbox0, const int64_t* nsrc,
+                      const int64_t* npts, const unsigned char* wimg, const unsigned char* kimg, float* Lx, int* err,
+                      int grid, cudaStream_t s) {
+  using Cfg = TcM2lCfg<NPAD, HALVES, STAGES>;
+  auto fn = m2l_tc_kernel<NPAD, HALVES, STAGES>;
+  HIKF_CUDA(cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM));
+  fn<<<grid, kThreads, Cfg::SMEM, s>>>(d, lt, dim, wbox0, nsrc, npts, wimg, kimg, Lx, err);
   HIKF_LAUNCH_CHECK("m2l_tc");
   return Status::Ok();
 }
 
+template <int NPAD, int HALVES>
+Status launch_npad_halves(const Variant& v, const Dims& d, const LevelTab& lt, int dim, int64_t wbox0,
+                          const int64_t* nsrc, const int64_t* npts, const unsigned char* wimg,
+                          const unsigned char* kimg, float* Lx, int* err, int sms, cudaStream_t s) {
+  const int64_t nitems = lt.item0[lt.nlev];
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(nitems, (int64_t)sms * v.per_sm));
+  if (v.stages == 3)
+    return launch_variant<NPAD, HALVES, 3>(d, lt, dim, wbox0, nsrc, npts, wimg, kimg, Lx, err, grid, s);
+  return launch_variant<NPAD, HALVES, 2>(d, lt, dim, wbox0, nsrc, npts, wimg, kimg, Lx, err, grid, s);
+}
+
+Status launch(const Variant& v, const Dims& d, const LevelTab& lt, int dim, int64_t wbox0, const int64_t* nsrc,
+              const int64_t* npts, const unsigned char* wimg, const unsigned char* kimg, float* Lx, int* err, int sms,
+              cudaStream_t s) {
+#define HIKF_M2L_CASE(NP, HV)                                                                              \
+  if (d.npad == NP && d.halves == HV)                                                                      \
+    return launch_npad_halves<NP, HV>(v, d, lt, dim, wbox0, nsrc, npts, wimg, kimg, Lx, err, sms, s);
+  HIKF_M2L_CASE(32, 1)
+  HIKF_M2L_CASE(64, 1)
+  HIKF_M2L_CASE(128, 1)
+  HIKF_M2L_CASE(32, 2)
+  HIKF_M2L_CASE(64, 2)
+  HIKF_M2L_CASE(128, 2)
+#undef HIKF_M2L_CASE
+  return make_status(HIKF_EINVAL, "tensor-core M2L: unsupported shape");
+}
+
+// shared memory and TMEM of one CTA of a variant (for the feasibility of stages and CTAs per SM)
+void variant_footprint(int npad, int halves, int stages, int* smem, int* tmem_cols) {
+  const int stage = 2 * (128 * halves) * 128 + 2 * npad * 128;
+  *smem = stages * stage + (2 * stages + 5) * 8 + 64 + 1024;
+  const int acc = 2 * halves * npad;
+  *tmem_cols = acc <= 32 ? 32 : (acc <= 64 ? 64 : (acc <= 128 ? 128 : (acc <= 256 ? 256 : 512)));
+}
+
+std::vector<Variant> feasible_variants(int npad, int halves) {
+  std::vector<Variant> out;
+  for (int st = 2; st <= 3; ++st) {
+    int smem = 0, tcols = 0;
+    variant_footprint(npad, halves, st, &smem, &tcols);
+    if (smem > 227 * 1024) continue;
+    for (int per = 1; per <= 2; ++per) {
+      if (per * (smem + 1024) > 228 * 1024 || per * tcols > 512) continue;
+      out.push_back(Variant{st, per});
+    }
+  }
+  return out;
+}
+
+// the autotuner's memory: (dim, npad, halves, work items) -> fastest variant
+std::mutex g_tune_mutex;
+std::map<std::tuple<int, int, int, int64_t>, Variant> g_tuned;
+
 }  // namespace
 
-bool m2l_tc_supported(int q, int ld) { return q <= 128 && ld <= 256; }
+bool m2l_tc_supported(int q, int ld) { return q >= 1 && ld >= 1; }
 
-Status m2l_tc_level(const M2lTcArgs& a, cudaStream_t s) {
-  Dims d;
-  d.q = a.q;
-  d.npad = a.q <= 32 ? 32 : (a.q <= 64 ? 64 : 128);  // MMA N of the instantiated kernel
-  d.nkc = (a.q + kKC - 1) / kKC;
-  d.ld = a.ld;
-  d.halves = a.ld <= 128 ? 1 : 2;
-  d.ldp = 128 * d.halves;
-  d.a_chunk_bytes = (int64_t)d.ldp * 128;
-  d.a_box_bytes = 2 * (int64_t)d.nkc * d.a_chunk_bytes;
-  d.b_chunk_bytes = (int64_t)d.npad * 128;
-  d.b_off_bytes = 2 * (int64_t)d.nkc * d.b_chunk_bytes;
-  const int noff = a.dim == 2 ? 49 : 343;
-  // images (stream-ordered scratch of this call)
-  unsigned char *wimg = nullptr, *kimg = nullptr;
-  HIKF_CUDA(cudaMallocAsync((void**)&wimg, (size_t)(a.nbox * d.a_box_bytes), s));
-  HIKF_CUDA(cudaMallocAsync((void**)&kimg, (size_t)(noff * d.b_off_bytes), s));
-  const int64_t wthreads = a.nbox * (int64_t)d.nkc * kKC * d.ldp;
-  pack_w_kernel<<<nblk(wthreads, 256), 256, 0, s>>>(a.W, a.box0, a.nbox, a.nsrc, d, wimg);
-  HIKF_LAUNCH_CHECK("pack_w");
-  const int64_t kthreads = (int64_t)noff * d.npad * d.nkc * kKC;
-  pack_k_kernel<<<nblk(kthreads, 256), 256, 0, s>>>(a.kop_level, noff, d, kimg);
-  HIKF_LAUNCH_CHECK("pack_k");
-  Status st;
-  const int npad = d.npad;
-  if (d.halves == 2) {
-    if (npad <= 32) st = launch_m2l_tc<32, 2>(d, a.lev, a.dim, a.box0, a.nbox, a.nsrc, a.npts, wimg, kimg, a.L, a.err, a.sms, s);
-    else if (npad <= 64) st = launch_m2l_tc<64, 2>(d, a.lev, a.dim, a.box0, a.nbox, a.nsrc, a.npts, wimg, kimg, a.L, a.err, a.sms, s);
-    else st = launch_m2l_tc<128, 2>(d, a.lev, a.dim, a.box0, a.nbox, a.nsrc, a.npts, wimg, kimg, a.L, a.err, a.sms, s);
-  } else {
-    if (npad <= 32) st = launch_m2l_tc<32, 1>(d, a.lev, a.dim, a.box0, a.nbox, a.nsrc, a.npts, wimg, kimg, a.L, a.err, a.sms, s);
-    else if (npad <= 64) st = launch_m2l_tc<64, 1>(d, a.lev, a.dim, a.box0, a.nbox, a.nsrc, a.npts, wimg, kimg, a.L, a.err, a.sms, s);
-    else st = launch_m2l_tc<128, 1>(d, a.lev, a.dim, a.box0, a.nbox, a.nsrc, a.npts, wimg, kimg, a.L, a.err, a.sms, s);
+Status m2l_tc_all(const M2lTcAll& a, cudaStream_t s) {
+  if (a.nlev < 1 || a.nlev > kMaxLevels) return make_status(HIKF_EINVAL, "tensor-core M2L: level count");
+  LevelTab lt;
+  lt.nlev = a.nlev;
+  int64_t items = 0;
+  for (int i = 0; i < a.nlev; ++i) {
+    lt.lev[i] = a.lev[i];
+    lt.box0[i] = a.box0[i];
+    lt.item0[i] = items;
+    items += a.nbox[i];
   }
-  HIKF_CUDA(cudaFreeAsync(wimg, s));
+  lt.item0[a.nlev] = items;
+  const int64_t wbox0 = a.box0[0];
+  const int64_t nboxes = items;  // the levels are contiguous in the all-level arrays
+  const int noff = a.dim == 2 ? 49 : 343;
+  const int nkc = (a.q + kKC - 1) / kKC;
+  // operator images of all levels for one pass of up to 128 operator rows (MMA N)
+  const int64_t b_chunk_max = 128 * 128, b_off_max = 2 * (int64_t)nkc * b_chunk_max;
+  unsigned char* kimg = nullptr;
+  HIKF_CUDA(cudaMallocAsync((void**)&kimg, (size_t)((int64_t)a.nlev * noff * b_off_max), s));
+  Status st;
+  // passes of up to 256 rays (two 128-row MMA halves); W is packed once per ray pass
+  for (int r0 = 0; r0 < a.ld && st.ok(); r0 += 256) {
+    Dims d;
+    d.q = a.q;
+    d.nkc = nkc;
+    d.ld = a.ld;
+    d.r0 = r0;
+    d.rw = std::min(256, a.ld - r0);
+    d.halves = d.rw <= 128 ? 1 : 2;
+    d.ldp = 128 * d.halves;
+    d.a_chunk_bytes = (int64_t)d.ldp * 128;
+    d.a_box_bytes = 2 * (int64_t)d.nkc * d.a_chunk_bytes;
+    unsigned char* wimg = nullptr;
+    HIKF_CUDA(cudaMallocAsync((void**)&wimg, (size_t)(nboxes * d.a_box_bytes), s));
+    const int64_t wthreads = nboxes * (int64_t)d.nkc * kKC * d.ldp;
+    pack_w_kernel<<<nblk(wthreads, 256), 256, 0, s>>>(a.W, wbox0, nboxes, a.nsrc, d, wimg);
+    HIKF_LAUNCH_CHECK("pack_w");
+    for (int a0 = 0; a0 < a.q && st.ok(); a0 += 128) {
+      d.a0 = a0;
+      d.aw = std::min(128, a.q - a0);
+      d.npad = d.aw <= 32 ? 32 : (d.aw <= 64 ? 64 : 128);  // MMA N of the instantiated kernel
+      d.b_chunk_bytes = (int64_t)d.npad * 128;
+      d.b_off_bytes = 2 * (int64_t)nkc * d.b_chunk_bytes;
+      const int64_t kthreads = (int64_t)a.nlev * noff * d.npad * nkc * kKC;
+      pack_k_kernel<<<nblk(kthreads, 256), 256, 0, s>>>(a.kop, a.nlev * noff, d, kimg);
+      HIKF_LAUNCH_CHECK("pack_k");
+      // the variant: tuned once per shape (every variant writes the same L, so timing one
+      // on the real data is harmless), then remembered
+      const auto key = std::make_tuple(a.dim, d.npad, d.halves, items);
+      Variant v;
+      bool known = false;
+      {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        auto f = g_tuned.find(key);
+        if (f != g_tuned.end()) {
+          v = f->second;
+          known = true;
+        }
+      }
+      if (!known && a.autotune) {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        const std::vector<Variant> cands = feasible_variants(d.npad, d.halves);
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        HIKF_CUDA(cudaEventCreate(&e0));
+        HIKF_CUDA(cudaEventCreate(&e1));
+        float best = 1e30f;
+        for (const Variant& c : cands) {
+          HIKF_CUDA(cudaEventRecord(e0, s));
+          st = launch(c, d, lt, a.dim, wbox0, a.nsrc, a.npts, wimg, kimg, a.L, a.err, a.sms, s);
+          if (!st.ok()) break;
+          HIKF_CUDA(cudaEventRecord(e1, s));
+          HIKF_CUDA(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          HIKF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+          if (ms < best) {
+            best = ms;
+            v = c;
+          }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (st.ok()) g_tuned[key] = v;  // L already holds this pass (every candidate wrote it)
+      } else {
+        st = launch(v, d, lt, a.dim, wbox0, a.nsrc, a.npts, wimg, kimg, a.L, a.err, a.sms, s);
+      }
+    }
+    HIKF_CUDA(cudaFreeAsync(wimg, s));
+  }
   HIKF_CUDA(cudaFreeAsync(kimg, s));
   return st;
 }

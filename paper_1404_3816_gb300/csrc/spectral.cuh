@@ -54,6 +54,10 @@ template <typename T>
 Status nspace_cross(const SpectralState& sp, const NspaceState& ns, const double* rd, int64_t m, int ld, int n,
                     const T* Gq, T* out, cudaStream_t s);
 
+// out (m x ld) = A (m x ld, first n columns) * B (n x n FP64), padding columns zeroed
+template <typename T>
+Status gemm_rows_small(const T* A, int64_t m, int ld, int n, const double* B, T* out, cudaStream_t s);
+
 // the current C_{t|t} = G W^T R
 template <typename T>
 Status eigen_cross(const SpectralState& sp, const double* rd, int64_t m, int ld, int n, const T* G, const T* Gq,

@@ -380,6 +380,16 @@ struct SweepCfg {
 
 // Per tile of BM rows: Cp = C + CQ into smem, K = Cp M (M streamed in BK-row stages),
 // epilogue: rowdot, x update, C <- K R.
+// (sh, sl) += (ph, pl) in double-float arithmetic (TwoSum, then renormalise)
+__device__ __forceinline__ void df_add(float& sh, float& sl, float ph, float pl) {
+  const float s = sh + ph;
+  const float bb = s - sh;
+  float e = (sh - (s - bb)) + (ph - bb);
+  e += sl + pl;
+  sh = s + e;
+  sl = e - (sh - s);
+}
+
 template <typename T, int NT, int TM>
 __global__ void __launch_bounds__(256) sweep_kernel(int64_t m, int ld, int n, const T* __restrict__ CQ,
                                                     T* __restrict__ C, const T* __restrict__ Msw,
@@ -513,12 +523,28 @@ __global__ void __launch_bounds__(256) sweep_kernel(int64_t m, int ld, int n, co
         }
         if (grow < m && c0 < ld) *reinterpret_cast<V*>(C + grow * ld + c0) = out;
       }
-      double rdv = (double)rd_s - (double)rd_c;
-      double xiv = (double)xi_s - (double)xi_c;
+      double rdv, xiv;
+      if (sizeof(T) == 4) {
+        // across the lanes in double-float (FP32 pairs; the Kahan pair (s, c) holds s - c):
+        // the FP64 rate of this part is low, so only the row's final value is FP64
+        float rh = (float)rd_s, rl = -(float)rd_c, xh = (float)xi_s, xl = -(float)xi_c;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        rdv += __shfl_xor_sync(0xffffffffu, rdv, o);
-        xiv += __shfl_xor_sync(0xffffffffu, xiv, o);
+        for (int o = 16; o > 0; o >>= 1) {
+          const float a = __shfl_xor_sync(0xffffffffu, rh, o), al = __shfl_xor_sync(0xffffffffu, rl, o);
+          const float b = __shfl_xor_sync(0xffffffffu, xh, o), bl = __shfl_xor_sync(0xffffffffu, xl, o);
+          df_add(rh, rl, a, al);
+          df_add(xh, xl, b, bl);
+        }
+        rdv = (double)rh + (double)rl;
+        xiv = (double)xh + (double)xl;
+      } else {
+        rdv = (double)rd_s - (double)rd_c;
+        xiv = (double)xi_s - (double)xi_c;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          rdv += __shfl_xor_sync(0xffffffffu, rdv, o);
+          xiv += __shfl_xor_sync(0xffffffffu, xiv, o);
+        }
       }
       if (tx == 0 && grow < m) {
         var[grow] += theta - rdv;

@@ -103,6 +103,47 @@ def test_tensor_core_m2l_across_orders(B, p):
     assert rel(got, ref) < TOL32
 
 
+@pytest.mark.parametrize("name", ["n300_140x130", "3d_16x16x16_n16", "ragged_61x37_n100"])
+def test_tensor_core_m2l_all_levels_and_ray_passes(B, name):
+    """The tensor-core M2L in FP32 mode: all levels in one launch per pass of 256 rays
+    (n = 300 takes two passes), 3D with q = 125 (MMA N 128)."""
+    w = CASES[name]()
+    with B.Filter.from_workload(w, precision="fp32", m2l="tensor") as f:
+        depth = f.info()["depth"]
+        got = f.cq()
+    ref = _oracle_h2(w, w.q, depth, w.cheb_order)
+    assert rel(got, ref) < TOL32
+
+
+def test_tensor_core_m2l_variants_agree_bit_for_bit(B):
+    """The first create of a shape times every feasible launch variant and keeps the
+    fastest; later creates reuse it. All variants compute the same sums in the same
+    order, so repeated products are identical."""
+    w = CASES["ragged_47x41_n24"]()
+    outs = []
+    for _ in range(3):
+        with B.Filter.from_workload(w, precision="mixed") as f:
+            outs.append(f.cq())
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[1], outs[2])
+
+
+def test_tensor_core_m2l_operator_row_passes(B):
+    """q = 12^2 = 144 > 128 operator rows: two passes of the MMA N dimension."""
+    w = W.small(grid=(75, 61), n=40, steps=1, seed=61)
+    with B.Filter.from_workload(w, precision="fp32", m2l="tensor", cheb_order=12) as f:
+        depth = f.info()["depth"]
+        got = f.cq()
+    ref = _oracle_h2(w, w.q, depth, 12)
+    assert rel(got, ref) < TOL32
+
+
+def test_tensor_core_m2l_option_is_checked(B):
+    w = CASES["m1024_n16"]()
+    with pytest.raises(B.HikfError) as e:
+        B.Filter.from_workload(w, precision="fp64", m2l="tensor")
+    assert e.value.code == B.HIKF_EINVAL
+
+
 def test_h2_product_close_to_exact_sum(B):
     w = CASES["m1024_n16"]()
     H = qht.h_csr(w.h_rowptr, w.h_col, w.h_val, w.m)
