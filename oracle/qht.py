@@ -69,3 +69,26 @@ def qht_gauss_grid(shape, theta: float, length: float, H: sp.csr_matrix) -> np.n
             img = np.moveaxis(np.tensordot(mat, img, axes=([1], [ax])), 0, ax)
         out[:, k] = theta * img.reshape(-1)
     return out
+
+
+def qht_gauss_grid_rows(shape, theta: float, length: float, H: sp.csr_matrix, rows) -> np.ndarray:
+    """Rows `rows` of the exact Q H^T for the Gaussian kernel on a full unit-cell grid.
+
+    Row i of Q is theta times the Kronecker product of the rows of the 1-D kernel
+    matrices at the cell's grid indices (same factorisation as qht_gauss_grid), so
+    [Q H^T]_i = H q_i with q_i formed on its own; for full-size checks on sampled rows.
+    """
+    shape = tuple(int(s) for s in shape)
+    centres = [np.arange(s, dtype=np.float64) + 0.5 for s in shape]
+    H = sp.csr_matrix(H)
+    rows = np.asarray(rows, dtype=np.int64)
+    idx = np.unravel_index(rows, shape)
+    out = np.zeros((rows.size, H.shape[0]))
+    for t in range(rows.size):
+        qi = np.ones(1)
+        for ax, c in enumerate(centres):
+            k = np.exp(-((c[idx[ax][t]] - c) ** 2) / (length * length))
+            qi = np.multiply.outer(qi, k).reshape(-1)
+        out[t] = H @ (theta * qi)
+    return out
+

@@ -4,9 +4,9 @@
 // (q x n, q = p^d Chebyshev nodes, n rays). Per target box this runs as the
 // transposed product  L_B^T (n x q) = sum_{B'} W_{B'}^T (n x q) K^T (q x q)  with the
 // rays as the MMA M dimension (128 per half, up to two halves per pass, passes of 256
-// rays), the operator rows as N (passes of up to 128 rows) and the source nodes as K. Operands are TF32 split
-// into two pieces (rounded hi + exact remainder) and three products are accumulated
-// in FP32 in TMEM:
+// rays), the operator rows as N (passes of up to 128 rows) and the source nodes as K.
+// Operands are TF32 split into two pieces (hi rounded, then the remainder rounded) and
+// three products are accumulated in FP32 in TMEM:
 //   A1 B1 + A1 B2 + A2 B1  (~2^-21 relative), no scaling needed (TF32 keeps FP32's range).
 // All levels go out in one persistent launch per pass: the work items are the
 // (level, box) pairs of every level, W of all levels is packed once into K-major
@@ -14,7 +14,10 @@
 // memory by bulk copies (TMA engine) through a multi-stage mbarrier pipeline. Warp 0
 // copies, warp 1 issues tcgen05.mma, warps 4-7 drain TMEM and write L (coalesced over
 // the rays); two TMEM accumulators let the drain of one box overlap the MMAs of the
-// next. The number of pipeline stages and of CTAs per SM are chosen by a small
+// next; the sources of a box are accumulated in groups (at most ~4096 products per
+// output element per group) whose partials are summed on the CUDA cores, because the
+// tensor core's FP32 accumulation drifts over long chains (3D boxes have up to 189
+// sources of up to 512 nodes). The number of pipeline stages and of CTAs per SM are chosen by a small
 // autotuner that times each feasible variant once per problem shape (the outputs of
 // all variants are identical) and remembers the fastest for the process. Bounded
 // waits as in the sweep kernel.
@@ -44,16 +47,23 @@ __host__ __device__ __forceinline__ uint32_t off32(int row, int k) {
   return (uint32_t)((row >> 3) * 1024 + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
 }
 
+__device__ __forceinline__ float tf32_round(float v) {
+  return __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xFFFFE000u);  // nearest, 10 mantissa bits
+}
+
+// v = hi + lo + O(2^-22 |v|): both pieces rounded to TF32, because kind::tf32 uses only
+// the TF32 bits of an operand; an unrounded lo would be truncated, with a bias that grows
+// with the length of the accumulation (thousands of terms per output in 3D)
 __device__ __forceinline__ void tf32_split(float v, float& hi, float& lo) {
-  const uint32_t u = (__float_as_uint(v) + 0x1000u) & 0xFFFFE000u;  // round to 10 mantissa bits
-  hi = __uint_as_float(u);
-  lo = v - hi;  // exact
+  hi = tf32_round(v);
+  lo = tf32_round(v - hi);  // v - hi is exact
 }
 
 struct Dims {
   int q, npad, nkc, ld, halves, ldp;  // ldp = 128 * halves
   int r0, rw;                         // rays [r0, r0 + rw) of this pass (rw <= ldp)
   int a0, aw;                         // operator rows (target nodes) [a0, a0 + aw) of this pass (aw <= npad)
+  int group;                          // source boxes accumulated in TMEM before a partial is drained
   int64_t a_box_bytes;                // one box: 2 pieces x nkc chunks x ldp x 128 B
   int64_t a_chunk_bytes;              // ldp x 128 B
   int64_t b_chunk_bytes;              // npad x 128 B
@@ -146,11 +156,13 @@ __device__ int interaction_list(int64_t B, int lev, int dim, const int64_t* __re
   return cnt;
 }
 
-__device__ bool has_interactions(int64_t B, int lev, int dim, const int64_t* __restrict__ nsrc, int64_t box0) {
+// number of boxes in the interaction list of box B (same test as interaction_list)
+__device__ int interaction_count(int64_t B, int lev, int dim, const int64_t* __restrict__ nsrc, int64_t box0) {
   int64_t cb[3] = {0, 0, 0};
   for (int bit = 0; bit < lev; ++bit)
     for (int d = 0; d < dim; ++d) cb[d] |= ((B >> (bit * dim + (dim - 1 - d))) & 1) << bit;
   const int ncand = dim == 2 ? 36 : 216;
+  int cnt = 0;
   for (int t = 0; t < ncand; ++t) {
     int tt = t;
     int64_t cc[3] = {0, 0, 0};
@@ -167,9 +179,9 @@ __device__ bool has_interactions(int64_t B, int lev, int dim, const int64_t* __r
     int64_t key = 0;
     for (int bit = lev - 1; bit >= 0; --bit)
       for (int d = 0; d < dim; ++d) key = (key << 1) | ((cc[d] >> bit) & 1);
-    if (nsrc[box0 + key] != 0) return true;
+    if (nsrc[box0 + key] != 0) ++cnt;
   }
-  return false;
+  return cnt;
 }
 
 template <int NPAD, int HALVES, int STAGES>
@@ -279,12 +291,17 @@ __global__ void __launch_bounds__(kThreads, 1) m2l_tc_kernel(Dims d, LevelTab lt
         if (npts[box0 + B] == 0) continue;
         const int nil = interaction_list(B, lev, dim, nsrc, box0, il_src, il_off);
         if (nil == 0) continue;
-        const int buf = (int)(nb & 1);
-        ok = mbar_wait(acc_empty0 + 8u * buf, (uint32_t)(((nb >> 1) & 1) ^ 1), err, s_abort);
-        if (!ok) break;
-        tc_fence_after();
-        const uint32_t dacc = tmem + (uint32_t)(buf * ACC_COLS);
+        uint32_t dacc = 0;
+        int buf = 0;
         for (int e = 0; e < nil && ok; ++e) {
+          const int ge = e % d.group;  // position in the current group of sources
+          if (ge == 0) {
+            buf = (int)(nb & 1);
+            ok = mbar_wait(acc_empty0 + 8u * buf, (uint32_t)(((nb >> 1) & 1) ^ 1), err, s_abort);
+            if (!ok) break;
+            tc_fence_after();
+            dacc = tmem + (uint32_t)(buf * ACC_COLS);
+          }
           for (int kc = 0; kc < d.nkc && ok; ++kc, ++j) {
             const int s = (int)(j % STAGES);
             ok = mbar_wait(full(s), (uint32_t)((j / STAGES) & 1), err, s_abort);
@@ -298,7 +315,7 @@ __global__ void __launch_bounds__(kThreads, 1) m2l_tc_kernel(Dims d, LevelTab lt
                 const uint64_t b1 = smem_desc(base + 2 * A_CHUNK + ks * 256, 128, 1024);
                 const uint64_t b2 = smem_desc(base + 2 * A_CHUNK + B_CHUNK + ks * 256, 128, 1024);
                 const uint32_t dd = dacc + (uint32_t)(h * NPAD);
-                const uint32_t acc = (e > 0 || kc > 0 || ks > 0) ? 1u : 0u;
+                const uint32_t acc = (ge > 0 || kc > 0 || ks > 0) ? 1u : 0u;
                 tc_mma_tf32(dd, a2, b1, idesc, acc);
                 tc_mma_tf32(dd, a1, b2, idesc, 1u);
                 tc_mma_tf32(dd, a1, b1, idesc, 1u);
@@ -306,10 +323,12 @@ __global__ void __launch_bounds__(kThreads, 1) m2l_tc_kernel(Dims d, LevelTab lt
             }
             tc_commit(empty(s));
           }
+          if (ok && (ge == d.group - 1 || e == nil - 1)) {
+            tc_commit(acc_full0 + 8u * buf);  // a partial over this group of sources
+            ++nb;
+          }
         }
         if (!ok) break;
-        tc_commit(acc_full0 + 8u * buf);
-        ++nb;
       }
       tc_commit(drain);
       mbar_wait_drain(drain, 0, err);
@@ -325,29 +344,37 @@ __global__ void __launch_bounds__(kThreads, 1) m2l_tc_kernel(Dims d, LevelTab lt
       const int lev = lt.lev[li];
       const int64_t B = it - lt.item0[li], box0 = lt.box0[li];
       if (npts[box0 + B] == 0) continue;
-      if (!has_interactions(B, lev, dim, nsrc, box0)) continue;
-      const int buf = (int)(nb & 1);
-      ok = __all_sync(0xffffffffu, mbar_wait(acc_full0 + 8u * buf, (uint32_t)((nb >> 1) & 1), err, s_abort));
-      if (!ok) break;
-      tc_fence_after();
+      const int nil = interaction_count(B, lev, dim, nsrc, box0);
+      const int ngroups = (nil + d.group - 1) / d.group;
       float* Lb = Lx + (box0 + B) * (int64_t)d.q * d.ld + (int64_t)d.a0 * d.ld + d.r0;
-      for (int h = 0; h < HALVES; ++h) {
-        const int r = h * 128 + q4 * 32 + lane;
-        for (int c0 = 0; c0 < NPAD; c0 += 32) {
-          uint32_t v[32];
-          tmem_ld32(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(buf * ACC_COLS + h * NPAD + c0), v);
-          tmem_wait_ld();
-          if (r < d.rw) {
+      for (int gi = 0; gi < ngroups && ok; ++gi) {
+        const int buf = (int)(nb & 1);
+        ok = __all_sync(0xffffffffu, mbar_wait(acc_full0 + 8u * buf, (uint32_t)((nb >> 1) & 1), err, s_abort));
+        if (!ok) break;
+        tc_fence_after();
+        // the first partial is written, later ones added (FP32, round to nearest): the
+        // tensor-core accumulation chains stay short
+        for (int h = 0; h < HALVES; ++h) {
+          const int r = h * 128 + q4 * 32 + lane;
+          for (int c0 = 0; c0 < NPAD; c0 += 32) {
+            uint32_t v[32];
+            tmem_ld32(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(buf * ACC_COLS + h * NPAD + c0), v);
+            tmem_wait_ld();
+            if (r < d.rw) {
 #pragma unroll
-            for (int u = 0; u < 32; ++u)
-              if (c0 + u < d.aw) Lb[(int64_t)(c0 + u) * d.ld + r] = __uint_as_float(v[u]);
+              for (int u = 0; u < 32; ++u)
+                if (c0 + u < d.aw) {
+                  float* dst = Lb + (int64_t)(c0 + u) * d.ld + r;
+                  *dst = gi == 0 ? __uint_as_float(v[u]) : *dst + __uint_as_float(v[u]);
+                }
+            }
           }
         }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(acc_empty0 + 8u * buf);
+        ++nb;
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(acc_empty0 + 8u * buf);
-      ++nb;
     }
     if (!ok) *s_abort = 1;
   }
@@ -474,6 +501,8 @@ Status m2l_tc_all(const M2lTcAll& a, cudaStream_t s) {
     const int64_t wthreads = nboxes * (int64_t)d.nkc * kKC * d.ldp;
     pack_w_kernel<<<nblk(wthreads, 256), 256, 0, s>>>(a.W, wbox0, nboxes, a.nsrc, d, wimg);
     HIKF_LAUNCH_CHECK("pack_w");
+    // sources per TMEM accumulation: at most ~4096 products per output element
+    d.group = std::max(1, 4096 / (nkc * kKC));
     for (int a0 = 0; a0 < a.q && st.ok(); a0 += 128) {
       d.a0 = a0;
       d.aw = std::min(128, a.q - a0);

@@ -31,6 +31,12 @@ namespace {
 
 constexpr int kEigThreads = 1024;
 
+__device__ __forceinline__ unsigned long long tc_now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 __device__ double block_sum(double v, double* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -104,14 +110,141 @@ __global__ void __launch_bounds__(kEigThreads) eig_tridiag_kernel(double* __rest
   if (tid == 0 && n >= 2) e[n - 2] = A[(int64_t)(n - 1) * n + (n - 2)];
 }
 
-// ---- 2. implicit symmetric QR with Wilkinson shifts on (d, e), one thread ----
-// (Golub & Van Loan, Alg. 8.3.2 with deflation.) The chase does not need the
-// eigenvectors: it records every Givens rotation (c, s) in order, and the active
-// block [l, m] of every sweep, for the row-parallel back-transformation.
-// Capacity: at most max_sweeps sweeps of at most n - 1 rotations each.
-// d and e live in shared memory, and the entries a sweep carries from one rotation
-// to the next (d[k], e[k] and the bulge) stay in registers, so the dependent chain
-// of a sweep is FP64 arithmetic only.
+// ---- 1'. the same reduction over a grid of co-resident CTAs --------------------
+// Per column k: every CTA forms v (and the norm) redundantly; w = A_sub v is split by
+// rows over the CTAs; after a grid barrier every CTA forms q = w - (v.w) v; the rank-2
+// update A -= 2 (v q^T + q v^T) is split by rows; a second grid barrier ends the column.
+// The FP64 work, O(n^3) in all, is spread over the SMs. The grid barrier is a counter
+// with a bounded wait (2 s), after which the CTA sets *err and leaves; the launch is
+// cooperative, so every CTA is resident.
+constexpr int kTriThreads = 256;
+
+__device__ bool grid_barrier(unsigned* bar, unsigned& gen, int* err, volatile int* s_abort) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned target = (gen + 1u) * gridDim.x;
+    atomicAdd(bar, 1u);
+    const unsigned long long t0 = tc_now_ns();
+    while (*(volatile unsigned*)bar < target) {
+      if (tc_now_ns() - t0 > 2000000000ull) {
+        atomicExch(err, 1);
+        *s_abort = 1;
+        break;
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  ++gen;
+  return *s_abort == 0;
+}
+
+__global__ void __launch_bounds__(kTriThreads) eig_tridiag_grid_kernel(double* __restrict__ A, int n,
+                                                                       double* __restrict__ d,
+                                                                       double* __restrict__ e,
+                                                                       double* __restrict__ hv,
+                                                                       double* __restrict__ wbuf, unsigned* bar,
+                                                                       int* __restrict__ err) {
+  __shared__ double red[32];
+  __shared__ double sv[kMaxN], sq[kMaxN];
+  __shared__ int s_abort;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int rank = blockIdx.x, nblk = gridDim.x;
+  if (tid == 0) s_abort = 0;
+  __syncthreads();
+  unsigned gen = 0;
+  for (int k = 0; k + 2 < n; ++k) {
+    double part = 0.0;
+    for (int i = k + 1 + tid; i < n; i += blockDim.x) {
+      const double x = A[(int64_t)i * n + k];
+      part += x * x;
+    }
+    const double ss = block_sum(part, red);
+    const double x0 = A[(int64_t)(k + 1) * n + k];
+    const double tail = ss - x0 * x0;
+    if (tail <= 0.0) {  // already tridiagonal in this column: H_k = I (every CTA decides alike)
+      if (rank == 0) {
+        for (int i = tid; i < n; i += blockDim.x) hv[(int64_t)k * n + i] = 0.0;
+        if (tid == 0) e[k] = x0;
+      }
+      __syncthreads();
+      continue;
+    }
+    const double alpha = x0 >= 0.0 ? -sqrt(ss) : sqrt(ss);
+    const double v0 = x0 - alpha;
+    const double vn = sqrt(tail + v0 * v0);
+    for (int i = tid; i < n; i += blockDim.x) {
+      double v = 0.0;
+      if (i == k + 1) v = v0 / vn;
+      else if (i > k + 1) v = A[(int64_t)i * n + k] / vn;
+      sv[i] = v;
+      if (rank == 0) hv[(int64_t)k * n + i] = v;
+    }
+    if (rank == 0 && tid == 0) e[k] = alpha;
+    __syncthreads();
+    // w = A_sub v: rows k+1 .. n-1 over the CTAs, a warp per row
+    for (int i = k + 1 + rank * nw + warp; i < n; i += nblk * nw) {
+      double sacc = 0.0;
+      for (int j = k + 1 + lane; j < n; j += 32) sacc += A[(int64_t)i * n + j] * sv[j];
+      for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+      if (lane == 0) wbuf[i] = sacc;
+    }
+    if (!grid_barrier(bar, gen, err, &s_abort)) return;
+    double cp = 0.0;
+    for (int i = k + 1 + tid; i < n; i += blockDim.x) cp += sv[i] * wbuf[i];
+    const double cc = block_sum(cp, red);
+    for (int i = k + 1 + tid; i < n; i += blockDim.x) sq[i] = wbuf[i] - cc * sv[i];  // q = w - (v.w) v
+    __syncthreads();
+    // A -= 2 (v q^T + q v^T) on this CTA's rows
+    for (int i = k + 1 + rank; i < n; i += nblk) {
+      const double vi = sv[i], qi = sq[i];
+      for (int j = k + 1 + tid; j < n; j += blockDim.x) A[(int64_t)i * n + j] -= 2.0 * (vi * sq[j] + qi * sv[j]);
+    }
+    if (!grid_barrier(bar, gen, err, &s_abort)) return;
+  }
+  if (rank == 0) {
+    for (int i = tid; i < n; i += blockDim.x) d[i] = A[(int64_t)i * n + i];
+    if (tid == 0 && n >= 2) e[n - 2] = A[(int64_t)(n - 1) * n + (n - 2)];
+  }
+}
+
+// ---- 2. implicit symmetric QR on (d, e), one thread, several bulges at once ----
+// (Golub & Van Loan, Alg. 8.3.2 with deflation.) Each batch chases kBulges bulges down
+// the active block [l, m], bulge b starting three columns behind bulge b-1, with shifts
+// from the 2 x 2 diagonal blocks at the bottom of the block (a single Wilkinson-shifted
+// bulge when the block is short). A rotation of one bulge depends only on its own
+// previous rotation and on entries the bulge ahead has finished with, so the bulges'
+// FP64 dependency chains overlap: the chase is latency-bound, and this part's FP64
+// latency is long. The chase does not need the eigenvectors: it records every Givens
+// rotation (c, s) and, per bulge, its block [l, m]. Recording bulge by bulge is a valid
+// order for the back-transformation, because a rotation of bulge b on columns (k, k+1)
+// that precedes one of bulge b-1 in time acts on columns at least three apart.
+// Capacity: at most max_sweeps bulges of at most n - 1 rotations each.
+// d and e live in shared memory; each bulge carries its d[k], e[k] and (x, z) in registers.
+constexpr int kBulges = 4;
+
+__device__ __forceinline__ void givens(double x, double z, double& r, double& c, double& s) {
+  // r = |(x, z)|, c = x / r, s = z / r: one reciprocal square root where x^2 + z^2 is
+  // safely inside the normal range (always, for the matrices of this library), hypot
+  // and a division otherwise
+  const double t2 = fma(x, x, z * z);
+  c = 1.0;
+  s = 0.0;
+  if (t2 > 1e-290 && t2 < 1e290) {
+    const double ir = rsqrt(t2);
+    r = t2 * ir;
+    c = x * ir;
+    s = z * ir;
+  } else {
+    r = hypot(x, z);
+    if (r > 0.0) {
+      c = x / r;
+      s = z / r;
+    }
+  }
+}
+
 __global__ void eig_qr_chase_kernel(double* __restrict__ dg, double* __restrict__ eg, int n, int max_sweeps,
                                     double2* __restrict__ rot, int2* __restrict__ sweep_lm,
                                     int* __restrict__ nsweeps, int* __restrict__ info) {
@@ -132,55 +265,69 @@ __global__ void eig_qr_chase_kernel(double* __restrict__ dg, double* __restrict_
         --m;
       }
       if (m == 0) break;
-      if (ns >= max_sweeps) {
+      int l = m - 1;
+      while (l > 0 && fabs(e[l - 1]) > eps * (fabs(d[l - 1]) + fabs(d[l]))) --l;
+      const int len = m - l;  // rotations per bulge
+      const int kb = len >= 4 * kBulges ? kBulges : 1;
+      if (ns + kb > max_sweeps) {
         bad = 1;
         break;
       }
-      int l = m - 1;
-      while (l > 0 && fabs(e[l - 1]) > eps * (fabs(d[l - 1]) + fabs(d[l]))) --l;
-      // Wilkinson shift from the trailing 2 x 2 block
-      const double a = d[m - 1], b = e[m - 1], c2 = d[m];
-      const double delta = 0.5 * (a - c2);
-      const double sgn = delta >= 0.0 ? 1.0 : -1.0;
-      const double mu = c2 - b * b / (delta + sgn * hypot(delta, b));
-      double x = d[l] - mu, z = e[l];
-      double ak = d[l], bk = e[l];  // d[k], e[k] of the current rotation (carried)
-      for (int k = l; k < m; ++k) {
-        const double ck = d[k + 1];
-        const double f = k + 1 < m ? e[k + 1] : 0.0;
-        // r = |(x, z)|, c = x / r, s = z / r: one reciprocal square root where x^2 + z^2
-        // is safely inside the normal range (always, for the matrices of this library),
-        // hypot and a division otherwise
-        const double t2 = fma(x, x, z * z);
-        double r, c = 1.0, s = 0.0;
-        if (t2 > 1e-290 && t2 < 1e290) {
-          const double ir = rsqrt(t2);
-          r = t2 * ir;
-          c = x * ir;
-          s = z * ir;
-        } else {
-          r = hypot(x, z);
-          if (r > 0.0) {
-            c = x / r;
-            s = z / r;
-          }
+      double mu[kBulges];
+      if (kb == 1) {
+        // Wilkinson shift from the trailing 2 x 2 block
+        const double a = d[m - 1], b = e[m - 1], c2 = d[m];
+        const double delta = 0.5 * (a - c2);
+        const double sgn = delta >= 0.0 ? 1.0 : -1.0;
+        mu[0] = c2 - b * b / (delta + sgn * hypot(delta, b));
+      } else {
+        // both eigenvalues of each of the kBulges/2 trailing 2 x 2 diagonal blocks
+        for (int j = 0; j < kBulges / 2; ++j) {
+          const int i1 = m - 2 * j;
+          const double a = d[i1 - 1], b = e[i1 - 1], c2 = d[i1];
+          const double mid = 0.5 * (a + c2), rad = hypot(0.5 * (a - c2), b);
+          mu[2 * j] = mid - rad;
+          mu[2 * j + 1] = mid + rad;
         }
-        if (k > l) e[k - 1] = r;
-        const double cc = c * c, ss = s * s, cs = c * s;
-        d[k] = ak * cc + 2.0 * bk * cs + ck * ss;
-        const double dk1 = ak * ss - 2.0 * bk * cs + ck * cc;
-        const double ek = (ck - ak) * cs + bk * (cc - ss);
-        rot[nr++] = make_double2(c, s);
-        x = ek;
-        if (k + 1 < m) {
-          z = f * s;
-          bk = f * c;
-        }
-        e[k] = ek;
-        ak = dk1;
       }
-      d[m] = ak;
-      sweep_lm[ns++] = make_int2(l, m);
+      // bulge state: carried d[k], e[k] and the (x, z) to annihilate
+      double x[kBulges], z[kBulges], ak[kBulges], bk[kBulges];
+      const int steps = len + 3 * (kb - 1);
+      for (int st = 0; st < steps; ++st) {
+#pragma unroll
+        for (int bb = 0; bb < kBulges; ++bb) {
+          if (bb >= kb) continue;
+          const int k = l + st - 3 * bb;
+          if (k < l || k >= m) continue;
+          if (k == l) {  // the bulge enters the block
+            ak[bb] = d[l];
+            bk[bb] = e[l];
+            x[bb] = d[l] - mu[bb];
+            z[bb] = e[l];
+          }
+          const double ck = d[k + 1];
+          const double f = k + 1 < m ? e[k + 1] : 0.0;
+          double r, c, s;
+          givens(x[bb], z[bb], r, c, s);
+          if (k > l) e[k - 1] = r;
+          const double cc = c * c, ss = s * s, cs = c * s;
+          d[k] = ak[bb] * cc + 2.0 * bk[bb] * cs + ck * ss;
+          const double dk1 = ak[bb] * ss - 2.0 * bk[bb] * cs + ck * cc;
+          const double ek = (ck - ak[bb]) * cs + bk[bb] * (cc - ss);
+          rot[nr + (int64_t)bb * len + (k - l)] = make_double2(c, s);
+          x[bb] = ek;
+          if (k + 1 < m) {
+            z[bb] = f * s;
+            bk[bb] = f * c;
+          }
+          e[k] = ek;
+          ak[bb] = dk1;
+          if (k == m - 1) d[m] = dk1;  // the bulge leaves the block
+        }
+      }
+      for (int bb = 0; bb < kb; ++bb) sweep_lm[ns + bb] = make_int2(l, m);
+      ns += kb;
+      nr += (int64_t)kb * len;
     }
     *info = bad;
     *nsweeps = ns;
@@ -192,47 +339,65 @@ __global__ void eig_qr_chase_kernel(double* __restrict__ dg, double* __restrict_
   }
 }
 
-// ---- 3. eigenvectors V = H_0 ... H_{n-3} G_1 G_2 ... , one thread per row ----
-// Row i of V is e_i^T times the product; each factor acts on a row independently,
-// so the rows are spread over many CTAs (each row held in shared memory).
-constexpr int kVecRows = 8;  // rows (threads) per CTA
-__global__ void __launch_bounds__(kVecRows) eig_vectors_kernel(const double* __restrict__ hv,
-                                                               const double2* __restrict__ rot,
-                                                               const int2* __restrict__ sweep_lm,
-                                                               const int* __restrict__ nsweeps,
-                                                               const int* __restrict__ info, int n,
-                                                               double* __restrict__ V) {
+// ---- 3. eigenvectors V = H_0 ... H_{n-3} G_1 G_2 ... , rows in parallel ----
+// Row i of V is e_i^T times the product; each factor acts on a row independently. One
+// thread carries kVecRows rows (held in shared memory) through the factors together, so
+// the rows' FP64 dependency chains interleave; the row groups are spread over CTAs.
+constexpr int kVecRows = 8;  // rows per thread (one thread per CTA)
+__global__ void __launch_bounds__(32) eig_vectors_kernel(const double* __restrict__ hv,
+                                                         const double2* __restrict__ rot,
+                                                         const int2* __restrict__ sweep_lm,
+                                                         const int* __restrict__ nsweeps,
+                                                         const int* __restrict__ info, int n,
+                                                         double* __restrict__ V) {
   extern __shared__ double srow[];  // kVecRows x (n + 1)
-  const int i = blockIdx.x * kVecRows + threadIdx.x;
-  if (*info || i >= n) return;
-  double* vr = srow + threadIdx.x * (n + 1);
-  for (int j = 0; j < n; ++j) vr[j] = j == i ? 1.0 : 0.0;
+  if (threadIdx.x != 0 || *info) return;
+  const int i0 = blockIdx.x * kVecRows;
+  const int nr = min(kVecRows, n - i0);
+  if (nr <= 0) return;
+  const int ld = n + 1;
+  for (int r = 0; r < kVecRows; ++r)
+    for (int j = 0; j < n; ++j) srow[r * ld + j] = (r < nr && j == i0 + r) ? 1.0 : 0.0;
   // row <- row (I - 2 v_k v_k^T), k = 0 .. n-3
   for (int k = 0; k + 2 < n; ++k) {
     const double* vk = hv + (int64_t)k * n;
-    double dot = 0.0;
-    for (int j = k + 1; j < n; ++j) dot += vr[j] * vk[j];
-    const double t = 2.0 * dot;
-    if (t != 0.0)
-      for (int j = k + 1; j < n; ++j) vr[j] -= t * vk[j];
+    double dot[kVecRows];
+#pragma unroll
+    for (int r = 0; r < kVecRows; ++r) dot[r] = 0.0;
+    for (int j = k + 1; j < n; ++j) {
+      const double v = vk[j];
+#pragma unroll
+      for (int r = 0; r < kVecRows; ++r) dot[r] = fma(srow[r * ld + j], v, dot[r]);
+    }
+    for (int j = k + 1; j < n; ++j) {
+      const double v = vk[j];
+#pragma unroll
+      for (int r = 0; r < kVecRows; ++r) srow[r * ld + j] -= 2.0 * dot[r] * v;
+    }
   }
   // row <- row G, sweep by sweep, rotations in recorded order
   const int ns = *nsweeps;
   int64_t off = 0;
   for (int sw = 0; sw < ns; ++sw) {
     const int2 lm = sweep_lm[sw];
-    double vk = vr[lm.x];
-#pragma unroll 4
+    double vk[kVecRows];
+#pragma unroll
+    for (int r = 0; r < kVecRows; ++r) vk[r] = srow[r * ld + lm.x];
     for (int k = lm.x; k < lm.y; ++k) {
       const double2 cs = rot[off + (k - lm.x)];
-      const double vk1 = vr[k + 1];
-      vr[k] = cs.x * vk + cs.y * vk1;
-      vk = -cs.y * vk + cs.x * vk1;
+#pragma unroll
+      for (int r = 0; r < kVecRows; ++r) {
+        const double vk1 = srow[r * ld + k + 1];
+        srow[r * ld + k] = cs.x * vk[r] + cs.y * vk1;
+        vk[r] = -cs.y * vk[r] + cs.x * vk1;
+      }
     }
-    vr[lm.y] = vk;
+#pragma unroll
+    for (int r = 0; r < kVecRows; ++r) srow[r * ld + lm.y] = vk[r];
     off += lm.y - lm.x;
   }
-  for (int j = 0; j < n; ++j) V[(int64_t)i * n + j] = vr[j];
+  for (int r = 0; r < nr; ++r)
+    for (int j = 0; j < n; ++j) V[(int64_t)(i0 + r) * n + j] = srow[r * ld + j];
 }
 
 // B~ = D sym(HCQ) D with D = R^{-1/2}
@@ -385,28 +550,53 @@ Status spectral_setup(SpectralState& sp, const double* hcq_sym, const double* rd
   double *A = nullptr, *V = nullptr, *hv = nullptr, *e = nullptr;
   double2* rot = nullptr;
   int2* lm = nullptr;
-  int* ints = nullptr;  // info, nsweeps
+  int* ints = nullptr;
   HIKF_CUDA(cudaMallocAsync((void**)&A, sizeof(double) * nn, s));
   HIKF_CUDA(cudaMallocAsync((void**)&V, sizeof(double) * nn, s));
   HIKF_CUDA(cudaMallocAsync((void**)&hv, sizeof(double) * nn, s));
   HIKF_CUDA(cudaMallocAsync((void**)&e, sizeof(double) * n, s));
   HIKF_CUDA(cudaMallocAsync((void**)&rot, sizeof(double2) * max_rot, s));
   HIKF_CUDA(cudaMallocAsync((void**)&lm, sizeof(int2) * max_sweeps, s));
-  HIKF_CUDA(cudaMallocAsync((void**)&ints, 2 * sizeof(int), s));
+  double* wbuf = nullptr;
+  HIKF_CUDA(cudaMallocAsync((void**)&wbuf, sizeof(double) * n, s));
+  HIKF_CUDA(cudaMallocAsync((void**)&ints, 4 * sizeof(int), s));  // info, nsweeps, barrier, tridiag error
+  HIKF_CUDA(cudaMemsetAsync(ints, 0, 4 * sizeof(int), s));
   HIKF_CUDA(cudaMemsetAsync(e, 0, sizeof(double) * n, s));
   scale_b_kernel<<<nblk(nn, 256), 256, 0, s>>>(hcq_sym, rd, n, A);
   HIKF_LAUNCH_CHECK("scale_b");
-  eig_tridiag_kernel<<<1, kEigThreads, 0, s>>>(A, n, sp.lam, e, hv);
-  HIKF_LAUNCH_CHECK("eig_tridiag");
+  {
+    // cooperative grid: at most one CTA per SM, all resident
+    int dev = 0, sms = 1, per_sm = 0;
+    HIKF_CUDA(cudaGetDevice(&dev));
+    HIKF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    HIKF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, eig_tridiag_grid_kernel, kTriThreads, 0));
+    const int grid = std::max(1, std::min({64, sms * std::max(per_sm, 0), std::max(1, n / 4)}));
+    if (per_sm >= 1) {
+      double* Ap = A;
+      double* dp = sp.lam;
+      double* ep = e;
+      double* hp = hv;
+      double* wp = wbuf;
+      unsigned* bp = reinterpret_cast<unsigned*>(ints + 2);
+      int* errp = ints + 3;
+      int nn_ = n;
+      void* args[] = {&Ap, &nn_, &dp, &ep, &hp, &wp, &bp, &errp};
+      HIKF_CUDA(cudaLaunchCooperativeKernel((const void*)eig_tridiag_grid_kernel, dim3(grid), dim3(kTriThreads), args,
+                                            0, s));
+    } else {
+      eig_tridiag_kernel<<<1, kEigThreads, 0, s>>>(A, n, sp.lam, e, hv);
+    }
+    HIKF_LAUNCH_CHECK("eig_tridiag");
+  }
   eig_qr_chase_kernel<<<1, 32, 0, s>>>(sp.lam, e, n, max_sweeps, rot, lm, ints + 1, ints);
   HIKF_LAUNCH_CHECK("eig_qr_chase");
   const size_t vsmem = sizeof(double) * kVecRows * (size_t)(n + 1);
-  eig_vectors_kernel<<<nblk(n, kVecRows), kVecRows, vsmem, s>>>(hv, rot, lm, ints + 1, ints, n, V);
+  eig_vectors_kernel<<<nblk(n, kVecRows), 32, vsmem, s>>>(hv, rot, lm, ints + 1, ints, n, V);
   HIKF_LAUNCH_CHECK("eig_vectors");
   spec_init_kernel<<<nblk(nn, 256), 256, 0, s>>>(V, sp.lam, rd, n, c, sp.W64, sp.W32, sp.s, flag);
   HIKF_LAUNCH_CHECK("spec_init");
-  int hinfo = 0;
-  HIKF_CUDA(cudaMemcpyAsync(&hinfo, ints, sizeof(int), cudaMemcpyDeviceToHost, s));
+  int hinfo[4] = {0, 0, 0, 0};
+  HIKF_CUDA(cudaMemcpyAsync(hinfo, ints, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
   HIKF_CUDA(cudaStreamSynchronize(s));
   HIKF_CUDA(cudaFreeAsync(A, s));
   HIKF_CUDA(cudaFreeAsync(V, s));
@@ -415,7 +605,9 @@ Status spectral_setup(SpectralState& sp, const double* hcq_sym, const double* rd
   HIKF_CUDA(cudaFreeAsync(rot, s));
   HIKF_CUDA(cudaFreeAsync(lm, s));
   HIKF_CUDA(cudaFreeAsync(ints, s));
-  if (hinfo) return make_status(HIKF_ECUDA, "eigensolver did not converge");
+  HIKF_CUDA(cudaFreeAsync(wbuf, s));
+  if (hinfo[3]) return make_status(HIKF_ETIMEOUT, "a bounded grid barrier in the tridiagonalisation timed out");
+  if (hinfo[0]) return make_status(HIKF_ECUDA, "eigensolver did not converge");
   return Status::Ok();
 }
 

@@ -17,6 +17,7 @@ import pytest
 
 from oracle import h2, kf, qht
 from paper_1404_3816_gb300 import workload as W
+from tests.sym_recurrence import symmetric_recurrence
 
 pytestmark = pytest.mark.gpu
 
@@ -261,6 +262,50 @@ def test_update_with_given_cq_matches_oracle(B):
         assert rel(f.mean(), ref["x"]) < TOL32
         assert rel(f.variance(), ref["var"]) < TOL32
         assert f.info()["step"] == Y.shape[0]
+
+
+def _gauss3d(grid=(16, 16, 16), n=64, length=4.0, steps=3):
+    w = W.make(grid=grid, n=n, q=W.KernelSpec(W.GAUSS, 0.01, length), p0=W.KernelSpec(W.GAUSS, 1.0, length),
+               r=1e-3, steps=steps, seed=4, cheb_order=6)
+    Y, _ = W.measurements(w)
+    H = qht.h_csr(w.h_rowptr, w.h_col, w.h_val, w.m)
+    return w, Y, H
+
+
+def test_update_follows_the_symmetric_recurrence_on_an_approximate_cq(B):
+    """A perturbed C_Q (H C_Q not symmetric) on an ill-conditioned 3D Gaussian case: the
+    FP64 update equals the symmetric n x n recurrence of H C_{t+1|t} to rounding, and
+    not Alg. 2 applied to the raw product (which drifts away by ~1e-3 here)."""
+    w, Y, H = _gauss3d()
+    cq = qht.qht_gauss_grid(w.grid, w.q.theta, w.q.length, H)
+    cq = cq + 1e-6 * np.sqrt(np.mean(cq * cq)) * np.random.default_rng(3).standard_normal(cq.shape)
+    args = (cq, 100.0 * cq, np.full(w.m, 1.0), w.q.theta, H, w.r_diag, w.x0, Y)
+    model = symmetric_recurrence(*args)
+    raw = kf.hikf_cross(*args)
+    with B.Filter(w.points, w.q, w.h_rowptr, w.h_col, w.h_val, w.r_diag, w.x0, w.p0, cq=cq, c0=100.0 * cq,
+                  precision="fp64") as f:
+        for y in Y:
+            f.assimilate(y)
+        x, v = f.mean(), f.variance()
+    assert rel(x, model["x"]) < 1e-8
+    assert rel(v, model["var"]) < TOL64
+    assert rel(x, raw["x"]) > 1e-5          # the two readings really differ on this input
+
+
+@pytest.mark.parametrize("form", ["cross", "eigen", "nspace"])
+def test_spectral_forms_follow_the_symmetric_recurrence(B, form):
+    """The eigenbasis and n-space forms (B~ = R^{-1/2} sym(H C_Q) R^{-1/2}) and the
+    spectral chain of the cross form take the same reading: on their own H^2 product,
+    read back, they equal the symmetric recurrence in FP64."""
+    w, Y, H = _gauss3d()
+    with B.Filter.from_workload(w, precision="fp64", form=form, chain="spectral", m2l="simt") as f:
+        cq = f.cq()
+        for y in Y:
+            f.assimilate(y)
+        x, v = f.mean(), f.variance()
+    model = symmetric_recurrence(cq, 100.0 * cq, np.full(w.m, 1.0), w.q.theta, H, w.r_diag, w.x0, Y)
+    assert rel(x, model["x"]) < 1e-8
+    assert rel(v, model["var"]) < TOL64
 
 
 def test_nonfinite_measurement_is_rejected_and_state_kept(B):

@@ -46,3 +46,5 @@ def test_separable_gaussian_product_equals_direct_sum(grid):
     H = qht.h_csr(w.h_rowptr, w.h_col, w.h_val, w.m)
     direct = qht.qht(w.points, kf.gcf(0.3, 4.0, 2), H)
     assert np.allclose(qht.qht_gauss_grid(grid, 0.3, 4.0, H), direct, rtol=1e-12, atol=1e-15)
+    rows = np.array([0, 3, w.m // 2, w.m - 1])
+    assert np.allclose(qht.qht_gauss_grid_rows(grid, 0.3, 4.0, H, rows), direct[rows], rtol=1e-12, atol=1e-15)
