@@ -209,6 +209,7 @@ typedef struct {
   int sweep_launches; /* kernel launches of one measurement update */
   int chain;          /* HIKF_CHAIN_FACTOR or HIKF_CHAIN_SPECTRAL: the form in use */
   int form;           /* HIKF_FORM_CROSS, HIKF_FORM_EIGEN or HIKF_FORM_NSPACE */
+  int eig_sweeps;     /* Jacobi sweeps of the create-time eigendecomposition (0: factor chain) */
 } hikf_info_t;
 
 hikf_status hikf_info(const hikf_t* h, hikf_info_t* info);

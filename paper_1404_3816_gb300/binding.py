@@ -57,7 +57,7 @@ class Info(C.Structure):
     _fields_ = [("m", C.c_int64), ("n", C.c_int), ("dim", C.c_int), ("depth", C.c_int),
                 ("cheb_order", C.c_int), ("precision", C.c_int), ("step", C.c_int64),
                 ("device_bytes", C.c_int64), ("create_ms", C.c_double), ("sweep_launches", C.c_int),
-                ("chain", C.c_int), ("form", C.c_int)]
+                ("chain", C.c_int), ("form", C.c_int), ("eig_sweeps", C.c_int)]
 
 
 _lib = None

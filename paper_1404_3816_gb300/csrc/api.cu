@@ -818,6 +818,7 @@ hikf_status hikf_info(const hikf_t* h, hikf_info_t* info) {
   info->sweep_launches = h->launches;
   info->chain = h->spectral ? HIKF_CHAIN_SPECTRAL : HIKF_CHAIN_FACTOR;
   info->form = h->nspace ? HIKF_FORM_NSPACE : (h->eigen ? HIKF_FORM_EIGEN : HIKF_FORM_CROSS);
+  info->eig_sweeps = h->spectral ? h->sp.sweeps : 0;
   return HIKF_OK;
 }
 

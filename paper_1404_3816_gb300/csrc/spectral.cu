@@ -12,12 +12,15 @@
 // step, whose FP64 cost and conditioning (cond(S) ~ 1e8 and more) would
 // otherwise dominate the update.
 //
-// Eigensolver (FP64): Householder reduction to tridiagonal form on one CTA;
-// implicit symmetric QR steps with Wilkinson shifts (Golub & Van Loan, Sec. 8.3)
-// chased by one thread, which only records the rotations; then the eigenvectors
-// V = Q G_1 G_2 ... row by row over many CTAs (rows are independent). The FP64
-// rate per SM is low on this part, so the O(n^3) work is spread over SMs and
-// the serial chase does O(n^2) work only.
+// Eigensolver (FP64): parallel cyclic Jacobi (Golub & Van Loan, Sec. 8.5) on the full
+// matrix. A sweep is N - 1 rounds of a round-robin ordering; a round rotates N / 2
+// disjoint index pairs at once, so every 2 x 2 block of A and every pair of columns of V
+// is updated independently. On this part an FP64 instruction occupies its SM
+// sub-partition for 64 cycles whatever the number of active lanes, and a dependent
+// divide or square root takes several hundred cycles. So the work is laid out to keep
+// every lane of every sub-partition busy across all SMs, and serial FP64 chains are kept
+// to one rotation per round. A QR algorithm on the tridiagonal form would chase its
+// rotations one after another on a single thread.
 #include <math.h>
 
 #include <algorithm>
@@ -29,96 +32,14 @@ namespace hikf {
 
 namespace {
 
-constexpr int kEigThreads = 1024;
-
 __device__ __forceinline__ unsigned long long tc_now_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
 
-__device__ double block_sum(double v, double* red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  double s = 0.0;
-  for (int w = 0; w < nw; ++w) s += red[w];
-  return s;
-}
-
-// ---- 1. Householder tridiagonalisation (one CTA) --------------------------
-// A (n x n, row-major, symmetric; destroyed) -> T = Q^T A Q with diagonal d and
-// sub-diagonal e; Q = H_0 H_1 ... H_{n-3}, H_k = I - 2 v_k v_k^T with v_k (unit,
-// zero at indices <= k) stored as row k of hv.
-__global__ void __launch_bounds__(kEigThreads) eig_tridiag_kernel(double* __restrict__ A, int n,
-                                                                 double* __restrict__ d, double* __restrict__ e,
-                                                                 double* __restrict__ hv) {
-  __shared__ double red[32];
-  __shared__ double sv[kMaxN], sw[kMaxN];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  for (int k = 0; k + 2 < n; ++k) {
-    double part = 0.0;
-    for (int i = k + 1 + tid; i < n; i += blockDim.x) {
-      double x = A[(int64_t)i * n + k];
-      part += x * x;
-    }
-    const double ss = block_sum(part, red);
-    const double x0 = A[(int64_t)(k + 1) * n + k];
-    const double tail = ss - x0 * x0;
-    double* vk = hv + (int64_t)k * n;
-    if (tail <= 0.0) {  // already tridiagonal in this column: H_k = I
-      for (int i = tid; i < n; i += blockDim.x) vk[i] = 0.0;
-      if (tid == 0) e[k] = x0;
-      __syncthreads();
-      continue;
-    }
-    const double alpha = x0 >= 0.0 ? -sqrt(ss) : sqrt(ss);
-    const double v0 = x0 - alpha;
-    const double vn = sqrt(tail + v0 * v0);
-    for (int i = tid; i < n; i += blockDim.x) {
-      double v = 0.0;
-      if (i == k + 1) v = v0 / vn;
-      else if (i > k + 1) v = A[(int64_t)i * n + k] / vn;
-      sv[i] = v;
-      vk[i] = v;
-    }
-    if (tid == 0) e[k] = alpha;
-    __syncthreads();
-    // w = A_sub v (rows k+1..n-1), warp per row
-    for (int i = k + 1 + warp; i < n; i += nw) {
-      double s = 0.0;
-      for (int j = k + 1 + lane; j < n; j += 32) s += A[(int64_t)i * n + j] * sv[j];
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) sw[i] = s;
-    }
-    __syncthreads();
-    double cp = 0.0;
-    for (int i = k + 1 + tid; i < n; i += blockDim.x) cp += sv[i] * sw[i];
-    const double cc = block_sum(cp, red);
-    for (int i = k + 1 + tid; i < n; i += blockDim.x) sw[i] = sw[i] - cc * sv[i];  // q = w - (v.w) v
-    __syncthreads();
-    const int len = n - k - 1;
-    for (int64_t t = tid; t < (int64_t)len * len; t += blockDim.x) {
-      int i = k + 1 + (int)(t / len), j = k + 1 + (int)(t % len);
-      A[(int64_t)i * n + j] -= 2.0 * (sv[i] * sw[j] + sw[i] * sv[j]);
-    }
-    __syncthreads();
-  }
-  for (int i = tid; i < n; i += blockDim.x) d[i] = A[(int64_t)i * n + i];
-  if (tid == 0 && n >= 2) e[n - 2] = A[(int64_t)(n - 1) * n + (n - 2)];
-}
-
-// ---- 1'. the same reduction over a grid of co-resident CTAs --------------------
-// Per column k: every CTA forms v (and the norm) redundantly; w = A_sub v is split by
-// rows over the CTAs; after a grid barrier every CTA forms q = w - (v.w) v; the rank-2
-// update A -= 2 (v q^T + q v^T) is split by rows; a second grid barrier ends the column.
-// The FP64 work, O(n^3) in all, is spread over the SMs. The grid barrier is a counter
-// with a bounded wait (2 s), after which the CTA sets *err and leaves; the launch is
-// cooperative, so every CTA is resident.
-constexpr int kTriThreads = 256;
-
+// Grid barrier over a cooperative launch (every CTA resident): a counter with a bounded
+// wait (2 s), after which the CTA sets *err and *s_abort, and the caller leaves.
 __device__ bool grid_barrier(unsigned* bar, unsigned& gen, int* err, volatile int* s_abort) {
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -140,273 +61,230 @@ __device__ bool grid_barrier(unsigned* bar, unsigned& gen, int* err, volatile in
   return *s_abort == 0;
 }
 
-__global__ void __launch_bounds__(kTriThreads) eig_tridiag_grid_kernel(double* __restrict__ A, int n,
-                                                                       double* __restrict__ d,
-                                                                       double* __restrict__ e,
-                                                                       double* __restrict__ hv,
-                                                                       double* __restrict__ wbuf, unsigned* bar,
-                                                                       int* __restrict__ err) {
-  __shared__ double red[32];
-  __shared__ double sv[kMaxN], sq[kMaxN];
-  __shared__ int s_abort;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  const int rank = blockIdx.x, nblk = gridDim.x;
-  if (tid == 0) s_abort = 0;
-  __syncthreads();
-  unsigned gen = 0;
-  for (int k = 0; k + 2 < n; ++k) {
-    double part = 0.0;
-    for (int i = k + 1 + tid; i < n; i += blockDim.x) {
-      const double x = A[(int64_t)i * n + k];
-      part += x * x;
-    }
-    const double ss = block_sum(part, red);
-    const double x0 = A[(int64_t)(k + 1) * n + k];
-    const double tail = ss - x0 * x0;
-    if (tail <= 0.0) {  // already tridiagonal in this column: H_k = I (every CTA decides alike)
-      if (rank == 0) {
-        for (int i = tid; i < n; i += blockDim.x) hv[(int64_t)k * n + i] = 0.0;
-        if (tid == 0) e[k] = x0;
-      }
-      __syncthreads();
-      continue;
-    }
-    const double alpha = x0 >= 0.0 ? -sqrt(ss) : sqrt(ss);
-    const double v0 = x0 - alpha;
-    const double vn = sqrt(tail + v0 * v0);
-    for (int i = tid; i < n; i += blockDim.x) {
-      double v = 0.0;
-      if (i == k + 1) v = v0 / vn;
-      else if (i > k + 1) v = A[(int64_t)i * n + k] / vn;
-      sv[i] = v;
-      if (rank == 0) hv[(int64_t)k * n + i] = v;
-    }
-    if (rank == 0 && tid == 0) e[k] = alpha;
-    __syncthreads();
-    // w = A_sub v: rows k+1 .. n-1 over the CTAs, a warp per row
-    for (int i = k + 1 + rank * nw + warp; i < n; i += nblk * nw) {
-      double sacc = 0.0;
-      for (int j = k + 1 + lane; j < n; j += 32) sacc += A[(int64_t)i * n + j] * sv[j];
-      for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
-      if (lane == 0) wbuf[i] = sacc;
-    }
-    if (!grid_barrier(bar, gen, err, &s_abort)) return;
-    double cp = 0.0;
-    for (int i = k + 1 + tid; i < n; i += blockDim.x) cp += sv[i] * wbuf[i];
-    const double cc = block_sum(cp, red);
-    for (int i = k + 1 + tid; i < n; i += blockDim.x) sq[i] = wbuf[i] - cc * sv[i];  // q = w - (v.w) v
-    __syncthreads();
-    // A -= 2 (v q^T + q v^T) on this CTA's rows
-    for (int i = k + 1 + rank; i < n; i += nblk) {
-      const double vi = sv[i], qi = sq[i];
-      for (int j = k + 1 + tid; j < n; j += blockDim.x) A[(int64_t)i * n + j] -= 2.0 * (vi * sq[j] + qi * sv[j]);
-    }
-    if (!grid_barrier(bar, gen, err, &s_abort)) return;
+// ---- parallel cyclic Jacobi ------------------------------------------------------------
+// Round-robin ordering over N (even) indices: in round r, index N - 1 meets r, and every
+// other index a meets (2r - a) mod (N - 1); pair 0 is (r, N - 1), pair k >= 1 is
+// ((r + k), (r - k)) mod (N - 1). Over N - 1 rounds every pair meets once.
+__device__ __forceinline__ int rr_mod(int a, int m) {
+  a %= m;
+  return a < 0 ? a + m : a;
+}
+__device__ __forceinline__ void rr_pair(int r, int k, int N, int& p, int& q) {
+  if (k == 0) {
+    p = r;
+    q = N - 1;
+  } else {
+    p = rr_mod(r + k, N - 1);
+    q = rr_mod(r - k, N - 1);
   }
-  if (rank == 0) {
-    for (int i = tid; i < n; i += blockDim.x) d[i] = A[(int64_t)i * n + i];
-    if (tid == 0 && n >= 2) e[n - 2] = A[(int64_t)(n - 1) * n + (n - 2)];
+  if (p > q) {
+    const int t = p;
+    p = q;
+    q = t;
   }
 }
+// index of the pair that holds a in round r, and a's partner
+__device__ __forceinline__ int rr_slot(int r, int a, int N, int& partner) {
+  if (a == N - 1 || a == r) {
+    partner = a == r ? N - 1 : r;
+    return 0;
+  }
+  partner = rr_mod(2 * r - a, N - 1);
+  const int d = rr_mod(a - r, N - 1);
+  return min(d, N - 1 - d);
+}
 
-// ---- 2. implicit symmetric QR on (d, e), one thread, several bulges at once ----
-// (Golub & Van Loan, Alg. 8.3.2 with deflation.) Each batch chases kBulges bulges down
-// the active block [l, m], bulge b starting three columns behind bulge b-1, with shifts
-// from the 2 x 2 diagonal blocks at the bottom of the block (a single Wilkinson-shifted
-// bulge when the block is short). A rotation of one bulge depends only on its own
-// previous rotation and on entries the bulge ahead has finished with, so the bulges'
-// FP64 dependency chains overlap: the chase is latency-bound, and this part's FP64
-// latency is long. The chase does not need the eigenvectors: it records every Givens
-// rotation (c, s) and, per bulge, its block [l, m]. Recording bulge by bulge is a valid
-// order for the back-transformation, because a rotation of bulge b on columns (k, k+1)
-// that precedes one of bulge b-1 in time acts on columns at least three apart.
-// Capacity: at most max_sweeps bulges of at most n - 1 rotations each.
-// d and e live in shared memory; each bulge carries its d[k], e[k] and (x, z) in registers.
-constexpr int kBulges = 4;
-
-__device__ __forceinline__ void givens(double x, double z, double& r, double& c, double& s) {
-  // r = |(x, z)|, c = x / r, s = z / r: one reciprocal square root where x^2 + z^2 is
-  // safely inside the normal range (always, for the matrices of this library), hypot
-  // and a division otherwise
-  const double t2 = fma(x, x, z * z);
+// One Jacobi rotation J (J_pp = J_qq = c, J_pq = s, J_qp = -s) with (J^T A J)_pq = 0:
+// t = tan(phi) is the smaller root of t^2 + 2 tau t - 1 = 0, tau = (a_qq - a_pp) / (2 a_pq),
+// written as t = sign(d) b / (|d| + hypot(d, b)) with d = a_qq - a_pp, b = 2 a_pq (one
+// division); c = 1 / sqrt(1 + t^2), s = t c. A pair whose off-diagonal entry is negligible
+// (|a_pq| <= eps sqrt(|a_pp a_qq|), or below the absolute floor) is not rotated: t = 0.
+__device__ __forceinline__ bool jacobi_rotation(double app, double aqq, double apq, double floor_abs, double& c,
+                                                double& s, double& t) {
   c = 1.0;
   s = 0.0;
-  if (t2 > 1e-290 && t2 < 1e290) {
-    const double ir = rsqrt(t2);
-    r = t2 * ir;
-    c = x * ir;
-    s = z * ir;
+  t = 0.0;
+  const double aa = fabs(apq);
+  if (aa <= floor_abs || aa <= 2.220446049250313e-16 * sqrt(fabs(app)) * sqrt(fabs(aqq))) return false;
+  const double d = aqq - app, b = 2.0 * apq;
+  const double h2 = fma(d, d, b * b);
+  double h;
+  if (h2 > 1e-290 && h2 < 1e290) {
+    h = h2 * rsqrt(h2);
   } else {
-    r = hypot(x, z);
-    if (r > 0.0) {
-      c = x / r;
-      s = z / r;
-    }
+    h = hypot(d, b);
   }
+  t = (d >= 0.0 ? b : -b) / (fabs(d) + h);
+  c = rsqrt(fma(t, t, 1.0));
+  s = t * c;
+  return true;
 }
 
-__global__ void eig_qr_chase_kernel(double* __restrict__ dg, double* __restrict__ eg, int n, int max_sweeps,
-                                    double2* __restrict__ rot, int2* __restrict__ sweep_lm,
-                                    int* __restrict__ nsweeps, int* __restrict__ info) {
-  __shared__ double d[kMaxN], e[kMaxN];
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    d[i] = dg[i];
-    e[i] = eg[i];
+constexpr int kJacThreads = 256;
+
+// A (N x N, row-major, symmetric) -> diag(lambda) in place; VT (N x N) -> V^T (row j =
+// eigenvector j). diag and pq are round-parity double buffers (2 x N and 2 x N/2): the
+// rotations of a round read only them, and the round's updates write the other parity,
+// so a CTA that is still forming rotations never sees A change under it, and one grid
+// barrier per round suffices. Every CTA forms all N/2 rotations of a round itself (the
+// same inputs give the same rotations and the same convergence decision in every CTA).
+// info[0] = 1 when max_sweeps sweeps did not converge; *sweeps = sweeps run.
+__global__ void __launch_bounds__(kJacThreads) eig_jacobi_kernel(double* __restrict__ A, double* __restrict__ VT,
+                                                                 int N, int max_sweeps,
+                                                                 double* __restrict__ diag,
+                                                                 double* __restrict__ pq,
+                                                                 unsigned* bar, int* err, int* info,
+                                                                 int* sweeps) {
+  __shared__ double sc[kMaxN / 2], ssn[kMaxN / 2], st[kMaxN / 2];
+  __shared__ int spi[kMaxN / 2], sqi[kMaxN / 2];
+  __shared__ int s_rot;
+  __shared__ volatile int s_abort;
+  const int P = N / 2;
+  const int tid = threadIdx.x;
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + tid, gthreads = (int64_t)gridDim.x * blockDim.x;
+  unsigned gen = 0;
+  if (tid == 0) s_abort = 0;
+  // V = I; round-0 inputs into parity 0
+  for (int64_t u = gtid; u < (int64_t)N * N; u += gthreads) VT[u] = (u / N == u % N) ? 1.0 : 0.0;
+  for (int64_t u = gtid; u < N; u += gthreads) diag[u] = A[u * N + u];
+  for (int64_t k = gtid; k < P; k += gthreads) {
+    int p, q;
+    rr_pair(0, (int)k, N, p, q);
+    pq[k] = A[(int64_t)p * N + q];
+  }
+  if (!grid_barrier(bar, gen, err, &s_abort)) return;
+  // absolute floor for a negligible off-diagonal entry: eps max|a_ii| / N, so the entries
+  // left out add up (Frobenius) to at most eps max|a_ii|, the backward error of any FP64
+  // eigensolver. It ends the iteration on graded spectra (a smooth kernel's), where the
+  // entries coupling the smallest eigenvalues carry rounding from rotations with the
+  // largest ones and never fall below eps relative to their own diagonal. Every CTA forms
+  // the same value.
+  __shared__ double s_dmax;
+  if (tid == 0) {
+    double m = 0.0;
+    for (int i = 0; i < N; ++i) m = fmax(m, fabs(diag[i]));
+    s_dmax = m;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    const double eps = 2.220446049250313e-16;
-    int m = n - 1, ns = 0;
-    int64_t nr = 0;
-    int bad = 0;
-    while (true) {
-      while (m > 0 && fabs(e[m - 1]) <= eps * (fabs(d[m - 1]) + fabs(d[m]))) {
-        e[m - 1] = 0.0;
-        --m;
+  const double floor_abs = 2.220446049250313e-16 * s_dmax / N;
+  const int64_t nA = (int64_t)P * P, nunits = nA + (int64_t)P * N;
+  int par = 0, sw = 0;
+  bool converged = false;
+  for (; sw < max_sweeps && !converged; ++sw) {
+    if (tid == 0) s_rot = 0;
+    for (int r = 0; r + 1 < N; ++r) {
+      const int rn = r + 2 < N ? r + 1 : 0;  // the next round (wraps into the next sweep)
+      const double* dg = diag + par * N;
+      const double* pg = pq + par * P;
+      double* dn = diag + (par ^ 1) * N;
+      double* pn = pq + (par ^ 1) * P;
+      __syncthreads();
+      for (int k = tid; k < P; k += blockDim.x) {
+        int p, q;
+        rr_pair(r, k, N, p, q);
+        double c, s_, t;
+        if (jacobi_rotation(dg[p], dg[q], pg[k], floor_abs, c, s_, t)) atomicAdd(&s_rot, 1);
+        sc[k] = c;
+        ssn[k] = s_;
+        st[k] = t;
+        spi[k] = p;
+        sqi[k] = q;
       }
-      if (m == 0) break;
-      int l = m - 1;
-      while (l > 0 && fabs(e[l - 1]) > eps * (fabs(d[l - 1]) + fabs(d[l]))) --l;
-      const int len = m - l;  // rotations per bulge
-      const int kb = len >= 4 * kBulges ? kBulges : 1;
-      if (ns + kb > max_sweeps) {
-        bad = 1;
-        break;
-      }
-      double mu[kBulges];
-      if (kb == 1) {
-        // Wilkinson shift from the trailing 2 x 2 block
-        const double a = d[m - 1], b = e[m - 1], c2 = d[m];
-        const double delta = 0.5 * (a - c2);
-        const double sgn = delta >= 0.0 ? 1.0 : -1.0;
-        mu[0] = c2 - b * b / (delta + sgn * hypot(delta, b));
-      } else {
-        // both eigenvalues of each of the kBulges/2 trailing 2 x 2 diagonal blocks
-        for (int j = 0; j < kBulges / 2; ++j) {
-          const int i1 = m - 2 * j;
-          const double a = d[i1 - 1], b = e[i1 - 1], c2 = d[i1];
-          const double mid = 0.5 * (a + c2), rad = hypot(0.5 * (a - c2), b);
-          mu[2 * j] = mid - rad;
-          mu[2 * j + 1] = mid + rad;
-        }
-      }
-      // bulge state: carried d[k], e[k] and the (x, z) to annihilate
-      double x[kBulges], z[kBulges], ak[kBulges], bk[kBulges];
-      const int steps = len + 3 * (kb - 1);
-      for (int st = 0; st < steps; ++st) {
+      __syncthreads();
+      for (int64_t u = gtid; u < nunits; u += gthreads) {
+        if (u < nA) {
+          const int i = (int)(u / P), j = (int)(u % P);
+          if (i > j) continue;
+          const int p = spi[i], q = sqi[i];
+          if (i == j) {  // diagonal block: a_pp - t a_pq, a_qq + t a_pq, a_pq -> 0
+            const double t = st[i], apq = A[(int64_t)p * N + q];
+            const double app = A[(int64_t)p * N + p] - t * apq, aqq = A[(int64_t)q * N + q] + t * apq;
+            A[(int64_t)p * N + p] = app;
+            A[(int64_t)q * N + q] = aqq;
+            A[(int64_t)p * N + q] = 0.0;
+            A[(int64_t)q * N + p] = 0.0;
+            dn[p] = app;
+            dn[q] = aqq;
+            int partner;
+            const int slot = rr_slot(rn, p, N, partner);
+            if (partner == q) pn[slot] = 0.0;  // N = 2: the same pair meets again
+            continue;
+          }
+          const int u0 = spi[j], v0 = sqi[j];
+          double x00 = A[(int64_t)p * N + u0], x01 = A[(int64_t)p * N + v0];
+          double x10 = A[(int64_t)q * N + u0], x11 = A[(int64_t)q * N + v0];
+          const double c1 = sc[i], s1 = ssn[i], c2 = sc[j], s2 = ssn[j];
+          if (s1 != 0.0 || s2 != 0.0) {
+            // rows: J_i^T X
+            const double y00 = c1 * x00 - s1 * x10, y01 = c1 * x01 - s1 * x11;
+            const double y10 = s1 * x00 + c1 * x10, y11 = s1 * x01 + c1 * x11;
+            // columns: Y J_j
+            x00 = c2 * y00 - s2 * y01;
+            x01 = s2 * y00 + c2 * y01;
+            x10 = c2 * y10 - s2 * y11;
+            x11 = s2 * y10 + c2 * y11;
+            A[(int64_t)p * N + u0] = x00;
+            A[(int64_t)p * N + v0] = x01;
+            A[(int64_t)q * N + u0] = x10;
+            A[(int64_t)q * N + v0] = x11;
+            A[(int64_t)u0 * N + p] = x00;
+            A[(int64_t)v0 * N + p] = x01;
+            A[(int64_t)u0 * N + q] = x10;
+            A[(int64_t)v0 * N + q] = x11;
+          }
+          // export the entries that form a pair of the next round
+          const int rows[2] = {p, q}, cols[2] = {u0, v0};
+          const double xv[4] = {x00, x01, x10, x11};
 #pragma unroll
-        for (int bb = 0; bb < kBulges; ++bb) {
-          if (bb >= kb) continue;
-          const int k = l + st - 3 * bb;
-          if (k < l || k >= m) continue;
-          if (k == l) {  // the bulge enters the block
-            ak[bb] = d[l];
-            bk[bb] = e[l];
-            x[bb] = d[l] - mu[bb];
-            z[bb] = e[l];
+          for (int a = 0; a < 2; ++a) {
+            int partner;
+            const int slot = rr_slot(rn, rows[a], N, partner);
+#pragma unroll
+            for (int b2 = 0; b2 < 2; ++b2)
+              if (partner == cols[b2]) pn[slot] = xv[a * 2 + b2];
           }
-          const double ck = d[k + 1];
-          const double f = k + 1 < m ? e[k + 1] : 0.0;
-          double r, c, s;
-          givens(x[bb], z[bb], r, c, s);
-          if (k > l) e[k - 1] = r;
-          const double cc = c * c, ss = s * s, cs = c * s;
-          d[k] = ak[bb] * cc + 2.0 * bk[bb] * cs + ck * ss;
-          const double dk1 = ak[bb] * ss - 2.0 * bk[bb] * cs + ck * cc;
-          const double ek = (ck - ak[bb]) * cs + bk[bb] * (cc - ss);
-          rot[nr + (int64_t)bb * len + (k - l)] = make_double2(c, s);
-          x[bb] = ek;
-          if (k + 1 < m) {
-            z[bb] = f * s;
-            bk[bb] = f * c;
-          }
-          e[k] = ek;
-          ak[bb] = dk1;
-          if (k == m - 1) d[m] = dk1;  // the bulge leaves the block
+        } else {
+          const int64_t v = u - nA;
+          const int k = (int)(v / N), comp = (int)(v % N);
+          const double s_ = ssn[k];
+          if (s_ == 0.0) continue;
+          const double c = sc[k];
+          double* vp = VT + (int64_t)spi[k] * N + comp;
+          double* vq = VT + (int64_t)sqi[k] * N + comp;
+          const double a = *vp, b = *vq;
+          *vp = c * a - s_ * b;
+          *vq = s_ * a + c * b;
         }
       }
-      for (int bb = 0; bb < kb; ++bb) sweep_lm[ns + bb] = make_int2(l, m);
-      ns += kb;
-      nr += (int64_t)kb * len;
+      par ^= 1;
+      if (!grid_barrier(bar, gen, err, &s_abort)) return;
     }
-    *info = bad;
-    *nsweeps = ns;
+    __syncthreads();
+    converged = s_rot == 0;
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    dg[i] = d[i];
-    eg[i] = e[i];
+  if (blockIdx.x == 0 && tid == 0) {
+    *info = converged ? 0 : 1;
+    *sweeps = sw;
   }
 }
 
-// ---- 3. eigenvectors V = H_0 ... H_{n-3} G_1 G_2 ... , rows in parallel ----
-// Row i of V is e_i^T times the product; each factor acts on a row independently. One
-// thread carries kVecRows rows (held in shared memory) through the factors together, so
-// the rows' FP64 dependency chains interleave; the row groups are spread over CTAs.
-constexpr int kVecRows = 8;  // rows per thread (one thread per CTA)
-__global__ void __launch_bounds__(32) eig_vectors_kernel(const double* __restrict__ hv,
-                                                         const double2* __restrict__ rot,
-                                                         const int2* __restrict__ sweep_lm,
-                                                         const int* __restrict__ nsweeps,
-                                                         const int* __restrict__ info, int n,
-                                                         double* __restrict__ V) {
-  extern __shared__ double srow[];  // kVecRows x (n + 1)
-  if (threadIdx.x != 0 || *info) return;
-  const int i0 = blockIdx.x * kVecRows;
-  const int nr = min(kVecRows, n - i0);
-  if (nr <= 0) return;
-  const int ld = n + 1;
-  for (int r = 0; r < kVecRows; ++r)
-    for (int j = 0; j < n; ++j) srow[r * ld + j] = (r < nr && j == i0 + r) ? 1.0 : 0.0;
-  // row <- row (I - 2 v_k v_k^T), k = 0 .. n-3
-  for (int k = 0; k + 2 < n; ++k) {
-    const double* vk = hv + (int64_t)k * n;
-    double dot[kVecRows];
-#pragma unroll
-    for (int r = 0; r < kVecRows; ++r) dot[r] = 0.0;
-    for (int j = k + 1; j < n; ++j) {
-      const double v = vk[j];
-#pragma unroll
-      for (int r = 0; r < kVecRows; ++r) dot[r] = fma(srow[r * ld + j], v, dot[r]);
-    }
-    for (int j = k + 1; j < n; ++j) {
-      const double v = vk[j];
-#pragma unroll
-      for (int r = 0; r < kVecRows; ++r) srow[r * ld + j] -= 2.0 * dot[r] * v;
-    }
-  }
-  // row <- row G, sweep by sweep, rotations in recorded order
-  const int ns = *nsweeps;
-  int64_t off = 0;
-  for (int sw = 0; sw < ns; ++sw) {
-    const int2 lm = sweep_lm[sw];
-    double vk[kVecRows];
-#pragma unroll
-    for (int r = 0; r < kVecRows; ++r) vk[r] = srow[r * ld + lm.x];
-    for (int k = lm.x; k < lm.y; ++k) {
-      const double2 cs = rot[off + (k - lm.x)];
-#pragma unroll
-      for (int r = 0; r < kVecRows; ++r) {
-        const double vk1 = srow[r * ld + k + 1];
-        srow[r * ld + k] = cs.x * vk[r] + cs.y * vk1;
-        vk[r] = -cs.y * vk[r] + cs.x * vk1;
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < kVecRows; ++r) srow[r * ld + lm.y] = vk[r];
-    off += lm.y - lm.x;
-  }
-  for (int r = 0; r < nr; ++r)
-    for (int j = 0; j < n; ++j) V[(int64_t)(i0 + r) * n + j] = srow[r * ld + j];
+// lambda_j = A_jj, V (n x n, row i = component i) from V^T (N x N)
+__global__ void eig_jacobi_out_kernel(const double* __restrict__ A, const double* __restrict__ VT, int N, int n,
+                                      double* __restrict__ lam, double* __restrict__ V) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * n) return;
+  const int i = (int)(t / n), j = (int)(t % n);
+  V[t] = VT[(int64_t)j * N + i];
+  if (i == 0) lam[j] = A[(int64_t)j * N + j];
 }
 
-// B~ = D sym(HCQ) D with D = R^{-1/2}
-__global__ void scale_b_kernel(const double* __restrict__ hcq_sym, const double* __restrict__ rd, int n,
+// B~ = D sym(HCQ) D with D = R^{-1/2}, into an N x N buffer (N >= n) padded with zeros
+__global__ void scale_b_kernel(const double* __restrict__ hcq_sym, const double* __restrict__ rd, int n, int N,
                                double* __restrict__ out) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)n * n) return;
-  int i = (int)(t / n), j = (int)(t % n);
-  out[t] = hcq_sym[t] / sqrt(rd[i] * rd[j]);
+  if (t >= (int64_t)N * N) return;
+  int i = (int)(t / N), j = (int)(t % N);
+  out[t] = (i < n && j < n) ? hcq_sym[(int64_t)i * n + j] / sqrt(rd[i] * rd[j]) : 0.0;
 }
 
 // W = D V (FP64 and FP32 copies); s_1 = (1 + c) lambda + 1
@@ -544,70 +422,55 @@ inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 Status spectral_setup(SpectralState& sp, const double* hcq_sym, const double* rd, int n, double c, int* flag,
                       cudaStream_t s) {
-  const int64_t nn = (int64_t)n * n;
-  const int max_sweeps = 40 * n + 100;
-  const int64_t max_rot = (int64_t)max_sweeps * std::max(1, n - 1);
-  double *A = nullptr, *V = nullptr, *hv = nullptr, *e = nullptr;
-  double2* rot = nullptr;
-  int2* lm = nullptr;
+  const int N = n + (n & 1);  // even; an odd n gets one zero row and column
+  const int64_t nn = (int64_t)n * n, NN = (int64_t)N * N;
+  constexpr int kMaxSweeps = 60;
+  double *A = nullptr, *VT = nullptr, *V = nullptr, *dbuf = nullptr;
   int* ints = nullptr;
-  HIKF_CUDA(cudaMallocAsync((void**)&A, sizeof(double) * nn, s));
+  HIKF_CUDA(cudaMallocAsync((void**)&A, sizeof(double) * NN, s));
+  HIKF_CUDA(cudaMallocAsync((void**)&VT, sizeof(double) * NN, s));
   HIKF_CUDA(cudaMallocAsync((void**)&V, sizeof(double) * nn, s));
-  HIKF_CUDA(cudaMallocAsync((void**)&hv, sizeof(double) * nn, s));
-  HIKF_CUDA(cudaMallocAsync((void**)&e, sizeof(double) * n, s));
-  HIKF_CUDA(cudaMallocAsync((void**)&rot, sizeof(double2) * max_rot, s));
-  HIKF_CUDA(cudaMallocAsync((void**)&lm, sizeof(int2) * max_sweeps, s));
-  double* wbuf = nullptr;
-  HIKF_CUDA(cudaMallocAsync((void**)&wbuf, sizeof(double) * n, s));
-  HIKF_CUDA(cudaMallocAsync((void**)&ints, 4 * sizeof(int), s));  // info, nsweeps, barrier, tridiag error
+  HIKF_CUDA(cudaMallocAsync((void**)&dbuf, sizeof(double) * 3 * N, s));  // diag[2][N], pq[2][N/2]
+  HIKF_CUDA(cudaMallocAsync((void**)&ints, 4 * sizeof(int), s));         // info, sweeps, barrier, error
   HIKF_CUDA(cudaMemsetAsync(ints, 0, 4 * sizeof(int), s));
-  HIKF_CUDA(cudaMemsetAsync(e, 0, sizeof(double) * n, s));
-  scale_b_kernel<<<nblk(nn, 256), 256, 0, s>>>(hcq_sym, rd, n, A);
+  scale_b_kernel<<<nblk(NN, 256), 256, 0, s>>>(hcq_sym, rd, n, N, A);
   HIKF_LAUNCH_CHECK("scale_b");
   {
-    // cooperative grid: at most one CTA per SM, all resident
+    // cooperative grid: one CTA per SM, all resident
     int dev = 0, sms = 1, per_sm = 0;
     HIKF_CUDA(cudaGetDevice(&dev));
     HIKF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    HIKF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, eig_tridiag_grid_kernel, kTriThreads, 0));
-    const int grid = std::max(1, std::min({64, sms * std::max(per_sm, 0), std::max(1, n / 4)}));
-    if (per_sm >= 1) {
-      double* Ap = A;
-      double* dp = sp.lam;
-      double* ep = e;
-      double* hp = hv;
-      double* wp = wbuf;
-      unsigned* bp = reinterpret_cast<unsigned*>(ints + 2);
-      int* errp = ints + 3;
-      int nn_ = n;
-      void* args[] = {&Ap, &nn_, &dp, &ep, &hp, &wp, &bp, &errp};
-      HIKF_CUDA(cudaLaunchCooperativeKernel((const void*)eig_tridiag_grid_kernel, dim3(grid), dim3(kTriThreads), args,
-                                            0, s));
-    } else {
-      eig_tridiag_kernel<<<1, kEigThreads, 0, s>>>(A, n, sp.lam, e, hv);
-    }
-    HIKF_LAUNCH_CHECK("eig_tridiag");
+    HIKF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, eig_jacobi_kernel, kJacThreads, 0));
+    if (per_sm < 1) return make_status(HIKF_ECUDA, "the Jacobi eigensolver cannot be made resident");
+    const int grid = std::max(1, std::min(sms, (int)((NN / 2 + kJacThreads - 1) / kJacThreads)));
+    double* Ap = A;
+    double* Vp = VT;
+    int Np = N, msw = kMaxSweeps;
+    double* dp = dbuf;
+    double* pp = dbuf + 2 * N;
+    unsigned* bp = reinterpret_cast<unsigned*>(ints + 2);
+    int* errp = ints + 3;
+    int* infop = ints;
+    int* swp = ints + 1;
+    void* args[] = {&Ap, &Vp, &Np, &msw, &dp, &pp, &bp, &errp, &infop, &swp};
+    HIKF_CUDA(cudaLaunchCooperativeKernel((const void*)eig_jacobi_kernel, dim3(grid), dim3(kJacThreads), args, 0, s));
+    HIKF_LAUNCH_CHECK("eig_jacobi");
   }
-  eig_qr_chase_kernel<<<1, 32, 0, s>>>(sp.lam, e, n, max_sweeps, rot, lm, ints + 1, ints);
-  HIKF_LAUNCH_CHECK("eig_qr_chase");
-  const size_t vsmem = sizeof(double) * kVecRows * (size_t)(n + 1);
-  eig_vectors_kernel<<<nblk(n, kVecRows), 32, vsmem, s>>>(hv, rot, lm, ints + 1, ints, n, V);
-  HIKF_LAUNCH_CHECK("eig_vectors");
+  eig_jacobi_out_kernel<<<nblk(nn, 256), 256, 0, s>>>(A, VT, N, n, sp.lam, V);
+  HIKF_LAUNCH_CHECK("eig_jacobi_out");
   spec_init_kernel<<<nblk(nn, 256), 256, 0, s>>>(V, sp.lam, rd, n, c, sp.W64, sp.W32, sp.s, flag);
   HIKF_LAUNCH_CHECK("spec_init");
   int hinfo[4] = {0, 0, 0, 0};
   HIKF_CUDA(cudaMemcpyAsync(hinfo, ints, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
   HIKF_CUDA(cudaStreamSynchronize(s));
   HIKF_CUDA(cudaFreeAsync(A, s));
+  HIKF_CUDA(cudaFreeAsync(VT, s));
   HIKF_CUDA(cudaFreeAsync(V, s));
-  HIKF_CUDA(cudaFreeAsync(hv, s));
-  HIKF_CUDA(cudaFreeAsync(e, s));
-  HIKF_CUDA(cudaFreeAsync(rot, s));
-  HIKF_CUDA(cudaFreeAsync(lm, s));
+  HIKF_CUDA(cudaFreeAsync(dbuf, s));
   HIKF_CUDA(cudaFreeAsync(ints, s));
-  HIKF_CUDA(cudaFreeAsync(wbuf, s));
-  if (hinfo[3]) return make_status(HIKF_ETIMEOUT, "a bounded grid barrier in the tridiagonalisation timed out");
-  if (hinfo[0]) return make_status(HIKF_ECUDA, "eigensolver did not converge");
+  sp.sweeps = hinfo[1];
+  if (hinfo[3]) return make_status(HIKF_ETIMEOUT, "a bounded grid barrier in the Jacobi eigensolver timed out");
+  if (hinfo[0]) return make_status(HIKF_ECUDA, "Jacobi eigensolver did not converge in 60 sweeps");
   return Status::Ok();
 }
 

@@ -7,6 +7,7 @@ namespace hikf {
 
 struct SpectralState {
   double* lam = nullptr;  // n eigenvalues of D sym(H C_Q) D, D = R^{-1/2}
+  int sweeps = 0;         // Jacobi sweeps the eigendecomposition took
   double* s = nullptr;    // n current s_t (eigenvalues of D S_t D)
   double* W64 = nullptr;  // n x n, D V
   float* W32 = nullptr;   // n x n, D V rounded to FP32

@@ -57,6 +57,7 @@ CASES = {
     "n300_30x30": lambda: W.small(grid=(30, 30), n=300, steps=3, seed=25),
     "n256_120x120": lambda: W.small(grid=(120, 120), n=256, steps=3, seed=32),
     "n300_140x130": lambda: W.small(grid=(140, 130), n=300, steps=3, seed=33),
+    "odd_45x39_n37": lambda: W.small(grid=(45, 39), n=37, steps=4, seed=34),
     "3d_16x16x16_n16": lambda: W.make(grid=(16, 16, 16), n=16, q=W.KernelSpec(W.GAUSS, 0.01, 4.0),
                                       p0=W.KernelSpec(W.GAUSS, 1.0, 4.0), r=1e-3, steps=3, seed=26, cheb_order=5),
 }
@@ -164,15 +165,33 @@ def test_depth_zero_is_direct_sum(B):
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 @pytest.mark.parametrize("chain", ["factor", "spectral"])
-@pytest.mark.parametrize("name", ["m1024_n16", "ragged_61x37_n100", "n300_140x130"])
+@pytest.mark.parametrize("name", ["m1024_n16", "ragged_61x37_n100", "n300_140x130", "odd_45x39_n37"])
 def test_both_forms_of_the_gain_chain_match_oracle(B, name, chain, prec):
-    """S_t^{-1} by a Cholesky factor every step, or by the eigen-recurrence."""
+    """S_t^{-1} by a Cholesky factor every step, or by the eigen-recurrence (odd n pads
+    the Jacobi eigensolver with one zero row and column)."""
     w = CASES[name]()
     x, v, _, depth, Y = _run(B, w, prec, chain=chain)
     ref = _oracle_run(w, depth, Y, w.cheb_order)
     tol = TOL32 if prec == "fp32" else TOL64
     assert rel(x, ref["x"]) < tol
     assert rel(v, ref["var"]) < tol
+
+
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_spectral_chain_with_one_to_three_rays(B, n):
+    """The degenerate sizes of the Jacobi eigensolver: one pair met in every round
+    (n = 1, 2) and one padded index (n = 1, 3)."""
+    w = W.small(grid=(20, 18), n=n, steps=4, seed=40 + n)
+    Y, _ = W.measurements(w)
+    with B.Filter.from_workload(w, precision="fp64", chain="spectral") as f:
+        depth = f.info()["depth"]
+        assert 1 <= f.info()["eig_sweeps"] <= 60
+        for y in Y:
+            f.assimilate(y)
+        x, v = f.mean(), f.variance()
+    ref = _oracle_run(w, depth, Y, w.cheb_order)
+    assert rel(x, ref["x"]) < TOL64
+    assert rel(v, ref["var"]) < TOL64
 
 
 def _run(B, w, prec="fp32", **kw):
