@@ -28,6 +28,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kPMax = 12;
 constexpr int kPT = 64;   // points per chunk in P2M / L2P / P2P
+constexpr int kNzStage = 512;   // H^T entries of one source chunk staged in shared memory (P2P)
 
 struct Geo {
   double lo[3];
@@ -38,6 +39,8 @@ struct Geo {
 };
 
 __host__ __device__ inline int64_t cmin64(int64_t a, int64_t b) { return a < b ? a : b; }
+
+__host__ __device__ constexpr int ipow_c(int b, int e) { return e == 0 ? 1 : b * ipow_c(b, e - 1); }
 
 __host__ __device__ inline int ipow(int b, int e) {
   int r = 1;
@@ -200,6 +203,7 @@ __global__ void __launch_bounds__(kThreads) p2m_kernel(Geo g, const double* __re
   T* w1 = tj + kPMax * kPMax;                            // kPT*3*kPMax
   T* S = w1 + kPT * 3 * kPMax;                           // kPT*q
   T* Hd = S + kPT * g.q;                                 // kPT*nch
+  int* act = reinterpret_cast<int*>(Hd + kPT * nch);     // flags (nch), count, active columns (nch)
   const int64_t b = blockIdx.x;
   if (nsrc[leaf_box0 + b] == 0) return;
   const int p = g.p, q = g.q, ld = g.ld;
@@ -212,16 +216,37 @@ __global__ void __launch_bounds__(kThreads) p2m_kernel(Geo g, const double* __re
     leaf_weights<T>(g, pts, ps, cnt, b, tj, w1, S);
     for (int r0 = 0; r0 < ld; r0 += nch) {
       for (int t = threadIdx.x; t < kPT * nch; t += blockDim.x) Hd[t] = (T)0;
+      for (int t = threadIdx.x; t < nch; t += blockDim.x) act[t] = 0;
       __syncthreads();
       for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
         for (int64_t e = trowptr[ps + i]; e < trowptr[ps + i + 1]; ++e) {
           int r = tcol[e] - r0;
-          if (r >= 0 && r < nch) Hd[i * nch + r] += (T)tval[e];
+          if (r >= 0 && r < nch) {
+            Hd[i * nch + r] += (T)tval[e];
+            act[r] = 1;
+          }
         }
       }
       __syncthreads();
-      for (int t = threadIdx.x; t < q * nch; t += blockDim.x) {
-        int a = t / nch, r = t % nch;
+      // the columns (rays) with a source among these points, in column order; the
+      // product below runs over them only (most rays miss a given leaf)
+      if (threadIdx.x < 32) {
+        int base = 0;
+        for (int c0 = 0; c0 < nch; c0 += 32) {
+          const int c = c0 + (int)threadIdx.x;
+          const bool on = c < nch && act[c] != 0;
+          const unsigned bal = __ballot_sync(0xffffffffu, on);
+          __syncwarp();
+          if (on) act[nch + 1 + base + __popc(bal & ((1u << threadIdx.x) - 1u))] = c;
+          base += __popc(bal);
+        }
+        if (threadIdx.x == 0) act[nch] = base;
+      }
+      __syncthreads();
+      const int nact = act[nch];
+      const int* cols = act + nch + 1;
+      for (int t = threadIdx.x; t < q * nact; t += blockDim.x) {
+        const int a = t / nact, r = cols[t % nact];
         if (r0 + r >= ld) continue;
         T acc = (T)0;
         for (int i = 0; i < cnt; ++i) acc += S[i * q + a] * Hd[i * nch + r];
@@ -349,6 +374,206 @@ __global__ void __launch_bounds__(kThreads) l2l_kernel(Geo g, int lev, const dou
 }
 
 // ---------------------------------------------------------------------------
+// M2M / L2L with the box data of one column in registers (q = P^DIM <= 64)
+// ---------------------------------------------------------------------------
+// One warp per (parent box, 32-column chunk); lane l owns column r0 + l, so every load
+// and store of a node row is one coalesced 128-byte access. The separable transfer
+// (T1[c_0] x ... x T1[c_{DIM-1}]) is applied axis by axis in registers: for each line of
+// P nodes along the axis, P temporaries, the P x P transfer matrix of that axis held in
+// registers. M2M: W_P = sum_c (x_ax T1[c_ax])^T W_c (plain store); L2L:
+// L_c += (x_ax T1[c_ax]) L_P. T1[cax] is [child node][parent node].
+constexpr int kRegWarps = 4;
+
+// cp.async of one 4- or 8-byte element (global -> shared), commit, wait
+__device__ __forceinline__ void cp_async_elem(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_elem(double* dst, const double* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <typename T, int P, int DIM, bool TRANSPOSED, typename Sink>
+__device__ __forceinline__ void transfer_column(T (&x)[ipow_c(P, DIM)], const T* __restrict__ t1s, int c,
+                                                Sink&& sink) {
+  // forward: out[a] = sum_k T1[k][a] in[k]; transposed: out[a] = sum_k T1[a][k] in[k]. Axes
+  // 0 .. DIM-2 are applied in place (P temporaries per line), the last axis streams its
+  // outputs into the sink, so only the q inputs are live; every output sums k in order,
+  // axis after axis, as the shared-memory kernel does. The matrices stay in shared memory
+  // (every lane reads the same entry); the empty asm statements keep the compiler from
+  // hoisting later reads over earlier work, which would raise the register count.
+  constexpr int Q = ipow_c(P, DIM);
+#pragma unroll
+  for (int ax = 0; ax + 1 < DIM; ++ax) {
+    asm volatile("" ::: "memory");
+    const T* mm = t1s + ((c >> (DIM - 1 - ax)) & 1) * P * P;
+    int stride = 1;
+#pragma unroll
+    for (int e = ax + 1; e < DIM; ++e) stride *= P;
+#pragma unroll
+    for (int o = 0; o < Q / P; ++o) {
+      if (Q > 49) asm volatile("" ::: "memory");
+      const int base = (o / stride) * stride * P + (o % stride);
+      T tmp[P];
+#pragma unroll
+      for (int a = 0; a < P; ++a) {
+        T acc = (T)0;
+#pragma unroll
+        for (int k = 0; k < P; ++k) acc += (TRANSPOSED ? mm[a * P + k] : mm[k * P + a]) * x[base + k * stride];
+        tmp[a] = acc;
+      }
+#pragma unroll
+      for (int a = 0; a < P; ++a) x[base + a * stride] = tmp[a];
+    }
+  }
+  asm volatile("" ::: "memory");
+  const T* mm = t1s + (c & 1) * P * P;  // the last axis (stride 1)
+#pragma unroll
+  for (int a = 0; a < P; ++a) {
+    if (Q > 49) asm volatile("" ::: "memory");
+    T m0[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) m0[k] = TRANSPOSED ? mm[a * P + k] : mm[k * P + a];
+#pragma unroll
+    for (int o = 0; o < Q / P; ++o) {
+      T acc = (T)0;
+#pragma unroll
+      for (int k = 0; k < P; ++k) acc += m0[k] * x[o * P + k];
+      sink(o * P + a, acc);
+    }
+  }
+}
+
+template <typename T, int P, int DIM, bool UP>
+__global__ void __launch_bounds__(32 * kRegWarps) transfer_reg_kernel(int ld, const double* __restrict__ tab,
+                                                                      const int64_t* __restrict__ cnt,
+                                                                      int64_t box0, int64_t child0, int64_t nparent,
+                                                                      T* __restrict__ X) {
+  constexpr int Q = ipow_c(P, DIM), NC = 1 << DIM;
+  __shared__ __align__(16) T t1s[2 * P * P];
+  // per warp: the parent's accumulator (M2M) or the parent's values (L2L), [node][lane]
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  for (int t = threadIdx.x; t < 2 * P * P; t += blockDim.x) t1s[t] = (T)tab[P * P + t];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  T* buf = reinterpret_cast<T*>(smem_raw) + (threadIdx.x >> 5) * Q * 32 + lane;
+  const int nchunk = ld / 32;
+  const int64_t item = (int64_t)blockIdx.x * kRegWarps + (threadIdx.x >> 5);
+  if (item >= nparent * nchunk) return;
+  const int64_t par = item / nchunk;
+  const int r = (int)(item % nchunk) * 32 + lane;
+  if (cnt[box0 + par] == 0) return;
+  T* Xp = X + (box0 + par) * (int64_t)Q * ld + r;
+  if (UP) {
+    // children with sources, in order; each child's column is copied into one of two
+    // shared stages with cp.async while the previous child is transformed, so the
+    // transform reads its inputs from shared memory (no values held across global loads)
+    int list[NC], nl = 0;
+    for (int c = 0; c < NC; ++c)
+      if (cnt[child0 + par * NC + c] != 0) list[nl++] = c;
+    T* stage = buf + Q * 32 * kRegWarps;  // two per-warp stages after the accumulators
+    auto issue = [&](int t) {
+      const T* Xc = X + (child0 + par * NC + list[t]) * (int64_t)Q * ld + r;
+      T* dst = stage + (t & 1) * Q * 32 * kRegWarps;
+#pragma unroll 8
+      for (int a = 0; a < Q; ++a) cp_async_elem(dst + a * 32, Xc + (int64_t)a * ld);
+      cp_async_commit();
+    };
+#pragma unroll
+    for (int a = 0; a < Q; ++a) buf[a * 32] = (T)0;
+    if (nl > 0) issue(0);
+    for (int t = 0; t < nl; ++t) {
+      if (t + 1 < nl) {
+        issue(t + 1);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      const T* src = stage + (t & 1) * Q * 32 * kRegWarps;
+      T x[Q];
+#pragma unroll
+      for (int a = 0; a < Q; ++a) x[a] = src[a * 32];
+      transfer_column<T, P, DIM, false>(x, t1s, list[t], [&](int a, T v) { buf[a * 32] += v; });
+    }
+#pragma unroll
+    for (int a = 0; a < Q; ++a, Xp += ld) *Xp = buf[a * 32];
+  } else {
+    // children with points, in order; each child's current column is copied into one of
+    // two shared stages with cp.async while the previous child is transformed, the
+    // transform adds into the stage, and the stage is written back with plain stores
+    int list[NC], nl = 0;
+    for (int c = 0; c < NC; ++c)
+      if (cnt[child0 + par * NC + c] != 0) list[nl++] = c;
+    T* stage = buf + Q * 32 * kRegWarps;
+    auto child_col = [&](int t) { return X + (child0 + par * NC + list[t]) * (int64_t)Q * ld + r; };
+    auto issue = [&](int t) {
+      const T* Xc = child_col(t);
+      T* dst = stage + (t & 1) * Q * 32 * kRegWarps;
+#pragma unroll 8
+      for (int a = 0; a < Q; ++a) cp_async_elem(dst + a * 32, Xc + (int64_t)a * ld);
+      cp_async_commit();
+    };
+    if (nl > 0) issue(0);
+#pragma unroll
+    for (int a = 0; a < Q; ++a, Xp += ld) buf[a * 32] = *Xp;
+    for (int t = 0; t < nl; ++t) {
+      if (t + 1 < nl) {
+        issue(t + 1);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      T* st = stage + (t & 1) * Q * 32 * kRegWarps;
+      T x[Q];
+#pragma unroll
+      for (int a = 0; a < Q; ++a) x[a] = buf[a * 32];
+      transfer_column<T, P, DIM, true>(x, t1s, list[t], [&](int a, T v) { st[a * 32] += v; });
+      T* Xc = child_col(t);
+#pragma unroll 8
+      for (int a = 0; a < Q; ++a) Xc[(int64_t)a * ld] = st[a * 32];
+    }
+  }
+}
+
+// launch the register kernel when (p, dim) has an instance; false otherwise
+template <typename T, bool UP>
+bool launch_transfer_reg(int p, int dim, int ld, const double* tab, const int64_t* cnt, int64_t box0,
+                         int64_t child0, int64_t nparent, T* X, cudaStream_t s) {
+  if (ld % 32 != 0) return false;
+  if (sizeof(T) == 8 && ipow(p, dim) > 36) return false;  // two FP64 q-vectors in registers
+  const int64_t items = nparent * (ld / 32);
+  const unsigned grid = (unsigned)((items + kRegWarps - 1) / kRegWarps);
+  // per warp: the accumulator (M2M) or the parent's values (L2L), plus two stages of a child's column
+  const size_t smem = sizeof(T) * (size_t)kRegWarps * ipow(p, dim) * 32 * 3;  // <= 108 KB
+#define HIKF_TRANSFER_CASE(PP, DD)                                                                        \
+  if (p == PP && dim == DD) {                                                                             \
+    if (cudaFuncSetAttribute(transfer_reg_kernel<T, PP, DD, UP>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             (int)smem) != cudaSuccess)                                                   \
+      return false;                                                                                       \
+    transfer_reg_kernel<T, PP, DD, UP><<<grid, 32 * kRegWarps, smem, s>>>(ld, tab, cnt, box0, child0, nparent, X); \
+    return true;                                                                                          \
+  }
+  HIKF_TRANSFER_CASE(2, 2)
+  HIKF_TRANSFER_CASE(3, 2)
+  HIKF_TRANSFER_CASE(4, 2)
+  HIKF_TRANSFER_CASE(5, 2)
+  HIKF_TRANSFER_CASE(6, 2)
+  HIKF_TRANSFER_CASE(7, 2)
+  HIKF_TRANSFER_CASE(8, 2)
+  HIKF_TRANSFER_CASE(2, 3)
+  HIKF_TRANSFER_CASE(3, 3)
+  HIKF_TRANSFER_CASE(4, 3)
+#undef HIKF_TRANSFER_CASE
+  return false;
+}
+
+// ---------------------------------------------------------------------------
 // M2L: L_B += sum_{B' in IL(B)} K_{lev, B'-B} W_B'   (tiled GEMM over the list)
 // ---------------------------------------------------------------------------
 constexpr int kM2L_BM = 64, kM2L_BN = 64, kM2L_BK = 16;
@@ -460,6 +685,21 @@ __global__ void __launch_bounds__(kThreads) m2l_kernel(Geo g, int lev, const T* 
   }
 }
 
+// eight consecutive values from a 16-byte aligned address
+__device__ __forceinline__ void load8(const float* __restrict__ p, float (&v)[8]) {
+  const float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 4);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+__device__ __forceinline__ void load8(const double* __restrict__ p, double (&v)[8]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double2 a = reinterpret_cast<const double2*>(p)[k];
+    v[2 * k] = a.x;
+    v[2 * k + 1] = a.y;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // L2P + P2P: C_Q rows of one leaf
 // ---------------------------------------------------------------------------
@@ -481,6 +721,14 @@ __global__ void __launch_bounds__(kThreads) l2p_p2p_kernel(Geo g, const double* 
   T* tx = Cs + kPT * (nch + 1);         // kPT x 3 target coords relative to the leaf centre
   T* sx = tx + kPT * 3;                 // kPT x 3 staged source coords
   int64_t* se = reinterpret_cast<int64_t*>(sx + kPT * 3 + 2);  // kPT x 2 H^T row ranges (8-byte aligned)
+  // kPT sources x kPT targets: kernel values. With one column chunk and q >= kPT they share
+  // storage with S (kPT x q): within a chunk of points, L2P reads S before P2P starts and
+  // S is formed again for the next chunk (the launch sizes shared memory the same way)
+  const bool alias_kv = q >= kPT && nch >= ld;
+  T* kvs = alias_kv ? S : reinterpret_cast<T*>(se + 2 * kPT);
+  T* zv = reinterpret_cast<T*>(se + 2 * kPT) + (alias_kv ? 0 : kPT * kPT);  // the chunk's H^T values (kNzStage)
+  int* zc = reinterpret_cast<int*>(zv + kNzStage);              // and their ray indices
+  __shared__ int se_cnt[2];                                     // crossed sources per staging warp
   const int64_t b = blockIdx.x;
   const int64_t p0 = leaf_start[b], p1 = leaf_start[b + 1];
   if (p1 == p0) return;
@@ -506,14 +754,35 @@ __global__ void __launch_bounds__(kThreads) l2p_p2p_kernel(Geo g, const double* 
     __syncthreads();
     for (int r0 = 0; r0 < ld; r0 += nch) {
       const int w = min(nch, ld - r0);
-      // L2P
-      for (int t = threadIdx.x; t < kPT * nch; t += blockDim.x) {
-        int i = t / nch, r = t % nch;
-        T acc = (T)0;
-        if (L >= 2 && i < cnt && r < w) {
-          for (int a = 0; a < q; ++a) acc += S[i * q + a] * Lb[(int64_t)a * ld + r0 + r];
+      // L2P: a 4-point x 8-column register tile per thread; L rows read as 16-byte vectors
+      {
+        const int ncg = nch / 8, ntile = (kPT / 4) * ncg;
+        for (int t = threadIdx.x; t < ntile; t += blockDim.x) {
+          const int i0 = (t / ncg) * 4, c0 = (t % ncg) * 8;
+          T acc[4][8];
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 8; ++v) acc[u][v] = (T)0;
+          if (L >= 2 && i0 < cnt && c0 < w) {
+            const T* lrow = Lb + r0 + c0;
+            for (int a = 0; a < q; ++a) {
+              T lv[8];
+              load8(lrow + (int64_t)a * ld, lv);
+              T sv[4];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) sv[u] = i0 + u < cnt ? S[(i0 + u) * q + a] : (T)0;
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 8; ++v) acc[u][v] += sv[u] * lv[v];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 8; ++v) Cs[(i0 + u) * (nch + 1) + c0 + v] = acc[u][v];
         }
-        Cs[i * (nch + 1) + r] = acc;
       }
       __syncthreads();
       // P2P over the touching leaves (exact kernel, sparse sources); the source
@@ -521,9 +790,6 @@ __global__ void __launch_bounds__(kThreads) l2p_p2p_kernel(Geo g, const double* 
       const int i = threadIdx.x % kPT, part = threadIdx.x / kPT;
       const int cw = (nch + parts - 1) / parts;
       const int rlo = part * cw, rhi = min(nch, rlo + cw);
-      T xi[3] = {(T)0, (T)0, (T)0};
-      if (i < cnt)
-        for (int d = 0; d < dim; ++d) xi[d] = tx[i * 3 + d];
       for (int nb = 0; nb < nnb; ++nb) {
         int64_t cn[3] = {0, 0, 0};
         int tt = nb;
@@ -540,25 +806,68 @@ __global__ void __launch_bounds__(kThreads) l2p_p2p_kernel(Geo g, const double* 
         if (nsrc[leaf_box0 + key] == 0) continue;
         for (int64_t js = leaf_start[key]; js < leaf_start[key + 1]; js += kPT) {
           const int jc = (int)cmin64(kPT, leaf_start[key + 1] - js);
-          for (int t = threadIdx.x; t < jc; t += blockDim.x) {
-            se[2 * t] = trowptr[js + t];
-            se[2 * t + 1] = trowptr[js + t + 1];
-            for (int d = 0; d < dim; ++d) sx[t * 3 + d] = (T)(pts[(js + t) * dim + d] - ctr[d]);
+          // stage only the sources some ray crosses, in point order (most cells are
+          // crossed by none); kPT = 64 sources are compacted by two warps' ballots
+          if (threadIdx.x < kPT) {
+            const int t = (int)threadIdx.x;
+            int64_t e0 = 0, e1 = 0;
+            if (t < jc) {
+              e0 = trowptr[js + t];
+              e1 = trowptr[js + t + 1];
+            }
+            const bool on = e1 > e0;
+            const unsigned bal = __ballot_sync(0xffffffffu, on);
+            const int below = __popc(bal & ((1u << (t & 31)) - 1u));
+            if ((t & 31) == 0) se_cnt[t >> 5] = __popc(bal);
+            __syncwarp();
+            // warp 1 needs warp 0's count: publish it through shared memory first
+            asm volatile("bar.sync 1, 64;" ::: "memory");
+            const int slot = (t >> 5 ? se_cnt[0] : 0) + below;
+            if (on) {
+              se[2 * slot] = e0;
+              se[2 * slot + 1] = e1;
+              for (int d = 0; d < dim; ++d) sx[slot * 3 + d] = (T)(pts[(js + t) * dim + d] - ctr[d]);
+            }
           }
           __syncthreads();
-          if (i < cnt) {
-            for (int j = 0; j < jc; ++j) {
-              const int64_t e0 = se[2 * j], e1 = se[2 * j + 1];
-              if (e0 == e1) continue;
+          const int ns = se_cnt[0] + se_cnt[1];
+          // every (target, source) kernel value once, shared by the column parts
+          for (int t = threadIdx.x; t < ns * kPT; t += blockDim.x) {
+            const int j = t / kPT, ii = t % kPT;
+            T v = (T)0;
+            if (ii < cnt) {
               T r2 = (T)0;
               for (int d = 0; d < dim; ++d) {
-                T dx = xi[d] - sx[j * 3 + d];
+                T dx = tx[ii * 3 + d] - sx[j * 3 + d];
                 r2 += dx * dx;
               }
-              const T kv = kernel_value<T>(r2, g.pow, theta, inv_len, inv_len2);
-              for (int64_t e = e0; e < e1; ++e) {
-                int r = tcol[e] - r0;
-                if (r >= rlo && r < rhi) Cs[i * (nch + 1) + r] += kv * (T)tval[e];
+              v = kernel_value<T>(r2, g.pow, theta, inv_len, inv_len2);
+            }
+            kvs[j * kPT + ii] = v;
+          }
+          // the chunk's H^T entries are one contiguous range; stage it when it fits
+          const int64_t eb = trowptr[js], ne = trowptr[js + jc] - eb;
+          const bool staged = ne <= kNzStage;
+          if (staged)
+            for (int t = threadIdx.x; t < (int)ne; t += blockDim.x) {
+              zc[t] = tcol[eb + t];
+              zv[t] = (T)tval[eb + t];
+            }
+          __syncthreads();
+          if (i < cnt) {
+            for (int j = 0; j < ns; ++j) {
+              const int64_t e0 = se[2 * j], e1 = se[2 * j + 1];
+              const T kv = kvs[j * kPT + i];
+              if (staged) {
+                for (int e = (int)(e0 - eb); e < (int)(e1 - eb); ++e) {
+                  const int r = zc[e] - r0;
+                  if (r >= rlo && r < rhi) Cs[i * (nch + 1) + r] += kv * zv[e];
+                }
+              } else {
+                for (int64_t e = e0; e < e1; ++e) {
+                  int r = tcol[e] - r0;
+                  if (r >= rlo && r < rhi) Cs[i * (nch + 1) + r] += kv * (T)tval[e];
+                }
               }
             }
           }
@@ -636,7 +945,7 @@ Status h2_product(const Tree& t, const SparseH& h, const FmmParams& fp, T* out, 
     HIKF_LAUNCH_CHECK("m2l_table");
     // P2M
     {
-      size_t sm = smem_pts + sizeof(T) * kPT * nch;
+      size_t sm = smem_pts + sizeof(T) * kPT * nch + sizeof(int) * (2 * (size_t)nch + 1);
       HIKF_TRY(set_smem<T>((const void*)p2m_kernel<T>, sm));
       p2m_kernel<T><<<(unsigned)t.nleaf, kThreads, sm, s>>>(g, t.pts, t.leaf_start, h.trowptr, h.tcol, h.tval, tab,
                                                              nsrc, leaf0, nch, W);
@@ -647,8 +956,11 @@ Status h2_product(const Tree& t, const SparseH& h, const FmmParams& fp, T* out, 
       size_t sm = sizeof(T) * (2 * kPMax * kPMax + 3 * (size_t)q * nch);
       HIKF_TRY(set_smem<T>((const void*)m2m_kernel<T>, sm));
       for (int lev = L - 1; lev >= 2; --lev) {
-        m2m_kernel<T><<<(unsigned)((int64_t)1 << (dim * lev)), kThreads, sm, s>>>(
-            g, lev, tab, nsrc, t.box_offset[lev], t.box_offset[lev + 1], nch, W);
+        const int64_t npar = (int64_t)1 << (dim * lev);
+        if (!launch_transfer_reg<T, true>(p, dim, ldc, tab, nsrc, t.box_offset[lev], t.box_offset[lev + 1], npar, W,
+                                          s))
+          m2m_kernel<T><<<(unsigned)npar, kThreads, sm, s>>>(g, lev, tab, nsrc, t.box_offset[lev],
+                                                            t.box_offset[lev + 1], nch, W);
         HIKF_LAUNCH_CHECK("m2m");
       }
     }
@@ -696,8 +1008,11 @@ Status h2_product(const Tree& t, const SparseH& h, const FmmParams& fp, T* out, 
       size_t sm = sizeof(T) * (2 * kPMax * kPMax + 3 * (size_t)q * nch);
       HIKF_TRY(set_smem<T>((const void*)l2l_kernel<T>, sm));
       for (int lev = 2; lev <= L - 1; ++lev) {
-        l2l_kernel<T><<<(unsigned)((int64_t)1 << (dim * lev)), kThreads, sm, s>>>(
-            g, lev, tab, npts, t.box_offset[lev], t.box_offset[lev + 1], nch, Lx);
+        const int64_t npar = (int64_t)1 << (dim * lev);
+        if (!launch_transfer_reg<T, false>(p, dim, ldc, tab, npts, t.box_offset[lev], t.box_offset[lev + 1], npar,
+                                           Lx, s))
+          l2l_kernel<T><<<(unsigned)npar, kThreads, sm, s>>>(g, lev, tab, npts, t.box_offset[lev],
+                                                            t.box_offset[lev + 1], nch, Lx);
         HIKF_LAUNCH_CHECK("l2l");
       }
     }
@@ -705,8 +1020,14 @@ Status h2_product(const Tree& t, const SparseH& h, const FmmParams& fp, T* out, 
   // L2P + P2P at the leaves
   {
     int nchp = ldc;
-    while (nchp > 32 && smem_pts + sizeof(T) * (size_t)kPT * (nchp + 1) > 160 * 1024) nchp /= 2;
-    size_t sm = smem_pts + sizeof(T) * ((size_t)kPT * (nchp + 1) + kPT * 6 + 4) + sizeof(int64_t) * 2 * kPT;
+    // P2P tables: kernel values (kPT x kPT) and the staged H^T entries of a source chunk
+    const size_t p2p_full = sizeof(T) * ((size_t)kPT * kPT + kNzStage) + sizeof(int) * kNzStage;
+    while (nchp > 32 && smem_pts + p2p_full + sizeof(T) * (size_t)kPT * (nchp + 1) > 190 * 1024) nchp /= 2;
+    nchp = std::max(8, nchp / 8 * 8);  // the L2P tile reads 8 columns at a time
+    // the kernel-value table lives in S's storage when there is one column chunk (as in the kernel)
+    const bool alias_kv = q >= kPT && nchp >= ldc;
+    const size_t p2p = p2p_full - (alias_kv ? sizeof(T) * (size_t)kPT * kPT : 0);
+    size_t sm = smem_pts + sizeof(T) * ((size_t)kPT * (nchp + 1) + kPT * 6 + 4) + sizeof(int64_t) * 2 * kPT + p2p;
     HIKF_TRY(set_smem<T>((const void*)l2p_p2p_kernel<T>, sm));
     l2p_p2p_kernel<T><<<(unsigned)t.nleaf, kThreads, sm, s>>>(g, t.pts, t.leaf_start, h.trowptr, h.tcol, h.tval,
                                                                 tab, nsrc, leaf0, nchp, Lx, out);
