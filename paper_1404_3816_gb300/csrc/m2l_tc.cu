@@ -73,20 +73,31 @@ struct Dims {
 // W[box][c][r] -> image[box][piece][chunk][core layout of (r, c mod 32)]
 __global__ void pack_w_kernel(const float* __restrict__ W, int64_t box0, int64_t nboxes,
                               const int64_t* __restrict__ nsrc, Dims d, unsigned char* __restrict__ img) {
+  // one thread: four consecutive nodes c (one 16-byte row of a core matrix) of one column
+  // r; consecutive threads take consecutive columns, so the loads of W and the 16-byte
+  // stores of both pieces are coalesced
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t per_box = (int64_t)d.nkc * kKC * d.ldp;
+  const int64_t per_box = (int64_t)d.nkc * (kKC / 4) * d.ldp;
   if (t >= nboxes * per_box) return;
   const int64_t b = t / per_box;
   if (nsrc[box0 + b] == 0) return;
   const int rem = (int)(t % per_box);
-  const int c = rem / d.ldp, r = rem % d.ldp;
-  const float v = (c < d.q && r < d.rw) ? W[(box0 + b) * (int64_t)d.q * d.ld + (int64_t)c * d.ld + d.r0 + r] : 0.f;
-  float hi, lo;
-  tf32_split(v, hi, lo);
-  const int kc = c / kKC, kk = c % kKC;
+  const int cq = rem / d.ldp, r = rem % d.ldp;  // cq: index of the quad of nodes
+  const int c0 = cq * 4;
+  const float* Wb = W + (box0 + b) * (int64_t)d.q * d.ld + d.r0 + r;
+  float4 hi, lo;
+  float* h = &hi.x;
+  float* l = &lo.x;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int c = c0 + u;
+    const float v = (c < d.q && r < d.rw) ? Wb[(int64_t)c * d.ld] : 0.f;
+    tf32_split(v, h[u], l[u]);
+  }
+  const int kc = c0 / kKC, kk = c0 % kKC;
   unsigned char* base = img + b * d.a_box_bytes + (int64_t)kc * d.a_chunk_bytes + off32(r, kk);
-  *reinterpret_cast<float*>(base) = hi;
-  *reinterpret_cast<float*>(base + (int64_t)d.nkc * d.a_chunk_bytes) = lo;
+  *reinterpret_cast<float4*>(base) = hi;
+  *reinterpret_cast<float4*>(base + (int64_t)d.nkc * d.a_chunk_bytes) = lo;
 }
 
 // operators K_off[a][c] (level slice of the FP32 table) -> image[off][piece][chunk][(a, c mod 32)]
@@ -498,7 +509,7 @@ Status m2l_tc_all(const M2lTcAll& a, cudaStream_t s) {
     d.a_box_bytes = 2 * (int64_t)d.nkc * d.a_chunk_bytes;
     unsigned char* wimg = nullptr;
     HIKF_CUDA(cudaMallocAsync((void**)&wimg, (size_t)(nboxes * d.a_box_bytes), s));
-    const int64_t wthreads = nboxes * (int64_t)d.nkc * kKC * d.ldp;
+    const int64_t wthreads = nboxes * (int64_t)d.nkc * (kKC / 4) * d.ldp;
     pack_w_kernel<<<nblk(wthreads, 256), 256, 0, s>>>(a.W, wbox0, nboxes, a.nsrc, d, wimg);
     HIKF_LAUNCH_CHECK("pack_w");
     // sources per TMEM accumulation: at most ~4096 products per output element

@@ -52,10 +52,59 @@ __global__ void gather_hc_kernel(const int64_t* __restrict__ rowptr, const int32
                                  const double* __restrict__ val, const T* __restrict__ C, int ld, int n,
                                  double* __restrict__ out, int accumulate) {
   const int r = blockIdx.x;
-  for (int c = threadIdx.x; c < n; c += blockDim.x) {
-    double acc = 0.0;
-    for (int64_t k = rowptr[r]; k < rowptr[r + 1]; ++k) acc += val[k] * (double)C[(int64_t)col[k] * ld + c];
-    if (accumulate) out[(int64_t)r * n + c] += acc; else out[(int64_t)r * n + c] = acc;
+  if constexpr (sizeof(T) == 4) {
+    // FP32 C: a double-float (hi + lo) sum of the products H_rk C_kc on the FP32 pipe (about
+    // 2^-48 relative per term, far below the FP32 rounding already in C). The ray's entries
+    // are split into FP32 pairs once, in shared memory, in chunks.
+    constexpr int kG = 1024, kCols = kMaxN / 256;  // columns per thread (blockDim = 256)
+    __shared__ float svh[kG], svl[kG];
+    __shared__ int scol[kG];
+    float sh[kCols], sl[kCols];
+#pragma unroll
+    for (int u = 0; u < kCols; ++u) sh[u] = sl[u] = 0.f;
+    const int64_t e0 = rowptr[r], e1 = rowptr[r + 1];
+    for (int64_t base = e0; base < e1; base += kG) {
+      const int cnt = (int)min((int64_t)kG, e1 - base);
+      for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+        const double v = val[base + t];
+        const float vh = (float)v;
+        svh[t] = vh;
+        svl[t] = (float)(v - (double)vh);
+        scol[t] = col[base + t];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < kCols; ++u) {
+        const int c = threadIdx.x + u * blockDim.x;
+        if (c >= n) break;
+        float h = sh[u], l = sl[u];
+        for (int t = 0; t < cnt; ++t) {
+          const float vh = svh[t], x = (float)C[(int64_t)scol[t] * ld + c];
+          const float p = vh * x;
+          const float e = fmaf(vh, x, -p) + svl[t] * x;  // v x = p + e to about 2^-48
+          const float s2 = h + p;                       // (h, l) += (p, e) by an exact two-sum
+          const float bp = s2 - h;
+          l += ((h - (s2 - bp)) + (p - bp)) + e;
+          h = s2;
+        }
+        sh[u] = h;
+        sl[u] = l;
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < kCols; ++u) {
+      const int c = threadIdx.x + u * blockDim.x;
+      if (c >= n) break;
+      const double acc = (double)sh[u] + (double)sl[u];
+      if (accumulate) out[(int64_t)r * n + c] += acc; else out[(int64_t)r * n + c] = acc;
+    }
+  } else {
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+      double acc = 0.0;
+      for (int64_t k = rowptr[r]; k < rowptr[r + 1]; ++k) acc += val[k] * (double)C[(int64_t)col[k] * ld + c];
+      if (accumulate) out[(int64_t)r * n + c] += acc; else out[(int64_t)r * n + c] = acc;
+    }
   }
 }
 
