@@ -96,9 +96,9 @@ __global__ void fill_kernel(double* __restrict__ v, int64_t m, double val) {
 // instruction): the same value as the FP64 product rounded to FP32 whenever f is exact in
 // FP32, as the ratios of kernel amplitudes in use are (c = 100)
 template <typename T>
-__global__ void scale_kernel(const T* __restrict__ src, T* __restrict__ dst, int64_t count, double f) {
+__global__ void scale_kernel(const T* __restrict__ src, T* __restrict__ dst, int64_t count, T f) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < count) dst[t] = src[t] * (T)f;
+  if (t < count) dst[t] = src[t] * f;
 }
 
 __global__ void count_step(const int* __restrict__ flag, long long* __restrict__ step) {
@@ -269,7 +269,7 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
       HIKF_CUDA(cudaMemsetAsync(C, 0, sizeof(T) * (size_t)m * ld, s));
     } else if (p0.pow == q.pow && p0.length == q.length) {
       // P_0 = (theta_0 / theta_Q) Q  =>  C_0 = P_0 H^T = (theta_0 / theta_Q) C_Q
-      hikf::scale_kernel<T><<<hikf::nblk(m * ld, 256), 256, 0, s>>>(CQ, C, m * ld, p0.theta / q.theta);
+      hikf::scale_kernel<T><<<hikf::nblk(m * ld, 256), 256, 0, s>>>(CQ, C, m * ld, (T)(p0.theta / q.theta));
       HIKF_LAUNCH_CHECK("scale");
     } else {
       hikf::FmmParams f0;

@@ -36,6 +36,8 @@ struct Geo {
   int dim, depth, p, q, ld, n;
   int pow;
   double theta, length;
+  double wl;                  // leaf width side / 2^depth (host-computed: no FP64 division per thread)
+  double inv_len, inv_len2;   // 1 / length, 1 / length^2
 };
 
 __host__ __device__ inline int64_t cmin64(int64_t a, int64_t b) { return a < b ? a : b; }
@@ -165,7 +167,7 @@ __device__ void leaf_weights(const Geo& g, const double* __restrict__ pts, int64
   int64_t c[3] = {0, 0, 0};
   for (int bit = 0; bit < g.depth; ++bit)
     for (int d = 0; d < dim; ++d) c[d] |= ((b >> (bit * dim + (dim - 1 - d))) & 1) << bit;
-  const double wl = g.side / (double)((int64_t)1 << g.depth);
+  const double wl = g.wl;
   for (int t = threadIdx.x; t < cnt * dim; t += blockDim.x) {
     int i = t / dim, d = t % dim;
     double ctr = g.lo[d] + ((double)c[d] + 0.5) * wl;
@@ -736,10 +738,10 @@ __global__ void __launch_bounds__(kThreads) l2p_p2p_kernel(Geo g, const double* 
   int64_t cb[3] = {0, 0, 0};
   for (int bit = 0; bit < L; ++bit)
     for (int d = 0; d < dim; ++d) cb[d] |= ((b >> (bit * dim + (dim - 1 - d))) & 1) << bit;
-  const double wl = g.side / (double)((int64_t)1 << L);
+  const double wl = g.wl;
   double ctr[3];
   for (int d = 0; d < dim; ++d) ctr[d] = g.lo[d] + ((double)cb[d] + 0.5) * wl;
-  const T theta = (T)g.theta, inv_len = (T)(1.0 / g.length), inv_len2 = (T)(1.0 / (g.length * g.length));
+  const T theta = (T)g.theta, inv_len = (T)g.inv_len, inv_len2 = (T)g.inv_len2;
   const T* Lb = Lx + (leaf_box0 + b) * (int64_t)q * ld;
   const int nnb = ipow(3, dim);
   const int parts = kThreads / kPT;  // threads per target point
@@ -907,6 +909,9 @@ Status h2_product(const Tree& t, const SparseH& h, const FmmParams& fp, T* out, 
   g.pow = fp.pow;
   g.theta = fp.theta;
   g.length = fp.length;
+  g.wl = t.side / (double)((int64_t)1 << t.depth);
+  g.inv_len = 1.0 / fp.length;
+  g.inv_len2 = 1.0 / (fp.length * fp.length);
   const int p = g.p, q = g.q, L = t.depth, dim = t.dim;
   const int64_t nbox = t.nbox_total;
   const int64_t m = t.m;
