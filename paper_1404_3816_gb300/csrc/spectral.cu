@@ -41,20 +41,23 @@ __device__ __forceinline__ unsigned long long tc_now_ns() {
 // Grid barrier over a cooperative launch (every CTA resident): a counter with a bounded
 // wait (2 s), after which the CTA sets *err and *s_abort, and the caller leaves.
 __device__ bool grid_barrier(unsigned* bar, unsigned& gen, int* err, volatile int* s_abort) {
+  // arrive with a release add, wait with acquire loads: the CTA's writes (ordered before
+  // thread 0 by the CTA barrier) are visible to every CTA that passes
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
     const unsigned target = (gen + 1u) * gridDim.x;
-    atomicAdd(bar, 1u);
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
     const unsigned long long t0 = tc_now_ns();
-    while (*(volatile unsigned*)bar < target) {
+    while (true) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+      if (v >= target) break;
       if (tc_now_ns() - t0 > 2000000000ull) {
         atomicExch(err, 1);
         *s_abort = 1;
         break;
       }
     }
-    __threadfence();
   }
   __syncthreads();
   ++gen;
@@ -95,28 +98,41 @@ __device__ __forceinline__ int rr_slot(int r, int a, int N, int& partner) {
 }
 
 // One Jacobi rotation J (J_pp = J_qq = c, J_pq = s, J_qp = -s) with (J^T A J)_pq = 0:
-// t = tan(phi) is the smaller root of t^2 + 2 tau t - 1 = 0, tau = (a_qq - a_pp) / (2 a_pq),
-// written as t = sign(d) b / (|d| + hypot(d, b)) with d = a_qq - a_pp, b = 2 a_pq (one
-// division); c = 1 / sqrt(1 + t^2), s = t c. A pair whose off-diagonal entry is negligible
-// (|a_pq| <= eps sqrt(|a_pp a_qq|), or below the absolute floor) is not rotated: t = 0.
+// t = tan(phi) is the smaller root of t^2 + 2 tau t - 1 = 0, tau = (a_qq - a_pp) / (2 a_pq).
+// With d = a_qq - a_pp, b = 2 a_pq, h = hypot(d, b), u = h + |d| this is t = sign(d) b / u,
+// and c = u / sqrt(2 h u), s = sign(d) b / sqrt(2 h u) (c^2 + s^2 = (u^2 + b^2) / (2 h u) = 1),
+// t = s / c = 2 h sign(d) b / (2 h u): two reciprocal square roots and no division, whose
+// FP64 latency (~650 cycles on this part) would sit on every round's critical path. A pair
+// whose off-diagonal entry is negligible (|a_pq| <= eps sqrt(|a_pp a_qq|), or below the
+// absolute floor) is not rotated: t = 0.
 __device__ __forceinline__ bool jacobi_rotation(double app, double aqq, double apq, double floor_abs, double& c,
                                                 double& s, double& t) {
   c = 1.0;
   s = 0.0;
   t = 0.0;
-  const double aa = fabs(apq);
-  if (aa <= floor_abs || aa <= 2.220446049250313e-16 * sqrt(fabs(app)) * sqrt(fabs(aqq))) return false;
-  const double d = aqq - app, b = 2.0 * apq;
-  const double h2 = fma(d, d, b * b);
-  double h;
-  if (h2 > 1e-290 && h2 < 1e290) {
-    h = h2 * rsqrt(h2);
-  } else {
-    h = hypot(d, b);
+  const double aa = fabs(apq), pa = fabs(app), qa = fabs(aqq);
+  if (aa <= floor_abs) return false;
+  if (pa < 1e150 && qa < 1e150 && aa > 1e-150) {  // squared: no square roots on the chain
+    if (aa * aa <= 4.930380657631324e-32 * pa * qa) return false;
+  } else if (aa <= 2.220446049250313e-16 * sqrt(pa) * sqrt(qa)) {
+    return false;
   }
-  t = (d >= 0.0 ? b : -b) / (fabs(d) + h);
-  c = rsqrt(fma(t, t, 1.0));
-  s = t * c;
+  const double d = aqq - app, b = 2.0 * apq;
+  const double sb = d >= 0.0 ? b : -b;
+  const double h2 = fma(d, d, b * b);
+  if (h2 > 1e-290 && h2 < 1e290) {
+    const double h = h2 * rsqrt(h2);
+    const double u = h + fabs(d);
+    const double r2 = rsqrt(2.0 * h * u);
+    c = u * r2;
+    s = sb * r2;
+    t = 2.0 * h * s * r2;
+  } else {
+    const double h = hypot(d, b);
+    t = sb / (fabs(d) + h);
+    c = 1.0 / sqrt(fma(t, t, 1.0));
+    s = t * c;
+  }
   return true;
 }
 
@@ -136,12 +152,13 @@ __global__ void __launch_bounds__(kJacThreads) eig_jacobi_kernel(double* __restr
                                                                  unsigned* bar, int* err, int* info,
                                                                  int* sweeps) {
   __shared__ double sc[kMaxN / 2], ssn[kMaxN / 2], st[kMaxN / 2];
-  __shared__ int spi[kMaxN / 2], sqi[kMaxN / 2];
+  __shared__ int spi[kMaxN / 2], sqi[kMaxN / 2], son[kMaxN / 2];
+  __shared__ int sslp[kMaxN / 2], sptp[kMaxN / 2], sslq[kMaxN / 2], sptq[kMaxN / 2];
   __shared__ int s_rot;
   __shared__ volatile int s_abort;
   const int P = N / 2;
   const int tid = threadIdx.x;
-  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + tid, gthreads = (int64_t)gridDim.x * blockDim.x;
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + tid, gthreads = (int64_t)gridDim.x * blockDim.x;  // setup only
   unsigned gen = 0;
   if (tid == 0) s_abort = 0;
   // V = I; round-0 inputs into parity 0
@@ -167,7 +184,6 @@ __global__ void __launch_bounds__(kJacThreads) eig_jacobi_kernel(double* __restr
   }
   __syncthreads();
   const double floor_abs = 2.220446049250313e-16 * s_dmax / N;
-  const int64_t nA = (int64_t)P * P, nunits = nA + (int64_t)P * N;
   int par = 0, sw = 0;
   bool converged = false;
   for (; sw < max_sweeps && !converged; ++sw) {
@@ -183,77 +199,79 @@ __global__ void __launch_bounds__(kJacThreads) eig_jacobi_kernel(double* __restr
         int p, q;
         rr_pair(r, k, N, p, q);
         double c, s_, t;
-        if (jacobi_rotation(dg[p], dg[q], pg[k], floor_abs, c, s_, t)) atomicAdd(&s_rot, 1);
+        const bool on = jacobi_rotation(dg[p], dg[q], pg[k], floor_abs, c, s_, t);
+        if (on) atomicAdd(&s_rot, 1);
         sc[k] = c;
         ssn[k] = s_;
         st[k] = t;
         spi[k] = p;
         sqi[k] = q;
+        son[k] = on ? 1 : 0;
+        // where p and q go in the next round: the slot of their pair and their partner
+        int pp, pq2;
+        sslp[k] = rr_slot(rn, p, N, pp);
+        sptp[k] = pp;
+        sslq[k] = rr_slot(rn, q, N, pq2);
+        sptq[k] = pq2;
       }
       __syncthreads();
-      for (int64_t u = gtid; u < nunits; u += gthreads) {
-        if (u < nA) {
-          const int i = (int)(u / P), j = (int)(u % P);
-          if (i > j) continue;
-          const int p = spi[i], q = sqi[i];
-          if (i == j) {  // diagonal block: a_pp - t a_pq, a_qq + t a_pq, a_pq -> 0
-            const double t = st[i], apq = A[(int64_t)p * N + q];
-            const double app = A[(int64_t)p * N + p] - t * apq, aqq = A[(int64_t)q * N + q] + t * apq;
-            A[(int64_t)p * N + p] = app;
-            A[(int64_t)q * N + q] = aqq;
-            A[(int64_t)p * N + q] = 0.0;
-            A[(int64_t)q * N + p] = 0.0;
-            dn[p] = app;
-            dn[q] = aqq;
-            int partner;
-            const int slot = rr_slot(rn, p, N, partner);
-            if (partner == q) pn[slot] = 0.0;  // N = 2: the same pair meets again
-            continue;
-          }
-          const int u0 = spi[j], v0 = sqi[j];
-          double x00 = A[(int64_t)p * N + u0], x01 = A[(int64_t)p * N + v0];
-          double x10 = A[(int64_t)q * N + u0], x11 = A[(int64_t)q * N + v0];
-          const double c1 = sc[i], s1 = ssn[i], c2 = sc[j], s2 = ssn[j];
-          if (s1 != 0.0 || s2 != 0.0) {
-            // rows: J_i^T X
-            const double y00 = c1 * x00 - s1 * x10, y01 = c1 * x01 - s1 * x11;
-            const double y10 = s1 * x00 + c1 * x10, y11 = s1 * x01 + c1 * x11;
-            // columns: Y J_j
-            x00 = c2 * y00 - s2 * y01;
-            x01 = s2 * y00 + c2 * y01;
-            x10 = c2 * y10 - s2 * y11;
-            x11 = s2 * y10 + c2 * y11;
-            A[(int64_t)p * N + u0] = x00;
-            A[(int64_t)p * N + v0] = x01;
-            A[(int64_t)q * N + u0] = x10;
-            A[(int64_t)q * N + v0] = x11;
-            A[(int64_t)u0 * N + p] = x00;
-            A[(int64_t)v0 * N + p] = x01;
-            A[(int64_t)u0 * N + q] = x10;
-            A[(int64_t)v0 * N + q] = x11;
-          }
-          // export the entries that form a pair of the next round
-          const int rows[2] = {p, q}, cols[2] = {u0, v0};
-          const double xv[4] = {x00, x01, x10, x11};
-#pragma unroll
-          for (int a = 0; a < 2; ++a) {
-            int partner;
-            const int slot = rr_slot(rn, rows[a], N, partner);
-#pragma unroll
-            for (int b2 = 0; b2 < 2; ++b2)
-              if (partner == cols[b2]) pn[slot] = xv[a * 2 + b2];
+      // updates: tasks 0 .. P-1 are the block rows i (blocks j >= i), tasks P .. 2P-1 the
+      // column pairs of V; tasks are dealt to the CTAs in turn
+      for (int task = blockIdx.x; task < 2 * P; task += gridDim.x) {
+        if (task < P) {
+          const int i = task, p = spi[i], q = sqi[i];
+          for (int j = i + tid; j < P; j += blockDim.x) {
+            if (j == i) {  // diagonal block: a_pp - t a_pq, a_qq + t a_pq, a_pq -> 0
+              const double t = st[i], apq = A[(int64_t)p * N + q];
+              const double app = A[(int64_t)p * N + p] - t * apq, aqq = A[(int64_t)q * N + q] + t * apq;
+              A[(int64_t)p * N + p] = app;
+              A[(int64_t)q * N + q] = aqq;
+              A[(int64_t)p * N + q] = 0.0;
+              A[(int64_t)q * N + p] = 0.0;
+              dn[p] = app;
+              dn[q] = aqq;
+              if (sptp[i] == q) pn[sslp[i]] = 0.0;  // N = 2: the same pair meets again
+              continue;
+            }
+            const int u0 = spi[j], v0 = sqi[j];
+            double x00 = A[(int64_t)p * N + u0], x01 = A[(int64_t)p * N + v0];
+            double x10 = A[(int64_t)q * N + u0], x11 = A[(int64_t)q * N + v0];
+            if (son[i] | son[j]) {
+              const double c1 = sc[i], s1 = ssn[i], c2 = sc[j], s2 = ssn[j];
+              // rows: J_i^T X
+              const double y00 = c1 * x00 - s1 * x10, y01 = c1 * x01 - s1 * x11;
+              const double y10 = s1 * x00 + c1 * x10, y11 = s1 * x01 + c1 * x11;
+              // columns: Y J_j
+              x00 = c2 * y00 - s2 * y01;
+              x01 = s2 * y00 + c2 * y01;
+              x10 = c2 * y10 - s2 * y11;
+              x11 = s2 * y10 + c2 * y11;
+              A[(int64_t)p * N + u0] = x00;
+              A[(int64_t)p * N + v0] = x01;
+              A[(int64_t)q * N + u0] = x10;
+              A[(int64_t)q * N + v0] = x11;
+              A[(int64_t)u0 * N + p] = x00;
+              A[(int64_t)v0 * N + p] = x01;
+              A[(int64_t)u0 * N + q] = x10;
+              A[(int64_t)v0 * N + q] = x11;
+            }
+            // export the entries that form a pair of the next round
+            if (sptp[i] == u0) pn[sslp[i]] = x00;
+            if (sptp[i] == v0) pn[sslp[i]] = x01;
+            if (sptq[i] == u0) pn[sslq[i]] = x10;
+            if (sptq[i] == v0) pn[sslq[i]] = x11;
           }
         } else {
-          const int64_t v = u - nA;
-          const int k = (int)(v / N), comp = (int)(v % N);
-          const double s_ = ssn[k];
-          if (s_ == 0.0) continue;
-          const double c = sc[k];
-          double* vp = VT + (int64_t)spi[k] * N + comp;
-          double* vq = VT + (int64_t)sqi[k] * N + comp;
-          const double a = *vp, b = *vq;
-          *vp = c * a - s_ * b;
-          *vq = s_ * a + c * b;
+          const int k = task - P;
+          if (!son[k]) continue;
+          const double c = sc[k], s_ = ssn[k];
+          double* vp = VT + (int64_t)spi[k] * N;
+          double* vq = VT + (int64_t)sqi[k] * N;
+          for (int comp = tid; comp < N; comp += blockDim.x) {
+            const double a = vp[comp], b = vq[comp];
+            vp[comp] = c * a - s_ * b;
+            vq[comp] = s_ * a + c * b;
+          }
         }
       }
       par ^= 1;
@@ -442,7 +460,7 @@ Status spectral_setup(SpectralState& sp, const double* hcq_sym, const double* rd
     HIKF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     HIKF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, eig_jacobi_kernel, kJacThreads, 0));
     if (per_sm < 1) return make_status(HIKF_ECUDA, "the Jacobi eigensolver cannot be made resident");
-    const int grid = std::max(1, std::min(sms, (int)((NN / 2 + kJacThreads - 1) / kJacThreads)));
+    const int grid = std::max(1, std::min(sms, N));  // the 2 x N/2 update tasks of a round over all SMs
     double* Ap = A;
     double* Vp = VT;
     int Np = N, msw = kMaxSweeps;
@@ -524,13 +542,6 @@ __device__ __forceinline__ void df_add(float& sh, float& sl, float ph, float pl)
   e += sl + pl;
   sh = s + e;
   sl = e - (sh - s);
-}
-
-__device__ __forceinline__ void kahan_add(float v, float& s, float& c) {
-  const float y = v - c;
-  const float t = s + y;
-  c = (t - s) - y;
-  s = t;
 }
 
 // FP32: one warp per group of kRows rows; every load of the group is issued before
