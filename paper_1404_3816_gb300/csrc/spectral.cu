@@ -143,7 +143,11 @@ constexpr int kJacThreads = 256;
 // rotations of a round read only them, and the round's updates write the other parity,
 // so a CTA that is still forming rotations never sees A change under it, and one grid
 // barrier per round suffices. Every CTA forms all N/2 rotations of a round itself (the
-// same inputs give the same rotations and the same convergence decision in every CTA).
+// same inputs give the same rotations and the same convergence decision in every CTA),
+// with each index's slot and partner in the next round, which tell a block's thread
+// which of its four new entries to export. The updates are dealt to the CTAs as tasks:
+// block row i of A (blocks j >= i, the diagonal block included, each written with its
+// mirror) or column pair k of V. Every entry of A and V has one writer per round.
 // info[0] = 1 when max_sweeps sweeps did not converge; *sweeps = sweeps run.
 __global__ void __launch_bounds__(kJacThreads) eig_jacobi_kernel(double* __restrict__ A, double* __restrict__ VT,
                                                                  int N, int max_sweeps,
