@@ -49,11 +49,13 @@ typedef enum {
 
 /* Exponent of the generalised covariance function (Eq. Q):
  * K(r) = theta * exp(-(r / length)^pow); pow = 1 exponential, pow = 2 Gaussian
- * (Sec. 3.3, kernels 1-2). theta = 0 gives the zero kernel. */
-enum { HIKF_KERNEL_EXP = 1, HIKF_KERNEL_GAUSS = 2 };
+ * (Sec. 3.3, kernels 1-2). theta = 0 gives the zero kernel.
+ * HIKF_KERNEL_WHITE (pow = 0, initial covariance only): P_0 = theta I, the
+ * initialisation of Sec. 3.1 (cells uncorrelated; length is ignored). */
+enum { HIKF_KERNEL_WHITE = 0, HIKF_KERNEL_EXP = 1, HIKF_KERNEL_GAUSS = 2 };
 
 typedef struct {
-  int pow;       /* HIKF_KERNEL_EXP or HIKF_KERNEL_GAUSS */
+  int pow;       /* HIKF_KERNEL_EXP or HIKF_KERNEL_GAUSS (HIKF_KERNEL_WHITE: p0 only) */
   double theta;  /* variance scale, >= 0 (theta = K(0) = diag of the covariance) */
   double length; /* correlation length l > 0, in the units of `points` */
 } hikf_kernel;
@@ -135,7 +137,10 @@ hikf_status hikf_options_default(hikf_options* opt);
  *   x0        host, m FP64 initial mean x_{0|0}; NULL = zero (Sec. 4.2).
  *   p0        initial covariance kernel P_0; theta = 0 gives P_0 = 0 (Sec. 4.2).
  *             If p0 has q's pow and length, C_0 = (p0.theta / q.theta) C_Q and no
- *             second H^2 product is run.
+ *             second H^2 product is run. pow = HIKF_KERNEL_WHITE gives P_0 = theta I
+ *             (Sec. 3.1): C_0 = theta H^T, and the gain chain factors S_t every step
+ *             (the spectral chain, and with it the eigenbasis and n-space forms, needs
+ *             P_0 = c Q).
  *   opt       NULL = defaults.
  * Errors: HIKF_EINVAL (sizes, null pointers, non-finite or negative values,
  * column index out of range), HIKF_ENOMEM, HIKF_ECUDA.

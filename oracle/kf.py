@@ -41,6 +41,20 @@ def gcf(theta: float, length: float, pow: int) -> KernelFn:
     return k
 
 
+def white(theta: float) -> KernelFn:
+    """The uncorrelated initial covariance P_0 = theta I of Sec. 3.1 (P_0 = alpha I), as a
+    kernel: theta where the two points coincide, 0 elsewhere."""
+    theta = float(theta)
+
+    def k(X: np.ndarray, Y: np.ndarray) -> np.ndarray:
+        diff = X[:, None, :] - Y[None, :, :]
+        r2 = np.einsum("abd,abd->ab", diff, diff)
+        return np.where(r2 == 0.0, theta, 0.0)
+
+    k.theta = theta
+    return k
+
+
 def covariance_matrix(points: np.ndarray, kern: KernelFn) -> np.ndarray:
     """Dense m x m covariance K(x_i, x_j) (Sec. 2.3: Q_ij = K(r_ij))."""
     return kern(points, points)

@@ -225,14 +225,27 @@ Status validate_common(int dim, int64_t m, const double* points, int n, const in
   return Status::Ok();
 }
 
-Status validate_kernel(const hikf_kernel& k, bool allow_zero) {
+Status validate_kernel(const hikf_kernel& k, bool allow_zero, bool allow_white) {
   using hikf::make_status;
-  if (k.pow != HIKF_KERNEL_EXP && k.pow != HIKF_KERNEL_GAUSS) return make_status(HIKF_EINVAL, "kernel pow must be 1 or 2");
+  const bool white = allow_white && k.pow == HIKF_KERNEL_WHITE;
+  if (!white && k.pow != HIKF_KERNEL_EXP && k.pow != HIKF_KERNEL_GAUSS)
+    return make_status(HIKF_EINVAL, allow_white ? "kernel pow must be 0, 1 or 2" : "kernel pow must be 1 or 2");
   if (!std::isfinite(k.theta) || k.theta < 0.0 || (!allow_zero && k.theta == 0.0))
     return make_status(HIKF_EINVAL, "kernel theta out of range");
-  if (k.theta != 0.0 && (!(k.length > 0.0) || !std::isfinite(k.length)))
+  if (!white && k.theta != 0.0 && (!(k.length > 0.0) || !std::isfinite(k.length)))
     return make_status(HIKF_EINVAL, "kernel length must be > 0");
   return Status::Ok();
+}
+
+// C_0 = theta H^T (P_0 = theta I, Sec. 3.1): row i (tree order) gets theta times the
+// entries of H^T's row i; one thread per row, rows are disjoint
+template <typename T>
+__global__ void white_c0_kernel(const int64_t* __restrict__ trowptr, const int32_t* __restrict__ tcol,
+                                const double* __restrict__ tval, int64_t m, int ld, double theta,
+                                T* __restrict__ C) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  for (int64_t e = trowptr[i]; e < trowptr[i + 1]; ++e) C[i * ld + tcol[e]] += (T)(theta * tval[e]);
 }
 
 template <typename T>
@@ -267,6 +280,11 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
     HIKF_TRY(hikf::h2_product<T>(h->tree, h->H, fp, CQ, ld, s));
     if (p0.theta == 0.0) {
       HIKF_CUDA(cudaMemsetAsync(C, 0, sizeof(T) * (size_t)m * ld, s));
+    } else if (p0.pow == HIKF_KERNEL_WHITE) {
+      HIKF_CUDA(cudaMemsetAsync(C, 0, sizeof(T) * (size_t)m * ld, s));
+      white_c0_kernel<T><<<hikf::nblk(m, 256), 256, 0, s>>>(h->H.trowptr, h->H.tcol, h->H.tval, m, ld,
+                                                                   p0.theta, C);
+      HIKF_LAUNCH_CHECK("white_c0");
     } else if (p0.pow == q.pow && p0.length == q.length) {
       // P_0 = (theta_0 / theta_Q) Q  =>  C_0 = P_0 H^T = (theta_0 / theta_Q) C_Q
       hikf::scale_kernel<T><<<hikf::nblk(m * ld, 256), 256, 0, s>>>(CQ, C, m * ld, (T)(p0.theta / q.theta));
@@ -602,9 +620,9 @@ hikf_status create_impl(hikf_t** out, int dim, int64_t m, const double* points, 
   if (opt) o = *opt;
   Status st = validate_common(dim, m, points, n, rowptr, col, val, r_diag, x0, o);
   if (!st.ok()) return fail(nullptr, st);
-  st = validate_kernel(q, cq != nullptr);
+  st = validate_kernel(q, cq != nullptr, false);
   if (!st.ok()) return fail(nullptr, st);
-  st = validate_kernel(p0, true);
+  st = validate_kernel(p0, true, true);
   if (!st.ok()) return fail(nullptr, st);
   if (cq && !c0) return fail(nullptr, hikf::make_status(HIKF_EINVAL, "c0 is NULL"));
   if (o.precision == HIKF_PREC_MIXED && hikf::padded_ld(n) > 256)

@@ -24,6 +24,7 @@ from typing import Dict, List, Optional, Sequence, Tuple
 
 import numpy as np
 
+WHITE = 0  # initial covariance only: P_0 = theta I (Sec. 3.1), no correlation between cells
 EXP = 1    # GCF exponent p = 1: theta * exp(-r / l)
 GAUSS = 2  # GCF exponent p = 2: theta * exp(-r^2 / l^2)
 

@@ -283,6 +283,37 @@ def test_update_with_given_cq_matches_oracle(B):
         assert f.info()["step"] == Y.shape[0]
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_white_initial_covariance(B, prec):
+    """P_0 = theta_0 I (Sec. 3.1, HIKF_KERNEL_WHITE): C_0 = theta_0 H^T, the gain chain
+    factors S_t every step; against Alg. 2 in FP64 from the same start."""
+    w = W.small(grid=(47, 41), n=24, steps=6, seed=51)
+    Y, _ = W.measurements(w)
+    p0 = W.KernelSpec(W.WHITE, 0.5, 1.0)
+    with B.Filter(w.points, w.q, w.h_rowptr, w.h_col, w.h_val, w.r_diag, w.x0, p0, precision=prec,
+                  cheb_order=w.cheb_order, leaf_size=w.leaf_size) as f:
+        info = f.info()
+        assert info["chain"] == B.CHAIN_FACTOR
+        for y in Y:
+            f.assimilate(y)
+        x, v = f.mean(), f.variance()
+    H = qht.h_csr(w.h_rowptr, w.h_col, w.h_val, w.m)
+    cq = _oracle_h2(w, w.q, info["depth"], w.cheb_order)
+    c0 = qht.qht(w.points, kf.white(p0.theta), H)
+    ref = kf.hikf_cross(cq, c0, np.full(w.m, p0.theta), w.q.theta, H, w.r_diag, w.x0, Y)
+    tol = TOL64 if prec == "fp64" else TOL32
+    assert rel(x, ref["x"]) < tol
+    assert rel(v, ref["var"]) < tol
+
+
+def test_white_initial_covariance_rejects_the_spectral_forms(B):
+    w = W.small(grid=(20, 18), n=8, steps=2, seed=52)
+    with pytest.raises(B.HikfError) as e:
+        B.Filter(w.points, w.q, w.h_rowptr, w.h_col, w.h_val, w.r_diag, w.x0, W.KernelSpec(W.WHITE, 0.5, 1.0),
+                 form="eigen")
+    assert e.value.code == B.HIKF_EINVAL
+
+
 def _gauss3d(grid=(16, 16, 16), n=64, length=4.0, steps=3):
     w = W.make(grid=grid, n=n, q=W.KernelSpec(W.GAUSS, 0.01, length), p0=W.KernelSpec(W.GAUSS, 1.0, length),
                r=1e-3, steps=steps, seed=4, cheb_order=6)

@@ -9,6 +9,7 @@ Each check comes from the mathematics, not from the oracle's own formulas:
     (x_T, y_1..y_T) (Eq. random_walk: Cov(x_s, x_t) = P0 + min(s,t) Q).
   * invariants: P symmetric, PSD, positive diagonal, variance not increased by an update.
   * Alg. 2 (cross-covariance form) equals Alg. 1 (Sec. 3.1: equivalent formulation).
+  * P_0 = alpha I (Sec. 3.1): C_0 = alpha H^T, and Alg. 2 equals Alg. 1 from it.
 """
 import numpy as np
 import pytest
@@ -144,6 +145,28 @@ def test_cross_form_equals_full_kf_every_step():
     cq = qht.qht(w.points, kq, H)
     c0 = qht.qht(w.points, k0, H)
     cross = kf.hikf_cross(cq, c0, np.full(w.m, w.p0.theta), w.q.theta, H, w.r_diag, w.x0, Y, record=True)
+    for t in range(Y.shape[0]):
+        assert kf.relative_error(cross["xs"][t], full["xs"][t]) < 1e-11
+        assert kf.relative_error(cross["vars"][t], full["vars"][t]) < 1e-11
+
+
+def test_white_initial_covariance_alpha_identity():
+    """P_0 = alpha I (the initialisation of Sec. 3.1): the white kernel gives alpha I as a
+    matrix and alpha H^T as the product P_0 H^T (brute-force sums), and Alg. 2 started from
+    C_0 = alpha H^T, delta^2_0 = alpha equals Alg. 1 started from P_0 = alpha I."""
+    w = W.small(grid=(18, 15), n=9, steps=6, seed=12)
+    Y, _ = W.measurements(w)
+    H = qht.h_csr(w.h_rowptr, w.h_col, w.h_val, w.m)
+    alpha = 0.7
+    kw = kf.white(alpha)
+    assert np.array_equal(kf.covariance_matrix(w.points, kw), alpha * np.eye(w.m))
+    c0 = qht.qht(w.points, kw, H)
+    assert np.allclose(c0, alpha * H.toarray().T, rtol=0, atol=1e-15)
+    kq = kf.gcf(w.q.theta, w.q.length, w.q.pow)
+    Q = kf.covariance_matrix(w.points, kq)
+    full = kf.kf_full(alpha * np.eye(w.m), Q, H, w.r_diag, w.x0, Y, record=True)
+    cross = kf.hikf_cross(qht.qht(w.points, kq, H), c0, np.full(w.m, alpha), w.q.theta, H, w.r_diag, w.x0, Y,
+                          record=True)
     for t in range(Y.shape[0]):
         assert kf.relative_error(cross["xs"][t], full["xs"][t]) < 1e-11
         assert kf.relative_error(cross["vars"][t], full["vars"][t]) < 1e-11
