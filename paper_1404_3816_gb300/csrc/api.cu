@@ -52,7 +52,6 @@ int padded_ld(int n) { return (n + 31) / 32 * 32; }
 
 namespace {
 
-constexpr int kThreads = 256;
 inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 template <typename T>
@@ -97,8 +96,24 @@ __global__ void fill_kernel(double* __restrict__ v, int64_t m, double val) {
 // FP32, as the ratios of kernel amplitudes in use are (c = 100)
 template <typename T>
 __global__ void scale_kernel(const T* __restrict__ src, T* __restrict__ dst, int64_t count, T f) {
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < count) dst[t] = src[t] * f;
+  // 16 bytes per thread when the buffers are 16-byte aligned (the m x ld matrices are)
+  constexpr int kV = 16 / sizeof(T);
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0;
+  if (vec) {
+    const int64_t i0 = t * kV;
+    if (i0 + kV <= count) {
+      struct alignas(16) V { T v[kV]; };
+      V a = *reinterpret_cast<const V*>(src + i0);
+#pragma unroll
+      for (int k = 0; k < kV; ++k) a.v[k] *= f;
+      *reinterpret_cast<V*>(dst + i0) = a;
+    } else {
+      for (int64_t i = i0; i < count; ++i) dst[i] = src[i] * f;
+    }
+  } else {
+    for (int64_t i = t * kV; i < count && i < (t + 1) * kV; ++i) dst[i] = src[i] * f;
+  }
 }
 
 __global__ void count_step(const int* __restrict__ flag, long long* __restrict__ step) {
@@ -287,7 +302,8 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
       HIKF_LAUNCH_CHECK("white_c0");
     } else if (p0.pow == q.pow && p0.length == q.length) {
       // P_0 = (theta_0 / theta_Q) Q  =>  C_0 = P_0 H^T = (theta_0 / theta_Q) C_Q
-      hikf::scale_kernel<T><<<hikf::nblk(m * ld, 256), 256, 0, s>>>(CQ, C, m * ld, (T)(p0.theta / q.theta));
+      hikf::scale_kernel<T><<<hikf::nblk((m * ld + 16 / (int)sizeof(T) - 1) / (16 / (int)sizeof(T)), 256), 256, 0, s>>>(
+          CQ, C, m * ld, (T)(p0.theta / q.theta));
       HIKF_LAUNCH_CHECK("scale");
     } else {
       hikf::FmmParams f0;
@@ -420,7 +436,7 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
       // H x_0 = -(0 - H x_0)
       HIKF_CUDA(cudaMemsetAsync(h->ybuf, 0, sizeof(double) * n, s));
       HIKF_TRY(hikf::launch_innovation(h->ybuf, h->H, h->x, ns.hx0, h->flag, s));
-      hikf::scale_kernel<double><<<hikf::nblk(n, 256), 256, 0, s>>>(ns.hx0, ns.hx0, n, -1.0);
+      hikf::scale_kernel<double><<<hikf::nblk((n + 1) / 2, 256), 256, 0, s>>>(ns.hx0, ns.hx0, n, -1.0);
       HIKF_LAUNCH_CHECK("scale");
       h->var0 = p0.theta;
       h->nspace = true;

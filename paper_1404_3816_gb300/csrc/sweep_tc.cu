@@ -512,7 +512,7 @@ Status encode_map(CUtensorMap* map, const float* base, int64_t m, int ld, int bo
   if (!fn) {
     cudaDriverEntryPointQueryResult q;
     void* p = nullptr;
-    HIKF_CUDA(cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q));
+    HIKF_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
     if (q != cudaDriverEntryPointSuccess || !p) return make_status(HIKF_ECUDA, "cuTensorMapEncodeTiled unavailable");
     fn = (EncodeTiledFn)p;
   }
