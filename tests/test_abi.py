@@ -52,6 +52,8 @@ def test_invalid_arguments_are_rejected_before_any_device_work(lib):
         dict(r_diag=np.zeros(w.n)),
         dict(h_col=np.where(np.arange(w.nnz) == 0, w.m + 5, w.h_col)),
         dict(q=W.KernelSpec(3, 0.01, 8.0)),
+        dict(q=W.KernelSpec(W.WHITE, 0.01, 8.0)),      # the white kernel is for P_0 only
+        dict(p0=W.KernelSpec(3, 1.0, 8.0)),
         dict(q=W.KernelSpec(1, -1.0, 8.0)),
         dict(points=np.where(np.arange(w.m * 2).reshape(w.m, 2) == 3, np.nan, w.points)),
     ]
@@ -76,3 +78,38 @@ def test_serving_schedule_and_footprint_without_gpu():
     assert all(0 <= s < 64 for _, s in sched)
     big = max(streams, key=lambda w: w.m)
     assert serve.footprint_bytes(big) > 2 * big.m * 4 * ((big.n + 31) // 32 * 32)
+
+
+_CTYPES = {"int": "c_int", "double": "c_double", "int64_t": "c_int64", "void*": "c_void_p"}
+
+
+def _header_structs():
+    """{typedef name: [(C type, field name), ...]} of the plain structs in include/hikf.h."""
+    text = (ROOT / "include" / "hikf.h").read_text()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = {}
+    for body, name in re.findall(r"typedef\s+struct\s*\{(.*?)\}\s*(\w+)\s*;", text, flags=re.S):
+        fields = []
+        for decl in body.split(";"):
+            decl = " ".join(decl.split())
+            if not decl:
+                continue
+            m = re.match(r"([A-Za-z_][\w ]*?\s*\*?)\s*(\w+)$", decl)
+            assert m, decl
+            fields.append((m.group(1).replace(" ", ""), m.group(2)))
+        out[name] = fields
+    return out
+
+
+@pytest.mark.parametrize("cname,pyname", [("hikf_kernel", "Kernel"), ("hikf_options", "Options"),
+                                          ("hikf_info_t", "Info")])
+def test_binding_structs_match_the_header(cname, pyname):
+    """The ctypes mirrors of the ABI structs have the header's fields, in order, with the
+    same C types (a mismatch would shift every later field)."""
+    import ctypes as C
+    from paper_1404_3816_gb300 import binding
+    header = _header_structs()[cname]
+    mirror = getattr(binding, pyname)._fields_
+    assert [f for _, f in header] == [f for f, _ in mirror]
+    for (ctype, field), (_, pytype) in zip(header, mirror):
+        assert pytype is getattr(C, _CTYPES[ctype]), (cname, field, ctype, pytype)
