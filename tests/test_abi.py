@@ -113,3 +113,48 @@ def test_binding_structs_match_the_header(cname, pyname):
     assert [f for _, f in header] == [f for f, _ in mirror]
     for (ctype, field), (_, pytype) in zip(header, mirror):
         assert pytype is getattr(C, _CTYPES[ctype]), (cname, field, ctype, pytype)
+
+
+def _cc():
+    import shutil
+    return shutil.which("gcc") or shutil.which("cc")
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/hikf.h compiles as C99 on its own (no C++ or CUDA types in the boundary)."""
+    import subprocess
+    cc = _cc()
+    if not cc:
+        pytest.skip("no C compiler")
+    src = tmp_path / "h.c"
+    src.write_text('#include "hikf.h"\nint main(void) { return 0; }\n')
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", str(ROOT / "include"),
+                        "-fsyntax-only", str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+
+
+def test_c_program_links_and_calls_the_library(tmp_path, lib):
+    """A C program links against libhikf.so and calls a host-only entry point: the
+    defaults, and the rejection of a NULL argument with HIKF_EINVAL."""
+    import subprocess
+    from paper_1404_3816_gb300 import binding
+    cc = _cc()
+    if not cc:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use.c"
+    src.write_text(
+        '#include <stdio.h>\n#include "hikf.h"\n'
+        "int main(void) {\n"
+        "  hikf_options o;\n"
+        "  if (hikf_options_default(&o) != HIKF_OK) return 1;\n"
+        "  if (hikf_options_default(NULL) != HIKF_EINVAL) return 2;\n"
+        '  printf("%d %d %d %d %d %d\\n", o.cheb_order, o.leaf_size, o.max_depth, o.precision, o.graph, o.m2l);\n'
+        "  return 0;\n}\n")
+    exe = tmp_path / "use"
+    libdir = binding.LIB_PATH.parent
+    r = subprocess.run([cc, "-std=c99", "-I", str(ROOT / "include"), str(src), "-o", str(exe), "-L", str(libdir),
+                        "-lhikf", f"-Wl,-rpath,{libdir}"], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, (r.returncode, r.stderr)
+    assert r.stdout.split() == ["8", "64", "-1", "0", "1", "0"]
