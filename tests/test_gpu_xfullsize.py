@@ -195,11 +195,13 @@ def test_m2p21_3d_update_fp64_on_the_h2_product(B, case3d):
 
 
 @pytest.mark.parametrize("form", ["eigen", "nspace"])
-def test_m2p21_3d_fp32_forms_conditioning_bound(B, case3d, form):
+def test_m2p21_3d_fp32_forms_on_their_h2_product(B, case3d, form):
     """The FP32 eigenbasis and n-space forms at the 3D workload's full size, each on its
     own H^2 product (tensor-core M2L), against the filter run with the exact C_Q in FP64.
-    A regression bound: FP32 storage of G = C R^{-1/2} V and the conditioning of H C + R
-    put the mean beyond the 1e-5 target, which this workload meets in FP64 only."""
+    They land where the FP64 update fed the same product lands (1.52e-4 / 2.78e-5
+    measured): the 3.7e-6 error of the order-8 H^2 product, amplified by the conditioning
+    of H C + R, sets the accuracy here, not FP32 storage; the bounds are those of the FP64
+    test above."""
     import torch
     w, Y, H, exact, cq, ref = case3d
     with B.Filter.from_workload(w, precision="fp32", form=form, m2l="tensor") as f:
@@ -209,5 +211,5 @@ def test_m2p21_3d_fp32_forms_conditioning_bound(B, case3d, form):
         f.sync()
         x, v = f.mean(), f.variance()
     print(f"\n3d fp32 {form}: vs exact-C_Q filter mean {rel(x, ref['x']):.3g} var {rel(v, ref['var']):.3g}")
-    assert rel(x, ref["x"]) < 1e-2
-    assert rel(v, ref["var"]) < 1e-3
+    assert rel(x, ref["x"]) < 5e-4          # 1.52e-4 measured
+    assert rel(v, ref["var"]) < 1e-4        # 2.78e-5 measured
