@@ -219,6 +219,10 @@ typedef struct {
 
 hikf_status hikf_info(const hikf_t* h, hikf_info_t* info);
 
+/* Measurement updates applied so far (hikf_info's `step`); -1 when h is NULL or the
+ * count cannot be read. Waits for the handle's stream. */
+int64_t hikf_step(const hikf_t* h);
+
 /* Timing of the sweep, the O(n^2 m) pass of every update: while enabled,
  * CUDA events on the handle's stream bracket each sweep launch (up to 4096
  * launches; later ones are not recorded). Enabling resets the record. */

@@ -33,7 +33,7 @@ M2LS = {"auto": M2L_AUTO, "tensor": M2L_TENSOR, "simt": M2L_SIMT}
 EXPORTED = ["hikf_options_default", "hikf_create", "hikf_create_with_cq", "hikf_assimilate",
             "hikf_assimilate_device", "hikf_sync", "hikf_get_mean", "hikf_get_variance",
             "hikf_get_mean_device", "hikf_get_variance_device", "hikf_get_cq", "hikf_get_cross",
-            "hikf_get_perm", "hikf_info", "hikf_stream", "hikf_last_error", "hikf_destroy", "hikf_h2_qht",
+            "hikf_get_perm", "hikf_info", "hikf_step", "hikf_stream", "hikf_last_error", "hikf_destroy", "hikf_h2_qht",
             "hikf_profile_enable", "hikf_profile_read", "hikf_spd_inverse", "hikf_spd_inverse_noalloc"]
 
 
@@ -99,11 +99,11 @@ def load(path: Optional[os.PathLike] = None) -> C.CDLL:
     lib.hikf_spd_inverse.argtypes = [vp, C.c_int, vp, vp]
     lib.hikf_spd_inverse_noalloc.argtypes = [vp, C.c_int, vp, vp]
     lib.hikf_h2_qht.argtypes = [C.c_int, C.c_int64, dp, Kernel, C.c_int, ip, ip, dp, C.POINTER(Options), dp]
+    lib.hikf_step.argtypes = [H]
+    lib.hikf_step.restype = C.c_int64
     for nm in EXPORTED:
-        fn = getattr(lib, nm)
-        if fn.restype is C.c_int or nm not in ("hikf_stream", "hikf_last_error", "hikf_destroy"):
-            if nm not in ("hikf_stream", "hikf_last_error", "hikf_destroy"):
-                fn.restype = C.c_int
+        if nm not in ("hikf_stream", "hikf_last_error", "hikf_destroy", "hikf_step"):
+            getattr(lib, nm).restype = C.c_int
     if path is None:
         _lib = lib
     return lib
@@ -264,6 +264,10 @@ class Filter:
         out = np.empty(self.m, dtype=np.int64)
         _check(load().hikf_get_perm(self.h, _ip(out)), self.h)
         return out
+
+    def step(self) -> int:
+        """Measurement updates applied so far."""
+        return int(load().hikf_step(self.h))
 
     def info(self) -> dict:
         i = Info()

@@ -859,6 +859,12 @@ hikf_status hikf_info(const hikf_t* h, hikf_info_t* info) {
   return HIKF_OK;
 }
 
+int64_t hikf_step(const hikf_t* h) {
+  hikf_info_t i;
+  if (hikf_info(h, &i) != HIKF_OK) return -1;
+  return i.step;
+}
+
 hikf_status hikf_profile_enable(hikf_t* h, int enable) {
   if (!h) return HIKF_EINVAL;
   if (enable && h->ev.empty()) {

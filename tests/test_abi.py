@@ -134,8 +134,8 @@ def test_header_is_plain_c(tmp_path):
 
 
 def test_c_program_links_and_calls_the_library(tmp_path, lib):
-    """A C program links against libhikf.so and calls a host-only entry point: the
-    defaults, and the rejection of a NULL argument with HIKF_EINVAL."""
+    """A C program links against libhikf.so and calls host-only entry points: the
+    defaults, the rejection of a NULL argument with HIKF_EINVAL, hikf_step of no handle."""
     import subprocess
     from paper_1404_3816_gb300 import binding
     cc = _cc()
@@ -148,6 +148,7 @@ def test_c_program_links_and_calls_the_library(tmp_path, lib):
         "  hikf_options o;\n"
         "  if (hikf_options_default(&o) != HIKF_OK) return 1;\n"
         "  if (hikf_options_default(NULL) != HIKF_EINVAL) return 2;\n"
+        "  if (hikf_step(NULL) != -1) return 3;\n"
         '  printf("%d %d %d %d %d %d\\n", o.cheb_order, o.leaf_size, o.max_depth, o.precision, o.graph, o.m2l);\n'
         "  return 0;\n}\n")
     exe = tmp_path / "use"

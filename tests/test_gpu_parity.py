@@ -281,6 +281,7 @@ def test_update_with_given_cq_matches_oracle(B):
         assert rel(f.mean(), ref["x"]) < TOL32
         assert rel(f.variance(), ref["var"]) < TOL32
         assert f.info()["step"] == Y.shape[0]
+        assert f.step() == Y.shape[0]
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
