@@ -240,6 +240,23 @@ def job_rate(units_per_rank: int, seconds: float, world: int, device=None):
     return units_per_rank * world / seconds, seconds
 
 
+def oracle_rate_one_core(w, config: str, rows: int, steps: int = 1) -> float:
+    """Steps/s of the oracle on one host core (BLAS and OpenMP pinned to one thread in a
+    child process), on the first `rows` points and scaled to all m, for comparison with
+    the paper's single-core timings."""
+    code = ("import json, sys; sys.path.insert(0, {root!r}); import bench; "
+            "from paper_1404_3816_gb300 import workload as W; "
+            "print(json.dumps(bench.oracle_steps(W.config({cfg!r}), {steps}, rows={rows})))").format(
+                root=str(Path(__file__).resolve().parent), cfg=config, steps=steps, rows=rows)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               BLIS_NUM_THREADS="1", VECLIB_MAXIMUM_THREADS="1", NUMEXPR_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        raise RuntimeError("one-core oracle run failed: " + r.stderr[-500:])
+    dt = float(json.loads(r.stdout.strip().splitlines()[-1]))
+    return steps / (dt * w.m / rows)
+
+
 def run_reference(args, rank, world):
     """The oracle timed on the host cores. Each step is a bounded sample: the O-cross
     update on the first `rows` points (rows = m / 2^k, chosen from one probe step so that
@@ -260,6 +277,8 @@ def run_reference(args, rank, world):
     dt = oracle_steps(w, steps, rows=rows)
     dt_full = dt * (w.m / rows)
     value = steps / dt_full
+    rows1 = max(w.m // 1024, rows // 16)
+    one_core = oracle_rate_one_core(w, args.config, rows1)
     line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus, "steps": steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * dt_full / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -268,7 +287,9 @@ def run_reference(args, rank, world):
                        "note": "FP64 numpy oracle of Alg. 2 on the host cores"},
             "cpu_baseline": {"value": value, "unit": "steps/s", "cores": cpu_threads(), "kind": "oracle",
                              "sample": f"{steps} O-cross updates on {rows} of the m={w.m} points (n={w.n}, PSD "
-                                       f"stand-in C_Q), time scaled by m/{rows}"},
+                                       f"stand-in C_Q), time scaled by m/{rows}",
+                             "one_core": {"value": one_core, "unit": "steps/s", "cores": 1,
+                                          "sample": f"1 O-cross update on {rows1} points, scaled by m/{rows1}"}},
             "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0

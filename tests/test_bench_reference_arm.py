@@ -23,6 +23,8 @@ def test_reference_arm_json_line():
     assert d["value"] > 0 and d["config"]["workload"] == "crosswell2d_m1048576_n256"
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
+    one = cb["one_core"]                     # the oracle on one core, beside the all-core figure
+    assert one["cores"] == 1 and one["value"] > 0 and one["sample"]
     e2e = d["e2e"]
     assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
