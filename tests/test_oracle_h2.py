@@ -7,6 +7,8 @@
 * With depth <= 1 every pair of leaves touches: Q~ = Q.
 * Q~ is symmetric (targets and sources are interpolated alike), keeps the
   exact kernel on touching leaves, and converges to Q as p grows.
+* The same exactness and convergence hold in 3D (q = p^3 nodes, interaction lists of
+  up to 189 boxes).
 """
 import numpy as np
 import numpy.polynomial.chebyshev as npc
@@ -95,3 +97,39 @@ def test_auto_depth_matches_leaf_size():
     assert h2.auto_depth(65536, 2, 64) == 5
     assert h2.auto_depth(1 << 20, 2, 64) == 7
     assert h2.auto_depth(1 << 21, 3, 64) == 5
+
+
+def _small3d(grid=(12, 12, 12), n=16, length=3.0, seed=31):
+    return W.make(grid=grid, n=n, q=W.KernelSpec(W.GAUSS, 0.01, length), p0=W.KernelSpec(W.GAUSS, 1.0, length),
+                  r=1e-3, steps=1, seed=seed)
+
+
+def test_polynomial_kernel_is_exact_3d():
+    """3D: the tensor-product interpolant (q = p^3 nodes, up to 189 interaction-list
+    boxes) reproduces a kernel of degree 2 per coordinate at p = 4."""
+    w = _small3d()
+    H = qht.h_csr(w.h_rowptr, w.h_col, w.h_val, w.m)
+    exact = qht.qht(w.points, _poly_kernel, H)
+    approx = h2.h2_qht(w.points, _poly_kernel, H, p=4, depth=2)
+    assert np.linalg.norm(approx - exact) / np.linalg.norm(exact) < 1e-13
+
+
+def test_shallow_tree_is_exact_3d():
+    w = _small3d(grid=(9, 8, 7), seed=32)
+    H = qht.h_csr(w.h_rowptr, w.h_col, w.h_val, w.m)
+    k = kf.gcf(w.q.theta, w.q.length, w.q.pow)
+    exact = qht.qht(w.points, k, H)
+    for depth in (0, 1):
+        assert np.allclose(h2.h2_qht(w.points, k, H, p=3, depth=depth), exact, rtol=1e-13, atol=1e-16)
+
+
+def test_converges_with_order_3d():
+    """3D Gaussian kernel: the error falls with every added node per axis."""
+    w = _small3d()
+    H = qht.h_csr(w.h_rowptr, w.h_col, w.h_val, w.m)
+    k = kf.gcf(w.q.theta, w.q.length, w.q.pow)
+    exact = qht.qht(w.points, k, H)
+    errs = [np.linalg.norm(h2.h2_qht(w.points, k, H, p=p, depth=2) - exact) / np.linalg.norm(exact)
+            for p in (3, 4, 5, 6)]
+    assert all(e1 < 0.5 * e0 for e0, e1 in zip(errs, errs[1:])), errs
+    assert errs[-1] < 1e-4, errs
