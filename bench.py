@@ -278,7 +278,11 @@ def run_reference(args, rank, world):
     dt_full = dt * (w.m / rows)
     value = steps / dt_full
     rows1 = max(w.m // 1024, rows // 16)
-    one_core = oracle_rate_one_core(w, args.config, rows1)
+    try:
+        one_core = {"value": oracle_rate_one_core(w, args.config, rows1), "unit": "steps/s", "cores": 1,
+                    "sample": f"1 O-cross update on {rows1} points, scaled by m/{rows1}"}
+    except Exception as e:  # a secondary figure: never lose the line over it
+        one_core = {"value": None, "unit": "steps/s", "cores": 1, "error": str(e)[:200]}
     line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus, "steps": steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * dt_full / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -288,8 +292,7 @@ def run_reference(args, rank, world):
             "cpu_baseline": {"value": value, "unit": "steps/s", "cores": cpu_threads(), "kind": "oracle",
                              "sample": f"{steps} O-cross updates on {rows} of the m={w.m} points (n={w.n}, PSD "
                                        f"stand-in C_Q), time scaled by m/{rows}",
-                             "one_core": {"value": one_core, "unit": "steps/s", "cores": 1,
-                                          "sample": f"1 O-cross update on {rows1} points, scaled by m/{rows1}"}},
+                             "one_core": one_core},
             "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
