@@ -170,3 +170,37 @@ def test_white_initial_covariance_alpha_identity():
     for t in range(Y.shape[0]):
         assert kf.relative_error(cross["xs"][t], full["xs"][t]) < 1e-11
         assert kf.relative_error(cross["vars"][t], full["vars"][t]) < 1e-11
+
+
+def test_cross_form_equals_full_kf_on_random_problems():
+    """Property: on random small problems (sizes, kernel family and lengths, noise level,
+    prior), Alg. 2 fed the exact C_Q = Q H^T and C_0 = P_0 H^T reproduces Alg. 1, and no
+    update increases a variance."""
+    hyp = pytest.importorskip("hypothesis")
+    st = pytest.importorskip("hypothesis.strategies")
+
+    @hyp.settings(max_examples=25, deadline=None)
+    @hyp.given(seed=st.integers(0, 10_000), nx=st.integers(3, 9), ny=st.integers(3, 8), n=st.integers(1, 7),
+               T=st.integers(1, 4), pw=st.sampled_from([1, 2]), lq=st.floats(0.5, 6.0), l0=st.floats(0.5, 6.0),
+               r=st.floats(1e-4, 1e-1), white=st.booleans())
+    def check(seed, nx, ny, n, T, pw, lq, l0, r, white):
+        rng = np.random.default_rng(seed)
+        pts = W.grid_points((nx, ny))
+        m = pts.shape[0]
+        Q = kf.covariance_matrix(pts, kf.gcf(0.05, lq, pw))
+        P0 = 0.7 * np.eye(m) if white else kf.covariance_matrix(pts, kf.gcf(1.0, l0, pw))
+        H = rng.uniform(0.0, 1.0, (n, m)) * (rng.uniform(size=(n, m)) < 0.5)
+        H[:, rng.integers(m)] += 0.5                      # no empty ray
+        R = np.full(n, r)
+        x0 = rng.normal(size=m)
+        Y = rng.normal(size=(T, n))
+        full = kf.kf_full(P0, Q, H, R, x0, Y, record=True)
+        cross = kf.hikf_cross(Q @ H.T, P0 @ H.T, np.diag(P0).copy(), np.diag(Q), H, R, x0, Y, record=True)
+        prior = np.diag(P0).copy()
+        for t in range(T):
+            assert kf.relative_error(cross["xs"][t], full["xs"][t]) < 1e-9
+            assert kf.relative_error(cross["vars"][t], full["vars"][t]) < 1e-9
+            assert np.all(cross["vars"][t] <= prior + np.diag(Q) + 1e-12)
+            prior = cross["vars"][t]
+
+    check()
