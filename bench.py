@@ -47,7 +47,38 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--serve-seconds", type=float, default=20.0,
                     help="length of the served-latency run (64 streams, Poisson arrivals); 0 skips it")
+    ap.add_argument("--profile-case", nargs="+", metavar="ARG",
+                    help="PRECISION FORM [SIDE] [STEPS]: a short run of one update path for kernel "
+                         "profilers (no JSON line)")
     return ap.parse_args()
+
+
+def profile_case(argv) -> int:
+    """STEPS (default 4) updates of the crosswell workload on a SIDE x SIDE grid (default 512:
+    m = 2^18, C and C_Q 256 MB each, larger than L2) with n = 256 rays, PRECISION in
+    {fp32, mixed, fp64} and FORM in {cross, eigen, nspace}. With 4 steps the sweep kernel (for
+    nspace: the kernel that forms x and delta^2, run after every step) launches 4 times;
+    profile one of the later launches (-s 1 -c 1)."""
+    import torch
+    from paper_1404_3816_gb300 import binding, workload as W
+    prec = argv[0]
+    form = argv[1] if len(argv) > 1 else "cross"
+    side = int(argv[2]) if len(argv) > 2 else 512
+    steps = int(argv[3]) if len(argv) > 3 else 4
+    w = W.config(CONFIG_NAME, grid=(side, side))
+    Y, _ = W.measurements(w, steps=steps)
+    dY = torch.tensor(Y, dtype=torch.float64, device="cuda")
+    dx = torch.empty(w.m, dtype=torch.float64, device="cuda")
+    dv = torch.empty_like(dx)
+    with binding.Filter.from_workload(w, precision=prec, form=form) as f:
+        for i in range(steps):
+            f.assimilate_device(dY[i])
+            if form == "nspace":      # x and delta^2 formed after every step
+                f.mean_into(dx)
+                f.variance_into(dv)
+        f.sync()
+    print("ok", prec, form, side, steps)
+    return 0
 
 
 def dist_info():
@@ -304,6 +335,8 @@ def run_reference(args, rank, world):
 def main():
     args = parse()
     rank, world, local = dist_info()
+    if args.profile_case:
+        return profile_case(args.profile_case)
     if args.impl == "reference":
         return run_reference(args, rank, world)
     import torch

@@ -8,7 +8,7 @@
  * m x n cross-covariance C = P H^T instead of the m x m covariance P
  * (Alg. 2). The model-error cross-covariance C_Q = Q H^T is computed once by a
  * black-box FMM (Chebyshev-interpolated H^2 product, Sec. 3.2-3.3), and each
- * measurement update costs O(n^2 m) (Sec. 3.4).
+ * measurement update costs O(n^2 m) (Alg. 2's cost column; Sec. 3.1 and 3.3).
  *
  * Conventions shared by every call:
  *   - All pointers are plain host or device pointers as stated per argument;
@@ -168,8 +168,13 @@ hikf_status hikf_create_with_cq(hikf_t** out, int dim, int64_t m, const double* 
  *   x_{t+1|t+1} = x_{t+1|t} + K (y_{t+1} - H x_{t+1|t})
  *   delta^2_{t+1|t+1} = delta^2_{t+1|t} - sum_j K_ij (C_{t+1|t})_ij
  *   C_{t+1|t+1} = C_{t+1|t} - K H C_{t+1|t}
- * Synchronous: returns when the step is complete. Transactional: on any error
- * (HIKF_EINVAL for a non-finite y, HIKF_ENOTPD) the state is unchanged.
+ * Synchronous: returns when the step is complete. Transactional: on HIKF_EINVAL
+ * (a non-finite y) and HIKF_ENOTPD the state is unchanged.
+ * HIKF_ETIMEOUT (a bounded wait inside the tensor-core sweep ran out) is different:
+ * the sweep updates C, x and delta^2 in place tile by tile, so the state is then
+ * undefined. The timeout is reported once; from then on every call on the handle
+ * that reads or advances the state returns HIKF_ESTATE, until the handle is
+ * destroyed and created again.
  */
 hikf_status hikf_assimilate(hikf_t* h, const double* y);
 
@@ -178,7 +183,9 @@ hikf_status hikf_assimilate(hikf_t* h, const double* y);
  * enqueued on the handle's stream without waiting. A failure inside the step
  * (non-finite y, HIKF_ENOTPD) leaves the state unchanged, turns the following
  * enqueued steps into no-ops, and is reported by the next hikf_sync (or any
- * synchronous call), after which the handle works again.
+ * synchronous call), after which the handle works again. A timed-out step
+ * (HIKF_ETIMEOUT, reported the same way) leaves the state undefined, and later
+ * calls return HIKF_ESTATE as for hikf_assimilate.
  */
 hikf_status hikf_assimilate_device(hikf_t* h, const double* d_y);
 
@@ -241,6 +248,13 @@ const char* hikf_last_error(const hikf_t* h);
 
 /* Free the handle and all of its device memory. NULL is ignored. */
 void hikf_destroy(hikf_t* h);
+
+/* Test hook: the limit (ns) of the tensor-core sweep's abortable device-side waits
+ * for launches captured or enqueued from now on (process-wide); 0 restores the
+ * default of about two seconds. A tiny limit makes the next MIXED step time out
+ * (HIKF_ETIMEOUT) through the sweep's normal abort path: it drains its copies and
+ * tensor-core work in flight, frees its tensor memory and returns. */
+hikf_status hikf_test_set_wait_limit(uint64_t ns);
 
 /*
  * hikf_h2_qht — the H^2 product alone (Alg. 2 precomputation, Sec. 3.2:

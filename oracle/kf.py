@@ -56,7 +56,7 @@ def white(theta: float) -> KernelFn:
 
 
 def covariance_matrix(points: np.ndarray, kern: KernelFn) -> np.ndarray:
-    """Dense m x m covariance K(x_i, x_j) (Sec. 2.3: Q_ij = K(r_ij))."""
+    """Dense m x m covariance K(x_i, x_j) (Sec. 3.1: Q_ij = K(r_ij), K a GCF; Eq. Q in Sec. 4.2)."""
     return kern(points, points)
 
 

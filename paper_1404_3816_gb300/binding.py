@@ -34,7 +34,8 @@ EXPORTED = ["hikf_options_default", "hikf_create", "hikf_create_with_cq", "hikf_
             "hikf_assimilate_device", "hikf_sync", "hikf_get_mean", "hikf_get_variance",
             "hikf_get_mean_device", "hikf_get_variance_device", "hikf_get_cq", "hikf_get_cross",
             "hikf_get_perm", "hikf_info", "hikf_step", "hikf_stream", "hikf_last_error", "hikf_destroy", "hikf_h2_qht",
-            "hikf_profile_enable", "hikf_profile_read", "hikf_spd_inverse", "hikf_spd_inverse_noalloc"]
+            "hikf_profile_enable", "hikf_profile_read", "hikf_spd_inverse", "hikf_spd_inverse_noalloc",
+            "hikf_test_set_wait_limit"]
 
 
 class HikfError(RuntimeError):
@@ -99,6 +100,7 @@ def load(path: Optional[os.PathLike] = None) -> C.CDLL:
     lib.hikf_spd_inverse.argtypes = [vp, C.c_int, vp, vp]
     lib.hikf_spd_inverse_noalloc.argtypes = [vp, C.c_int, vp, vp]
     lib.hikf_h2_qht.argtypes = [C.c_int, C.c_int64, dp, Kernel, C.c_int, ip, ip, dp, C.POINTER(Options), dp]
+    lib.hikf_test_set_wait_limit.argtypes = [C.c_uint64]
     lib.hikf_step.argtypes = [H]
     lib.hikf_step.restype = C.c_int64
     for nm in EXPORTED:
@@ -151,6 +153,54 @@ def options(cheb_order: int = 8, leaf_size: int = 64, max_depth: int = -1, preci
     return o
 
 
+def _device_f64(t, shape, what: str, device=None) -> int:
+    """Pointer of a CUDA float64 tensor after checking it, before anything is launched.
+
+    The kernels behind a device pointer read or write exactly prod(shape) contiguous
+    float64 values on the handle's device; anything else (another dtype, a host or
+    strided tensor, a short buffer, another device) would make them read or write
+    outside it, so it is refused here with HIKF_EINVAL.
+    """
+    import torch
+    if not (hasattr(t, "data_ptr") and hasattr(t, "is_cuda") and hasattr(t, "is_contiguous")):
+        raise HikfError(HIKF_EINVAL, f"{what}: expected a torch CUDA tensor, got {type(t).__name__}")
+    if not t.is_cuda:
+        raise HikfError(HIKF_EINVAL, f"{what}: tensor is not on a CUDA device ({t.device})")
+    if t.dtype != torch.float64:
+        raise HikfError(HIKF_EINVAL, f"{what}: dtype {t.dtype}, expected torch.float64")
+    if tuple(t.shape) != tuple(shape):
+        raise HikfError(HIKF_EINVAL, f"{what}: shape {tuple(t.shape)}, expected {tuple(shape)}")
+    if not t.is_contiguous():
+        raise HikfError(HIKF_EINVAL, f"{what}: tensor is not contiguous")
+    if device is not None and t.device.index != device:
+        raise HikfError(HIKF_EINVAL, f"{what}: tensor on cuda:{t.device.index}, the handle on cuda:{device}")
+    return int(t.data_ptr())
+
+
+def _host_f64(a, count: int, what: str) -> int:
+    """Address of a host float64 buffer of exactly `count` contiguous values (numpy or a CPU tensor)."""
+    if hasattr(a, "data_ptr"):
+        import torch
+        if a.is_cuda or a.dtype != torch.float64 or not a.is_contiguous() or a.numel() != count:
+            raise HikfError(HIKF_EINVAL, f"{what}: expected a contiguous host float64 tensor of {count} values")
+        return int(a.data_ptr())
+    if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags.c_contiguous or a.size != count:
+        raise HikfError(HIKF_EINVAL, f"{what}: expected a contiguous float64 array of {count} values")
+    return int(a.ctypes.data)
+
+
+def _current_device():
+    """The CUDA device current at handle creation (None when torch has not set one up)."""
+    import sys
+    torch = sys.modules.get("torch")
+    try:
+        if torch is not None and torch.cuda.is_available() and torch.cuda.is_initialized():
+            return int(torch.cuda.current_device())
+    except Exception:
+        pass
+    return None
+
+
 def _check(code: int, h=None):
     if code != HIKF_OK:
         msg = load().hikf_last_error(h)
@@ -185,6 +235,7 @@ class Filter:
             self.h = None
             _check(code, None)
         self.m, self.n, self.dim = m, n, dim
+        self.device = _current_device()
 
     @classmethod
     def from_workload(cls, w, **opts):
@@ -213,12 +264,13 @@ class Filter:
     # --- measurement update -------------------------------------------------
     def assimilate(self, y):
         ya = _f64(y)
-        assert ya.shape == (self.n,)
+        if ya.shape != (self.n,):
+            raise HikfError(HIKF_EINVAL, f"y: shape {ya.shape}, expected ({self.n},)")
         _check(load().hikf_assimilate(self.h, _dp(ya)), self.h)
 
     def assimilate_device(self, d_y):
-        """y as a device pointer (int) or a CUDA tensor of n float64; asynchronous."""
-        ptr = d_y.data_ptr() if hasattr(d_y, "data_ptr") else int(d_y)
+        """y as a CUDA tensor of n float64 (contiguous, on the handle's device); asynchronous."""
+        ptr = _device_f64(d_y, (self.n,), "y", self.device)
         _check(load().hikf_assimilate_device(self.h, C.c_void_p(ptr)), self.h)
 
     def sync(self):
@@ -236,19 +288,19 @@ class Filter:
         return out
 
     def mean_into(self, out) -> None:
-        """Host (numpy, possibly pinned) or device (torch CUDA tensor) m-vector of float64."""
-        if hasattr(out, "is_cuda") and out.is_cuda:
-            _check(load().hikf_get_mean_device(self.h, C.c_void_p(out.data_ptr())), self.h)
-        else:
-            _check(load().hikf_get_mean(self.h, C.cast(C.c_void_p(_host_ptr(out)), C.POINTER(C.c_double))),
-                   self.h)
+        """Host (numpy or CPU tensor, possibly pinned) or device (torch CUDA tensor) m-vector of float64."""
+        self._vec_into(out, "hikf_get_mean", "hikf_get_mean_device", "mean out")
 
     def variance_into(self, out) -> None:
-        if hasattr(out, "is_cuda") and out.is_cuda:
-            _check(load().hikf_get_variance_device(self.h, C.c_void_p(out.data_ptr())), self.h)
+        self._vec_into(out, "hikf_get_variance", "hikf_get_variance_device", "variance out")
+
+    def _vec_into(self, out, host_fn: str, dev_fn: str, what: str) -> None:
+        if getattr(out, "is_cuda", False):
+            ptr = _device_f64(out, (self.m,), what, self.device)
+            _check(getattr(load(), dev_fn)(self.h, C.c_void_p(ptr)), self.h)
         else:
-            _check(load().hikf_get_variance(self.h, C.cast(C.c_void_p(_host_ptr(out)), C.POINTER(C.c_double))),
-                   self.h)
+            ptr = _host_f64(out, self.m, what)
+            _check(getattr(load(), host_fn)(self.h, C.cast(C.c_void_p(ptr), C.POINTER(C.c_double))), self.h)
 
     def cq(self) -> np.ndarray:
         out = np.empty((self.m, self.n))
@@ -289,12 +341,6 @@ class Filter:
         return int(load().hikf_stream(self.h) or 0)
 
 
-def _host_ptr(a) -> int:
-    if hasattr(a, "data_ptr"):
-        return a.data_ptr()
-    return a.ctypes.data
-
-
 def h2_qht(points, kernel, h_rowptr, h_col, h_val, **opts) -> np.ndarray:
     """The H^2 product Q H^T alone (m x n, caller order)."""
     lib = load()
@@ -309,15 +355,32 @@ def h2_qht(points, kernel, h_rowptr, h_col, h_val, **opts) -> np.ndarray:
     return out
 
 
+def _spd_args(d_S, d_M):
+    n = int(d_S.shape[0]) if hasattr(d_S, "shape") and len(d_S.shape) == 2 else -1
+    if n < 1:
+        raise HikfError(HIKF_EINVAL, "S: expected an n x n CUDA float64 tensor")
+    dev = d_S.device.index if getattr(d_S, "is_cuda", False) else None
+    ps = _device_f64(d_S, (n, n), "S")
+    pm = _device_f64(d_M, (n, n), "M", dev)
+    return n, ps, pm
+
+
+def _stream_ptr(stream):
+    return None if stream is None else C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+
+
 def spd_inverse(d_S, d_M, stream=None):
     """M = S^{-1} for device tensors (n x n float64) through hikf_spd_inverse."""
-    n = int(d_S.shape[0])
-    st = None if stream is None else C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
-    _check(load().hikf_spd_inverse(C.c_void_p(d_S.data_ptr()), n, C.c_void_p(d_M.data_ptr()), st), None)
+    n, ps, pm = _spd_args(d_S, d_M)
+    _check(load().hikf_spd_inverse(C.c_void_p(ps), n, C.c_void_p(pm), _stream_ptr(stream)), None)
 
 
 def spd_inverse_noalloc(d_S, d_M, stream=None):
     """hikf_spd_inverse_noalloc: the same inverse with the library's static device scratch."""
-    n = int(d_S.shape[0])
-    st = None if stream is None else C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
-    _check(load().hikf_spd_inverse_noalloc(C.c_void_p(d_S.data_ptr()), n, C.c_void_p(d_M.data_ptr()), st), None)
+    n, ps, pm = _spd_args(d_S, d_M)
+    _check(load().hikf_spd_inverse_noalloc(C.c_void_p(ps), n, C.c_void_p(pm), _stream_ptr(stream)), None)
+
+
+def set_wait_limit(ns: int) -> None:
+    """Test hook hikf_test_set_wait_limit: limit (ns) of the sweep's abortable waits; 0 = default."""
+    _check(load().hikf_test_set_wait_limit(int(ns)), None)

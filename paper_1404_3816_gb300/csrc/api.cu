@@ -124,6 +124,11 @@ thread_local std::string g_create_error;
 
 }  // namespace
 
+hikf_status set_global_error(const Status& s) {
+  g_create_error = s.msg;
+  return s.code;
+}
+
 }  // namespace hikf
 
 using hikf::Status;
@@ -171,6 +176,9 @@ struct hikf_handle {
   long long* dstep = nullptr;
   int* flag = nullptr;
   std::string err;
+  // a bounded device wait ran out inside a step: the step wrote part of its tiles in place,
+  // so the state is undefined from then on and every later call is refused (HIKF_ESTATE)
+  bool dead = false;
   double create_ms = 0.0;
   int launches = 0;
   // the update as a CUDA graph (HIKF options.graph)
@@ -613,12 +621,23 @@ Status read_flag(hikf_t* h, int* out) {
   HIKF_CUDA(cudaMemcpyAsync(f, h->flag, sizeof(int) * 4, cudaMemcpyDeviceToHost, h->stream));
   HIKF_CUDA(cudaStreamSynchronize(h->stream));
   *out = f[0] | (f[2] ? 8 : 0);
+  if (f[2]) h->dead = true;
   if (*out) HIKF_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int) * 4, h->stream));
   return Status::Ok();
 }
 
+// HIKF_ESTATE for every call on a handle whose state a timed-out step left undefined
+bool refuse_dead(hikf_t* h, hikf_status* code) {
+  if (!h->dead) return false;
+  h->err = "the state is undefined after a timed-out step (HIKF_ETIMEOUT); destroy the handle and create a new one";
+  *code = HIKF_ESTATE;
+  return true;
+}
+
 Status flag_status(int f) {
-  if (f & 8) return hikf::make_status(HIKF_ETIMEOUT, "a bounded wait in the tensor-core sweep timed out");
+  if (f & 8)
+    return hikf::make_status(HIKF_ETIMEOUT,
+                             "a bounded wait in the tensor-core sweep timed out; the state is now undefined");
   if (f & 1) return hikf::make_status(HIKF_EINVAL, "non-finite measurement y; step not applied");
   if (f & 2) return hikf::make_status(HIKF_ENOTPD, "H C + R is not positive definite; step not applied");
   return Status::Ok();
@@ -729,12 +748,15 @@ hikf_status hikf_create_with_cq(hikf_t** out, int dim, int64_t m, const double* 
 
 hikf_status hikf_assimilate(hikf_t* h, const double* y) {
   if (!h || !y) return h ? fail(h, hikf::make_status(HIKF_EINVAL, "y is NULL")) : HIKF_EINVAL;
+  hikf_status dead_code;
+  if (refuse_dead(h, &dead_code)) return dead_code;
   for (int r = 0; r < h->n; ++r)
     if (!std::isfinite(y[r])) return fail(h, hikf::make_status(HIKF_EINVAL, "non-finite measurement y"));
   int f = 0;
   Status st = read_flag(h, &f);
   if (!st.ok()) return fail(h, st);
-  if (f) return fail(h, hikf::make_status(HIKF_ESTATE, "an earlier asynchronous step failed: " + flag_status(f).msg));
+  if (f) return fail(h, hikf::make_status(f & 8 ? HIKF_ETIMEOUT : HIKF_ESTATE,
+                                          "an earlier asynchronous step failed: " + flag_status(f).msg));
   cudaError_t e = cudaMemcpyAsync(h->ybuf, y, sizeof(double) * h->n, cudaMemcpyHostToDevice, h->stream);
   if (e != cudaSuccess) return fail(h, hikf::cuda_status(e, "copy y", __FILE__, __LINE__));
   st = enqueue(h);
@@ -748,6 +770,8 @@ hikf_status hikf_assimilate(hikf_t* h, const double* y) {
 
 hikf_status hikf_assimilate_device(hikf_t* h, const double* d_y) {
   if (!h || !d_y) return h ? fail(h, hikf::make_status(HIKF_EINVAL, "d_y is NULL")) : HIKF_EINVAL;
+  hikf_status dead_code;
+  if (refuse_dead(h, &dead_code)) return dead_code;
   cudaError_t e = cudaMemcpyAsync(h->ybuf, d_y, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, h->stream);
   if (e != cudaSuccess) return fail(h, hikf::cuda_status(e, "copy y", __FILE__, __LINE__));
   Status st = enqueue(h);
@@ -757,6 +781,8 @@ hikf_status hikf_assimilate_device(hikf_t* h, const double* d_y) {
 
 hikf_status hikf_sync(hikf_t* h) {
   if (!h) return HIKF_EINVAL;
+  hikf_status dead_code;
+  if (refuse_dead(h, &dead_code)) return dead_code;
   int f = 0;
   Status st = read_flag(h, &f);
   if (!st.ok()) return fail(h, st);
@@ -767,6 +793,8 @@ hikf_status hikf_sync(hikf_t* h) {
 
 static hikf_status get_vec(hikf_t* h, const double* src, double* out, bool device) {
   if (!h || !out) return h ? fail(h, hikf::make_status(HIKF_EINVAL, "out is NULL")) : HIKF_EINVAL;
+  hikf_status dead_code;
+  if (refuse_dead(h, &dead_code)) return dead_code;
   Status fs = form_outputs(h);
   if (!fs.ok()) return fail(h, fs);
   hikf::vec_to_caller<<<hikf::nblk(h->m, 256), 256, 0, h->stream>>>(src, h->tree.perm, h->m,
@@ -810,6 +838,8 @@ static hikf_status get_mat(hikf_t* h, const void* src, double* out) {
 
 hikf_status hikf_get_cq(hikf_t* h, double* out) { return get_mat(h, h ? h->CQ : nullptr, out); }
 hikf_status hikf_get_cross(hikf_t* h, double* out) {
+  hikf_status dead_code;
+  if (h && refuse_dead(h, &dead_code)) return dead_code;
   if (h && h->eigen) {
     // C_{t|t} = (G - Gq) W^T R, formed on request into the C buffer (unused by this form)
     Status st = h->fp64() ? hikf::eigen_cross<double>(h->sp, h->rd, h->m, h->ld, h->n, (const double*)h->G,
@@ -935,6 +965,11 @@ hikf_status hikf_spd_inverse(const double* d_S, int n, double* d_M, void* stream
   cudaFreeAsync(flag, s);
   if (!st.ok()) return fail(nullptr, st);
   if (f[0] & 2) return fail(nullptr, hikf::make_status(HIKF_ENOTPD, "matrix is not positive definite"));
+  return HIKF_OK;
+}
+
+hikf_status hikf_test_set_wait_limit(uint64_t ns) {
+  hikf::tc_set_wait_limit((unsigned long long)ns);
   return HIKF_OK;
 }
 

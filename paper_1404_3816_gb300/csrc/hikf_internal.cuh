@@ -26,6 +26,8 @@ struct Status {
 
 Status make_status(hikf_status c, const std::string& m);
 Status cuda_status(cudaError_t e, const char* what, const char* file, int line);
+// message returned by hikf_last_error(NULL) (calls that take no handle); returns s.code
+hikf_status set_global_error(const Status& s);
 
 #define HIKF_CUDA(call)                                                           \
   do {                                                                            \

@@ -281,12 +281,9 @@ __global__ void __launch_bounds__(kThreads, 1) m2l_tc_kernel(Dims d, LevelTab lt
           }
         }
       }
-      if (!ok) {
-        *s_abort = 1;
-        const unsigned long long t0 = now_ns();
-        while (now_ns() - t0 < 5000000ull) {
-        }
-      }
+      if (!ok) *s_abort = 1;
+      // every copy issued (j of them) has landed before the CTA may exit
+      drain_ring(full(0), STAGES, j, err);
     }
   } else if (warp == 1) {
     int il_src[216], il_off[216];

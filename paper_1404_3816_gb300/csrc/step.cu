@@ -815,8 +815,11 @@ Status noalloc_scratch(double** scratch, int** flag) {
 
 extern "C" hikf_status hikf_spd_inverse_noalloc(const double* d_S, int n, double* d_M, void* stream) {
   using hikf::Status;
-  if (!d_S || !d_M) return HIKF_EINVAL;
-  if (n < 1 || n > HIKF_NOALLOC_MAX_N) return HIKF_EINVAL;
+  using hikf::make_status;
+  using hikf::set_global_error;
+  if (!d_S || !d_M) return set_global_error(make_status(HIKF_EINVAL, "null matrix pointer"));
+  if (n < 1 || n > HIKF_NOALLOC_MAX_N)
+    return set_global_error(make_status(HIKF_EINVAL, "n out of range [1, 256] (the size of the static scratch)"));
   cudaStream_t s = (cudaStream_t)stream;
   double* scratch = nullptr;
   int* flag = nullptr;
@@ -828,7 +831,7 @@ extern "C" hikf_status hikf_spd_inverse_noalloc(const double* d_S, int n, double
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) st = hikf::cuda_status(e, "spd_inverse_noalloc", __FILE__, __LINE__);
   }
-  if (!st.ok()) return st.code;
-  if (f[0] & 2) return HIKF_ENOTPD;
+  if (!st.ok()) return set_global_error(st);
+  if (f[0] & 2) return set_global_error(make_status(HIKF_ENOTPD, "matrix is not positive definite"));
   return HIKF_OK;
 }

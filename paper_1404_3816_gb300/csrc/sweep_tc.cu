@@ -23,7 +23,9 @@
 //   warp 1      TMEM allocation and the single-thread tcgen05.mma issue
 // TMEM (512 columns): accumulator K in columns [0, 256), C_p in [256, 512).
 // Every wait is bounded (about two seconds); a timeout sets an error code,
-// drains the copies and MMAs in flight, frees TMEM and returns.
+// drains the copies and MMAs in flight, frees TMEM and returns. The cross-covariance
+// is updated in place tile by tile, so after a timeout its state is undefined (the
+// host reports HIKF_ETIMEOUT once and HIKF_ESTATE for every later call).
 #include <cuda.h>
 #include <cuda_fp16.h>
 #include <math.h>
@@ -133,6 +135,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
   const uint32_t tmem = *s_tmem;
   const int64_t ntiles = (args.m + kBM - 1) / kBM;
   const int beta_exp = *args.beta_exp;
+  const unsigned long long wlim = args.wait_ns;
 
   if (warp == 0) {
     // ---------------- producer ----------------
@@ -140,37 +143,38 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
       int bs = 0;
       uint32_t bph = 0;
       int64_t j = 0;
+      int64_t raw_issued = 0, b_issued = 0;  // copies issued to the raw and B rings
       bool ok = true;
       for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         for (int kc = 0; kc < NK && ok; ++kc, ++j) {
           const int rs = (int)(j % kRawStages);
           const uint32_t rph = (uint32_t)((j / kRawStages) & 1);
-          ok = mbar_wait(raw_empty(rs), rph ^ 1u, args.err, s_abort);
+          ok = mbar_wait(raw_empty(rs), rph ^ 1u, args.err, s_abort, wlim);
           if (!ok) break;
           const uint32_t rbase = smem_u32(smem + Lay::RawOff + rs * 2 * kRawBytes);
           mbar_expect_tx(raw_full(rs), 2 * kRawBytes);
           tma_load_2d(rbase, &tmC, kc * kKC, (int)(tile * kBM), raw_full(rs));
           tma_load_2d(rbase + kRawBytes, &tmCQ, kc * kKC, (int)(tile * kBM), raw_full(rs));
-          ok = mbar_wait(b_empty(bs), bph ^ 1u, args.err, s_abort);
+          ++raw_issued;
+          ok = mbar_wait(b_empty(bs), bph ^ 1u, args.err, s_abort, wlim);
           if (!ok) break;
           const uint32_t bbase = smem_u32(smem + Lay::BOff + bs * kPieces * Lay::BPiece);
           mbar_expect_tx(b_full(bs), kPieces * Lay::BPiece);
           for (int pc = 0; pc < kPieces; ++pc)
             bulk_load(bbase + pc * Lay::BPiece, args.bimg + ((size_t)pc * NK + kc) * (Lay::BPiece / 2), Lay::BPiece,
                       b_full(bs));
+          ++b_issued;
           if (++bs == kBStages) {
             bs = 0;
             bph ^= 1u;
           }
         }
       }
-      if (!ok) {
-        *s_abort = 1;
-        // copies already issued land within microseconds; give them 5 ms before the CTA exits
-        const unsigned long long t0 = now_ns();
-        while (now_ns() - t0 < 5000000ull) {
-        }
-      }
+      if (!ok) *s_abort = 1;
+      // every copy this thread issued has landed before the CTA may exit (on the normal path
+      // the consumers have waited for all of them already)
+      drain_ring(raw_full(0), kRawStages, raw_issued, args.err);
+      drain_ring(b_full(0), kBStages, b_issued, args.err);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
@@ -180,12 +184,12 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
       uint32_t aph = 0, bph = 0, eph = 0;
       bool ok = true;
       for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        ok = mbar_wait(acc_empty, eph ^ 1u, args.err, s_abort);
+        ok = mbar_wait(acc_empty, eph ^ 1u, args.err, s_abort, wlim);
         eph ^= 1u;
         if (!ok) break;
         tc_fence_after();
         for (int kc = 0; kc < NK && ok; ++kc) {
-          ok = mbar_wait(a_full(as), aph, args.err, s_abort) && mbar_wait(b_full(bs), bph, args.err, s_abort);
+          ok = mbar_wait(a_full(as), aph, args.err, s_abort, wlim) && mbar_wait(b_full(bs), bph, args.err, s_abort, wlim);
           if (!ok) break;
           tc_fence_after();
           const uint32_t abase = smem_u32(smem + Lay::AOff + as * kPieces * kAPieceBytes);
@@ -272,7 +276,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
       for (int kc = g; kc < NK; kc += kGroups, j += kGroups) {
         const int rs = (int)(j % kRawStages);
         const uint32_t rph = (uint32_t)((j / kRawStages) & 1);
-        ok = __all_sync(0xffffffffu, mbar_wait(raw_full(rs), rph, args.err, s_abort));
+        ok = __all_sync(0xffffffffu, mbar_wait(raw_full(rs), rph, args.err, s_abort, wlim));
         if (!ok) break;
         const unsigned char* rc = smem + Lay::RawOff + rs * 2 * kRawBytes;
         float cp[kKC];
@@ -308,7 +312,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
         tmem_st32(tq + 256 + kc * kKC, reinterpret_cast<const uint32_t*>(cp));
         const int as = (int)(j % kAStages);
         const uint32_t aph = (uint32_t)((j / kAStages) & 1);
-        ok = __all_sync(0xffffffffu, mbar_wait(a_empty(as), aph ^ 1u, args.err, s_abort));
+        ok = __all_sync(0xffffffffu, mbar_wait(a_empty(as), aph ^ 1u, args.err, s_abort, wlim));
         if (!ok) break;
         unsigned char* ab = smem + Lay::AOff + as * kPieces * kAPieceBytes;
 #pragma unroll
@@ -338,7 +342,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
       if (!ok) break;
       tmem_wait_st();
       // ---- epilogue: output column chunks [g NK/2, (g+1) NK/2) ----
-      ok = __all_sync(0xffffffffu, mbar_wait(acc_full, fph, args.err, s_abort));
+      ok = __all_sync(0xffffffffu, mbar_wait(acc_full, fph, args.err, s_abort, wlim));
       fph ^= 1u;
       if (!ok) break;
       tc_fence_after();
@@ -404,7 +408,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
       // group 1 finishes the rows, so group 0 can start converting the next tile's first
       // chunk (the first the next MMAs need) at once
       if (g == 0) {
-        ok = __all_sync(0xffffffffu, mbar_wait(red_empty, redph ^ 1u, args.err, s_abort));
+        ok = __all_sync(0xffffffffu, mbar_wait(red_empty, redph ^ 1u, args.err, s_abort, wlim));
         if (!ok) break;
         red[r * 5 + 0] = rs_;
         red[r * 5 + 1] = rc_;
@@ -414,7 +418,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
         __syncwarp();
         if (lane == 0) mbar_arrive(red_full);
       } else {
-        ok = __all_sync(0xffffffffu, mbar_wait(red_full, redph, args.err, s_abort));
+        ok = __all_sync(0xffffffffu, mbar_wait(red_full, redph, args.err, s_abort, wlim));
         if (!ok) break;
         if (valid) {
           const double rd = ((double)rs_ - (double)rc_) + ((double)red[r * 5 + 0] - (double)red[r * 5 + 1]);
@@ -429,6 +433,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
       redph ^= 1u;
     }
     if (!ok) *s_abort = 1;
+    tmem_wait_st();  // an abort may leave this warp's C_p stores to TMEM unwaited
     if (lane == 0) bulk_wait0();
   }
   tc_fence_before();
@@ -565,7 +570,14 @@ Status tc_pack(const TcState& tc, const float* Msw, int nt_src, int n, const int
   return Status::Ok();
 }
 
+namespace {
+unsigned long long g_wait_ns = 0;  // 0: the default limit
+}  // namespace
+
+void tc_set_wait_limit(unsigned long long ns) { g_wait_ns = ns; }
+
 Status tc_sweep(const TcState& tc, TcArgs args, int sms, cudaStream_t s) {
+  args.wait_ns = g_wait_ns ? g_wait_ns : tc::kWaitNs;
   const int64_t ntiles = (args.m + kBM - 1) / kBM;
   const int grid = (int)std::min<int64_t>(ntiles, sms);
   args.bimg = tc.bimg;

@@ -24,6 +24,7 @@ struct TcArgs {
   const __half* bimg = nullptr;   // 3 pieces x (n_t / 32) chunks of n_t x 32 FP16 images of beta M
   float* cmax = nullptr;        // m: max_j |C_ij| of the current C (row-scale bound)
   const float* cqmax = nullptr; // m: max_j |C_Q,ij|
+  unsigned long long wait_ns = 0;  // limit of the abortable waits (set by tc_sweep)
 };
 
 struct TcState {
@@ -44,5 +45,9 @@ Status tc_setup(TcState& tc, const float* C, const float* CQ, int64_t m, int ld,
 Status tc_init_rows(const TcState& tc, const float* C, const float* CQ, int64_t m, int ld, cudaStream_t s);
 Status tc_pack(const TcState& tc, const float* Msw, int nt_src, int n, const int* flag, cudaStream_t s);
 Status tc_sweep(const TcState& tc, TcArgs args, int sms, cudaStream_t s);
+
+// Limit (ns) of the sweep's abortable waits for launches enqueued from now on; 0 restores
+// the default (about two seconds). Test hook: a tiny limit makes a step time out.
+void tc_set_wait_limit(unsigned long long ns);
 
 }  // namespace hikf

@@ -36,14 +36,16 @@ __device__ __forceinline__ unsigned long long now_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// bounded wait: false (and *err set) after ~2 s
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, const volatile int* abort_flag) {
+// bounded wait: false (and *err set) after `limit` ns (default ~2 s), or false at once when
+// another role of the CTA has given up (abort flag)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, const volatile int* abort_flag,
+                                          unsigned long long limit = kWaitNs) {
   if (mbar_try(bar, parity)) return true;
   const unsigned long long t0 = now_ns();
   while (true) {
     if (mbar_try(bar, parity)) return true;
     if (*abort_flag) return false;
-    if (now_ns() - t0 > kWaitNs) {
+    if (now_ns() - t0 > limit) {
       atomicExch(err, 1);
       return false;
     }
@@ -60,6 +62,18 @@ __device__ __forceinline__ bool mbar_wait_drain(uint32_t bar, uint32_t parity, i
     }
   }
   return true;
+}
+// Wait (bounded, ignoring the abort flag) until every copy issued to a ring of `stages`
+// full barriers (8 bytes apart from full0, used cyclically: copy j went to stage j % stages)
+// has landed. A producer that stops early calls this before its CTA may exit, so no copy
+// still writes into the shared memory of a finished CTA. Per stage at most the last copy
+// can be outstanding (the producer waited for the stage to be emptied before reusing it),
+// so the parity of the stage's last phase tells whether it has landed.
+__device__ __forceinline__ void drain_ring(uint32_t full0, int stages, int64_t issued, int* err) {
+  for (int s = 0; s < stages; ++s) {
+    const int64_t c = issued > s ? (issued - s + stages - 1) / stages : 0;
+    if (c > 0) mbar_wait_drain(full0 + 8u * (uint32_t)s, (uint32_t)((c - 1) & 1), err);
+  }
 }
 __device__ __forceinline__ void fence_barrier_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
