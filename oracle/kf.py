@@ -149,6 +149,19 @@ def hikf_cross(C_Q: np.ndarray, C0: np.ndarray, var0: np.ndarray, q_diag, H, R, 
     return out
 
 
+def closed_rows(H, rows) -> np.ndarray:
+    """Sorted union of `rows` and the support of H (the cells that some ray crosses).
+
+    Every operation of Alg. 2 is row by row (row i of C_{t+1|t}, K, x and delta^2 needs
+    only row i), except H C_{t+1|t} and H s_{t+1|t}, which read only the rows on the
+    support of H. So Alg. 2 run on the rows of such a set, with H restricted to its
+    columns, computes exactly those rows of the full run (used at full size, where
+    the m x n state of every row is out of CPU reach for many steps).
+    """
+    Hs = sp.csr_matrix(H)
+    return np.union1d(np.unique(Hs.indices), np.asarray(rows, dtype=np.int64))
+
+
 def relative_error(est: np.ndarray, ref: np.ndarray) -> float:
     """e = ||x_est - x_ref||_2 / ||x_ref||_2 (Eq. RelativeEstErr)."""
     ref = np.asarray(ref, dtype=np.float64)

@@ -204,3 +204,45 @@ def test_cross_form_equals_full_kf_on_random_problems():
             prior = cross["vars"][t]
 
     check()
+
+
+def test_rows_closed_under_h_reproduce_the_full_run():
+    """Alg. 2 on the rows of supp(H) plus any extra rows (H restricted to those columns)
+    gives exactly those rows of the full run (Alg. 1), at every step: the full-size checks
+    rely on it. Leaving out one cell that a ray crosses breaks it."""
+    w = W.small(grid=(30, 26), n=9, steps=6, seed=12)
+    Y, _ = W.measurements(w)
+    H = qht.h_csr(w.h_rowptr, w.h_col, w.h_val, w.m)
+    kq = kf.gcf(w.q.theta, w.q.length, w.q.pow)
+    Q = kf.covariance_matrix(w.points, kq)
+    P0 = 100.0 * Q
+    x0 = np.random.default_rng(1).normal(size=w.m) * 0.1
+    full = kf.kf_full(P0, Q, H, w.r_diag, x0, Y, record=True)
+    extra = np.random.default_rng(2).choice(w.m, 20, replace=False)
+    R = kf.closed_rows(H, extra)
+    assert np.all(np.isin(extra, R)) and np.all(np.isin(np.unique(H.indices), R)) and R.size < w.m
+    cq = qht.qht(w.points, kq, H)
+    part = kf.hikf_cross(cq[R], 100.0 * cq[R], np.full(R.size, w.p0.theta), w.q.theta, H[:, R], w.r_diag, x0[R],
+                         Y, record=True)
+    for t in range(Y.shape[0]):
+        assert kf.relative_error(part["xs"][t], full["xs"][t][R]) < 1e-11
+        assert kf.relative_error(part["vars"][t], full["vars"][t][R]) < 1e-11
+    # planted: a crossed cell missing from the rows changes H C and H x
+    drop = np.setdiff1d(R, [np.unique(H.indices)[3]])
+    bad = kf.hikf_cross(cq[drop], 100.0 * cq[drop], np.full(drop.size, w.p0.theta), w.q.theta, H[:, drop],
+                        w.r_diag, x0[drop], Y)
+    assert kf.relative_error(bad["x"], full["x"][drop]) > 1e-6
+
+
+def test_chained_runs_equal_one_run():
+    """Alg. 2 carries only (C, x, delta^2) from step to step: running T1 steps and then
+    the rest from the returned state equals one run of all steps (the golden-file script
+    records intermediate horizons this way)."""
+    w = W.small(grid=(20, 18), n=7, steps=6, seed=13)
+    Y, _ = W.measurements(w)
+    H = qht.h_csr(w.h_rowptr, w.h_col, w.h_val, w.m)
+    cq = qht.qht(w.points, kf.gcf(w.q.theta, w.q.length, w.q.pow), H)
+    one = kf.hikf_cross(cq, 100.0 * cq, np.full(w.m, 1.0), w.q.theta, H, w.r_diag, w.x0, Y)
+    a = kf.hikf_cross(cq, 100.0 * cq, np.full(w.m, 1.0), w.q.theta, H, w.r_diag, w.x0, Y[:2])
+    b = kf.hikf_cross(cq, a["C"], a["var"], w.q.theta, H, w.r_diag, a["x"], Y[2:])
+    assert np.array_equal(b["x"], one["x"]) and np.array_equal(b["var"], one["var"])

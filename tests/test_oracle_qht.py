@@ -48,3 +48,38 @@ def test_separable_gaussian_product_equals_direct_sum(grid):
     assert np.allclose(qht.qht_gauss_grid(grid, 0.3, 4.0, H), direct, rtol=1e-12, atol=1e-15)
     rows = np.array([0, 3, w.m // 2, w.m - 1])
     assert np.allclose(qht.qht_gauss_grid_rows(grid, 0.3, 4.0, H, rows), direct[rows], rtol=1e-12, atol=1e-15)
+
+
+@pytest.mark.parametrize("grid", [(18, 14), (33, 20), (9, 7, 6)])
+@pytest.mark.parametrize("pow_", [1, 2])
+def test_grid_convolution_equals_direct_sum(grid, pow_):
+    # the FFT (circulant-embedding) form of Q h^(k) against the direct sums, every row
+    w = W.make(grid=grid, n=6 if len(grid) == 2 else 16, q=W.KernelSpec(pow_, 0.3, 4.0),
+               p0=W.KernelSpec(pow_, 1.0, 4.0), r=1e-3, steps=1, seed=8)
+    H = qht.h_csr(w.h_rowptr, w.h_col, w.h_val, w.m)
+    k = kf.gcf(0.3, 4.0, pow_)
+    direct = qht.qht(w.points, k, H)
+    fft = qht.qht_grid_fft(grid, k, H)
+    assert np.abs(fft - direct).max() <= 1e-13 * np.abs(direct).max()
+    rows = np.array([0, 7, w.m // 2, w.m - 1])
+    assert np.array_equal(qht.qht_grid_fft(grid, k, H, rows=rows), fft[rows])
+
+
+def test_grid_convolution_equals_kronecker_gaussian():
+    # two different exact methods for the Gaussian on a 64 x 48 grid (no direct sums)
+    w = W.make(grid=(64, 48), n=16, q=W.KernelSpec(2, 0.01, 16.0), p0=W.KernelSpec(2, 1.0, 16.0), r=1e-3,
+               steps=1, seed=9)
+    H = qht.h_csr(w.h_rowptr, w.h_col, w.h_val, w.m)
+    a = qht.qht_grid_fft(w.grid, kf.gcf(0.01, 16.0, 2), H)
+    b = qht.qht_gauss_grid(w.grid, 0.01, 16.0, H)
+    assert np.linalg.norm(a - b) <= 1e-14 * np.linalg.norm(b)
+
+
+def test_grid_convolution_constant_kernel_gives_ray_lengths():
+    # K == theta: every row of Q H^T is theta times the ray lengths (no wrap-around term
+    # of the circulant embedding may leak in: a wrapped offset would double-count cells)
+    w = W.small(grid=(20, 16), n=8, seed=3)
+    H = qht.h_csr(w.h_rowptr, w.h_col, w.h_val, w.m)
+    cq = qht.qht_grid_fft(w.grid, kf.gcf(0.7, 1e30, 1), H)
+    lengths = np.linalg.norm(w.receivers - w.sources, axis=1)
+    assert np.allclose(cq, 0.7 * lengths[None, :], rtol=1e-12)
