@@ -100,7 +100,15 @@ typedef struct {
                         with no pass over the m rows. hikf_get_mean / hikf_get_variance
                         (and the _device forms) form x and delta^2 in one pass over G_Q
                         when the state has changed since the last call; hikf_get_cross
-                        forms C_{t|t}. Same conditions as HIKF_FORM_EIGEN. */
+                        forms C_{t|t}. Same conditions as HIKF_FORM_EIGEN.
+                        HIKF_FORM_AUTO (default): HIKF_FORM_CROSS, unless the spectral chain
+                        is in use, the precision is FP32 or MIXED and the bound on cond(S_t)
+                        (hikf_info's cond_s) is above what the cross form's explicit FP32
+                        inverse carries to 1e-5 (5e4 for FP32, 1e4 for MIXED; or n > 256 for
+                        MIXED): then HIKF_FORM_EIGEN, whose update is a sum of positive terms
+                        and keeps FP32 accuracy at any cond(S). hikf_info reports the form
+                        chosen. With MIXED the eigenbasis and n-space sweeps run on the CUDA
+                        cores (FP32); the H^2 product still uses the tensor cores. */
   int graph;         /* 1 (default): each update is replayed as one CUDA graph, captured on
                         the first update; 0: kernels are launched one by one. */
   int m2l;           /* where the M2L translations of the H^2 product run:
@@ -113,7 +121,7 @@ typedef struct {
 } hikf_options;
 
 enum { HIKF_CHAIN_AUTO = 0, HIKF_CHAIN_FACTOR = 1, HIKF_CHAIN_SPECTRAL = 2 };
-enum { HIKF_FORM_CROSS = 0, HIKF_FORM_EIGEN = 1, HIKF_FORM_NSPACE = 2 };
+enum { HIKF_FORM_CROSS = 0, HIKF_FORM_EIGEN = 1, HIKF_FORM_NSPACE = 2, HIKF_FORM_AUTO = 3 };
 enum { HIKF_M2L_AUTO = 0, HIKF_M2L_TENSOR = 1, HIKF_M2L_SIMT = 2 };
 
 /* Fill *opt with the defaults listed above. */
@@ -222,6 +230,12 @@ typedef struct {
   int chain;          /* HIKF_CHAIN_FACTOR or HIKF_CHAIN_SPECTRAL: the form in use */
   int form;           /* HIKF_FORM_CROSS, HIKF_FORM_EIGEN or HIKF_FORM_NSPACE */
   int eig_sweeps;     /* Jacobi sweeps of the create-time eigendecomposition (0: factor chain) */
+  double cond_s;      /* conditioning of S_t = H C_{t|t-1} + R, the matrix the gain inverts
+                         (Eq. kalmangin_new): spectral chain, a bound on the 2-norm condition
+                         number valid for every step, cond(R) max s / min s over the eigenvalue
+                         recurrences; factor chain, the 1-norm condition number of S_1. The
+                         cross form's explicit FP32 inverse loses accuracy in proportion to it
+                         (see HIKF_FORM_AUTO); INFINITY when S_1 is not positive definite. */
 } hikf_info_t;
 
 hikf_status hikf_info(const hikf_t* h, hikf_info_t* info);

@@ -24,8 +24,8 @@ PREC_FP32, PREC_MIXED, PREC_FP64 = 0, 1, 2
 PRECISIONS = {"fp32": PREC_FP32, "mixed": PREC_MIXED, "fp64": PREC_FP64}
 CHAIN_AUTO, CHAIN_FACTOR, CHAIN_SPECTRAL = 0, 1, 2
 CHAINS = {"auto": CHAIN_AUTO, "factor": CHAIN_FACTOR, "spectral": CHAIN_SPECTRAL}
-FORM_CROSS, FORM_EIGEN, FORM_NSPACE = 0, 1, 2
-FORMS = {"cross": FORM_CROSS, "eigen": FORM_EIGEN, "nspace": FORM_NSPACE}
+FORM_CROSS, FORM_EIGEN, FORM_NSPACE, FORM_AUTO = 0, 1, 2, 3
+FORMS = {"cross": FORM_CROSS, "eigen": FORM_EIGEN, "nspace": FORM_NSPACE, "auto": FORM_AUTO}
 M2L_AUTO, M2L_TENSOR, M2L_SIMT = 0, 1, 2
 M2LS = {"auto": M2L_AUTO, "tensor": M2L_TENSOR, "simt": M2L_SIMT}
 
@@ -58,7 +58,7 @@ class Info(C.Structure):
     _fields_ = [("m", C.c_int64), ("n", C.c_int), ("dim", C.c_int), ("depth", C.c_int),
                 ("cheb_order", C.c_int), ("precision", C.c_int), ("step", C.c_int64),
                 ("device_bytes", C.c_int64), ("create_ms", C.c_double), ("sweep_launches", C.c_int),
-                ("chain", C.c_int), ("form", C.c_int), ("eig_sweeps", C.c_int)]
+                ("chain", C.c_int), ("form", C.c_int), ("eig_sweeps", C.c_int), ("cond_s", C.c_double)]
 
 
 _lib = None
@@ -137,7 +137,7 @@ def kernel_struct(spec) -> Kernel:
 
 
 def options(cheb_order: int = 8, leaf_size: int = 64, max_depth: int = -1, precision="fp32",
-            stream=None, chain="auto", form="cross", graph=True, m2l="auto") -> Options:
+            stream=None, chain="auto", form="auto", graph=True, m2l="auto") -> Options:
     o = Options()
     load().hikf_options_default(C.byref(o))
     o.cheb_order = int(cheb_order)

@@ -179,6 +179,7 @@ struct hikf_handle {
   // a bounded device wait ran out inside a step: the step wrote part of its tiles in place,
   // so the state is undefined from then on and every later call is refused (HIKF_ESTATE)
   bool dead = false;
+  double cond_s = 0.0;       // estimate of cond(S_t) (hikf_info)
   double create_ms = 0.0;
   int launches = 0;
   // the update as a CUDA graph (HIKF options.graph)
@@ -238,13 +239,12 @@ Status validate_common(int dim, int64_t m, const double* points, int n, const in
   if (o.precision != HIKF_PREC_FP32 && o.precision != HIKF_PREC_FP64 && o.precision != HIKF_PREC_MIXED)
     return make_status(HIKF_EINVAL, "unknown precision");
   if (o.chain < HIKF_CHAIN_AUTO || o.chain > HIKF_CHAIN_SPECTRAL) return make_status(HIKF_EINVAL, "unknown chain");
-  if (o.form != HIKF_FORM_CROSS && o.form != HIKF_FORM_EIGEN && o.form != HIKF_FORM_NSPACE)
+  if (o.form != HIKF_FORM_CROSS && o.form != HIKF_FORM_EIGEN && o.form != HIKF_FORM_NSPACE &&
+      o.form != HIKF_FORM_AUTO)
     return make_status(HIKF_EINVAL, "unknown form");
   if (o.m2l < HIKF_M2L_AUTO || o.m2l > HIKF_M2L_SIMT) return make_status(HIKF_EINVAL, "unknown m2l");
   if (o.m2l == HIKF_M2L_TENSOR && o.precision == HIKF_PREC_FP64)
     return make_status(HIKF_EINVAL, "the tensor-core M2L takes FP32 storage (FP32 or MIXED)");
-  if (o.form != HIKF_FORM_CROSS && o.precision == HIKF_PREC_MIXED)
-    return make_status(HIKF_EINVAL, "the eigenbasis and n-space forms run on the CUDA cores (FP32 or FP64)");
   return Status::Ok();
 }
 
@@ -269,6 +269,92 @@ __global__ void white_c0_kernel(const int64_t* __restrict__ trowptr, const int32
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
   for (int64_t e = trowptr[i]; e < trowptr[i + 1]; ++e) C[i * ld + tcol[e]] += (T)(theta * tval[e]);
+}
+
+// Largest cond(S_t) the explicit-inverse sweep is claimed for (1e-5 relative on mean and
+// variance): measured on the parity cases and the full-size workloads, the FP32 sweep's
+// variance error grows about like eps_32 cond(S_t) / 30 and reaches 1e-5 near cond ~ 5e4; the
+// split-FP16 tensor-core sweep (FP32 accumulation in the tensor core) about 5x earlier.
+constexpr double kCondCrossFp32 = 5e4;
+constexpr double kCondCrossMixed = 1e4;
+
+// Spectral chain: with D = R^{-1/2}, D S_t D = V diag(s_t) V^T, s_1 = (1 + c) lambda + 1 and
+// s_{t+1} = lambda + 2 - 1/s_t per eigenvalue, so cond(S_t) <= cond(R) max_k s_t,k / min_k s_t,k
+// (equality for R = sigma^2 I). The recurrence is run here over the steps until every s_k
+// has settled; each s_k moves monotonically to its fixed point s* = (lambda + 2 +
+// sqrt(lambda^2 + 4 lambda)) / 2, so past the last step run the ratio is bounded by
+// max_k max(s_T, s*) / min_k min(s_T, s*). The result bounds cond(S_t) for every t.
+double spectral_cond_bound(const std::vector<double>& lam, const double* r_diag, int n, double c) {
+  std::vector<double> sv(n), sf(n);
+  double rmax = 0.0, rmin = INFINITY;
+  for (int k = 0; k < n; ++k) {
+    const double l = std::max(lam[k], 0.0);
+    sv[k] = (1.0 + c) * l + 1.0;
+    sf[k] = 0.5 * (l + 2.0 + std::sqrt(l * l + 4.0 * l));
+    rmax = std::max(rmax, r_diag[k]);
+    rmin = std::min(rmin, r_diag[k]);
+  }
+  double worst = 0.0;
+  for (int t = 0; t < 20000; ++t) {
+    double hi = 0.0, lo = INFINITY, move = 0.0;
+    for (int k = 0; k < n; ++k) {
+      hi = std::max(hi, sv[k]);
+      lo = std::min(lo, sv[k]);
+    }
+    worst = std::max(worst, hi / lo);
+    for (int k = 0; k < n; ++k) {
+      const double l = std::max(lam[k], 0.0);
+      const double nx = l + 2.0 - 1.0 / sv[k];
+      move = std::max(move, std::fabs(nx - sv[k]) / sv[k]);
+      sv[k] = nx;
+    }
+    if (move < 1e-13) break;
+  }
+  double hi = 0.0, lo = INFINITY;
+  for (int k = 0; k < n; ++k) {
+    hi = std::max(hi, std::max(sv[k], sf[k]));
+    lo = std::min(lo, std::min(sv[k], sf[k]));
+  }
+  worst = std::max(worst, hi / lo);
+  return (rmax / rmin) * worst;
+}
+
+// Factor chain: the 1-norm condition number ||S_1||_1 ||S_1^{-1}||_1 of the first step's S
+// (within a factor n of the 2-norm one), S_1^{-1} by the library's FP64 Cholesky inverse.
+Status factor_cond(const double* dS, int n, double* scratch, cudaStream_t s, double* cond) {
+  double* dM = nullptr;
+  int* dflag = nullptr;
+  HIKF_CUDA(cudaMallocAsync((void**)&dM, sizeof(double) * (size_t)n * n, s));
+  HIKF_CUDA(cudaMallocAsync((void**)&dflag, sizeof(int) * 2, s));
+  Status st = hikf::spd_inverse_f64(dS, n, dM, scratch, dflag, s);
+  std::vector<double> S((size_t)n * n), M((size_t)n * n);
+  int f[2] = {0, 0};
+  if (st.ok()) {
+    cudaError_t e = cudaMemcpyAsync(S.data(), dS, sizeof(double) * S.size(), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(M.data(), dM, sizeof(double) * M.size(), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(f, dflag, sizeof(int) * 2, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = hikf::cuda_status(e, "condition estimate", __FILE__, __LINE__);
+  }
+  cudaFreeAsync(dM, s);
+  cudaFreeAsync(dflag, s);
+  HIKF_TRY(st);
+  if (f[0] & 2) {
+    *cond = INFINITY;  // not positive definite: the first step reports HIKF_ENOTPD
+    return Status::Ok();
+  }
+  double ns = 0.0, nm = 0.0;
+  for (int j = 0; j < n; ++j) {
+    double cs = 0.0, cm = 0.0;
+    for (int i = 0; i < n; ++i) {
+      cs += std::fabs(S[(size_t)i * n + j]);
+      cm += std::fabs(M[(size_t)i * n + j]);
+    }
+    ns = std::max(ns, cs);
+    nm = std::max(nm, cm);
+  }
+  *cond = ns * nm;
+  return Status::Ok();
 }
 
 template <typename T>
@@ -396,10 +482,14 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
   const bool can_spec = cq == nullptr && p0_is_cq;
   if (chain_opt == HIKF_CHAIN_SPECTRAL && !can_spec)
     return hikf::make_status(HIKF_EINVAL, "spectral chain needs P0 = c Q and a computed C_Q");
-  if (form_opt != HIKF_FORM_CROSS && (!can_spec || chain_opt == HIKF_CHAIN_FACTOR))
+  if ((form_opt == HIKF_FORM_EIGEN || form_opt == HIKF_FORM_NSPACE) && (!can_spec || chain_opt == HIKF_CHAIN_FACTOR))
     return hikf::make_status(HIKF_EINVAL,
                              "the eigenbasis and n-space forms need the spectral chain (P0 = c Q, computed C_Q)");
   h->spectral = can_spec && chain_opt != HIKF_CHAIN_FACTOR;
+  if (!h->spectral) {
+    HIKF_TRY(factor_cond(h->S, n, c.L64, s, &h->cond_s));
+    if (form_opt == HIKF_FORM_AUTO) form_opt = HIKF_FORM_CROSS;  // no other form without the spectral chain
+  }
   if (h->spectral) {
     hikf::SpectralState& sp = h->sp;
     HIKF_TRY(hikf::arena_alloc(h->arena, &sp.lam, n));
@@ -415,6 +505,18 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
     HIKF_CUDA(cudaMemcpyAsync(f, h->flag, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
     HIKF_CUDA(cudaStreamSynchronize(s));
     if (f[0]) return hikf::make_status(HIKF_ENOTPD, "H C_1 + R is not positive definite");
+    {
+      std::vector<double> lam(n);
+      HIKF_CUDA(cudaMemcpy(lam.data(), sp.lam, sizeof(double) * n, cudaMemcpyDeviceToHost));
+      h->cond_s = spectral_cond_bound(lam, r_diag, n, cfac);
+    }
+    if (form_opt == HIKF_FORM_AUTO) {
+      // the paper's cross-covariance form where its explicit inverse keeps 1e-5, else the
+      // eigenbasis form (the same filter with a diagonal update, see include/hikf.h)
+      const double lim = h->mixed() ? kCondCrossMixed : kCondCrossFp32;
+      const bool tc_fits = h->ld <= 256;  // the tensor-core sweep's accumulator width
+      form_opt = (!h->fp64() && (h->cond_s > lim || (h->mixed() && !tc_fits))) ? HIKF_FORM_EIGEN : HIKF_FORM_CROSS;
+    }
     if (form_opt == HIKF_FORM_EIGEN) {
       T *G = nullptr, *Gq = nullptr;
       HIKF_TRY(hikf::arena_alloc(h->arena, &G, (size_t)m * ld));
@@ -450,7 +552,7 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
       h->nspace = true;
     }
   }
-  if (h->mixed()) {
+  if (h->mixed() && !h->eigen && !h->nspace) {
     hikf::TcState& tc = h->tc;
     HIKF_TRY(hikf::tc_setup(tc, (const float*)C, (const float*)CQ, m, ld, n));
     HIKF_TRY(hikf::arena_alloc(h->arena, &tc.bimg, (size_t)3 * tc.nt * tc.nt));
@@ -660,8 +762,8 @@ hikf_status create_impl(hikf_t** out, int dim, int64_t m, const double* points, 
   st = validate_kernel(p0, true, true);
   if (!st.ok()) return fail(nullptr, st);
   if (cq && !c0) return fail(nullptr, hikf::make_status(HIKF_EINVAL, "c0 is NULL"));
-  if (o.precision == HIKF_PREC_MIXED && hikf::padded_ld(n) > 256)
-    return fail(nullptr, hikf::make_status(HIKF_EINVAL, "MIXED precision supports n <= 256"));
+  if (o.precision == HIKF_PREC_MIXED && o.form == HIKF_FORM_CROSS && hikf::padded_ld(n) > 256)
+    return fail(nullptr, hikf::make_status(HIKF_EINVAL, "the tensor-core sweep (MIXED, cross form) supports n <= 256"));
   hikf_t* h = new (std::nothrow) hikf_handle();
   if (!h) return fail(nullptr, hikf::make_status(HIKF_ENOMEM, "host allocation failed"));
   auto bail = [&](const Status& s) {
@@ -726,7 +828,7 @@ hikf_status hikf_options_default(hikf_options* opt) {
   opt->precision = HIKF_PREC_FP32;
   opt->cuda_stream = nullptr;
   opt->chain = HIKF_CHAIN_AUTO;
-  opt->form = HIKF_FORM_CROSS;
+  opt->form = HIKF_FORM_AUTO;
   opt->graph = 1;
   opt->m2l = HIKF_M2L_AUTO;
   return HIKF_OK;
@@ -886,6 +988,7 @@ hikf_status hikf_info(const hikf_t* h, hikf_info_t* info) {
   info->chain = h->spectral ? HIKF_CHAIN_SPECTRAL : HIKF_CHAIN_FACTOR;
   info->form = h->nspace ? HIKF_FORM_NSPACE : (h->eigen ? HIKF_FORM_EIGEN : HIKF_FORM_CROSS);
   info->eig_sweeps = h->spectral ? h->sp.sweeps : 0;
+  info->cond_s = h->cond_s;
   return HIKF_OK;
 }
 

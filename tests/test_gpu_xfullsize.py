@@ -1,5 +1,6 @@
-"""Full-size parity: the m = 2^20, n = 256 workload the benchmark times, and the
-m = 65536, n = 64 workload of 200 steps, checked against the FP64 oracle.
+"""Full-size parity: the m = 2^20, n = 256 workload the benchmark times (over its
+100-step horizon), and the m = 65536, n = 64 workload of 200 steps, checked against
+the FP64 oracle.
 
 * exponential kernel, m = 2^20: the exact direct sums are out of reach for all
   rows, so sampled rows of C_Q are compared with the exact sum and with the H^2
@@ -87,6 +88,49 @@ def test_m2p20_gaussian_full_pipeline(B, gauss_case, prec, form):
         assert rel(f.variance(), ref["var"]) < TOL
 
 
+def _golden(case):
+    """Expected mean and variance on sampled rows after 10 and 100 steps: Alg. 2 in FP64
+    with the exact C_Q (written by tests/golden/make_horizon_rows.py from the oracle only)."""
+    import json
+    from pathlib import Path
+    p = Path(__file__).resolve().parent / "golden" / f"crosswell2d_m1048576_n256_{case}_rows.json"
+    d = json.loads(p.read_text())
+    return np.asarray(d["rows"]), {int(k): (np.asarray(v["x"]), np.asarray(v["var"])) for k, v in d["steps"].items()}
+
+
+def _run_horizons(f, dY, horizons):
+    """(mean, variance) after each horizon, steps enqueued from device memory."""
+    out, done = {}, 0
+    for hz in horizons:
+        for t in range(done, hz):
+            f.assimilate_device(dY[t])
+        f.sync()
+        out[hz] = (f.mean(), f.variance())
+        done = hz
+    return out
+
+
+@pytest.mark.parametrize("prec,form", [("mixed", "cross"), ("fp32", "cross"), ("fp32", "eigen"),
+                                       ("fp32", "nspace")])
+def test_m2p20_benchmarked_workload_100_steps_against_oracle(B, prec, form):
+    """The benchmarked workload end to end (H^2 product at order 8 + 100 updates, the
+    launch path bench.py times) against Alg. 2 in FP64 with the exact C_Q of the
+    exponential kernel, on 2048 sampled rows, after 10 and after 100 steps (the
+    workload's horizon). The oracle ran on supp(H) plus those rows, which is exact for
+    them (Alg. 2 reads other rows only through H)."""
+    import torch
+    rows, ref = _golden("exp")
+    w = W.config("crosswell2d_m1048576_n256")
+    Y, _ = W.measurements(w, steps=max(ref))
+    dY = torch.tensor(Y, dtype=torch.float64, device="cuda")
+    with B.Filter.from_workload(w, precision=prec, form=form) as f:
+        got = _run_horizons(f, dY, sorted(ref))
+    for hz, (x_ref, v_ref) in ref.items():
+        ex, ev = rel(got[hz][0][rows], x_ref), rel(got[hz][1][rows], v_ref)
+        print(f"\n{prec} {form} after {hz} steps: mean {ex:.3g} variance {ev:.3g}")
+        assert ex < TOL and ev < TOL
+
+
 def _mixture_cq(w, H):
     # a sum of Gaussians of lengths 16, 48, 160 (heavier tail than one Gaussian)
     out = None
@@ -100,23 +144,23 @@ def _mixture_cq(w, H):
 def test_m2p20_update_sweep_in_bench_configuration(B, prec):
     """The FP32 and tensor-core cross-covariance sweeps at m = 2^20, n = 256 (the
     timed workload's sizes and launch path), with an exact C_Q of a Gaussian
-    mixture kernel handed in through hikf_create_with_cq."""
+    mixture kernel handed in through hikf_create_with_cq, over the workload's 100
+    steps, against Alg. 2 in FP64 with the same exact C_Q on 2048 sampled rows."""
     import torch
+    rows, ref = _golden("mixture")
     w = W.config("crosswell2d_m1048576_n256")
-    T = 3
-    Y, _ = W.measurements(w, steps=T)
+    Y, _ = W.measurements(w, steps=max(ref))
     H = qht.h_csr(w.h_rowptr, w.h_col, w.h_val, w.m)
     cq = _mixture_cq(w, H)
-    ref = kf.hikf_cross(cq, 100.0 * cq, np.full(w.m, 1.0), 0.01, H, w.r_diag, w.x0, Y)
     with B.Filter(w.points, (1, 0.01, 1.0), w.h_rowptr, w.h_col, w.h_val, w.r_diag, w.x0, (1, 1.0, 1.0),
                   cq=cq, c0=100.0 * cq, precision=prec) as f:
         del cq
         dY = torch.tensor(Y, dtype=torch.float64, device="cuda")
-        for t in range(T):
-            f.assimilate_device(dY[t])
-        f.sync()
-        assert rel(f.mean(), ref["x"]) < TOL
-        assert rel(f.variance(), ref["var"]) < TOL
+        got = _run_horizons(f, dY, sorted(ref))
+    for hz, (x_ref, v_ref) in ref.items():
+        ex, ev = rel(got[hz][0][rows], x_ref), rel(got[hz][1][rows], v_ref)
+        print(f"\n{prec} mixture sweep after {hz} steps: mean {ex:.3g} variance {ev:.3g}")
+        assert ex < TOL and ev < TOL
 
 
 def test_m65536_200_steps_end_to_end(B):
