@@ -5,18 +5,23 @@
 //   x += C_p a,  C <- K R  (= C_p - K H C_p, Eq. KF_pred_new, since H C_p = S - R).
 //
 // K = C_p M is a dense (m x n) x (n x n) contraction. To keep FP32-level accuracy
-// on FP16 tensor cores each operand is split into three FP16 pieces after a
-// power-of-two scaling (row scale alpha_i for C_p, one scale beta for M):
-//   alpha C_p = A1 + A2 + A3,  beta M = B1 + B2 + B3  (about 33 significant bits),
-//   K = (A1 B1 + A1 B2 + A2 B1 + A1 B3 + A2 B2 + A3 B1) / (alpha beta),
+// on FP16 tensor cores each operand is split into FP16 pieces after a power-of-two
+// scaling (row scale alpha_i for C_p, one scale beta for M):
+//   alpha C_p = A1 + A2 (22 significant bits),  beta M = B1 + B2 + B3 (33 bits),
+//   K = (A1 B1 + A1 B2 + A2 B1 + A1 B3 + A2 B2) / (alpha beta),
 // i.e. every product down to 2^-22 of the leading one; products are exact in the
-// FP32 accumulator. (Two pieces, 22 bits, lose ~3 bits against FP32 over long runs.)
+// FP32 accumulator. Measured against the FP64 oracle, a third piece of C_p (a sixth
+// product) changes neither the mean nor the variance error (the FP32 accumulation of
+// the tensor core sets them); it would cost a sixth more tensor-core time, which sets
+// the pace of a tile (each M=128, N=256, K=16 instruction takes ~72 ns).
 // The row scale comes from a bound carried from the previous step:
 // |C_p,ij| <= max_j |C_{t|t}| + max_j |C_Q|.
 //
 // Data path (one persistent CTA per SM, warp-specialised):
 //   warp 0      TMA: raw FP32 tiles of C and C_Q (128 rows x 32 columns, 128B
-//               swizzle) and the pre-laid-out FP16 images of M (bulk copies)
+//               swizzle)
+//   warp 2      bulk copies of the pre-laid-out FP16 images of M (a producer of its
+//               own, so the raw ring runs ahead of the MMAs)
 //   warps 4-7   one thread per row: C_p = C + C_Q, x increment, split into FP16
 //               pieces in the canonical no-swizzle K-major layout, C_p into TMEM;
 //               after the MMAs: epilogue from TMEM (rowdot, C <- K R, row max)
@@ -44,7 +49,8 @@ constexpr int kBM = 128;                 // rows per tile (MMA M)
 constexpr int kKC = 32;                  // K per stage
 constexpr int kGroups = 2;               // converter/epilogue warp groups (4 warps each, one per TMEM lane quarter)
 constexpr int kRawStages = 2;            // chunk j -> raw stage j % 2 (= its group)
-constexpr int kPieces = 3;               // FP16 pieces per operand (3 x 11 bits)
+constexpr int kPiecesA = 2;              // FP16 pieces of alpha C_p (2 x 11 bits)
+constexpr int kPieces = 3;               // FP16 pieces of beta M (3 x 11 bits)
 constexpr int kAStages = 2;              // chunk j -> A stage j % 2 (= its group)
 constexpr int kBStages = 2;
 constexpr int kThreadsTc = 128 + 128 * kGroups;
@@ -56,7 +62,7 @@ struct TcLayout {
   static constexpr int BPiece = NT * kKC * 2;                        // one FP16 B piece per stage
   static constexpr int RawOff = 0;
   static constexpr int AOff = RawOff + kRawStages * 2 * kRawBytes;
-  static constexpr int BOff = AOff + kAStages * kPieces * kAPieceBytes;
+  static constexpr int BOff = AOff + kAStages * kPiecesA * kAPieceBytes;
   static constexpr int VecOff = BOff + kBStages * kPieces * BPiece;  // a (NT floats), r (NT floats)
   static constexpr int RedOff = VecOff + 2 * NT * 4;                 // group-0 partials: 128 x {rd hi, rd lo, x hi, x lo, max}
   static constexpr int BarOff = RedOff + 128 * 5 * 4;
@@ -138,12 +144,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
   const unsigned long long wlim = args.wait_ns;
 
   if (warp == 0) {
-    // ---------------- producer ----------------
+    // ---------------- producer: raw tiles ----------------
     if (lane == 0) {
-      int bs = 0;
-      uint32_t bph = 0;
       int64_t j = 0;
-      int64_t raw_issued = 0, b_issued = 0;  // copies issued to the raw and B rings
       bool ok = true;
       for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         for (int kc = 0; kc < NK && ok; ++kc, ++j) {
@@ -155,26 +158,32 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
           mbar_expect_tx(raw_full(rs), 2 * kRawBytes);
           tma_load_2d(rbase, &tmC, kc * kKC, (int)(tile * kBM), raw_full(rs));
           tma_load_2d(rbase + kRawBytes, &tmCQ, kc * kKC, (int)(tile * kBM), raw_full(rs));
-          ++raw_issued;
-          ok = mbar_wait(b_empty(bs), bph ^ 1u, args.err, s_abort, wlim);
+        }
+      }
+      if (!ok) *s_abort = 1;
+      // every copy this thread issued (j of them) has landed before the CTA may exit
+      drain_ring(raw_full(0), kRawStages, j, args.err);
+    }
+  } else if (warp == 2) {
+    // ---------------- producer: B images (its own warp, so the raw ring runs ahead of
+    // the MMAs instead of in step with the B ring) ----------------
+    if (lane == 0) {
+      int64_t j = 0;
+      bool ok = true;
+      for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        for (int kc = 0; kc < NK && ok; ++kc, ++j) {
+          const int bs = (int)(j % kBStages);
+          ok = mbar_wait(b_empty(bs), (uint32_t)(((j / kBStages) & 1) ^ 1), args.err, s_abort, wlim);
           if (!ok) break;
           const uint32_t bbase = smem_u32(smem + Lay::BOff + bs * kPieces * Lay::BPiece);
           mbar_expect_tx(b_full(bs), kPieces * Lay::BPiece);
           for (int pc = 0; pc < kPieces; ++pc)
             bulk_load(bbase + pc * Lay::BPiece, args.bimg + ((size_t)pc * NK + kc) * (Lay::BPiece / 2), Lay::BPiece,
                       b_full(bs));
-          ++b_issued;
-          if (++bs == kBStages) {
-            bs = 0;
-            bph ^= 1u;
-          }
         }
       }
       if (!ok) *s_abort = 1;
-      // every copy this thread issued has landed before the CTA may exit (on the normal path
-      // the consumers have waited for all of them already)
-      drain_ring(raw_full(0), kRawStages, raw_issued, args.err);
-      drain_ring(b_full(0), kBStages, b_issued, args.err);
+      drain_ring(b_full(0), kBStages, j, args.err);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
@@ -192,18 +201,16 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
           ok = mbar_wait(a_full(as), aph, args.err, s_abort, wlim) && mbar_wait(b_full(bs), bph, args.err, s_abort, wlim);
           if (!ok) break;
           tc_fence_after();
-          const uint32_t abase = smem_u32(smem + Lay::AOff + as * kPieces * kAPieceBytes);
+          const uint32_t abase = smem_u32(smem + Lay::AOff + as * kPiecesA * kAPieceBytes);
           const uint32_t bbase = smem_u32(smem + Lay::BOff + bs * kPieces * Lay::BPiece);
           for (int ks = 0; ks < kKC / 16; ++ks) {
             const uint64_t a1 = smem_desc(abase + ks * 256, 128, 512);
             const uint64_t a2 = smem_desc(abase + kAPieceBytes + ks * 256, 128, 512);
-            const uint64_t a3 = smem_desc(abase + 2 * kAPieceBytes + ks * 256, 128, 512);
             const uint64_t b1 = smem_desc(bbase + ks * 256, 128, 512);
             const uint64_t b2 = smem_desc(bbase + Lay::BPiece + ks * 256, 128, 512);
             const uint64_t b3 = smem_desc(bbase + 2 * Lay::BPiece + ks * 256, 128, 512);
             // smallest terms first
-            tc_mma_f16(tmem, a3, b1, idesc, (kc > 0 || ks > 0) ? 1u : 0u);
-            tc_mma_f16(tmem, a2, b2, idesc, 1u);
+            tc_mma_f16(tmem, a2, b2, idesc, (kc > 0 || ks > 0) ? 1u : 0u);
             tc_mma_f16(tmem, a1, b3, idesc, 1u);
             tc_mma_f16(tmem, a2, b1, idesc, 1u);
             tc_mma_f16(tmem, a1, b2, idesc, 1u);
@@ -314,26 +321,21 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
         const uint32_t aph = (uint32_t)((j / kAStages) & 1);
         ok = __all_sync(0xffffffffu, mbar_wait(a_empty(as), aph ^ 1u, args.err, s_abort, wlim));
         if (!ok) break;
-        unsigned char* ab = smem + Lay::AOff + as * kPieces * kAPieceBytes;
+        unsigned char* ab = smem + Lay::AOff + as * kPiecesA * kAPieceBytes;
 #pragma unroll
         for (int gg = 0; gg < kKC / 8; ++gg) {
-          __align__(16) __half2 p1[4], p2[4], p3[4];
+          __align__(16) __half2 p1[4], p2[4];
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const float2 sv = make_float2(cp[8 * gg + 2 * u] * alpha, cp[8 * gg + 2 * u + 1] * alpha);
             const __half2 h1 = __float22half2_rn(sv);
             const float2 f1 = __half22float2(h1);
-            const float2 r1 = make_float2(sv.x - f1.x, sv.y - f1.y);  // exact in FP32
-            const __half2 h2 = __float22half2_rn(r1);
-            const float2 f2 = __half22float2(h2);
             p1[u] = h1;
-            p2[u] = h2;
-            p3[u] = __float22half2_rn(make_float2(r1.x - f2.x, r1.y - f2.y));
+            p2[u] = __float22half2_rn(make_float2(sv.x - f1.x, sv.y - f1.y));  // residual exact in FP32
           }
           const uint32_t off = core_off(r, 8 * gg);
           *reinterpret_cast<uint4*>(ab + off) = *reinterpret_cast<const uint4*>(p1);
           *reinterpret_cast<uint4*>(ab + kAPieceBytes + off) = *reinterpret_cast<const uint4*>(p2);
-          *reinterpret_cast<uint4*>(ab + 2 * kAPieceBytes + off) = *reinterpret_cast<const uint4*>(p3);
         }
         fence_proxy_async();
         __syncwarp();
@@ -352,7 +354,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
       // 128B-swizzled like the C tensor map) in the bytes its own rows occupy in A pieces
       // 0 and 1 of the group's A stage; no MMA reads that stage during the epilogue, and
       // only this warp writes those bytes (its converter rows), so no other warp waits
-      unsigned char* stg = smem + Lay::AOff + g * kPieces * kAPieceBytes + (lane >> 4) * kAPieceBytes + q * 2048;
+      unsigned char* stg = smem + Lay::AOff + g * kPiecesA * kAPieceBytes + (lane >> 4) * kAPieceBytes + q * 2048;
       for (int jc = g * (NK / kGroups); jc < (g + 1) * (NK / kGroups); ++jc) {
         uint32_t kv[32], cv[32];
         tmem_ld32(tq + jc * kKC, kv);
@@ -391,7 +393,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
           __syncwarp();
           // rows past m are clipped by the tensor map
           if (lane == 0) {
-            unsigned char* s0 = smem + Lay::AOff + g * kPieces * kAPieceBytes + q * 2048;
+            unsigned char* s0 = smem + Lay::AOff + g * kPiecesA * kAPieceBytes + q * 2048;
             tma_store_2d(&tmCst, smem_u32(s0), col0, (int)(tile * kBM + q * 32));
             tma_store_2d(&tmCst, smem_u32(s0 + kAPieceBytes), col0, (int)(tile * kBM + q * 32 + 16));
             bulk_commit();
