@@ -169,7 +169,7 @@ def peaks():
 # the source of each timed kernel (its definition and the device helpers it calls, plus
 # whole headers): a committed traffic figure counts only while this text is unchanged
 KERNEL_SOURCES = {
-    "mixed": ("sweep_tc.cu", ("sweep_tc_kernel", "pow2_exp"), ("tc_ptx.cuh",)),
+    "mixed": ("sweep_tc.cu", ("sweep_tc_kernel", "pow2_exp", "two_sum"), ("tc_ptx.cuh",)),
     "fp32": ("step.cu", ("sweep_kernel", "df_add", "cp_async16", "cp_async_commit", "cp_async_wait"), ()),
     "eigen": ("spectral.cu", ("eigen_sweep_f32_kernel", "df_add"), ()),
     "nspace": ("nspace.cu", ("nspace_outputs_f32_kernel", "dd_add", "two_sum"), ()),

@@ -80,6 +80,14 @@ __device__ __forceinline__ int pow2_exp(float bound) {
   return e;
 }
 
+// a + b = s + err exactly (Knuth's two-sum), in FP32
+__device__ __forceinline__ float two_sum(float a, float b, float& err) {
+  const float s = a + b;
+  const float bb = s - a;
+  err = (a - (s - bb)) + (b - bb);
+  return s;
+}
+
 template <int NT>
 __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_constant__ CUtensorMap tmC,
                                                           const __grid_constant__ CUtensorMap tmCQ,
@@ -245,6 +253,33 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
     const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16);
     float* red = reinterpret_cast<float*>(smem + Lay::RedOff);
     uint32_t fph = 0, redph = 0;
+    // group 1: the row results of the previous tile, finished during the next tile
+    bool pend = false, p_valid = false;
+    int64_t p_row = 0;
+    float p_rs = 0.f, p_rc = 0.f, p_xs = 0.f, p_xc = 0.f, p_rmax = 0.f;
+    double p_v = 0.0, p_x = 0.0;
+    uint32_t p_ph = 0;
+    // combine both groups' partials of the pending rows (group 0's come through shared memory)
+    auto finish_rows = [&]() -> bool {
+      if (!__all_sync(0xffffffffu, mbar_wait(red_full, p_ph, args.err, s_abort, wlim))) return false;
+      if (p_valid) {
+        // the two groups' compensated sums are combined in FP32 (an exact two-sum of the
+        // leading parts, the compensations added to the error term) and only the result
+        // goes through FP64: an FP64 instruction holds its SM sub-partition for ~64 cycles
+        float rd_lo, xi_lo;
+        const float rd_hi = two_sum(p_rs, red[r * 5 + 0], rd_lo);
+        const float xi_hi = two_sum(p_xs, red[r * 5 + 2], xi_lo);
+        rd_lo -= p_rc + red[r * 5 + 1];
+        xi_lo -= p_xc + red[r * 5 + 3];
+        args.var[p_row] = (p_v + args.theta) - ((double)rd_hi + (double)rd_lo);
+        args.x[p_row] = p_x + ((double)xi_hi + (double)xi_lo);
+        args.cmax[p_row] = fmaxf(p_rmax, red[r * 5 + 4]);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(red_empty);
+      pend = false;
+      return true;
+    };
     int64_t j = g;  // global chunk counter of this group (stride kGroups)
     bool ok = true;
     // row scalars of the next tile are loaded one tile ahead (hides their latency)
@@ -321,6 +356,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
         const uint32_t aph = (uint32_t)((j / kAStages) & 1);
         ok = __all_sync(0xffffffffu, mbar_wait(a_empty(as), aph ^ 1u, args.err, s_abort, wlim));
         if (!ok) break;
+        if (kc == g) {
+          // the A stage held this warp's output staging: its last tile stores have read it
+          if (lane == 0) bulk_wait_read0();
+          __syncwarp();
+        }
         unsigned char* ab = smem + Lay::AOff + as * kPiecesA * kAPieceBytes;
 #pragma unroll
         for (int gg = 0; gg < kKC / 8; ++gg) {
@@ -340,10 +380,15 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
         fence_proxy_async();
         __syncwarp();
         if (lane == 0) mbar_arrive(a_full(as));
+        if (pend) {
+          ok = finish_rows();
+          if (!ok) break;
+        }
       }
       if (!ok) break;
       tmem_wait_st();
-      // ---- epilogue: output column chunks [g NK/2, (g+1) NK/2) ----
+      // ---- epilogue: output column chunks [0, e0) for group 0, [e0, NK) for group 1 ----
+      // (group 0 takes fewer: it converts the chunk the next tile's MMAs start with)
       ok = __all_sync(0xffffffffu, mbar_wait(acc_full, fph, args.err, s_abort, wlim));
       fph ^= 1u;
       if (!ok) break;
@@ -355,7 +400,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
       // 0 and 1 of the group's A stage; no MMA reads that stage during the epilogue, and
       // only this warp writes those bytes (its converter rows), so no other warp waits
       unsigned char* stg = smem + Lay::AOff + g * kPiecesA * kAPieceBytes + (lane >> 4) * kAPieceBytes + q * 2048;
-      for (int jc = g * (NK / kGroups); jc < (g + 1) * (NK / kGroups); ++jc) {
+      constexpr int e0 = NK / 4;
+      for (int jc = g == 0 ? 0 : e0; jc < (g == 0 ? e0 : NK); ++jc) {
         uint32_t kv[32], cv[32];
         tmem_ld32(tq + jc * kKC, kv);
         tmem_ld32(tq + 256 + jc * kKC, cv);
@@ -403,9 +449,6 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(acc_empty);
-      // this warp's converter rows overwrite the staging bytes next
-      if (lane == 0) bulk_wait_read0();
-      __syncwarp();
       // combine the two groups' row partials through shared memory (bounded mbarrier handoff);
       // group 1 finishes the rows, so group 0 can start converting the next tile's first
       // chunk (the first the next MMAs need) at once
@@ -420,20 +463,24 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
         __syncwarp();
         if (lane == 0) mbar_arrive(red_full);
       } else {
-        ok = __all_sync(0xffffffffu, mbar_wait(red_full, redph, args.err, s_abort, wlim));
-        if (!ok) break;
-        if (valid) {
-          const double rd = ((double)rs_ - (double)rc_) + ((double)red[r * 5 + 0] - (double)red[r * 5 + 1]);
-          const double xi = ((double)xs - (double)xc) + ((double)red[r * 5 + 2] - (double)red[r * 5 + 3]);
-          args.var[row] = cur_v + args.theta - rd;
-          args.x[row] = cur_x + xi;
-          args.cmax[row] = fmaxf(rmax, red[r * 5 + 4]);
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(red_empty);
+        // group 1 finishes these rows later, after converting its first chunk of the next
+        // tile: its FP64 work would otherwise hold the SM sub-partitions while group 0
+        // converts the chunk the next tile's MMAs wait for
+        pend = true;
+        p_valid = valid;
+        p_row = row;
+        p_rs = rs_;
+        p_rc = rc_;
+        p_xs = xs;
+        p_xc = xc;
+        p_rmax = rmax;
+        p_v = cur_v;
+        p_x = cur_x;
+        p_ph = redph;
       }
       redph ^= 1u;
     }
+    if (ok && pend) ok = finish_rows();  // the last tile's rows
     if (!ok) *s_abort = 1;
     tmem_wait_st();  // an abort may leave this warp's C_p stores to TMEM unwaited
     if (lane == 0) bulk_wait0();
