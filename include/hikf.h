@@ -47,17 +47,34 @@ typedef enum {
   HIKF_ESTATE = 6    /* the handle holds an unreported error or the call is out of order */
 } hikf_status;
 
-/* Exponent of the generalised covariance function (Eq. Q):
- * K(r) = theta * exp(-(r / length)^pow); pow = 1 exponential, pow = 2 Gaussian
- * (Sec. 3.3, kernels 1-2). theta = 0 gives the zero kernel.
- * HIKF_KERNEL_WHITE (pow = 0, initial covariance only): P_0 = theta I, the
- * initialisation of Sec. 3.1 (cells uncorrelated; length is ignored). */
-enum { HIKF_KERNEL_WHITE = 0, HIKF_KERNEL_EXP = 1, HIKF_KERNEL_GAUSS = 2 };
+/* Kernel families (the field `pow` of hikf_kernel):
+ *   HIKF_KERNEL_EXP    K(r) = theta exp(-r / l)        (Sec. 3.3, kernel 2)
+ *   HIKF_KERNEL_GAUSS  K(r) = theta exp(-r^2 / l^2)    (Sec. 3.3, kernel 1)
+ *   HIKF_KERNEL_GCF    K(r) = theta exp(-(r / l)^p), the generalised covariance
+ *                      function of Eq. Q with any exponent 0 < p <= 2 (shape = p;
+ *                      p = 1 and p = 2 are the two kernels above)
+ *   HIKF_KERNEL_LOG    K(r) = theta log(l / r) for r > 0, i.e. A log r with A = -theta < 0
+ *                      (Sec. 3.3, kernel 3) plus the constant theta log l; the kernel is
+ *                      singular at r = 0, so its diagonal is stated: K(0) = theta log(l / r0)
+ *                      with r0 = shape > 0 (e.g. r0 = half a cell). A generalised covariance,
+ *                      not a covariance: accepted by hikf_h2_qht only, not as Q or P_0.
+ *   HIKF_KERNEL_WHITE  (P_0 only) P_0 = theta I, the initialisation of Sec. 3.1 (cells
+ *                      uncorrelated; length and shape ignored).
+ * theta = 0 gives the zero kernel. */
+enum {
+  HIKF_KERNEL_WHITE = 0,
+  HIKF_KERNEL_EXP = 1,
+  HIKF_KERNEL_GAUSS = 2,
+  HIKF_KERNEL_GCF = 3,
+  HIKF_KERNEL_LOG = 4
+};
 
 typedef struct {
-  int pow;       /* HIKF_KERNEL_EXP or HIKF_KERNEL_GAUSS (HIKF_KERNEL_WHITE: p0 only) */
-  double theta;  /* variance scale, >= 0 (theta = K(0) = diag of the covariance) */
+  int pow;       /* kernel family HIKF_KERNEL_* (HIKF_KERNEL_WHITE: p0 only; LOG: hikf_h2_qht only) */
+  double theta;  /* scale, >= 0 (for the covariances theta = K(0) = diag of the covariance) */
   double length; /* correlation length l > 0, in the units of `points` */
+  double shape;  /* HIKF_KERNEL_GCF: the exponent p, 0 < p <= 2; HIKF_KERNEL_LOG: r0 > 0;
+                    ignored by the other families */
 } hikf_kernel;
 
 /* Arithmetic of the device path.
@@ -156,6 +173,24 @@ hikf_status hikf_options_default(hikf_options* opt);
 hikf_status hikf_create(hikf_t** out, int dim, int64_t m, const double* points, hikf_kernel q, int n,
                         const int64_t* h_rowptr, const int64_t* h_col, const double* h_val,
                         const double* r_diag, const double* x0, hikf_kernel p0, const hikf_options* opt);
+
+/*
+ * hikf_create_dense_r — as hikf_create, with a full measurement-error covariance R
+ * (Eq. R generalised from sigma^2 I to correlated errors) instead of its diagonal:
+ *   r_full  host, n x n FP64, row-major, symmetric positive definite.
+ * The filter is run in the whitened measurement space: with R = L L^T (FP64 Cholesky on
+ * the device), the measurements L^{-1} y, the operator L^{-1} H and the error covariance
+ * I give the same posterior mean and variance (Alg. 1 and 2 are invariant under this
+ * change of measurement coordinates). C_Q and C_{0|0} are transformed once at create
+ * (C L^{-T}) and each innovation by L^{-1}; the O(n^2 m) update itself is the diagonal-R
+ * one. hikf_get_cq and hikf_get_cross return the untransformed C_Q and C_{t|t}; hikf_info's
+ * cond_s refers to the whitened S_t = L^{-1} (H C_{t|t-1} + R) L^{-T}.
+ * Errors: as hikf_create; HIKF_EINVAL also when r_full is not finite, not symmetric
+ * (|R_ij - R_ji| > 1e-12 max |R|) or not positive definite.
+ */
+hikf_status hikf_create_dense_r(hikf_t** out, int dim, int64_t m, const double* points, hikf_kernel q, int n,
+                                const int64_t* h_rowptr, const int64_t* h_col, const double* h_val,
+                                const double* r_full, const double* x0, hikf_kernel p0, const hikf_options* opt);
 
 /*
  * hikf_create_with_cq — as hikf_create, but C_Q and C_{0|0} are given instead
@@ -273,7 +308,8 @@ hikf_status hikf_test_set_wait_limit(uint64_t ns);
 /*
  * hikf_h2_qht — the H^2 product alone (Alg. 2 precomputation, Sec. 3.2:
  * Q H^T = [Q h^(1) ... Q h^(n)]), without a filter. Arguments as in
- * hikf_create; `out` is host m x n FP64, row-major, caller's point order.
+ * hikf_create (any kernel family, HIKF_KERNEL_LOG included); `out` is host m x n FP64,
+ * row-major, caller's point order.
  * Allocates its device memory for the call and frees it before returning.
  */
 hikf_status hikf_h2_qht(int dim, int64_t m, const double* points, hikf_kernel k, int n,

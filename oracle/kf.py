@@ -41,6 +41,23 @@ def gcf(theta: float, length: float, pow: int) -> KernelFn:
     return k
 
 
+def log_kernel(theta: float, length: float, r0: float) -> KernelFn:
+    """The logarithmic kernel of Sec. 3.3 (kernel 3, A log r with A = -theta < 0) shifted by the
+    constant theta log(length): theta log(length / r) for r > 0, and the stated diagonal value
+    theta log(length / r0) where two points coincide (the kernel is singular at r = 0). A
+    generalised covariance, used for the H^2 product only."""
+    theta, length, r0 = float(theta), float(length), float(r0)
+
+    def k(X: np.ndarray, Y: np.ndarray) -> np.ndarray:
+        diff = X[:, None, :] - Y[None, :, :]
+        r = np.sqrt(np.einsum("abd,abd->ab", diff, diff))
+        with np.errstate(divide="ignore"):
+            return np.where(r > 0.0, theta * np.log(length / np.where(r > 0.0, r, 1.0)), theta * np.log(length / r0))
+
+    k.theta = theta * np.log(length / r0)
+    return k
+
+
 def white(theta: float) -> KernelFn:
     """The uncorrelated initial covariance P_0 = theta I of Sec. 3.1 (P_0 = alpha I), as a
     kernel: theta where the two points coincide, 0 elsewhere."""

@@ -19,7 +19,7 @@ LIB_PATH = Path(__file__).resolve().parent / "_lib" / "libhikf.so"
 HIKF_OK, HIKF_EINVAL, HIKF_ENOMEM, HIKF_ECUDA, HIKF_ENOTPD, HIKF_ETIMEOUT, HIKF_ESTATE = range(7)
 STATUS_NAMES = {0: "HIKF_OK", 1: "HIKF_EINVAL", 2: "HIKF_ENOMEM", 3: "HIKF_ECUDA", 4: "HIKF_ENOTPD",
                 5: "HIKF_ETIMEOUT", 6: "HIKF_ESTATE"}
-KERNEL_EXP, KERNEL_GAUSS = 1, 2
+KERNEL_WHITE, KERNEL_EXP, KERNEL_GAUSS, KERNEL_GCF, KERNEL_LOG = 0, 1, 2, 3, 4
 PREC_FP32, PREC_MIXED, PREC_FP64 = 0, 1, 2
 PRECISIONS = {"fp32": PREC_FP32, "mixed": PREC_MIXED, "fp64": PREC_FP64}
 CHAIN_AUTO, CHAIN_FACTOR, CHAIN_SPECTRAL = 0, 1, 2
@@ -30,7 +30,7 @@ M2L_AUTO, M2L_TENSOR, M2L_SIMT = 0, 1, 2
 M2LS = {"auto": M2L_AUTO, "tensor": M2L_TENSOR, "simt": M2L_SIMT}
 
 # every symbol include/hikf.h declares
-EXPORTED = ["hikf_options_default", "hikf_create", "hikf_create_with_cq", "hikf_assimilate",
+EXPORTED = ["hikf_options_default", "hikf_create", "hikf_create_dense_r", "hikf_create_with_cq", "hikf_assimilate",
             "hikf_assimilate_device", "hikf_sync", "hikf_get_mean", "hikf_get_variance",
             "hikf_get_mean_device", "hikf_get_variance_device", "hikf_get_cq", "hikf_get_cross",
             "hikf_get_perm", "hikf_info", "hikf_step", "hikf_stream", "hikf_last_error", "hikf_destroy", "hikf_h2_qht",
@@ -45,7 +45,7 @@ class HikfError(RuntimeError):
 
 
 class Kernel(C.Structure):
-    _fields_ = [("pow", C.c_int), ("theta", C.c_double), ("length", C.c_double)]
+    _fields_ = [("pow", C.c_int), ("theta", C.c_double), ("length", C.c_double), ("shape", C.c_double)]
 
 
 class Options(C.Structure):
@@ -78,6 +78,8 @@ def load(path: Optional[os.PathLike] = None) -> C.CDLL:
     lib.hikf_options_default.argtypes = [C.POINTER(Options)]
     lib.hikf_create.argtypes = [C.POINTER(H), C.c_int, C.c_int64, dp, Kernel, C.c_int, ip, ip, dp, dp, dp,
                                 Kernel, C.POINTER(Options)]
+    lib.hikf_create_dense_r.argtypes = [C.POINTER(H), C.c_int, C.c_int64, dp, Kernel, C.c_int, ip, ip, dp, dp, dp,
+                                        Kernel, C.POINTER(Options)]
     lib.hikf_create_with_cq.argtypes = [C.POINTER(H), C.c_int, C.c_int64, dp, Kernel, C.c_int, ip, ip, dp, dp,
                                         dp, Kernel, dp, dp, C.POINTER(Options)]
     lib.hikf_assimilate.argtypes = [H, dp]
@@ -130,10 +132,10 @@ def _i64(a) -> np.ndarray:
 
 
 def kernel_struct(spec) -> Kernel:
-    """From an object with .pow/.theta/.length or a (pow, theta, length) tuple."""
+    """From an object with .pow/.theta/.length[/.shape] or a (pow, theta, length[, shape]) tuple."""
     if isinstance(spec, tuple):
-        return Kernel(int(spec[0]), float(spec[1]), float(spec[2]))
-    return Kernel(int(spec.pow), float(spec.theta), float(spec.length))
+        return Kernel(int(spec[0]), float(spec[1]), float(spec[2]), float(spec[3]) if len(spec) > 3 else 1.0)
+    return Kernel(int(spec.pow), float(spec.theta), float(spec.length), float(getattr(spec, "shape", 1.0)))
 
 
 def options(cheb_order: int = 8, leaf_size: int = 64, max_depth: int = -1, precision="fp32",
@@ -211,19 +213,27 @@ class Filter:
     """One HiKF filter (a handle of the C ABI)."""
 
     def __init__(self, points, q, h_rowptr, h_col, h_val, r_diag, x0=None, p0=None, cq=None, c0=None,
-                 **opts):
+                 r_full=None, **opts):
+        """r_diag: the diagonal of R (n); or r_full: the full n x n R (hikf_create_dense_r)."""
         lib = load()
         self._keep = []
         pts = _f64(points)
         m, dim = pts.shape
         rowptr, col, val = _i64(h_rowptr), _i64(h_col), _f64(h_val)
-        rd = _f64(r_diag)
+        rd = None if r_diag is None else _f64(r_diag)
         n = rowptr.shape[0] - 1
         x0a = None if x0 is None else _f64(x0)
-        p0k = kernel_struct(p0) if p0 is not None else Kernel(int(getattr(q, "pow", 1)), 0.0, 1.0)
+        p0k = kernel_struct(p0) if p0 is not None else Kernel(int(getattr(q, "pow", 1)), 0.0, 1.0,
+                                                              float(getattr(q, "shape", 1.0)))
         o = options(**opts)
         self.h = C.c_void_p()
-        if cq is None:
+        if r_full is not None:
+            rf = _f64(r_full)
+            if rf.shape != (n, n):
+                raise HikfError(HIKF_EINVAL, f"r_full: shape {rf.shape}, expected ({n}, {n})")
+            code = lib.hikf_create_dense_r(C.byref(self.h), dim, m, _dp(pts), kernel_struct(q), n, _ip(rowptr),
+                                           _ip(col), _dp(val), _dp(rf), _dp(x0a), p0k, C.byref(o))
+        elif cq is None:
             code = lib.hikf_create(C.byref(self.h), dim, m, _dp(pts), kernel_struct(q), n, _ip(rowptr), _ip(col),
                                    _dp(val), _dp(rd), _dp(x0a), p0k, C.byref(o))
         else:

@@ -180,6 +180,13 @@ struct hikf_handle {
   // so the state is undefined from then on and every later call is refused (HIKF_ESTATE)
   bool dead = false;
   double cond_s = 0.0;       // estimate of cond(S_t) (hikf_info)
+  bool qht_only = false;     // hikf_h2_qht: the H^2 product only, no filter state
+  // dense R = L L^T: the filter runs on L^{-1} y, L^{-1} H and R = I (hikf_create_dense_r)
+  bool whiten = false;
+  double* Linv = nullptr;    // n x n, L^{-1}
+  double* LT = nullptr;      // n x n, L^T (back to the caller's C = C' L^T)
+  double* eraw = nullptr;    // n, the innovation before whitening
+  double* yw = nullptr;      // n, L^{-1} y (n-space form)
   double create_ms = 0.0;
   int launches = 0;
   // the update as a CUDA graph (HIKF options.graph)
@@ -248,16 +255,30 @@ Status validate_common(int dim, int64_t m, const double* points, int n, const in
   return Status::Ok();
 }
 
-Status validate_kernel(const hikf_kernel& k, bool allow_zero, bool allow_white) {
+Status validate_kernel(const hikf_kernel& k, bool allow_zero, bool allow_white, bool allow_log) {
   using hikf::make_status;
   const bool white = allow_white && k.pow == HIKF_KERNEL_WHITE;
-  if (!white && k.pow != HIKF_KERNEL_EXP && k.pow != HIKF_KERNEL_GAUSS)
-    return make_status(HIKF_EINVAL, allow_white ? "kernel pow must be 0, 1 or 2" : "kernel pow must be 1 or 2");
+  const bool fam = k.pow == HIKF_KERNEL_EXP || k.pow == HIKF_KERNEL_GAUSS || k.pow == HIKF_KERNEL_GCF ||
+                   (allow_log && k.pow == HIKF_KERNEL_LOG);
+  if (!white && !fam)
+    return make_status(HIKF_EINVAL, k.pow == HIKF_KERNEL_LOG
+                                        ? "the log kernel is a generalised covariance: hikf_h2_qht only"
+                                        : (allow_white ? "kernel family must be WHITE, EXP, GAUSS or GCF"
+                                                       : "kernel family must be EXP, GAUSS or GCF"));
   if (!std::isfinite(k.theta) || k.theta < 0.0 || (!allow_zero && k.theta == 0.0))
     return make_status(HIKF_EINVAL, "kernel theta out of range");
   if (!white && k.theta != 0.0 && (!(k.length > 0.0) || !std::isfinite(k.length)))
     return make_status(HIKF_EINVAL, "kernel length must be > 0");
+  if (k.pow == HIKF_KERNEL_GCF && k.theta != 0.0 && !(k.shape > 0.0 && k.shape <= 2.0))
+    return make_status(HIKF_EINVAL, "GCF exponent (shape) must be in (0, 2]");
+  if (k.pow == HIKF_KERNEL_LOG && k.theta != 0.0 && !(k.shape > 0.0 && std::isfinite(k.shape)))
+    return make_status(HIKF_EINVAL, "log kernel: the self-distance r0 (shape) must be > 0");
   return Status::Ok();
+}
+
+// the same covariance function up to its scale theta (P_0 = c Q)
+bool same_shape(const hikf_kernel& a, const hikf_kernel& b) {
+  return a.pow == b.pow && a.length == b.length && (a.pow != HIKF_KERNEL_GCF || a.shape == b.shape);
 }
 
 // C_0 = theta H^T (P_0 = theta I, Sec. 3.1): row i (tree order) gets theta times the
@@ -359,7 +380,7 @@ Status factor_cond(const double* dS, int n, double* scratch, cudaStream_t s, dou
 
 template <typename T>
 Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const double* x0, const double* cq,
-                   const double* c0, const double* r_diag, int chain_opt, int form_opt) {
+                   const double* c0, const double* r_diag, const double* r_full, int chain_opt, int form_opt) {
   cudaStream_t s = h->stream;
   const int64_t m = h->m;
   const int n = h->n, ld = h->ld;
@@ -386,7 +407,9 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
     fp.pow = q.pow;
     fp.theta = q.theta;
     fp.length = q.length;
+    fp.shape = q.shape;
     HIKF_TRY(hikf::h2_product<T>(h->tree, h->H, fp, CQ, ld, s));
+    if (h->qht_only) return Status::Ok();
     if (p0.theta == 0.0) {
       HIKF_CUDA(cudaMemsetAsync(C, 0, sizeof(T) * (size_t)m * ld, s));
     } else if (p0.pow == HIKF_KERNEL_WHITE) {
@@ -394,7 +417,7 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
       white_c0_kernel<T><<<hikf::nblk(m, 256), 256, 0, s>>>(h->H.trowptr, h->H.tcol, h->H.tval, m, ld,
                                                                    p0.theta, C);
       HIKF_LAUNCH_CHECK("white_c0");
-    } else if (p0.pow == q.pow && p0.length == q.length) {
+    } else if (same_shape(p0, q)) {
       // P_0 = (theta_0 / theta_Q) Q  =>  C_0 = P_0 H^T = (theta_0 / theta_Q) C_Q
       hikf::scale_kernel<T><<<hikf::nblk((m * ld + 16 / (int)sizeof(T) - 1) / (16 / (int)sizeof(T)), 256), 256, 0, s>>>(
           CQ, C, m * ld, (T)(p0.theta / q.theta));
@@ -407,9 +430,55 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
       f0.pow = p0.pow;
       f0.theta = p0.theta;
       f0.length = p0.length;
+      f0.shape = p0.shape;
       HIKF_TRY(hikf::h2_product<T>(h->tree, h->H, f0, C, ld, s));
     }
   }
+  // dense R = L L^T: C_Q <- C_Q L^{-T}, C_0 <- C_0 L^{-T}; from here on the filter runs with
+  // the measurement-space operators whitened and R = I (the diagonal-R path)
+  std::vector<double> r_unit;
+  if (r_full) {
+    const size_t nn0 = (size_t)n * n;
+    double *dR = nullptr, *w1 = nullptr, *w2 = nullptr, *linvT = nullptr;
+    int* wflag = nullptr;
+    HIKF_TRY(hikf::arena_alloc(h->arena, &h->Linv, nn0));
+    HIKF_TRY(hikf::arena_alloc(h->arena, &h->LT, nn0));
+    HIKF_TRY(hikf::arena_alloc(h->arena, &h->eraw, n));
+    HIKF_TRY(hikf::arena_alloc(h->arena, &h->yw, n));
+    HIKF_CUDA(cudaMallocAsync((void**)&dR, sizeof(double) * nn0, s));
+    HIKF_CUDA(cudaMallocAsync((void**)&w1, sizeof(double) * nn0, s));
+    HIKF_CUDA(cudaMallocAsync((void**)&w2, sizeof(double) * nn0, s));
+    HIKF_CUDA(cudaMallocAsync((void**)&linvT, sizeof(double) * nn0, s));
+    HIKF_CUDA(cudaMallocAsync((void**)&wflag, sizeof(int) * 2, s));
+    HIKF_CUDA(cudaMemcpyAsync(dR, r_full, sizeof(double) * nn0, cudaMemcpyHostToDevice, s));
+    HIKF_TRY(hikf::launch_whiten_factors(dR, n, w1, w2, h->Linv, linvT, h->LT, wflag, s));
+    int wf[2] = {0, 0};
+    HIKF_CUDA(cudaMemcpyAsync(wf, wflag, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+    HIKF_CUDA(cudaStreamSynchronize(s));
+    if (wf[0] & 2) return hikf::make_status(HIKF_EINVAL, "R is not positive definite");
+    T* tmp = nullptr;
+    HIKF_CUDA(cudaMallocAsync((void**)&tmp, sizeof(T) * (size_t)m * ld, s));
+    HIKF_TRY(hikf::gemm_rows_small<T>(CQ, m, ld, n, linvT, tmp, s));
+    HIKF_CUDA(cudaMemcpyAsync(CQ, tmp, sizeof(T) * (size_t)m * ld, cudaMemcpyDeviceToDevice, s));
+    HIKF_TRY(hikf::gemm_rows_small<T>(C, m, ld, n, linvT, tmp, s));
+    HIKF_CUDA(cudaMemcpyAsync(C, tmp, sizeof(T) * (size_t)m * ld, cudaMemcpyDeviceToDevice, s));
+    HIKF_CUDA(cudaFreeAsync(tmp, s));
+    for (double* b : {dR, w1, w2, linvT}) HIKF_CUDA(cudaFreeAsync(b, s));
+    HIKF_CUDA(cudaFreeAsync(wflag, s));
+    r_unit.assign(n, 1.0);
+    r_diag = r_unit.data();
+    h->whiten = true;
+  }
+  // n x n products H A of the whitened operator: L^{-1} (H A), in place through a scratch
+  double* wscr = nullptr;
+  if (h->whiten) HIKF_CUDA(cudaMallocAsync((void**)&wscr, sizeof(double) * (size_t)n * n, s));
+  auto whiten_nn = [&](double* A) -> Status {
+    if (!h->whiten) return Status::Ok();
+    HIKF_TRY(hikf::launch_left_lower(h->Linv, A, n, wscr, s));
+    HIKF_CUDA(cudaMemcpyAsync(A, wscr, sizeof(double) * (size_t)n * n, cudaMemcpyDeviceToDevice, s));
+    return Status::Ok();
+  };
+
   // mean, variance
   HIKF_TRY(hikf::arena_alloc(h->arena, &h->x, m));
   HIKF_TRY(hikf::arena_alloc(h->arena, &h->var, m));
@@ -436,9 +505,11 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
   HIKF_CUDA(cudaMallocAsync((void**)&zero, sizeof(double) * n, s));
   HIKF_CUDA(cudaMemsetAsync(zero, 0, sizeof(double) * n, s));
   HIKF_TRY(hikf::launch_gather_hc<T>(h->H, CQ, ld, hcq, 0, s));
+  HIKF_TRY(whiten_nn(hcq));
   HIKF_TRY(hikf::launch_form_s(hcq, zero, n, h->hcq_sym, s));
   HIKF_TRY(hikf::launch_gather_hc<T>(h->H, C, ld, a1, 0, s));
   HIKF_TRY(hikf::launch_gather_hc<T>(h->H, CQ, ld, a1, 1, s));
+  HIKF_TRY(whiten_nn(a1));
   HIKF_TRY(hikf::launch_form_s(a1, h->rd, n, h->S, s));
   HIKF_CUDA(cudaFreeAsync(hcq, s));
   HIKF_CUDA(cudaFreeAsync(a1, s));
@@ -478,7 +549,7 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
   HIKF_TRY(hikf::prepare_chain());
 
   // spectral chain when P_0 = c Q (c >= 0) and C_Q is our own H^2 product
-  const bool p0_is_cq = p0.theta == 0.0 || (p0.pow == q.pow && p0.length == q.length);
+  const bool p0_is_cq = p0.theta == 0.0 || same_shape(p0, q);
   const bool can_spec = cq == nullptr && p0_is_cq;
   if (chain_opt == HIKF_CHAIN_SPECTRAL && !can_spec)
     return hikf::make_status(HIKF_EINVAL, "spectral chain needs P0 = c Q and a computed C_Q");
@@ -542,12 +613,17 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
       HIKF_CUDA(cudaMemsetAsync(ns.b, 0, sizeof(double) * n, s));
       HIKF_CUDA(cudaMemsetAsync(ns.h, 0, sizeof(double) * n, s));
       HIKF_TRY(hikf::launch_gather_hc<T>(h->H, Gq, ld, ns.P, 0, s));
+      HIKF_TRY(whiten_nn(ns.P));
       HIKF_CUDA(cudaMemcpyAsync(h->x0t, h->x, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
       // H x_0 = -(0 - H x_0)
       HIKF_CUDA(cudaMemsetAsync(h->ybuf, 0, sizeof(double) * n, s));
       HIKF_TRY(hikf::launch_innovation(h->ybuf, h->H, h->x, ns.hx0, h->flag, s));
       hikf::scale_kernel<double><<<hikf::nblk((n + 1) / 2, 256), 256, 0, s>>>(ns.hx0, ns.hx0, n, -1.0);
       HIKF_LAUNCH_CHECK("scale");
+      if (h->whiten) {
+        HIKF_CUDA(cudaMemcpyAsync(h->eraw, ns.hx0, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        HIKF_TRY(hikf::launch_whiten_vec(h->Linv, h->eraw, n, ns.hx0, s));
+      }
       h->var0 = p0.theta;
       h->nspace = true;
     }
@@ -562,7 +638,15 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
     HIKF_TRY(hikf::arena_alloc(h->arena, &tc.beta_exp, 1));
     HIKF_TRY(hikf::tc_init_rows(tc, (const float*)C, (const float*)CQ, m, ld, s));
   }
+  if (wscr) HIKF_CUDA(cudaFreeAsync(wscr, s));
   return Status::Ok();
+}
+
+// e = y - H x; with a dense R, e = L^{-1} (y - H x) (the innovation of the whitened measurements)
+Status innovation(hikf_t* h, cudaStream_t s) {
+  if (!h->whiten) return hikf::launch_innovation(h->ybuf, h->H, h->x, h->e, h->flag, s);
+  HIKF_TRY(hikf::launch_innovation(h->ybuf, h->H, h->x, h->eraw, h->flag, s));
+  return hikf::launch_whiten_vec(h->Linv, h->eraw, h->n, h->e, s);
 }
 
 // One measurement update on the handle's stream. ev0/ev1 (may be null) bracket the sweep.
@@ -573,13 +657,18 @@ Status enqueue_step(hikf_t* h, cudaEvent_t ev0, cudaEvent_t ev1) {
   int launches = 0;
   if (h->nspace) {
     if (ev0) HIKF_CUDA(cudaEventRecordWithFlags(ev0, s, h->capturing ? cudaEventRecordExternal : 0));
-    HIKF_TRY(hikf::nspace_step(h->sp, h->ns, h->n, h->ybuf, h->e, h->flag, h->dstep, s));
+    const double* y = h->ybuf;
+    if (h->whiten) {  // L^{-1} y against the whitened L^{-1} H x_0 and L^{-1} H G_Q
+      HIKF_TRY(hikf::launch_whiten_vec(h->Linv, h->ybuf, h->n, h->yw, s));
+      y = h->yw;
+    }
+    HIKF_TRY(hikf::nspace_step(h->sp, h->ns, h->n, y, h->e, h->flag, h->dstep, s));
     if (ev1) HIKF_CUDA(cudaEventRecordWithFlags(ev1, s, h->capturing ? cudaEventRecordExternal : 0));
     h->launches = 3;
     return Status::Ok();
   }
   if (h->eigen) {
-    HIKF_TRY(hikf::launch_innovation(h->ybuf, h->H, h->x, h->e, h->flag, s));
+    HIKF_TRY(innovation(h, s));
     HIKF_TRY(hikf::eigen_u(h->sp, h->n, h->e, h->flag, s));
     if (ev0) HIKF_CUDA(cudaEventRecordWithFlags(ev0, s, h->capturing ? cudaEventRecordExternal : 0));
     HIKF_TRY(hikf::eigen_step<T>(h->sp, h->m, h->ld, h->n, (T*)h->G, (const T*)h->Gq, h->theta_q, h->x, h->var,
@@ -592,13 +681,13 @@ Status enqueue_step(hikf_t* h, cudaEvent_t ev0, cudaEvent_t ev1) {
     return Status::Ok();
   }
   if (h->spectral) {
-    HIKF_TRY(hikf::launch_innovation(h->ybuf, h->H, h->x, h->e, h->flag, s));
+    HIKF_TRY(innovation(h, s));
     HIKF_TRY(hikf::spectral_gain<T>(h->sp, h->n, h->e, h->a, (T*)h->Msw, h->nt, h->flag, s));
     launches += sizeof(T) == 4 ? 5 : 4;
   } else {
     HIKF_TRY(hikf::launch_chain(c, s));
     launches += c.fp64 ? 1 : (2 + 3 * c.refine_iters + 3);
-    HIKF_TRY(hikf::launch_innovation(h->ybuf, h->H, h->x, h->e, h->flag, s));
+    HIKF_TRY(innovation(h, s));
     HIKF_TRY(hikf::launch_gemv<T>(c.Mh, c.Ml, c.M64, h->n, c.ldm, h->e, h->a, (T*)h->Msw, h->nt, h->flag, s));
     launches += 2;
   }
@@ -748,18 +837,34 @@ Status flag_status(int f) {
 hikf_status create_impl(hikf_t** out, int dim, int64_t m, const double* points, hikf_kernel q, int n,
                         const int64_t* rowptr, const int64_t* col, const double* val, const double* r_diag,
                         const double* x0, hikf_kernel p0, const double* cq, const double* c0,
-                        const hikf_options* opt) {
+                        const hikf_options* opt, const double* r_full = nullptr, bool qht_only = false) {
   auto t0 = std::chrono::steady_clock::now();
   if (!out) return fail(nullptr, hikf::make_status(HIKF_EINVAL, "out is NULL"));
   *out = nullptr;
   hikf_options o;
   hikf_options_default(&o);
   if (opt) o = *opt;
+  std::vector<double> r_from_full;
+  if (r_full) {
+    if (n < 1 || n > hikf::kMaxN) return fail(nullptr, hikf::make_status(HIKF_EINVAL, "n out of range [1, 512]"));
+    double rmax = 0.0;
+    for (int64_t i = 0; i < (int64_t)n * n; ++i) {
+      if (!std::isfinite(r_full[i])) return fail(nullptr, hikf::make_status(HIKF_EINVAL, "non-finite R"));
+      rmax = std::max(rmax, std::fabs(r_full[i]));
+    }
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < i; ++j)
+        if (std::fabs(r_full[(int64_t)i * n + j] - r_full[(int64_t)j * n + i]) > 1e-12 * rmax)
+          return fail(nullptr, hikf::make_status(HIKF_EINVAL, "R is not symmetric"));
+    r_from_full.resize(n);
+    for (int i = 0; i < n; ++i) r_from_full[i] = r_full[(int64_t)i * n + i];
+    r_diag = r_from_full.data();
+  }
   Status st = validate_common(dim, m, points, n, rowptr, col, val, r_diag, x0, o);
   if (!st.ok()) return fail(nullptr, st);
-  st = validate_kernel(q, cq != nullptr, false);
+  st = validate_kernel(q, cq != nullptr, false, qht_only);
   if (!st.ok()) return fail(nullptr, st);
-  st = validate_kernel(p0, true, true);
+  st = validate_kernel(p0, true, true, qht_only);
   if (!st.ok()) return fail(nullptr, st);
   if (cq && !c0) return fail(nullptr, hikf::make_status(HIKF_EINVAL, "c0 is NULL"));
   if (o.precision == HIKF_PREC_MIXED && o.form == HIKF_FORM_CROSS && hikf::padded_ld(n) > 256)
@@ -780,6 +885,7 @@ hikf_status create_impl(hikf_t** out, int dim, int64_t m, const double* points, 
   h->order = o.cheb_order;
   h->use_graph = o.graph != 0;
   h->m2l = o.m2l;
+  h->qht_only = qht_only;
   if (o.cuda_stream) {
     h->stream = (cudaStream_t)o.cuda_stream;
     if (h->stream == cudaStreamLegacy) h->use_graph = false;  // the legacy stream cannot be captured
@@ -806,8 +912,8 @@ hikf_status create_impl(hikf_t** out, int dim, int64_t m, const double* points, 
   if (!st.ok()) return bail(st);
   st = hikf::build_sparse(h->H, h->arena, h->tree, rowptr, col, val, n, h->stream);
   if (!st.ok()) return bail(st);
-  st = h->fp64() ? setup_state<double>(h, q, p0, x0, cq, c0, r_diag, o.chain, o.form)
-                 : setup_state<float>(h, q, p0, x0, cq, c0, r_diag, o.chain, o.form);
+  st = h->fp64() ? setup_state<double>(h, q, p0, x0, cq, c0, r_diag, r_full, o.chain, o.form)
+                 : setup_state<float>(h, q, p0, x0, cq, c0, r_diag, r_full, o.chain, o.form);
   if (!st.ok()) return bail(st);
   e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return bail(hikf::cuda_status(e, "create", __FILE__, __LINE__));
@@ -838,6 +944,14 @@ hikf_status hikf_create(hikf_t** out, int dim, int64_t m, const double* points, 
                         const int64_t* h_rowptr, const int64_t* h_col, const double* h_val, const double* r_diag,
                         const double* x0, hikf_kernel p0, const hikf_options* opt) {
   return create_impl(out, dim, m, points, q, n, h_rowptr, h_col, h_val, r_diag, x0, p0, nullptr, nullptr, opt);
+}
+
+hikf_status hikf_create_dense_r(hikf_t** out, int dim, int64_t m, const double* points, hikf_kernel q, int n,
+                                const int64_t* h_rowptr, const int64_t* h_col, const double* h_val,
+                                const double* r_full, const double* x0, hikf_kernel p0, const hikf_options* opt) {
+  if (!r_full) return fail(nullptr, hikf::make_status(HIKF_EINVAL, "r_full is NULL"));
+  return create_impl(out, dim, m, points, q, n, h_rowptr, h_col, h_val, nullptr, x0, p0, nullptr, nullptr, opt,
+                     r_full);
 }
 
 hikf_status hikf_create_with_cq(hikf_t** out, int dim, int64_t m, const double* points, hikf_kernel q, int n,
@@ -924,6 +1038,26 @@ static hikf_status get_mat(hikf_t* h, const void* src, double* out) {
   const size_t bytes = sizeof(double) * (size_t)h->m * h->n;
   cudaError_t e = cudaMallocAsync((void**)&d, bytes, h->stream);
   if (e != cudaSuccess) return fail(h, hikf::cuda_status(e, "cudaMallocAsync", __FILE__, __LINE__));
+  void* unw = nullptr;
+  if (h->whiten) {
+    // the matrices are held in the whitened measurement space: C = C' L^T for the caller
+    const size_t tb = (h->fp64() ? sizeof(double) : sizeof(float)) * (size_t)h->m * h->ld;
+    e = cudaMallocAsync(&unw, tb, h->stream);
+    if (e != cudaSuccess) {
+      cudaFreeAsync(d, h->stream);
+      return fail(h, hikf::cuda_status(e, "cudaMallocAsync", __FILE__, __LINE__));
+    }
+    Status st = h->fp64() ? hikf::gemm_rows_small<double>((const double*)src, h->m, h->ld, h->n, h->LT,
+                                                          (double*)unw, h->stream)
+                          : hikf::gemm_rows_small<float>((const float*)src, h->m, h->ld, h->n, h->LT, (float*)unw,
+                                                         h->stream);
+    if (!st.ok()) {
+      cudaFreeAsync(d, h->stream);
+      cudaFreeAsync(unw, h->stream);
+      return fail(h, st);
+    }
+    src = unw;
+  }
   if (h->fp64())
     hikf::rows_to_caller<double><<<hikf::nblk(h->m * h->n, 256), 256, 0, h->stream>>>(
         (const double*)src, h->tree.perm, h->m, h->n, h->ld, d);
@@ -933,6 +1067,7 @@ static hikf_status get_mat(hikf_t* h, const void* src, double* out) {
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, bytes, cudaMemcpyDeviceToHost, h->stream);
   cudaFreeAsync(d, h->stream);
+  if (unw) cudaFreeAsync(unw, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return fail(h, hikf::cuda_status(e, "get matrix", __FILE__, __LINE__));
   return HIKF_OK;
@@ -1080,9 +1215,10 @@ hikf_status hikf_h2_qht(int dim, int64_t m, const double* points, hikf_kernel k,
                         const int64_t* h_col, const double* h_val, const hikf_options* opt, double* out) {
   if (!out) return fail(nullptr, hikf::make_status(HIKF_EINVAL, "out is NULL"));
   std::vector<double> rd(std::max(n, 1), 1.0);
-  hikf_kernel zero = {k.pow, 0.0, 1.0};
+  hikf_kernel zero = {k.pow, 0.0, 1.0, k.shape};
   hikf_t* h = nullptr;
-  hikf_status s = hikf_create(&h, dim, m, points, k, n, h_rowptr, h_col, h_val, rd.data(), nullptr, zero, opt);
+  hikf_status s = create_impl(&h, dim, m, points, k, n, h_rowptr, h_col, h_val, rd.data(), nullptr, zero, nullptr,
+                              nullptr, opt, nullptr, true);
   if (s != HIKF_OK) return s;
   s = hikf_get_cq(h, out);
   if (s != HIKF_OK) hikf::g_create_error = h->err;

@@ -34,8 +34,10 @@ struct Geo {
   double lo[3];
   double side;
   int dim, depth, p, q, ld, n;
-  int pow;
+  int pow;                    // HIKF_KERNEL_EXP / GAUSS / GCF / LOG
   double theta, length;
+  double shape;               // GCF: the exponent p of Eq. Q; LOG: the self-distance r0
+  double kdiag;               // LOG: the value at r = 0, theta log(length / r0)
   double wl;                  // leaf width side / 2^depth (host-computed: no FP64 division per thread)
   double inv_len, inv_len2;   // 1 / length, 1 / length^2
 };
@@ -79,23 +81,36 @@ __global__ void cheb_tables(int p, double* __restrict__ tab) {
   }
 }
 
-__device__ __forceinline__ double kernel_value_d(double r2, int pow, double theta, double length) {
-  if (pow == 2) return theta * exp(-r2 / (length * length));
+// K(r) of the kernel families (r2 = r^2):
+//   EXP    theta exp(-r / l)            GAUSS  theta exp(-r^2 / l^2)        (Sec. 3.3, kernels 1-2)
+//   GCF    theta exp(-(r / l)^p)        (Eq. Q, 0 < p <= 2)
+//   LOG    theta log(l / r), r > 0; theta log(l / r0) at r = 0   (Sec. 3.3, kernel 3: A log r
+//          with A = -theta < 0, shifted by the constant theta log l; r0 is the stated diagonal)
+__device__ __forceinline__ double kernel_value_d(double r2, int fam, double theta, double length, double shape,
+                                                 double kdiag) {
+  if (fam == HIKF_KERNEL_GAUSS) return theta * exp(-r2 / (length * length));
+  if (fam == HIKF_KERNEL_GCF) return theta * exp(-pow(sqrt(r2) / length, shape));
+  if (fam == HIKF_KERNEL_LOG) return r2 > 0.0 ? -0.5 * theta * log(r2 / (length * length)) : kdiag;
   return theta * exp(-sqrt(r2) / length);
 }
 
 template <typename T>
-__device__ __forceinline__ T kernel_value(T r2, int pow, T theta, T inv_len, T inv_len2);
+__device__ __forceinline__ T kernel_value(T r2, int fam, T theta, T inv_len, T inv_len2, T shape, T kdiag);
 
 template <>
-__device__ __forceinline__ float kernel_value<float>(float r2, int pow, float theta, float inv_len, float inv_len2) {
-  if (pow == 2) return theta * expf(-r2 * inv_len2);
+__device__ __forceinline__ float kernel_value<float>(float r2, int fam, float theta, float inv_len, float inv_len2,
+                                                    float shape, float kdiag) {
+  if (fam == HIKF_KERNEL_GAUSS) return theta * expf(-r2 * inv_len2);
+  if (fam == HIKF_KERNEL_GCF) return theta * expf(-powf(sqrtf(r2) * inv_len, shape));
+  if (fam == HIKF_KERNEL_LOG) return r2 > 0.f ? -0.5f * theta * logf(r2 * inv_len2) : kdiag;
   return theta * expf(-sqrtf(r2) * inv_len);
 }
 template <>
-__device__ __forceinline__ double kernel_value<double>(double r2, int pow, double theta, double inv_len,
-                                                       double inv_len2) {
-  if (pow == 2) return theta * exp(-r2 * inv_len2);
+__device__ __forceinline__ double kernel_value<double>(double r2, int fam, double theta, double inv_len,
+                                                       double inv_len2, double shape, double kdiag) {
+  if (fam == HIKF_KERNEL_GAUSS) return theta * exp(-r2 * inv_len2);
+  if (fam == HIKF_KERNEL_GCF) return theta * exp(-pow(sqrt(r2) * inv_len, shape));
+  if (fam == HIKF_KERNEL_LOG) return r2 > 0.0 ? -0.5 * theta * log(r2 * inv_len2) : kdiag;
   return theta * exp(-sqrt(r2) * inv_len);
 }
 
@@ -124,7 +139,7 @@ __global__ void m2l_table(Geo g, const double* __restrict__ tab, T* __restrict__
     double diff = 0.5 * s * (xa - xc) - s * od;
     r2 += diff * diff;
   }
-  kop[t] = (T)kernel_value_d(r2, g.pow, g.theta, g.length);
+  kop[t] = (T)kernel_value_d(r2, g.pow, g.theta, g.length, g.shape, g.kdiag);
 }
 
 // per-box count of H^T nonzeros (sources) below the box
@@ -843,7 +858,7 @@ __global__ void __launch_bounds__(kThreads) l2p_p2p_kernel(Geo g, const double* 
                 T dx = tx[ii * 3 + d] - sx[j * 3 + d];
                 r2 += dx * dx;
               }
-              v = kernel_value<T>(r2, g.pow, theta, inv_len, inv_len2);
+              v = kernel_value<T>(r2, g.pow, theta, inv_len, inv_len2, (T)g.shape, (T)g.kdiag);
             }
             kvs[j * kPT + ii] = v;
           }
@@ -909,6 +924,8 @@ Status h2_product(const Tree& t, const SparseH& h, const FmmParams& fp, T* out, 
   g.pow = fp.pow;
   g.theta = fp.theta;
   g.length = fp.length;
+  g.shape = fp.shape;
+  g.kdiag = fp.pow == HIKF_KERNEL_LOG ? fp.theta * std::log(fp.length / fp.shape) : 0.0;
   g.wl = t.side / (double)((int64_t)1 << t.depth);
   g.inv_len = 1.0 / fp.length;
   g.inv_len2 = 1.0 / (fp.length * fp.length);

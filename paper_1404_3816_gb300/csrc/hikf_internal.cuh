@@ -106,6 +106,7 @@ struct FmmParams {
   int pow = 1;
   double theta = 1.0;
   double length = 1.0;
+  double shape = 1.0;       // GCF exponent p / LOG self-distance r0 (hikf_kernel.shape)
   bool tensor_m2l = false;  // M2L on the tensor cores (FP32 storage only)
   bool autotune = true;     // tensor-core M2L: time the launch variants once per shape
   int sms = 1;

@@ -764,6 +764,81 @@ Status launch_recur(const double* hcq_sym, const double* rd, const float* Mh, co
 
 namespace hikf {
 
+// ---------------------------------------------------------------------------
+// dense R: the whitening factors of R = L L^T (FP64, one CTA): L^T, L^{-1} and L^{-T}
+// (full n x n, zeros outside the triangle); flag[0] |= 2 when R is not positive definite
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) whiten_factors_kernel(const double* __restrict__ R, int n,
+                                                              double* __restrict__ W1, double* __restrict__ W2,
+                                                              double* __restrict__ Linv, double* __restrict__ LinvT,
+                                                              double* __restrict__ LT, int* __restrict__ flag) {
+  __shared__ double colbuf[kMaxN];
+  const int64_t nn = (int64_t)n * n;
+  for (int64_t t = threadIdx.x; t < nn; t += blockDim.x) W1[t] = R[t];
+  __syncthreads();
+  LowerTri<double> A{W1, n, false};
+  if (!chol_lower<double>(A, n)) {
+    if (threadIdx.x == 0) atomicOr(flag, 2);
+    return;
+  }
+  for (int64_t t = threadIdx.x; t < nn; t += blockDim.x) W2[t] = W1[t];
+  __syncthreads();
+  LowerTri<double> X{W2, n, false};
+  trtri_lower<double>(X, n, colbuf);
+  __syncthreads();
+  for (int64_t t = threadIdx.x; t < nn; t += blockDim.x) {
+    const int i = (int)(t / n), j = (int)(t % n);
+    const double l = j <= i ? W1[t] : 0.0;
+    const double li = j <= i ? W2[t] : 0.0;
+    Linv[t] = li;
+    LinvT[(int64_t)j * n + i] = li;
+    LT[(int64_t)j * n + i] = l;
+  }
+}
+
+// out = L^{-1} in (n-vectors, L^{-1} lower triangular): one warp per row
+__global__ void whiten_vec_kernel(const double* __restrict__ Linv, const double* __restrict__ in, int n,
+                                  double* __restrict__ out) {
+  const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (i >= n) return;
+  double acc = 0.0;
+  for (int j = lane; j <= i; j += 32) acc += Linv[(int64_t)i * n + j] * in[j];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) out[i] = acc;
+}
+
+// out = L^{-1} A (n x n): one thread per output entry
+__global__ void left_lower_kernel(const double* __restrict__ Linv, const double* __restrict__ A, int n,
+                                  double* __restrict__ out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * n) return;
+  const int i = (int)(t / n), j = (int)(t % n);
+  double acc = 0.0;
+  for (int k = 0; k <= i; ++k) acc += Linv[(int64_t)i * n + k] * A[(int64_t)k * n + j];
+  out[t] = acc;
+}
+
+Status launch_whiten_factors(const double* R, int n, double* W1, double* W2, double* Linv, double* LinvT, double* LT,
+                             int* flag, cudaStream_t s) {
+  HIKF_CUDA(cudaMemsetAsync(flag, 0, sizeof(int) * 2, s));
+  whiten_factors_kernel<<<1, 1024, 0, s>>>(R, n, W1, W2, Linv, LinvT, LT, flag);
+  HIKF_LAUNCH_CHECK("whiten_factors");
+  return Status::Ok();
+}
+
+Status launch_whiten_vec(const double* Linv, const double* in, int n, double* out, cudaStream_t s) {
+  whiten_vec_kernel<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(Linv, in, n, out);
+  HIKF_LAUNCH_CHECK("whiten_vec");
+  return Status::Ok();
+}
+
+Status launch_left_lower(const double* Linv, const double* A, int n, double* out, cudaStream_t s) {
+  const int64_t nn = (int64_t)n * n;
+  left_lower_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(Linv, A, n, out);
+  HIKF_LAUNCH_CHECK("left_lower");
+  return Status::Ok();
+}
+
 Status spd_inverse_f64(const double* S, int n, double* M, double* scratch, int* flag, cudaStream_t s) {
   HIKF_CUDA(cudaMemsetAsync(flag, 0, sizeof(int) * 2, s));
   // force = 1: factor S itself; the inverse goes to M (ldm = n)

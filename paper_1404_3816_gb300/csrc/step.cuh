@@ -66,6 +66,15 @@ Status launch_gemv(const float* Mh, const float* Ml, const double* M64, int n, i
 Status launch_recur(const double* hcq_sym, const double* rd, const float* Mh, const float* Ml, const double* M64,
                     int n, int ldm, const int* flag, double* S, cudaStream_t s);
 
+// Dense R = L L^T: L^{-1}, L^{-T} and L^T (n x n FP64 each, zeros outside the triangle), W1 and W2
+// n x n scratch; flag[0] & 2 when R is not positive definite.
+Status launch_whiten_factors(const double* R, int n, double* W1, double* W2, double* Linv, double* LinvT, double* LT,
+                             int* flag, cudaStream_t s);
+// out = L^{-1} in (n-vectors; in != out)
+Status launch_whiten_vec(const double* Linv, const double* in, int n, double* out, cudaStream_t s);
+// out = L^{-1} A (n x n; A != out)
+Status launch_left_lower(const double* Linv, const double* A, int n, double* out, cudaStream_t s);
+
 // Standalone S^{-1} (FP64 Cholesky on one CTA): scratch n x n FP64, flag 2 ints (flag[0] & 2: not PD).
 Status spd_inverse_f64(const double* S, int n, double* M, double* scratch, int* flag, cudaStream_t s);
 

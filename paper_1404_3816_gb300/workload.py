@@ -27,14 +27,18 @@ import numpy as np
 WHITE = 0  # initial covariance only: P_0 = theta I (Sec. 3.1), no correlation between cells
 EXP = 1    # GCF exponent p = 1: theta * exp(-r / l)
 GAUSS = 2  # GCF exponent p = 2: theta * exp(-r^2 / l^2)
+GCF = 3    # any GCF exponent 0 < p <= 2: theta * exp(-(r / l)^p), p = shape
+LOG = 4    # theta * log(l / r), value theta * log(l / shape) at r = 0 (H^2 product only)
 
 
 @dataclasses.dataclass
 class KernelSpec:
-    """Generalised covariance function theta * exp(-(r / length)^pow) (Eq. Q)."""
+    """Kernel family `pow`: the generalised covariance function theta * exp(-(r / length)^p)
+    (Eq. Q; p = 1, 2, or p = shape for GCF), or the log kernel (shape = its self-distance)."""
     pow: int
     theta: float
     length: float
+    shape: float = 1.0
 
 
 @dataclasses.dataclass

@@ -51,9 +51,13 @@ def test_invalid_arguments_are_rejected_before_any_device_work(lib):
     bad_cases = [
         dict(r_diag=np.zeros(w.n)),
         dict(h_col=np.where(np.arange(w.nnz) == 0, w.m + 5, w.h_col)),
-        dict(q=W.KernelSpec(3, 0.01, 8.0)),
+        dict(q=W.KernelSpec(5, 0.01, 8.0)),             # no such family
         dict(q=W.KernelSpec(W.WHITE, 0.01, 8.0)),      # the white kernel is for P_0 only
-        dict(p0=W.KernelSpec(3, 1.0, 8.0)),
+        dict(q=W.KernelSpec(W.LOG, 0.01, 8.0, 0.5)),   # a generalised covariance: H^2 product only
+        dict(q=W.KernelSpec(W.GCF, 0.01, 8.0, 2.5)),   # GCF exponent beyond (0, 2]
+        dict(q=W.KernelSpec(W.GCF, 0.01, 8.0, 0.0)),
+        dict(p0=W.KernelSpec(5, 1.0, 8.0)),
+        dict(p0=W.KernelSpec(W.LOG, 1.0, 8.0, 0.5)),
         dict(q=W.KernelSpec(1, -1.0, 8.0)),
         dict(points=np.where(np.arange(w.m * 2).reshape(w.m, 2) == 3, np.nan, w.points)),
     ]
@@ -65,6 +69,15 @@ def test_invalid_arguments_are_rejected_before_any_device_work(lib):
         assert e.value.code == binding.HIKF_EINVAL
     with pytest.raises(binding.HikfError):
         binding.Filter(**good, cheb_order=40)
+    # a full R that is not symmetric or not finite is refused on the host
+    bad_r = np.eye(w.n) * 1e-3
+    bad_r[0, 1] = 1e-4
+    for r_full in (bad_r, np.full((w.n, w.n), np.nan)):
+        kw = dict(good)
+        kw.pop("r_diag")
+        with pytest.raises(binding.HikfError) as e:
+            binding.Filter(**kw, r_diag=None, r_full=r_full)
+        assert e.value.code == binding.HIKF_EINVAL
 
 
 def test_serving_schedule_and_footprint_without_gpu():

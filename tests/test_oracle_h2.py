@@ -133,3 +133,19 @@ def test_converges_with_order_3d():
             for p in (3, 4, 5, 6)]
     assert all(e1 < 0.5 * e0 for e0, e1 in zip(errs, errs[1:])), errs
     assert errs[-1] < 1e-4, errs
+
+
+@pytest.mark.parametrize("kern", ["gcf0.5", "gcf1.5", "log"])
+def test_converges_with_order_other_families(kern):
+    """The GCF exponent of Eq. Q away from 1 and 2, and the log kernel of Sec. 3.3 (smooth
+    away from r = 0, where the near field is exact): the interpolation error falls with the
+    order and reaches the 1e-5 target by order 8."""
+    w = W.config("crosswell2d_m1024_n16")
+    H = qht.h_csr(w.h_rowptr, w.h_col, w.h_val, w.m)
+    k = {"gcf0.5": kf.gcf(0.01, 8.0, 0.5), "gcf1.5": kf.gcf(0.01, 8.0, 1.5),
+         "log": kf.log_kernel(0.01, 64.0, 0.5)}[kern]
+    exact = qht.qht(w.points, k, H)
+    errs = [np.linalg.norm(h2.h2_qht(w.points, k, H, p=p, depth=2) - exact) / np.linalg.norm(exact)
+            for p in (4, 6, 8)]
+    assert errs[1] < errs[0] and errs[2] < errs[1], errs
+    assert errs[-1] < 1e-5, errs

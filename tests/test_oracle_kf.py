@@ -246,3 +246,43 @@ def test_chained_runs_equal_one_run():
     a = kf.hikf_cross(cq, 100.0 * cq, np.full(w.m, 1.0), w.q.theta, H, w.r_diag, w.x0, Y[:2])
     b = kf.hikf_cross(cq, a["C"], a["var"], w.q.theta, H, w.r_diag, a["x"], Y[2:])
     assert np.array_equal(b["x"], one["x"]) and np.array_equal(b["var"], one["var"])
+
+
+def _ar1(n, sigma2=1e-2, rho=0.6):
+    """A dense, correlated measurement-error covariance: R_ij = sigma^2 rho^|i - j| (SPD)."""
+    i = np.arange(n)
+    return sigma2 * rho ** np.abs(i[:, None] - i[None, :])
+
+
+def test_q0_one_step_dense_r_equals_regression_posterior():
+    """Eq. R generalised to a full R: with Q = 0 one step of Alg. 1 is the Gaussian regression
+    posterior (P0^-1 + H^T R^-1 H)^-1 with the full R^-1."""
+    _, P0, _, H, _, x0, Y = _small_problem(7)
+    R = _ar1(H.shape[0])
+    out = kf.kf_full(P0, np.zeros_like(P0), H, R, x0, Y[:1])
+    Ri = np.linalg.inv(R)
+    Ppost = np.linalg.inv(np.linalg.inv(P0) + H.T @ Ri @ H)
+    xpost = Ppost @ (np.linalg.solve(P0, x0) + H.T @ Ri @ Y[0])
+    assert np.allclose(out["P"], Ppost, rtol=1e-8, atol=1e-10)
+    assert np.allclose(out["x"], xpost, rtol=1e-8, atol=1e-9)
+
+
+def test_dense_r_cross_form_equals_full_kf_and_whitened_filter():
+    """Alg. 2 with a full R equals Alg. 1 with it, and both equal the filter on the whitened
+    measurements L^-1 y with L^-1 H and R = I (R = L L^T): the identity the CUDA path uses."""
+    pts, P0, Q, H, _, x0, Y = _small_problem(8, T=5)
+    R = _ar1(H.shape[0], rho=0.45)
+    full = kf.kf_full(P0, Q, H, R, x0, Y, record=True)
+    cross = kf.hikf_cross(Q @ H.T, P0 @ H.T, np.diag(P0).copy(), np.diag(Q).copy(), H, R, x0, Y, record=True)
+    L = np.linalg.cholesky(R)
+    Hw = np.linalg.solve(L, H)
+    Yw = np.linalg.solve(L, Y.T).T
+    white = kf.kf_full(P0, Q, Hw, np.ones(H.shape[0]), x0, Yw, record=True)
+    for t in range(Y.shape[0]):
+        assert kf.relative_error(cross["xs"][t], full["xs"][t]) < 1e-11
+        assert kf.relative_error(cross["vars"][t], full["vars"][t]) < 1e-11
+        assert kf.relative_error(white["xs"][t], full["xs"][t]) < 1e-10
+        assert kf.relative_error(white["vars"][t], full["vars"][t]) < 1e-10
+    # planted: dropping the off-diagonal of R changes the posterior
+    diag = kf.kf_full(P0, Q, H, np.diag(R).copy(), x0, Y)
+    assert kf.relative_error(diag["x"], full["x"]) > 1e-3

@@ -16,7 +16,8 @@ def test_constant_kernel_gives_ray_lengths():
     assert np.allclose(cq, 0.7 * lengths[None, :], rtol=1e-12)
 
 
-@pytest.mark.parametrize("pow_, expect", [(1, np.exp(-5.0 / 8.0)), (2, np.exp(-25.0 / 64.0))])
+@pytest.mark.parametrize("pow_, expect", [(1, np.exp(-5.0 / 8.0)), (2, np.exp(-25.0 / 64.0)),
+                                          (1.5, np.exp(-0.625 * np.sqrt(0.625))), (0.5, np.exp(-np.sqrt(0.625)))])
 def test_single_source_values_at_3_4_5_distance(pow_, expect):
     pts = W.grid_points((10, 10))
     m = pts.shape[0]
@@ -83,3 +84,27 @@ def test_grid_convolution_constant_kernel_gives_ray_lengths():
     cq = qht.qht_grid_fft(w.grid, kf.gcf(0.7, 1e30, 1), H)
     lengths = np.linalg.norm(w.receivers - w.sources, axis=1)
     assert np.allclose(cq, 0.7 * lengths[None, :], rtol=1e-12)
+
+
+def test_log_kernel_values_and_diagonal():
+    # theta log(l / r): at the 3-4-5 distance theta log(8 / 5); at the source itself the
+    # stated diagonal theta log(8 / r0)
+    pts = W.grid_points((10, 10))
+    j0 = 1 * 10 + 2
+    H = qht.h_csr(np.array([0, 1]), np.array([j0]), np.array([2.5]), pts.shape[0])
+    cq = qht.qht(pts, kf.log_kernel(0.3, 8.0, 0.5), H)
+    i = (1 + 3) * 10 + (2 + 4)
+    assert cq[i, 0] == pytest.approx(2.5 * 0.3 * np.log(8.0 / 5.0), rel=1e-14)
+    assert cq[j0, 0] == pytest.approx(2.5 * 0.3 * np.log(8.0 / 0.5), rel=1e-14)
+    K = kf.covariance_matrix(pts[:20], kf.log_kernel(0.3, 8.0, 0.5))
+    assert np.array_equal(K, K.T)
+
+
+@pytest.mark.parametrize("grid", [(18, 14), (9, 7, 6)])
+def test_grid_convolution_gcf_and_log_equal_direct_sum(grid):
+    w = W.make(grid=grid, n=6 if len(grid) == 2 else 16, q=W.KernelSpec(1, 0.3, 4.0), p0=W.KernelSpec(1, 1.0, 4.0),
+               r=1e-3, steps=1, seed=8)
+    H = qht.h_csr(w.h_rowptr, w.h_col, w.h_val, w.m)
+    for k in (kf.gcf(0.3, 4.0, 1.3), kf.log_kernel(0.3, 40.0, 0.5)):
+        direct = qht.qht(w.points, k, H)
+        assert np.abs(qht.qht_grid_fft(grid, k, H) - direct).max() <= 1e-13 * np.abs(direct).max()
