@@ -298,6 +298,56 @@ const char* hikf_last_error(const hikf_t* h);
 /* Free the handle and all of its device memory. NULL is ignored. */
 void hikf_destroy(hikf_t* h);
 
+/*
+ * Row sharding — the filter split over `nranks` processes (one GPU each) by rows of the
+ * state. Alg. 2 is row-wise except for H C_{t+1|t} and H s_{t+1|t}, which sum over the rows
+ * on the support of H; the cost analysis of Alg. 2 and the O(mn) storage of Table 3 make the
+ * m x n state the quantity to split. Each rank owns a contiguous range of rows in the tree
+ * (Morton) order: its rows of C, C_Q, x and delta^2. The n x n quantities of the gain chain are
+ * replicated (every rank forms the same ones from the same sums), so the ranks exchange:
+ *   at create, once: the sums over ranks of the partial n x n products H_r C_Q,r and
+ *                    H_r C_1,r (2 n^2 doubles), through the caller's all-reduce callback;
+ *   every step:      the sum over ranks of the partial n-vector H_r x_r (the innovation),
+ *                    done by the caller between hikf_shard_step_begin and _end.
+ * The H^2 product is formed on every rank (H is small and replicated, so no multipole halo
+ * is needed) and each rank keeps its rows. Forms: cross and eigen (HIKF_FORM_NSPACE is
+ * refused); diagonal R only. Updates are enqueued on the handle's stream without a graph.
+ */
+typedef int (*hikf_allreduce_fn)(double* d_buf, int64_t count, void* ctx); /* sum in place over the ranks,
+                                                                               device buffer; 0 = success */
+typedef struct {
+  int rank;                    /* 0 <= rank < nranks */
+  int nranks;                  /* >= 1 */
+  hikf_allreduce_fn allreduce; /* called from hikf_create_shard with the stream synchronized;
+                                  may be NULL when nranks == 1 */
+  void* ctx;                   /* passed through to allreduce */
+} hikf_shard;
+
+/* hikf_create with the filter split by rows as described above; the other arguments as
+ * in hikf_create (every rank passes the same problem). HIKF_EINVAL for a bad rank/nranks,
+ * HIKF_FORM_NSPACE, or a missing allreduce with nranks > 1; HIKF_ECUDA when allreduce fails. */
+hikf_status hikf_create_shard(hikf_t** out, const hikf_shard* shard, int dim, int64_t m, const double* points,
+                              hikf_kernel q, int n, const int64_t* h_rowptr, const int64_t* h_col,
+                              const double* h_val, const double* r_diag, const double* x0, hikf_kernel p0,
+                              const hikf_options* opt);
+
+/* The rank's rows: tree-order positions [*first, *first + *count) of the m points. */
+hikf_status hikf_shard_rows(const hikf_t* h, int64_t* first, int64_t* count);
+/* host, count int64: the caller's index of each of the rank's rows (in the rank's order). */
+hikf_status hikf_shard_caller_index(hikf_t* h, int64_t* out);
+
+/* Step of a sharded filter, part 1: y_{t+1} (device, n FP64) is taken in, and the rank's
+ * partial H_r x_r is written to d_hx (device, n FP64). Enqueued on the handle's stream: the
+ * caller synchronises it, sums d_hx over the ranks in place, and calls part 2. */
+hikf_status hikf_shard_step_begin(hikf_t* h, const double* d_y, double* d_hx);
+/* Part 2: the rest of the step (Alg. 2 with H x_t = the summed d_hx, device n FP64) on the
+ * rank's rows. Enqueued; errors are latched and reported by hikf_sync as for
+ * hikf_assimilate_device. d_hx must stay valid until the stream has passed the call. */
+hikf_status hikf_shard_step_end(hikf_t* h, const double* d_hx);
+/* The rank's rows of x_{t|t} / delta^2_{t|t} (host, count FP64, the rank's order). Synchronous. */
+hikf_status hikf_shard_get_mean(hikf_t* h, double* out);
+hikf_status hikf_shard_get_variance(hikf_t* h, double* out);
+
 /* Test hook: the limit (ns) of the tensor-core sweep's abortable device-side waits
  * for launches captured or enqueued from now on (process-wide); 0 restores the
  * default of about two seconds. A tiny limit makes the next MIXED step time out

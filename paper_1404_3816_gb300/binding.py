@@ -35,7 +35,11 @@ EXPORTED = ["hikf_options_default", "hikf_create", "hikf_create_dense_r", "hikf_
             "hikf_get_mean_device", "hikf_get_variance_device", "hikf_get_cq", "hikf_get_cross",
             "hikf_get_perm", "hikf_info", "hikf_step", "hikf_stream", "hikf_last_error", "hikf_destroy", "hikf_h2_qht",
             "hikf_profile_enable", "hikf_profile_read", "hikf_spd_inverse", "hikf_spd_inverse_noalloc",
-            "hikf_test_set_wait_limit"]
+            "hikf_test_set_wait_limit", "hikf_create_shard", "hikf_shard_rows", "hikf_shard_caller_index",
+            "hikf_shard_step_begin", "hikf_shard_step_end", "hikf_shard_get_mean", "hikf_shard_get_variance"]
+
+# hikf_allreduce_fn: int (*)(double* d_buf, int64_t count, void* ctx)
+ALLREDUCE_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int64, C.c_void_p)
 
 
 class HikfError(RuntimeError):
@@ -52,6 +56,10 @@ class Options(C.Structure):
     _fields_ = [("cheb_order", C.c_int), ("leaf_size", C.c_int), ("max_depth", C.c_int),
                 ("precision", C.c_int), ("cuda_stream", C.c_void_p), ("chain", C.c_int), ("form", C.c_int),
                 ("graph", C.c_int), ("m2l", C.c_int)]
+
+
+class Shard(C.Structure):
+    _fields_ = [("rank", C.c_int), ("nranks", C.c_int), ("allreduce", ALLREDUCE_FN), ("ctx", C.c_void_p)]
 
 
 class Info(C.Structure):
@@ -103,6 +111,14 @@ def load(path: Optional[os.PathLike] = None) -> C.CDLL:
     lib.hikf_spd_inverse_noalloc.argtypes = [vp, C.c_int, vp, vp]
     lib.hikf_h2_qht.argtypes = [C.c_int, C.c_int64, dp, Kernel, C.c_int, ip, ip, dp, C.POINTER(Options), dp]
     lib.hikf_test_set_wait_limit.argtypes = [C.c_uint64]
+    lib.hikf_create_shard.argtypes = [C.POINTER(H), C.POINTER(Shard), C.c_int, C.c_int64, dp, Kernel, C.c_int, ip, ip,
+                                      dp, dp, dp, Kernel, C.POINTER(Options)]
+    lib.hikf_shard_rows.argtypes = [H, ip, ip]
+    lib.hikf_shard_caller_index.argtypes = [H, ip]
+    lib.hikf_shard_step_begin.argtypes = [H, vp, vp]
+    lib.hikf_shard_step_end.argtypes = [H, vp]
+    lib.hikf_shard_get_mean.argtypes = [H, dp]
+    lib.hikf_shard_get_variance.argtypes = [H, dp]
     lib.hikf_step.argtypes = [H]
     lib.hikf_step.restype = C.c_int64
     for nm in EXPORTED:

@@ -181,6 +181,13 @@ struct hikf_handle {
   bool dead = false;
   double cond_s = 0.0;       // estimate of cond(S_t) (hikf_info)
   bool qht_only = false;     // hikf_h2_qht: the H^2 product only, no filter state
+  // row sharding (hikf_create_shard): the state holds the rank's rows [r0, r0 + m) of m_full
+  bool shard = false;
+  hikf_shard sh = {0, 1, nullptr, nullptr};
+  int64_t r0 = 0, m_full = 0;
+  hikf::SparseH Hfull;       // H over all m_full points (the H^2 product); H: the rank's columns
+  const double* hx_ext = nullptr;  // step part 2: the summed H x_t
+  double* yzero = nullptr;   // n zeros (the partial H x through the innovation kernel)
   // dense R = L L^T: the filter runs on L^{-1} y, L^{-1} H and R = I (hikf_create_dense_r)
   bool whiten = false;
   double* Linv = nullptr;    // n x n, L^{-1}
@@ -378,6 +385,23 @@ Status factor_cond(const double* dS, int n, double* scratch, cudaStream_t s, dou
   return Status::Ok();
 }
 
+// The H^2 product into dst (the handle's rows, m x ld). A shard forms it for all m_full rows
+// (H is replicated, so every rank has every source) and keeps its own rows.
+template <typename T>
+Status h2_rows(hikf_t* h, const hikf::FmmParams& fp, T* dst, int ld, cudaStream_t s) {
+  if (!h->shard) return hikf::h2_product<T>(h->tree, h->Hfull, fp, dst, ld, s);
+  T* full = nullptr;
+  HIKF_CUDA(cudaMallocAsync((void**)&full, sizeof(T) * (size_t)h->m_full * ld, s));
+  Status st = hikf::h2_product<T>(h->tree, h->Hfull, fp, full, ld, s);
+  if (st.ok()) {
+    cudaError_t e = cudaMemcpyAsync(dst, full + (size_t)h->r0 * ld, sizeof(T) * (size_t)h->m * ld,
+                                    cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) st = hikf::cuda_status(e, "shard rows", __FILE__, __LINE__);
+  }
+  cudaFreeAsync(full, s);
+  return st;
+}
+
 template <typename T>
 Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const double* x0, const double* cq,
                    const double* c0, const double* r_diag, const double* r_full, int chain_opt, int form_opt) {
@@ -408,7 +432,7 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
     fp.theta = q.theta;
     fp.length = q.length;
     fp.shape = q.shape;
-    HIKF_TRY(hikf::h2_product<T>(h->tree, h->H, fp, CQ, ld, s));
+    HIKF_TRY(h2_rows<T>(h, fp, CQ, ld, s));
     if (h->qht_only) return Status::Ok();
     if (p0.theta == 0.0) {
       HIKF_CUDA(cudaMemsetAsync(C, 0, sizeof(T) * (size_t)m * ld, s));
@@ -431,7 +455,7 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
       f0.theta = p0.theta;
       f0.length = p0.length;
       f0.shape = p0.shape;
-      HIKF_TRY(hikf::h2_product<T>(h->tree, h->H, f0, C, ld, s));
+      HIKF_TRY(h2_rows<T>(h, f0, C, ld, s));
     }
   }
   // dense R = L L^T: C_Q <- C_Q L^{-T}, C_0 <- C_0 L^{-T}; from here on the filter runs with
@@ -483,7 +507,19 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
   HIKF_TRY(hikf::arena_alloc(h->arena, &h->x, m));
   HIKF_TRY(hikf::arena_alloc(h->arena, &h->var, m));
   HIKF_TRY(hikf::arena_alloc(h->arena, &h->outbuf, m));
-  if (x0) {
+  if (h->shard) {
+    // x_0 of all points in tree order, then the rank's rows
+    double *xc = nullptr, *xt = nullptr;
+    const int64_t mf = h->m_full;
+    HIKF_CUDA(cudaMallocAsync((void**)&xc, sizeof(double) * mf, s));
+    HIKF_CUDA(cudaMallocAsync((void**)&xt, sizeof(double) * mf, s));
+    if (x0) HIKF_CUDA(cudaMemcpyAsync(xc, x0, sizeof(double) * mf, cudaMemcpyHostToDevice, s));
+    hikf::vec_to_tree<<<hikf::nblk(mf, 256), 256, 0, s>>>(x0 ? xc : nullptr, h->tree.perm, mf, xt);
+    HIKF_LAUNCH_CHECK("vec_to_tree");
+    HIKF_CUDA(cudaMemcpyAsync(h->x, xt + h->r0, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+    HIKF_CUDA(cudaFreeAsync(xc, s));
+    HIKF_CUDA(cudaFreeAsync(xt, s));
+  } else if (x0) {
     HIKF_CUDA(cudaMemcpyAsync(h->outbuf, x0, sizeof(double) * m, cudaMemcpyHostToDevice, s));
     hikf::vec_to_tree<<<hikf::nblk(m, 256), 256, 0, s>>>(h->outbuf, h->tree.perm, m, h->x);
   } else {
@@ -500,19 +536,24 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
   HIKF_TRY(hikf::arena_alloc(h->arena, &h->S, (size_t)n * n));
   HIKF_CUDA(cudaMemcpyAsync(h->rd, r_diag, sizeof(double) * n, cudaMemcpyHostToDevice, s));
   double *hcq = nullptr, *a1 = nullptr, *zero = nullptr;
-  HIKF_CUDA(cudaMallocAsync((void**)&hcq, sizeof(double) * (size_t)n * n, s));
-  HIKF_CUDA(cudaMallocAsync((void**)&a1, sizeof(double) * (size_t)n * n, s));
+  HIKF_CUDA(cudaMallocAsync((void**)&hcq, sizeof(double) * 2 * (size_t)n * n, s));  // [H C_Q | H C_1]
+  a1 = hcq + (size_t)n * n;
   HIKF_CUDA(cudaMallocAsync((void**)&zero, sizeof(double) * n, s));
   HIKF_CUDA(cudaMemsetAsync(zero, 0, sizeof(double) * n, s));
   HIKF_TRY(hikf::launch_gather_hc<T>(h->H, CQ, ld, hcq, 0, s));
-  HIKF_TRY(whiten_nn(hcq));
-  HIKF_TRY(hikf::launch_form_s(hcq, zero, n, h->hcq_sym, s));
   HIKF_TRY(hikf::launch_gather_hc<T>(h->H, C, ld, a1, 0, s));
   HIKF_TRY(hikf::launch_gather_hc<T>(h->H, CQ, ld, a1, 1, s));
+  if (h->shard && h->sh.nranks > 1) {
+    // the sums over the ranks' rows of H C_Q and H C_1 (the only create-time exchange)
+    HIKF_CUDA(cudaStreamSynchronize(s));
+    if (h->sh.allreduce(hcq, 2 * (int64_t)n * n, h->sh.ctx) != 0)
+      return hikf::make_status(HIKF_ECUDA, "the caller's allreduce failed");
+  }
+  HIKF_TRY(whiten_nn(hcq));
+  HIKF_TRY(hikf::launch_form_s(hcq, zero, n, h->hcq_sym, s));
   HIKF_TRY(whiten_nn(a1));
   HIKF_TRY(hikf::launch_form_s(a1, h->rd, n, h->S, s));
   HIKF_CUDA(cudaFreeAsync(hcq, s));
-  HIKF_CUDA(cudaFreeAsync(a1, s));
   HIKF_CUDA(cudaFreeAsync(zero, s));
 
   // chain scratch
@@ -643,7 +684,22 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
 }
 
 // e = y - H x; with a dense R, e = L^{-1} (y - H x) (the innovation of the whitened measurements)
+// e = y - H x from the ranks' summed H x (sharded filter, step part 2)
+__global__ void external_innovation_kernel(const double* __restrict__ y, const double* __restrict__ hx, int n,
+                                           double* __restrict__ e, int* __restrict__ flag) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const double yv = y[r];
+  if (!isfinite(yv)) atomicOr(flag, 1);
+  e[r] = yv - hx[r];
+}
+
 Status innovation(hikf_t* h, cudaStream_t s) {
+  if (h->hx_ext) {
+    external_innovation_kernel<<<hikf::nblk(h->n, 256), 256, 0, s>>>(h->ybuf, h->hx_ext, h->n, h->e, h->flag);
+    HIKF_LAUNCH_CHECK("external_innovation");
+    return Status::Ok();
+  }
   if (!h->whiten) return hikf::launch_innovation(h->ybuf, h->H, h->x, h->e, h->flag, s);
   HIKF_TRY(hikf::launch_innovation(h->ybuf, h->H, h->x, h->eraw, h->flag, s));
   return hikf::launch_whiten_vec(h->Linv, h->eraw, h->n, h->e, s);
@@ -834,10 +890,60 @@ Status flag_status(int f) {
   return Status::Ok();
 }
 
+__global__ void iota_kernel(int64_t* __restrict__ a, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = i;
+}
+
+// The rank's rows [r0, r1) of the tree order (a balanced split) and H restricted to them
+// (columns renumbered from r0): the state, the gathers and the innovation of the shard use
+// this H; the H^2 product keeps the full one.
+Status make_shard(hikf_t* h, const hikf_shard& sh) {
+  cudaStream_t s = h->stream;
+  const int64_t m = h->m, n = h->n;
+  const int64_t r0 = m * sh.rank / sh.nranks, r1 = m * (sh.rank + 1) / sh.nranks;
+  const int64_t nnz = h->Hfull.nnz;
+  std::vector<int64_t> rp(n + 1);
+  std::vector<int32_t> cl(std::max<int64_t>(nnz, 1));
+  std::vector<double> vl(std::max<int64_t>(nnz, 1));
+  HIKF_CUDA(cudaMemcpyAsync(rp.data(), h->Hfull.rowptr, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, s));
+  if (nnz > 0) {
+    HIKF_CUDA(cudaMemcpyAsync(cl.data(), h->Hfull.col, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost, s));
+    HIKF_CUDA(cudaMemcpyAsync(vl.data(), h->Hfull.val, sizeof(double) * nnz, cudaMemcpyDeviceToHost, s));
+  }
+  HIKF_CUDA(cudaStreamSynchronize(s));
+  std::vector<int64_t> lrp(n + 1, 0), lcl;
+  std::vector<double> lvl;
+  for (int64_t r = 0; r < n; ++r) {
+    for (int64_t k = rp[r]; k < rp[r + 1]; ++k)
+      if (cl[k] >= r0 && cl[k] < r1) {
+        lcl.push_back(cl[k] - r0);
+        lvl.push_back(vl[k]);
+      }
+    lrp[r + 1] = (int64_t)lcl.size();
+  }
+  hikf::Tree local;  // the identity order over the rank's rows
+  local.m = r1 - r0;
+  HIKF_TRY(hikf::arena_alloc(h->arena, &local.iperm, local.m));
+  iota_kernel<<<hikf::nblk(local.m, 256), 256, 0, s>>>(local.iperm, local.m);
+  HIKF_LAUNCH_CHECK("iota");
+  HIKF_TRY(hikf::build_sparse(h->H, h->arena, local, lrp.data(), lcl.data(), lvl.data(), (int)n, s));
+  HIKF_TRY(hikf::arena_alloc(h->arena, &h->yzero, n));
+  HIKF_CUDA(cudaMemsetAsync(h->yzero, 0, sizeof(double) * n, s));
+  h->shard = true;
+  h->sh = sh;
+  h->r0 = r0;
+  h->m_full = m;
+  h->m = r1 - r0;
+  h->use_graph = false;  // the step is split around the caller's exchange
+  return Status::Ok();
+}
+
 hikf_status create_impl(hikf_t** out, int dim, int64_t m, const double* points, hikf_kernel q, int n,
                         const int64_t* rowptr, const int64_t* col, const double* val, const double* r_diag,
                         const double* x0, hikf_kernel p0, const double* cq, const double* c0,
-                        const hikf_options* opt, const double* r_full = nullptr, bool qht_only = false) {
+                        const hikf_options* opt, const double* r_full = nullptr, bool qht_only = false,
+                        const hikf_shard* shard = nullptr) {
   auto t0 = std::chrono::steady_clock::now();
   if (!out) return fail(nullptr, hikf::make_status(HIKF_EINVAL, "out is NULL"));
   *out = nullptr;
@@ -867,6 +973,15 @@ hikf_status create_impl(hikf_t** out, int dim, int64_t m, const double* points, 
   st = validate_kernel(p0, true, true, qht_only);
   if (!st.ok()) return fail(nullptr, st);
   if (cq && !c0) return fail(nullptr, hikf::make_status(HIKF_EINVAL, "c0 is NULL"));
+  if (shard) {
+    if (shard->nranks < 1 || shard->rank < 0 || shard->rank >= shard->nranks)
+      return fail(nullptr, hikf::make_status(HIKF_EINVAL, "shard rank / nranks out of range"));
+    if (shard->nranks > 1 && !shard->allreduce)
+      return fail(nullptr, hikf::make_status(HIKF_EINVAL, "a sharded filter over several ranks needs allreduce"));
+    if (o.form == HIKF_FORM_NSPACE)
+      return fail(nullptr, hikf::make_status(HIKF_EINVAL, "the n-space form is not sharded"));
+    if (shard->nranks > m) return fail(nullptr, hikf::make_status(HIKF_EINVAL, "more ranks than points"));
+  }
   if (o.precision == HIKF_PREC_MIXED && o.form == HIKF_FORM_CROSS && hikf::padded_ld(n) > 256)
     return fail(nullptr, hikf::make_status(HIKF_EINVAL, "the tensor-core sweep (MIXED, cross form) supports n <= 256"));
   hikf_t* h = new (std::nothrow) hikf_handle();
@@ -912,6 +1027,11 @@ hikf_status create_impl(hikf_t** out, int dim, int64_t m, const double* points, 
   if (!st.ok()) return bail(st);
   st = hikf::build_sparse(h->H, h->arena, h->tree, rowptr, col, val, n, h->stream);
   if (!st.ok()) return bail(st);
+  h->Hfull = h->H;
+  if (shard) {
+    st = make_shard(h, *shard);
+    if (!st.ok()) return bail(st);
+  }
   st = h->fp64() ? setup_state<double>(h, q, p0, x0, cq, c0, r_diag, r_full, o.chain, o.form)
                  : setup_state<float>(h, q, p0, x0, cq, c0, r_diag, r_full, o.chain, o.form);
   if (!st.ok()) return bail(st);
@@ -954,6 +1074,75 @@ hikf_status hikf_create_dense_r(hikf_t** out, int dim, int64_t m, const double* 
                      r_full);
 }
 
+hikf_status hikf_create_shard(hikf_t** out, const hikf_shard* shard, int dim, int64_t m, const double* points,
+                              hikf_kernel q, int n, const int64_t* h_rowptr, const int64_t* h_col,
+                              const double* h_val, const double* r_diag, const double* x0, hikf_kernel p0,
+                              const hikf_options* opt) {
+  if (!shard) return fail(nullptr, hikf::make_status(HIKF_EINVAL, "shard is NULL"));
+  return create_impl(out, dim, m, points, q, n, h_rowptr, h_col, h_val, r_diag, x0, p0, nullptr, nullptr, opt,
+                     nullptr, false, shard);
+}
+
+hikf_status hikf_shard_rows(const hikf_t* h, int64_t* first, int64_t* count) {
+  if (!h || !first || !count) return HIKF_EINVAL;
+  *first = h->shard ? h->r0 : 0;
+  *count = h->m;
+  return HIKF_OK;
+}
+
+hikf_status hikf_shard_caller_index(hikf_t* h, int64_t* out) {
+  if (!h || !out) return HIKF_EINVAL;
+  cudaError_t e = cudaMemcpyAsync(out, h->tree.perm + h->r0, sizeof(int64_t) * h->m, cudaMemcpyDeviceToHost,
+                                  h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return fail(h, hikf::cuda_status(e, "shard caller index", __FILE__, __LINE__));
+  return HIKF_OK;
+}
+
+hikf_status hikf_shard_step_begin(hikf_t* h, const double* d_y, double* d_hx) {
+  if (!h || !d_y || !d_hx) return h ? fail(h, hikf::make_status(HIKF_EINVAL, "null pointer")) : HIKF_EINVAL;
+  if (!h->shard) return fail(h, hikf::make_status(HIKF_ESTATE, "not a sharded filter"));
+  hikf_status dead_code;
+  if (refuse_dead(h, &dead_code)) return dead_code;
+  cudaError_t e = cudaMemcpyAsync(h->ybuf, d_y, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, h->stream);
+  if (e != cudaSuccess) return fail(h, hikf::cuda_status(e, "copy y", __FILE__, __LINE__));
+  // H_r x_r = -(0 - H_r x_r) through the innovation kernel over the rank's columns
+  Status st = hikf::launch_innovation(h->yzero, h->H, h->x, d_hx, h->flag, h->stream);
+  if (st.ok()) {
+    hikf::scale_kernel<double><<<hikf::nblk((h->n + 1) / 2, 256), 256, 0, h->stream>>>(d_hx, d_hx, h->n, -1.0);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) st = hikf::cuda_status(e, "scale", __FILE__, __LINE__);
+  }
+  if (!st.ok()) return fail(h, st);
+  return HIKF_OK;
+}
+
+hikf_status hikf_shard_step_end(hikf_t* h, const double* d_hx) {
+  if (!h || !d_hx) return h ? fail(h, hikf::make_status(HIKF_EINVAL, "d_hx is NULL")) : HIKF_EINVAL;
+  if (!h->shard) return fail(h, hikf::make_status(HIKF_ESTATE, "not a sharded filter"));
+  hikf_status dead_code;
+  if (refuse_dead(h, &dead_code)) return dead_code;
+  h->hx_ext = d_hx;
+  Status st = enqueue(h);
+  h->hx_ext = nullptr;
+  if (!st.ok()) return fail(h, st);
+  return HIKF_OK;
+}
+
+static hikf_status shard_vec(hikf_t* h, const double* src, double* out) {
+  if (!h || !out) return HIKF_EINVAL;
+  if (!h->shard) return fail(h, hikf::make_status(HIKF_ESTATE, "not a sharded filter"));
+  hikf_status dead_code;
+  if (refuse_dead(h, &dead_code)) return dead_code;
+  cudaError_t e = cudaMemcpyAsync(out, src, sizeof(double) * h->m, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return fail(h, hikf::cuda_status(e, "shard output", __FILE__, __LINE__));
+  return HIKF_OK;
+}
+
+hikf_status hikf_shard_get_mean(hikf_t* h, double* out) { return shard_vec(h, h ? h->x : nullptr, out); }
+hikf_status hikf_shard_get_variance(hikf_t* h, double* out) { return shard_vec(h, h ? h->var : nullptr, out); }
+
 hikf_status hikf_create_with_cq(hikf_t** out, int dim, int64_t m, const double* points, hikf_kernel q, int n,
                                 const int64_t* h_rowptr, const int64_t* h_col, const double* h_val,
                                 const double* r_diag, const double* x0, hikf_kernel p0, const double* cq,
@@ -964,6 +1153,7 @@ hikf_status hikf_create_with_cq(hikf_t** out, int dim, int64_t m, const double* 
 
 hikf_status hikf_assimilate(hikf_t* h, const double* y) {
   if (!h || !y) return h ? fail(h, hikf::make_status(HIKF_EINVAL, "y is NULL")) : HIKF_EINVAL;
+  if (h->shard) return fail(h, hikf::make_status(HIKF_ESTATE, "a sharded filter: hikf_shard_step_begin / _end"));
   hikf_status dead_code;
   if (refuse_dead(h, &dead_code)) return dead_code;
   for (int r = 0; r < h->n; ++r)
@@ -986,6 +1176,7 @@ hikf_status hikf_assimilate(hikf_t* h, const double* y) {
 
 hikf_status hikf_assimilate_device(hikf_t* h, const double* d_y) {
   if (!h || !d_y) return h ? fail(h, hikf::make_status(HIKF_EINVAL, "d_y is NULL")) : HIKF_EINVAL;
+  if (h->shard) return fail(h, hikf::make_status(HIKF_ESTATE, "a sharded filter: hikf_shard_step_begin / _end"));
   hikf_status dead_code;
   if (refuse_dead(h, &dead_code)) return dead_code;
   cudaError_t e = cudaMemcpyAsync(h->ybuf, d_y, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, h->stream);
@@ -1009,6 +1200,7 @@ hikf_status hikf_sync(hikf_t* h) {
 
 static hikf_status get_vec(hikf_t* h, const double* src, double* out, bool device) {
   if (!h || !out) return h ? fail(h, hikf::make_status(HIKF_EINVAL, "out is NULL")) : HIKF_EINVAL;
+  if (h->shard) return fail(h, hikf::make_status(HIKF_ESTATE, "a sharded filter: hikf_shard_get_mean / _variance"));
   hikf_status dead_code;
   if (refuse_dead(h, &dead_code)) return dead_code;
   Status fs = form_outputs(h);
@@ -1034,6 +1226,7 @@ hikf_status hikf_get_variance_device(hikf_t* h, double* d_out) {
 
 static hikf_status get_mat(hikf_t* h, const void* src, double* out) {
   if (!h || !out) return h ? fail(h, hikf::make_status(HIKF_EINVAL, "out is NULL")) : HIKF_EINVAL;
+  if (h->shard) return fail(h, hikf::make_status(HIKF_ESTATE, "not available on a sharded filter"));
   double* d = nullptr;
   const size_t bytes = sizeof(double) * (size_t)h->m * h->n;
   cudaError_t e = cudaMallocAsync((void**)&d, bytes, h->stream);
