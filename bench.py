@@ -416,6 +416,49 @@ def main():
                 "clocks": clk.summary(wall0, wall1) if clk else None, "info": f.info(),
                 "mean": f.mean(), "var": f.variance()}
 
+    def batch_compare(count, side=256):
+        """`count` filters of m = side^2 (n rays each, exponential kernel L = side/16), stepped
+        in rounds of one update each: as one hikf_assimilate_batch per round (their tensor-core
+        sweeps in one launch) and as one hikf_assimilate_device per filter (a sweep launch each,
+        on the filters' own streams). Wall time between full device synchronisations."""
+        L = side / 16.0
+        ws = [W.make(grid=(side, side), n=n, q=W.KernelSpec(W.EXP, 0.01, L), p0=W.KernelSpec(W.EXP, 1.0, L),
+                     r=1e-3, steps=1, seed=900 + i, name=f"batch{i}") for i in range(count)]
+        fs = [binding.Filter.from_workload(wi, cheb_order=args.order, precision="mixed") for wi in ws]
+        dYs = [torch.tensor(W.measurements(wi, steps=8)[0], dtype=torch.float64, device="cuda") for wi in ws]
+        rounds = max(50, args.steps // 4)
+        out = {"filters": count, "m_each": side * side, "n": n, "rounds": rounds, "unit": "filter-steps/s"}
+        try:
+            for mode in ("batched", "one_by_one"):
+                def rnd(t):
+                    if mode == "batched":
+                        binding.assimilate_batch(fs, [d[t % 8] for d in dYs])
+                    else:
+                        for fi, d in zip(fs, dYs):
+                            fi.assimilate_device(d[t % 8])
+                for t in range(max(3, args.warmup)):
+                    rnd(t)
+                for fi in fs:
+                    fi.sync()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for t in range(rounds):
+                    rnd(t)
+                for fi in fs:
+                    fi.sync()
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                out[mode] = {"value": count * rounds / dt, "ms_per_round": 1e3 * dt / rounds,
+                             "hbm_gbs_sweep_bytes": count * (12.0 * side * side * n + 24.0 * side * side) * rounds
+                             / dt / 1e9}
+        finally:
+            for fi in fs:
+                fi.close()
+        out["note"] = ("a round is one update of every filter; hbm_gbs_sweep_bytes = the sweeps' algorithmic "
+                       "bytes (12 m n + 24 m per filter) / wall time per round, all other kernels of the "
+                       "round included in the time")
+        return out
+
     head = timed(args.precision, "cross", clocks=True, barrier=True)
     f = head["f"]
     info = head["info"]
@@ -558,21 +601,37 @@ def main():
                          "method": "per-step time with outputs minus per-step time without"},
         }
         line["err_vs_oracle"]["fp32_nspace"] = err_vs_oracle("fp32", "nspace")
+        if args.precision == "mixed":
+            comps["mixed_batch16"] = batch_compare(16)
         line["compare"] = comps
 
     if rank == 0 and world == 1 and args.serve_seconds > 0:
         # served step latency: 64 monitoring streams (log-uniform m from 4096 to 2^20, n in
-        # {16..256}), Poisson arrivals at 500/s in total, HBM budget 150 GB
+        # {16..256}), Poisson arrivals at 500/s in total, HBM budget 150 GB; then the same
+        # streams at an offered rate the server cannot keep up with (saturation), with
+        # streams departing and new ones arriving through the admission queue
         from paper_1404_3816_gb300 import serve
-        sv = serve.run_serving(serve.serving_streams(64), rate=500.0, seconds=args.serve_seconds,
-                               budget_bytes=150 * 10**9, precision=args.precision, form="cross")
-        line["serving"] = {"p50_ms": sv["p50_ms"], "p99_ms": sv["p99_ms"], "mean_ms": sv["mean_ms"],
-                           "steps": sv["steps"], "steps_per_s": sv["steps_per_s"], "seconds": sv["seconds"],
-                           "rate_per_s": sv["rate_per_s"], "streams": sv["streams"], "admitted": sv["admitted"],
-                           "rejected": sv["rejected"], "hbm_reserved_gb": sv["hbm_reserved_gb"],
-                           "create_s_all": sv["create_s_all"],
-                           "workload": "64 streams, side log-uniform 64..1024, n in {16,32,64,128,256}, "
-                                       "exp L=side/16, R=1e-3 I, Poisson 500/s, budget 150 GB"}
+
+        def serving(rate, churn, seconds, batch=True):
+            sv = serve.run_serving(serve.serving_streams(64 + (16 if churn else 0)), rate=rate,
+                                   seconds=seconds, budget_bytes=150 * 10**9, precision=args.precision,
+                                   form="cross", active=64, churn_per_s=churn, batch=batch)
+            keep = ("p50_ms", "p99_ms", "mean_ms", "steps", "offered", "steps_per_s", "seconds", "rate_per_s",
+                    "streams", "active", "arrived", "departed", "admitted", "waiting", "rejected", "failed", "failures",
+                    "hbm_reserved_gb",
+                    "create_wall_s", "create_ms_p50", "create_ms_max")
+            return {k: sv[k] for k in keep}
+
+        line["serving"] = serving(500.0, 0.0, args.serve_seconds)
+        line["serving"]["workload"] = ("64 streams, side log-uniform 64..1024, n in {16,32,64,128,256}, "
+                                       "exp L=side/16, R=1e-3 I, Poisson 500/s, budget 150 GB; each round of "
+                                       "updates one hikf_assimilate_batch (grouped tensor-core sweeps)")
+        line["serving_saturated"] = serving(20000.0, 1.0, args.serve_seconds / 2)
+        line["serving_saturated"]["workload"] = ("the same 64 streams plus 16 arriving ones, offered 20000/s "
+                                                 "(beyond the device's rate), one departure + arrival per s")
+        line["serving_saturated_unbatched"] = serving(20000.0, 1.0, args.serve_seconds / 2, batch=False)
+        line["serving_saturated_unbatched"]["workload"] = ("as serving_saturated, each update its own "
+                                                           "hikf_assimilate_device (one sweep launch per stream)")
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dt, how = oracle_step_time(w, 30.0, 3)

@@ -232,6 +232,27 @@ hikf_status hikf_assimilate(hikf_t* h, const double* y);
  */
 hikf_status hikf_assimilate_device(hikf_t* h, const double* d_y);
 
+/*
+ * hikf_assimilate_batch — one step of each of `count` filters (Alg. 2 per filter, each
+ * with its own y: d_y[i], DEVICE memory, n_i FP64 of filter hs[i]), enqueued without
+ * waiting. The tensor-core sweeps (the O(m n^2) update of C, x and delta^2) of the filters
+ * in MIXED precision and the cross-covariance or spectral form run as ONE launch per MMA
+ * width (n_t = 128 or 256) over the row tiles of all of them, so that many small filters
+ * fill the SMs together; the rest of each step runs on the filter's own stream, and the
+ * other filters take their ordinary step (hikf_assimilate_device). Every filter's result
+ * is bit-identical to hikf_assimilate_device with the same y. The filters' streams are
+ * ordered against the shared launch by events (it runs on the first grouped filter's
+ * stream); each handle's stream has passed its step once hikf_sync of that handle returns.
+ * Errors inside a step are per filter and reported as for hikf_assimilate_device; a
+ * timed-out wait in a shared launch marks every filter of that launch (HIKF_ETIMEOUT, then
+ * HIKF_ESTATE). The sweep timing of hikf_profile_enable does not cover a shared launch.
+ * Argument errors (count < 0, a NULL pointer, a handle twice, a sharded or dead handle)
+ * return before anything is enqueued. The message of any failure is given by
+ * hikf_last_error(NULL) (and by the handle it concerns). hs and d_y are read during the
+ * call only.
+ */
+hikf_status hikf_assimilate_batch(hikf_t* const* hs, const double* const* d_y, int count);
+
 /* Wait for the handle's stream; return and clear a latched step error. */
 hikf_status hikf_sync(hikf_t* h);
 

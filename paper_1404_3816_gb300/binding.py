@@ -36,7 +36,8 @@ EXPORTED = ["hikf_options_default", "hikf_create", "hikf_create_dense_r", "hikf_
             "hikf_get_perm", "hikf_info", "hikf_step", "hikf_stream", "hikf_last_error", "hikf_destroy", "hikf_h2_qht",
             "hikf_profile_enable", "hikf_profile_read", "hikf_spd_inverse", "hikf_spd_inverse_noalloc",
             "hikf_test_set_wait_limit", "hikf_create_shard", "hikf_shard_rows", "hikf_shard_caller_index",
-            "hikf_shard_step_begin", "hikf_shard_step_end", "hikf_shard_get_mean", "hikf_shard_get_variance"]
+            "hikf_shard_step_begin", "hikf_shard_step_end", "hikf_shard_get_mean", "hikf_shard_get_variance",
+            "hikf_assimilate_batch"]
 
 # hikf_allreduce_fn: int (*)(double* d_buf, int64_t count, void* ctx)
 ALLREDUCE_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int64, C.c_void_p)
@@ -92,6 +93,7 @@ def load(path: Optional[os.PathLike] = None) -> C.CDLL:
                                         dp, Kernel, dp, dp, C.POINTER(Options)]
     lib.hikf_assimilate.argtypes = [H, dp]
     lib.hikf_assimilate_device.argtypes = [H, vp]
+    lib.hikf_assimilate_batch.argtypes = [C.POINTER(H), C.POINTER(vp), C.c_int]
     lib.hikf_sync.argtypes = [H]
     for nm in ("hikf_get_mean", "hikf_get_variance", "hikf_get_cq", "hikf_get_cross"):
         getattr(lib, nm).argtypes = [H, dp]
@@ -365,6 +367,18 @@ class Filter:
     @property
     def stream(self) -> int:
         return int(load().hikf_stream(self.h) or 0)
+
+
+def assimilate_batch(filters, d_ys) -> None:
+    """One step of each filter (filters[i] takes d_ys[i]: a CUDA tensor of its n float64),
+    asynchronous: the MIXED tensor-core sweeps of all of them in one launch per MMA width
+    (hikf_assimilate_batch); each filter's result is that of filters[i].assimilate_device."""
+    k = len(filters)
+    if len(d_ys) != k:
+        raise HikfError(HIKF_EINVAL, f"{k} filters, {len(d_ys)} measurement vectors")
+    hs = (C.c_void_p * max(k, 1))(*[f.h for f in filters])
+    ys = (C.c_void_p * max(k, 1))(*[_device_f64(y, (f.n,), "y", f.device) for f, y in zip(filters, d_ys)])
+    _check(load().hikf_assimilate_batch(hs, ys, k), None)  # the message: hikf_last_error(NULL)
 
 
 def h2_qht(points, kernel, h_rowptr, h_col, h_val, **opts) -> np.ndarray:

@@ -202,6 +202,8 @@ struct hikf_handle {
   cudaGraphExec_t graph_exec = nullptr;
   cudaEvent_t gev[2] = {nullptr, nullptr};
   cudaGraphNode_t gnode[2] = {nullptr, nullptr};
+  cudaGraphExec_t gpart[2] = {nullptr, nullptr};  // the step before / after a grouped sweep
+  cudaEvent_t bev = nullptr;  // orders this handle's stream against a grouped sweep
   bool capturing = false;  // event records become graph event-record nodes
   // sweep timing (hikf_profile_enable)
   bool prof = false;
@@ -677,6 +679,7 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
     HIKF_TRY(hikf::arena_alloc(h->arena, &tc.cqmax, m));
     HIKF_TRY(hikf::arena_alloc(h->arena, &tc.mmax, hikf::kAbsBlocks));
     HIKF_TRY(hikf::arena_alloc(h->arena, &tc.beta_exp, 1));
+    HIKF_TRY(hikf::arena_alloc(h->arena, &tc.vec32, (size_t)2 * tc.nt));
     HIKF_TRY(hikf::tc_init_rows(tc, (const float*)C, (const float*)CQ, m, ld, s));
   }
   if (wscr) HIKF_CUDA(cudaFreeAsync(wscr, s));
@@ -705,10 +708,36 @@ Status innovation(hikf_t* h, cudaStream_t s) {
   return hikf::launch_whiten_vec(h->Linv, h->eraw, h->n, h->e, s);
 }
 
-// One measurement update on the handle's stream. ev0/ev1 (may be null) bracket the sweep.
+// Parts of one update: the whole step, or the grouped sweep's halves (everything before
+// the tensor-core sweep, and everything after it).
+enum StepPart { kStepAll = 0, kStepPre = 1, kStepPost = 2 };
+
+// The tensor-core sweep's arguments of one handle (fixed pointers: the same every step)
+hikf::TcArgs tc_args(const hikf_t* h) {
+  hikf::TcArgs ta;
+  ta.m = h->m;
+  ta.ld = h->ld;
+  ta.n = h->n;
+  ta.C = (float*)h->C;
+  ta.a = h->a;
+  ta.rd = h->rd;
+  ta.theta = h->theta_q;
+  ta.x = h->x;
+  ta.var = h->var;
+  ta.flag = h->flag;
+  ta.err = h->flag + 2;
+  ta.beta_exp = h->tc.beta_exp;
+  return ta;
+}
+
+// Whether a handle's sweep can join a grouped launch (hikf_assimilate_batch): the MIXED
+// tensor-core sweep of the cross-covariance and spectral forms.
+bool groupable(const hikf_t* h) { return h->mixed() && !h->eigen && !h->nspace && !h->shard; }
+
+// One measurement update (or one part of it, see StepPart) on stream s. ev0/ev1 (may be
+// null) bracket the sweep.
 template <typename T>
-Status enqueue_step(hikf_t* h, cudaEvent_t ev0, cudaEvent_t ev1) {
-  cudaStream_t s = h->stream;
+Status enqueue_step(hikf_t* h, cudaEvent_t ev0, cudaEvent_t ev1, cudaStream_t s, int part) {
   hikf::ChainArgs& c = h->chain;
   int launches = 0;
   if (h->nspace) {
@@ -736,67 +765,62 @@ Status enqueue_step(hikf_t* h, cudaEvent_t ev0, cudaEvent_t ev1) {
     h->launches = 6;
     return Status::Ok();
   }
-  if (h->spectral) {
-    HIKF_TRY(innovation(h, s));
-    HIKF_TRY(hikf::spectral_gain<T>(h->sp, h->n, h->e, h->a, (T*)h->Msw, h->nt, h->flag, s));
-    launches += sizeof(T) == 4 ? 5 : 4;
-  } else {
-    HIKF_TRY(hikf::launch_chain(c, s));
-    launches += c.fp64 ? 1 : (2 + 3 * c.refine_iters + 3);
-    HIKF_TRY(innovation(h, s));
-    HIKF_TRY(hikf::launch_gemv<T>(c.Mh, c.Ml, c.M64, h->n, c.ldm, h->e, h->a, (T*)h->Msw, h->nt, h->flag, s));
-    launches += 2;
+  if (part != kStepPost) {
+    if (h->spectral) {
+      HIKF_TRY(innovation(h, s));
+      HIKF_TRY(hikf::spectral_gain<T>(h->sp, h->n, h->e, h->a, (T*)h->Msw, h->nt, h->flag, s));
+      launches += sizeof(T) == 4 ? 5 : 4;
+    } else {
+      HIKF_TRY(hikf::launch_chain(c, s));
+      launches += c.fp64 ? 1 : (2 + 3 * c.refine_iters + 3);
+      HIKF_TRY(innovation(h, s));
+      HIKF_TRY(hikf::launch_gemv<T>(c.Mh, c.Ml, c.M64, h->n, c.ldm, h->e, h->a, (T*)h->Msw, h->nt, h->flag, s));
+      launches += 2;
+    }
+    if (h->mixed()) {
+      HIKF_TRY(hikf::tc_pack(h->tc, (const float*)h->Msw, h->nt, h->n, h->a, h->rd, h->flag, s));
+      launches += 3;
+    }
+    if (part == kStepPre) {
+      h->launches = launches;
+      return Status::Ok();
+    }
+    if (ev0) HIKF_CUDA(cudaEventRecordWithFlags(ev0, s, h->capturing ? cudaEventRecordExternal : 0));
+    if (h->mixed()) {
+      HIKF_TRY(hikf::tc_sweep(h->tc, tc_args(h), h->sms, s));
+    } else {
+      hikf::SweepArgs<T> sa;
+      sa.m = h->m;
+      sa.ld = h->ld;
+      sa.n = h->n;
+      sa.CQ = (const T*)h->CQ;
+      sa.C = (T*)h->C;
+      sa.Msw = (const T*)h->Msw;
+      sa.a = h->a;
+      sa.rd = h->rd;
+      sa.theta = h->theta_q;
+      sa.x = h->x;
+      sa.var = h->var;
+      sa.flag = h->flag;
+      HIKF_TRY(hikf::launch_sweep<T>(sa, s, h->sms));
+    }
+    if (ev1) HIKF_CUDA(cudaEventRecordWithFlags(ev1, s, h->capturing ? cudaEventRecordExternal : 0));
+    launches += 1;
   }
-  hikf::SweepArgs<T> sa;
-  sa.m = h->m;
-  sa.ld = h->ld;
-  sa.n = h->n;
-  sa.CQ = (const T*)h->CQ;
-  sa.C = (T*)h->C;
-  sa.Msw = (const T*)h->Msw;
-  sa.a = h->a;
-  sa.rd = h->rd;
-  sa.theta = h->theta_q;
-  sa.x = h->x;
-  sa.var = h->var;
-  sa.flag = h->flag;
-  if (h->mixed()) {
-    HIKF_TRY(hikf::tc_pack(h->tc, (const float*)h->Msw, h->nt, h->n, h->flag, s));
-    launches += 3;
-  }
-  if (ev0) HIKF_CUDA(cudaEventRecordWithFlags(ev0, s, h->capturing ? cudaEventRecordExternal : 0));
-  if (h->mixed()) {
-    hikf::TcArgs ta;
-    ta.m = h->m;
-    ta.ld = h->ld;
-    ta.n = h->n;
-    ta.C = (float*)h->C;
-    ta.a = h->a;
-    ta.rd = h->rd;
-    ta.theta = h->theta_q;
-    ta.x = h->x;
-    ta.var = h->var;
-    ta.flag = h->flag;
-    ta.err = h->flag + 2;
-    ta.beta_exp = h->tc.beta_exp;
-    HIKF_TRY(hikf::tc_sweep(h->tc, ta, h->sms, s));
-  } else {
-    HIKF_TRY(hikf::launch_sweep<T>(sa, s, h->sms));
-  }
-  if (ev1) HIKF_CUDA(cudaEventRecordWithFlags(ev1, s, h->capturing ? cudaEventRecordExternal : 0));
   hikf::count_step<<<1, 1, 0, s>>>(h->flag, h->dstep);
   HIKF_LAUNCH_CHECK("count_step");
   if (h->spectral)
     HIKF_TRY(hikf::spectral_next(h->sp, h->n, h->flag, s));
   else
     HIKF_TRY(hikf::launch_recur(h->hcq_sym, h->rd, c.Mh, c.Ml, c.M64, h->n, c.ldm, h->flag, h->S, s));
-  launches += 3;
-  h->launches = launches;
+  launches += 2;
+  h->launches = part == kStepPost ? h->launches + launches : launches;
   return Status::Ok();
 }
 
-Status enqueue_direct(hikf_t* h, cudaEvent_t ev0, cudaEvent_t ev1) {
-  return h->fp64() ? enqueue_step<double>(h, ev0, ev1) : enqueue_step<float>(h, ev0, ev1);
+Status enqueue_direct(hikf_t* h, cudaEvent_t ev0, cudaEvent_t ev1, int part = kStepAll) {
+  return h->fp64() ? enqueue_step<double>(h, ev0, ev1, h->stream, part)
+                   : enqueue_step<float>(h, ev0, ev1, h->stream, part);
 }
 
 // The update as one CUDA graph, captured on first use (thread-local capture mode, so
@@ -832,6 +856,31 @@ Status build_graph(hikf_t* h) {
     if (ev == h->gev[1]) h->gnode[1] = nd;
   }
   if (!h->gnode[0] || !h->gnode[1]) return hikf::make_status(HIKF_ECUDA, "graph event nodes not found");
+  return Status::Ok();
+}
+
+// One half of a step around a grouped sweep (kStepPre / kStepPost) on the handle's stream,
+// as a CUDA graph captured on first use when the handle uses graphs.
+Status enqueue_part(hikf_t* h, int part) {
+  if (!h->use_graph) return enqueue_direct(h, nullptr, nullptr, part);
+  cudaGraphExec_t& ex = h->gpart[part - 1];
+  if (!ex) {
+    HIKF_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    h->capturing = true;
+    Status st = enqueue_direct(h, nullptr, nullptr, part);
+    h->capturing = false;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    if (!st.ok()) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (e != cudaSuccess) return hikf::cuda_status(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return hikf::cuda_status(e, "cudaGraphInstantiate", __FILE__, __LINE__);
+  }
+  HIKF_CUDA(cudaGraphLaunch(ex, h->stream));
   return Status::Ok();
 }
 
@@ -1186,6 +1235,96 @@ hikf_status hikf_assimilate_device(hikf_t* h, const double* d_y) {
   return HIKF_OK;
 }
 
+// An error of hikf_assimilate_batch: on the handle it concerns and for hikf_last_error(NULL)
+static hikf_status bfail(hikf_t* h, const Status& st) {
+  if (h) h->err = st.msg;
+  return hikf::set_global_error(st);
+}
+
+hikf_status hikf_assimilate_batch(hikf_t* const* hs, const double* const* d_y, int count) {
+  if (count < 0) return bfail(nullptr, hikf::make_status(HIKF_EINVAL, "count < 0"));
+  if (count == 0) return HIKF_OK;
+  if (!hs || !d_y) return bfail(nullptr, hikf::make_status(HIKF_EINVAL, "hs or d_y is NULL"));
+  for (int i = 0; i < count; ++i) {
+    hikf_t* h = hs[i];
+    if (!h) return bfail(nullptr, hikf::make_status(HIKF_EINVAL, "a handle of the batch is NULL"));
+    if (!d_y[i]) return bfail(h, hikf::make_status(HIKF_EINVAL, "d_y is NULL"));
+    if (h->shard) return bfail(h, hikf::make_status(HIKF_ESTATE, "a sharded filter: hikf_shard_step_begin / _end"));
+    hikf_status dead_code;
+    if (refuse_dead(h, &dead_code)) return dead_code;
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == h) return bfail(h, hikf::make_status(HIKF_EINVAL, "a handle appears twice in the batch"));
+  }
+  std::vector<hikf_t*> grp;
+  for (int i = 0; i < count; ++i) {
+    hikf_t* h = hs[i];
+    cudaError_t e = cudaMemcpyAsync(h->ybuf, d_y[i], sizeof(double) * h->n, cudaMemcpyDeviceToDevice, h->stream);
+    if (e != cudaSuccess) return bfail(h, hikf::cuda_status(e, "copy y", __FILE__, __LINE__));
+    if (groupable(h)) {
+      grp.push_back(h);
+      continue;
+    }
+    Status st = enqueue(h);  // its own step, as hikf_assimilate_device
+    if (!st.ok()) return bfail(h, st);
+  }
+  if (grp.empty()) return HIKF_OK;
+  if (grp.size() == 1) {  // nothing to group with
+    Status st = enqueue(grp[0]);
+    return st.ok() ? HIKF_OK : bfail(grp[0], st);
+  }
+  // the steps up to the sweep, each on its own stream; the sweeps run on the first
+  // handle's stream once all of those have finished
+  hikf_t* lead = grp[0];
+  for (hikf_t* h : grp) {
+    Status st = enqueue_part(h, kStepPre);
+    if (!st.ok()) return bfail(h, st);
+    cudaError_t e = h->bev ? cudaSuccess : cudaEventCreateWithFlags(&h->bev, cudaEventDisableTiming);
+    if (e == cudaSuccess && h != lead) {
+      e = cudaEventRecord(h->bev, h->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(lead->stream, h->bev, 0);
+    }
+    if (e != cudaSuccess) return bfail(h, hikf::cuda_status(e, "order the batch", __FILE__, __LINE__));
+  }
+  // one launch per MMA width n_t over the tiles of all its filters
+  for (int nt : {128, 256}) {
+    std::vector<hikf::TcItem> items;
+    int64_t tiles = 0;
+    for (hikf_t* h : grp) {
+      if (hikf::tc_nt(h->tc) != nt) continue;
+      hikf::TcItem it;
+      hikf::tc_item(h->tc, tc_args(h), &it);
+      it.tile0 = tiles;
+      tiles += hikf::tc_tiles(h->m);
+      items.push_back(it);
+    }
+    if (items.empty()) continue;
+    hikf::TcItem* d_items = nullptr;
+    const size_t bytes = sizeof(hikf::TcItem) * items.size();
+    cudaError_t e = cudaMallocAsync((void**)&d_items, bytes, lead->stream);
+    if (e == cudaSuccess)  // pageable source: staged before the call returns
+      e = cudaMemcpyAsync(d_items, items.data(), bytes, cudaMemcpyHostToDevice, lead->stream);
+    if (e != cudaSuccess) {
+      if (d_items) cudaFreeAsync(d_items, lead->stream);
+      return bfail(lead, hikf::cuda_status(e, "batch items", __FILE__, __LINE__));
+    }
+    Status st = hikf::tc_sweep_grouped(nt, d_items, (int)items.size(), tiles, lead->sms, lead->stream);
+    cudaFreeAsync(d_items, lead->stream);
+    if (!st.ok()) return bfail(lead, st);
+  }
+  cudaError_t e = cudaEventRecord(lead->bev, lead->stream);
+  if (e != cudaSuccess) return bfail(lead, hikf::cuda_status(e, "order the batch", __FILE__, __LINE__));
+  for (hikf_t* h : grp) {
+    if (h != lead) {
+      e = cudaStreamWaitEvent(h->stream, lead->bev, 0);
+      if (e != cudaSuccess) return bfail(h, hikf::cuda_status(e, "order the batch", __FILE__, __LINE__));
+    }
+    Status st = enqueue_part(h, kStepPost);
+    if (!st.ok()) return bfail(h, st);
+    ++h->enq;
+  }
+  return HIKF_OK;
+}
+
 hikf_status hikf_sync(hikf_t* h) {
   if (!h) return HIKF_EINVAL;
   hikf_status dead_code;
@@ -1368,6 +1507,9 @@ void hikf_destroy(hikf_t* h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
   if (h->graph) cudaGraphDestroy(h->graph);
+  for (auto& g : h->gpart)
+    if (g) cudaGraphExecDestroy(g);
+  if (h->bev) cudaEventDestroy(h->bev);
   for (auto& e : h->gev)
     if (e) cudaEventDestroy(e);
   h->arena.release();

@@ -283,6 +283,7 @@ __global__ void __launch_bounds__(kJacThreads) eig_jacobi_kernel(double* __restr
     }
     __syncthreads();
     converged = s_rot == 0;
+    __syncthreads();  // every thread has read s_rot before thread 0 resets it for the next sweep
   }
   if (blockIdx.x == 0 && tid == 0) {
     *info = converged ? 0 : 1;

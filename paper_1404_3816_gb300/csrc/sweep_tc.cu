@@ -34,6 +34,7 @@
 #include <cuda.h>
 #include <cuda_fp16.h>
 #include <math.h>
+#include <string.h>
 
 #include <algorithm>
 
@@ -88,7 +89,10 @@ __device__ __forceinline__ float two_sum(float a, float b, float& err) {
   return s;
 }
 
-template <int NT>
+// GROUPED: the tiles of several filters (args.items, in the order of their tile0) in one
+// launch; every role walks the same flat tile order and finds a tile's filter with a cursor.
+// A tile of a filter whose step was rejected is skipped by every role alike.
+template <int NT, bool GROUPED>
 __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_constant__ CUtensorMap tmC,
                                                           const __grid_constant__ CUtensorMap tmCQ,
                                                           const __grid_constant__ CUtensorMap tmCst, TcArgs args) {
@@ -97,7 +101,24 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (*args.flag) return;  // a rejected step is a no-op
+  if constexpr (!GROUPED) {
+    if (*args.flag) return;  // a rejected step is a no-op
+  }
+  const TcItem* its = args.items;
+  // the item of flat tile t (t never decreases along a role's cursor)
+  auto item_of = [&](int64_t t, int& s) {
+    if constexpr (GROUPED) {
+      while (s + 1 < args.nitems && t >= its[s + 1].tile0) ++s;
+    }
+  };
+  auto local_tile = [&](int64_t t, int s) -> int64_t {
+    if constexpr (GROUPED) return t - its[s].tile0;
+    return t;
+  };
+  auto skip = [&](int s) -> bool {
+    if constexpr (GROUPED) return *its[s].flag != 0;
+    return false;
+  };
 
   float* s_a = reinterpret_cast<float*>(smem + Lay::VecOff);
   float* s_r = s_a + NT;
@@ -117,10 +138,13 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
   const uint32_t red_full = acc_full + 24u;   // group 1's row partials written (4 warp arrivals)
   const uint32_t red_empty = acc_full + 32u;  // group 0 has read them (4 warp arrivals)
 
-  for (int j = threadIdx.x; j < NT; j += blockDim.x) {
-    s_a[j] = j < args.n ? (float)args.a[j] : 0.f;
-    s_r[j] = j < args.n ? (float)args.rd[j] : 0.f;
+  if constexpr (!GROUPED) {
+    for (int j = threadIdx.x; j < NT; j += blockDim.x) {
+      s_a[j] = j < args.n ? (float)args.a[j] : 0.f;
+      s_r[j] = j < args.n ? (float)args.rd[j] : 0.f;
+    }
   }
+  int* s_err = reinterpret_cast<int*>(s_tmem + 2);  // grouped: a wait timed out in this CTA
   if (threadIdx.x == 0) {
     for (int s = 0; s < kRawStages; ++s) {
       mbar_init(raw_full(s), 1);
@@ -140,6 +164,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
     mbar_init(red_full, 4);
     mbar_init(red_empty, 4);
     *s_abort = 0;
+    *s_err = 0;
     fence_barrier_init();
   }
   if (warp == 1) tmem_alloc(smem_u32(s_tmem), 512);
@@ -147,51 +172,69 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *s_tmem;
-  const int64_t ntiles = (args.m + kBM - 1) / kBM;
-  const int beta_exp = *args.beta_exp;
+  const int64_t ntiles = GROUPED ? args.ntiles_total : (args.m + kBM - 1) / kBM;
+  const int beta_exp0 = GROUPED ? 0 : *args.beta_exp;
   const unsigned long long wlim = args.wait_ns;
+  int* const errp = GROUPED ? s_err : args.err;  // a grouped launch reports to every item at the end
 
   if (warp == 0) {
     // ---------------- producer: raw tiles ----------------
     if (lane == 0) {
       int64_t j = 0;
+      int is = 0, fenced = -1;
       bool ok = true;
       for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        item_of(tile, is);
+        if (skip(is)) continue;
+        if constexpr (GROUPED) {
+          if (is != fenced) {
+            tensormap_acquire(&its[is].mapC);
+            tensormap_acquire(&its[is].mapCQ);
+            fenced = is;
+          }
+        }
+        const CUtensorMap* mC = GROUPED ? &its[is].mapC : &tmC;
+        const CUtensorMap* mCQ = GROUPED ? &its[is].mapCQ : &tmCQ;
+        const int row0 = (int)(local_tile(tile, is) * kBM);
         for (int kc = 0; kc < NK && ok; ++kc, ++j) {
           const int rs = (int)(j % kRawStages);
           const uint32_t rph = (uint32_t)((j / kRawStages) & 1);
-          ok = mbar_wait(raw_empty(rs), rph ^ 1u, args.err, s_abort, wlim);
+          ok = mbar_wait(raw_empty(rs), rph ^ 1u, errp, s_abort, wlim);
           if (!ok) break;
           const uint32_t rbase = smem_u32(smem + Lay::RawOff + rs * 2 * kRawBytes);
           mbar_expect_tx(raw_full(rs), 2 * kRawBytes);
-          tma_load_2d(rbase, &tmC, kc * kKC, (int)(tile * kBM), raw_full(rs));
-          tma_load_2d(rbase + kRawBytes, &tmCQ, kc * kKC, (int)(tile * kBM), raw_full(rs));
+          tma_load_2d(rbase, mC, kc * kKC, row0, raw_full(rs));
+          tma_load_2d(rbase + kRawBytes, mCQ, kc * kKC, row0, raw_full(rs));
         }
       }
       if (!ok) *s_abort = 1;
       // every copy this thread issued (j of them) has landed before the CTA may exit
-      drain_ring(raw_full(0), kRawStages, j, args.err);
+      drain_ring(raw_full(0), kRawStages, j, errp);
     }
   } else if (warp == 2) {
     // ---------------- producer: B images (its own warp, so the raw ring runs ahead of
     // the MMAs instead of in step with the B ring) ----------------
     if (lane == 0) {
       int64_t j = 0;
+      int is = 0;
       bool ok = true;
       for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        item_of(tile, is);
+        if (skip(is)) continue;
+        const __half* bimg = GROUPED ? its[is].bimg : args.bimg;
         for (int kc = 0; kc < NK && ok; ++kc, ++j) {
           const int bs = (int)(j % kBStages);
-          ok = mbar_wait(b_empty(bs), (uint32_t)(((j / kBStages) & 1) ^ 1), args.err, s_abort, wlim);
+          ok = mbar_wait(b_empty(bs), (uint32_t)(((j / kBStages) & 1) ^ 1), errp, s_abort, wlim);
           if (!ok) break;
           const uint32_t bbase = smem_u32(smem + Lay::BOff + bs * kPieces * Lay::BPiece);
           mbar_expect_tx(b_full(bs), kPieces * Lay::BPiece);
           for (int pc = 0; pc < kPieces; ++pc)
-            bulk_load(bbase + pc * Lay::BPiece, args.bimg + ((size_t)pc * NK + kc) * (Lay::BPiece / 2), Lay::BPiece,
+            bulk_load(bbase + pc * Lay::BPiece, bimg + ((size_t)pc * NK + kc) * (Lay::BPiece / 2), Lay::BPiece,
                       b_full(bs));
         }
       }
       if (!ok) *s_abort = 1;
-      drain_ring(b_full(0), kBStages, j, args.err);
+      drain_ring(b_full(0), kBStages, j, errp);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
@@ -199,14 +242,17 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
       const uint32_t idesc = (1u << 4) | ((uint32_t)(NT >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
       int as = 0, bs = 0;
       uint32_t aph = 0, bph = 0, eph = 0;
+      int is = 0;
       bool ok = true;
       for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        ok = mbar_wait(acc_empty, eph ^ 1u, args.err, s_abort, wlim);
+        item_of(tile, is);
+        if (skip(is)) continue;
+        ok = mbar_wait(acc_empty, eph ^ 1u, errp, s_abort, wlim);
         eph ^= 1u;
         if (!ok) break;
         tc_fence_after();
         for (int kc = 0; kc < NK && ok; ++kc) {
-          ok = mbar_wait(a_full(as), aph, args.err, s_abort, wlim) && mbar_wait(b_full(bs), bph, args.err, s_abort, wlim);
+          ok = mbar_wait(a_full(as), aph, errp, s_abort, wlim) && mbar_wait(b_full(bs), bph, errp, s_abort, wlim);
           if (!ok) break;
           tc_fence_after();
           const uint32_t abase = smem_u32(smem + Lay::AOff + as * kPiecesA * kAPieceBytes);
@@ -240,7 +286,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
       }
       // all issued MMAs complete before TMEM is released
       tc_commit(drain);
-      mbar_wait_drain(drain, 0, args.err);
+      mbar_wait_drain(drain, 0, errp);
       if (!ok) *s_abort = 1;
     }
   } else if (warp >= 4) {
@@ -256,12 +302,13 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
     // group 1: the row results of the previous tile, finished during the next tile
     bool pend = false, p_valid = false;
     int64_t p_row = 0;
+    int p_item = 0;
     float p_rs = 0.f, p_rc = 0.f, p_xs = 0.f, p_xc = 0.f, p_rmax = 0.f;
     double p_v = 0.0, p_x = 0.0;
     uint32_t p_ph = 0;
     // combine both groups' partials of the pending rows (group 0's come through shared memory)
     auto finish_rows = [&]() -> bool {
-      if (!__all_sync(0xffffffffu, mbar_wait(red_full, p_ph, args.err, s_abort, wlim))) return false;
+      if (!__all_sync(0xffffffffu, mbar_wait(red_full, p_ph, errp, s_abort, wlim))) return false;
       if (p_valid) {
         // the two groups' compensated sums are combined in FP32 (an exact two-sum of the
         // leading parts, the compensations added to the error term) and only the result
@@ -271,9 +318,13 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
         const float xi_hi = two_sum(p_xs, red[r * 5 + 2], xi_lo);
         rd_lo -= p_rc + red[r * 5 + 1];
         xi_lo -= p_xc + red[r * 5 + 3];
-        args.var[p_row] = (p_v + args.theta) - ((double)rd_hi + (double)rd_lo);
-        args.x[p_row] = p_x + ((double)xi_hi + (double)xi_lo);
-        args.cmax[p_row] = fmaxf(p_rmax, red[r * 5 + 4]);
+        double* var = GROUPED ? its[p_item].var : args.var;
+        double* xv = GROUPED ? its[p_item].x : args.x;
+        float* cmax = GROUPED ? its[p_item].cmax : args.cmax;
+        const double theta = GROUPED ? its[p_item].theta : args.theta;
+        var[p_row] = (p_v + theta) - ((double)rd_hi + (double)rd_lo);
+        xv[p_row] = p_x + ((double)xi_hi + (double)xi_lo);
+        cmax[p_row] = fmaxf(p_rmax, red[r * 5 + 4]);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(red_empty);
@@ -285,7 +336,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
     // row scalars of the next tile are loaded one tile ahead (hides their latency)
     float nb_c = 0.f, nb_q = 0.f;
     double nv = 0.0, nx = 0.0;
-    {
+    if constexpr (!GROUPED) {
       const int64_t row = (int64_t)blockIdx.x * kBM + r;
       if (blockIdx.x < ntiles && row < args.m) {
         nb_c = args.cmax[row];
@@ -296,12 +347,28 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
         }
       }
     }
+    int is = 0, fenced = -1;
     for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-      const int64_t row = tile * kBM + r;
-      const bool valid = row < args.m;
+      item_of(tile, is);
+      if (skip(is)) continue;
+      if constexpr (GROUPED) {  // lane 0 issues the tile's stores through the item's map
+        if (is != fenced) {
+          if (lane == 0) tensormap_acquire(&its[is].mapCst);
+          fenced = is;
+        }
+      }
+      const int64_t row = local_tile(tile, is) * kBM + r;  // the row within its filter
+      const int64_t mrows = GROUPED ? its[is].m : args.m;
+      const bool valid = row < mrows;
+      if constexpr (GROUPED) {  // a grouped launch reads the tile's row scalars when it starts it
+        nb_c = valid ? its[is].cmax[row] : 0.f;
+        nb_q = valid ? its[is].cqmax[row] : 0.f;
+        nv = (g == 1 && valid) ? its[is].var[row] : 0.0;
+        nx = (g == 1 && valid) ? its[is].x[row] : 0.0;
+      }
       const float bound = valid ? nb_c + nb_q : 0.f;
       const double cur_v = nv, cur_x = nx;
-      {
+      if constexpr (!GROUPED) {
         const int64_t nrow = (tile + gridDim.x) * kBM + r;
         if (tile + gridDim.x < ntiles && nrow < args.m) {
           nb_c = args.cmax[nrow];
@@ -318,7 +385,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
       for (int kc = g; kc < NK; kc += kGroups, j += kGroups) {
         const int rs = (int)(j % kRawStages);
         const uint32_t rph = (uint32_t)((j / kRawStages) & 1);
-        ok = __all_sync(0xffffffffu, mbar_wait(raw_full(rs), rph, args.err, s_abort, wlim));
+        ok = __all_sync(0xffffffffu, mbar_wait(raw_full(rs), rph, errp, s_abort, wlim));
         if (!ok) break;
         const unsigned char* rc = smem + Lay::RawOff + rs * 2 * kRawBytes;
         float cp[kKC];
@@ -336,8 +403,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
         if (lane == 0) mbar_arrive(raw_empty(rs));
         // x increment: chunk partial by FMA, chunks combined with compensation
         {
-          const float4* a4 = reinterpret_cast<const float4*>(s_a + kc * kKC);
           float part = 0.f;
+          // a grouped launch reads the item's FP32 copy of a (one address for all lanes)
+          const float4* a4 = reinterpret_cast<const float4*>((GROUPED ? its[is].a32 : s_a) + kc * kKC);
 #pragma unroll
           for (int c = 0; c < 8; ++c) {
             const float4 av = a4[c];
@@ -354,7 +422,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
         tmem_st32(tq + 256 + kc * kKC, reinterpret_cast<const uint32_t*>(cp));
         const int as = (int)(j % kAStages);
         const uint32_t aph = (uint32_t)((j / kAStages) & 1);
-        ok = __all_sync(0xffffffffu, mbar_wait(a_empty(as), aph ^ 1u, args.err, s_abort, wlim));
+        ok = __all_sync(0xffffffffu, mbar_wait(a_empty(as), aph ^ 1u, errp, s_abort, wlim));
         if (!ok) break;
         if (kc == g) {
           // the A stage held this warp's output staging: its last tile stores have read it
@@ -389,10 +457,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
       tmem_wait_st();
       // ---- epilogue: output column chunks [0, e0) for group 0, [e0, NK) for group 1 ----
       // (group 0 takes fewer: it converts the chunk the next tile's MMAs start with)
-      ok = __all_sync(0xffffffffu, mbar_wait(acc_full, fph, args.err, s_abort, wlim));
+      ok = __all_sync(0xffffffffu, mbar_wait(acc_full, fph, errp, s_abort, wlim));
       fph ^= 1u;
       if (!ok) break;
       tc_fence_after();
+      const int beta_exp = GROUPED ? *its[is].beta_exp : beta_exp0;
       const float inv = ldexpf(1.f, ea - 14 - beta_exp);  // 1 / (alpha beta)
       float rs_ = 0.f, rc_ = 0.f, rmax = 0.f;
       // output staging: this warp's 32 rows x 32 columns as two 16-row boxes (2 KB each,
@@ -408,7 +477,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
         tmem_wait_ld();
         float out[32];
         float part = 0.f;
-        const float4* r4 = reinterpret_cast<const float4*>(s_r + jc * kKC);
+        const float4* r4 = reinterpret_cast<const float4*>((GROUPED ? its[is].rd32 : s_r) + jc * kKC);
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
           const float4 rv = r4[c];
@@ -427,7 +496,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
         rc_ = (t - rs_) - y;
         rs_ = t;
         const int col0 = jc * kKC;
-        if (col0 < args.ld) {
+        if (col0 < (GROUPED ? its[is].ld : args.ld)) {
           // the previous store from this buffer has been read out of shared memory
           if (lane == 0) bulk_wait_read0();
           __syncwarp();
@@ -440,8 +509,10 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
           // rows past m are clipped by the tensor map
           if (lane == 0) {
             unsigned char* s0 = smem + Lay::AOff + g * kPiecesA * kAPieceBytes + q * 2048;
-            tma_store_2d(&tmCst, smem_u32(s0), col0, (int)(tile * kBM + q * 32));
-            tma_store_2d(&tmCst, smem_u32(s0 + kAPieceBytes), col0, (int)(tile * kBM + q * 32 + 16));
+            const CUtensorMap* mst = GROUPED ? &its[is].mapCst : &tmCst;
+            const int srow = (int)(local_tile(tile, is) * kBM + q * 32);
+            tma_store_2d(mst, smem_u32(s0), col0, srow);
+            tma_store_2d(mst, smem_u32(s0 + kAPieceBytes), col0, srow + 16);
             bulk_commit();
           }
         }
@@ -453,7 +524,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
       // group 1 finishes the rows, so group 0 can start converting the next tile's first
       // chunk (the first the next MMAs need) at once
       if (g == 0) {
-        ok = __all_sync(0xffffffffu, mbar_wait(red_empty, redph ^ 1u, args.err, s_abort, wlim));
+        ok = __all_sync(0xffffffffu, mbar_wait(red_empty, redph ^ 1u, errp, s_abort, wlim));
         if (!ok) break;
         red[r * 5 + 0] = rs_;
         red[r * 5 + 1] = rc_;
@@ -469,6 +540,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
         pend = true;
         p_valid = valid;
         p_row = row;
+        p_item = is;
         p_rs = rs_;
         p_rc = rc_;
         p_xs = xs;
@@ -491,6 +563,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
   if (warp == 1) {
     __syncwarp();
     tmem_dealloc(tmem, 512);
+  }
+  if constexpr (GROUPED) {
+    // a timed-out wait leaves every filter of the launch in an undefined state
+    if (threadIdx.x == 0 && *s_err)
+      for (int i = 0; i < args.nitems; ++i) atomicExch(its[i].err, 1);
   }
 }
 
@@ -527,10 +604,16 @@ __global__ void beta_kernel(const unsigned* __restrict__ mx, int* __restrict__ b
 
 template <int NT>
 __global__ void pack_b_dyn_kernel(const float* __restrict__ Msw, int nt_src, int n, const int* __restrict__ beta_exp,
-                                  __half* __restrict__ img, const int* __restrict__ flag) {
+                                  __half* __restrict__ img, const double* __restrict__ a,
+                                  const double* __restrict__ rd, float* __restrict__ vec32,
+                                  const int* __restrict__ flag) {
   if (*flag) return;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)NT * NT) return;
+  if (t < NT) {  // the FP32 vectors a grouped sweep reads (once per step, not per tile)
+    vec32[t] = t < n ? (float)a[t] : 0.f;
+    vec32[NT + t] = t < n ? (float)rd[t] : 0.f;
+  }
   const int nidx = (int)(t / NT), k = (int)(t % NT);
   const float v = (nidx < n && k < n) ? Msw[(int64_t)nidx * nt_src + k] * ldexpf(1.f, *beta_exp) : 0.f;
   const __half h1 = __float2half_rn(v);
@@ -592,8 +675,10 @@ Status tc_setup(TcState& tc, const float* C, const float* CQ, int64_t m, int ld,
   HIKF_TRY(encode_map(&tc.mapCst, C, m, ld, 16));
   HIKF_TRY(encode_map(&tc.mapCQ, CQ, m, ld));
   tc.smem = tc.nt == 128 ? TcLayout<128>::Smem : TcLayout<256>::Smem;
-  const void* fn = tc.nt == 128 ? (const void*)sweep_tc_kernel<128> : (const void*)sweep_tc_kernel<256>;
+  const void* fn = tc.nt == 128 ? (const void*)sweep_tc_kernel<128, false> : (const void*)sweep_tc_kernel<256, false>;
   HIKF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, tc.smem));
+  const void* fg = tc.nt == 128 ? (const void*)sweep_tc_kernel<128, true> : (const void*)sweep_tc_kernel<256, true>;
+  HIKF_CUDA(cudaFuncSetAttribute(fg, cudaFuncAttributeMaxDynamicSharedMemorySize, tc.smem));
   return Status::Ok();
 }
 
@@ -605,16 +690,19 @@ Status tc_init_rows(const TcState& tc, const float* C, const float* CQ, int64_t 
   return Status::Ok();
 }
 
-Status tc_pack(const TcState& tc, const float* Msw, int nt_src, int n, const int* flag, cudaStream_t s) {
+Status tc_pack(const TcState& tc, const float* Msw, int nt_src, int n, const double* a, const double* rd,
+               const int* flag, cudaStream_t s) {
   absmax_kernel<<<kAbsBlocks, 256, 0, s>>>(Msw, nt_src, n, tc.mmax);
   HIKF_LAUNCH_CHECK("absmax");
   beta_kernel<<<1, kAbsBlocks, 0, s>>>(tc.mmax, tc.beta_exp);
   HIKF_LAUNCH_CHECK("beta");
   const int64_t cnt = (int64_t)tc.nt * tc.nt;
   if (tc.nt == 128)
-    pack_b_dyn_kernel<128><<<nblk(cnt, 256), 256, 0, s>>>(Msw, nt_src, n, tc.beta_exp, tc.bimg, flag);
+    pack_b_dyn_kernel<128><<<nblk(cnt, 256), 256, 0, s>>>(Msw, nt_src, n, tc.beta_exp, tc.bimg, a, rd, tc.vec32,
+                                                          flag);
   else
-    pack_b_dyn_kernel<256><<<nblk(cnt, 256), 256, 0, s>>>(Msw, nt_src, n, tc.beta_exp, tc.bimg, flag);
+    pack_b_dyn_kernel<256><<<nblk(cnt, 256), 256, 0, s>>>(Msw, nt_src, n, tc.beta_exp, tc.bimg, a, rd, tc.vec32,
+                                                          flag);
   HIKF_LAUNCH_CHECK("pack_b");
   return Status::Ok();
 }
@@ -633,10 +721,53 @@ Status tc_sweep(const TcState& tc, TcArgs args, int sms, cudaStream_t s) {
   args.cmax = tc.cmax;
   args.cqmax = tc.cqmax;
   if (tc.nt == 128)
-    sweep_tc_kernel<128><<<grid, kThreadsTc, tc.smem, s>>>(tc.mapC, tc.mapCQ, tc.mapCst, args);
+    sweep_tc_kernel<128, false><<<grid, kThreadsTc, tc.smem, s>>>(tc.mapC, tc.mapCQ, tc.mapCst, args);
   else
-    sweep_tc_kernel<256><<<grid, kThreadsTc, tc.smem, s>>>(tc.mapC, tc.mapCQ, tc.mapCst, args);
+    sweep_tc_kernel<256, false><<<grid, kThreadsTc, tc.smem, s>>>(tc.mapC, tc.mapCQ, tc.mapCst, args);
   HIKF_LAUNCH_CHECK("sweep_tc");
+  return Status::Ok();
+}
+
+int tc_nt(const TcState& tc) { return tc.nt; }
+int64_t tc_tiles(int64_t m) { return (m + kBM - 1) / kBM; }
+
+void tc_item(const TcState& tc, const TcArgs& args, TcItem* it) {
+  it->mapC = tc.mapC;
+  it->mapCQ = tc.mapCQ;
+  it->mapCst = tc.mapCst;
+  it->m = args.m;
+  it->n = args.n;
+  it->ld = args.ld;
+  it->theta = args.theta;
+  it->a32 = tc.vec32;
+  it->rd32 = tc.vec32 + tc.nt;
+  it->x = args.x;
+  it->var = args.var;
+  it->flag = args.flag;
+  it->err = args.err;
+  it->beta_exp = args.beta_exp;
+  it->bimg = tc.bimg;
+  it->cmax = tc.cmax;
+  it->cqmax = tc.cqmax;
+  it->tile0 = 0;
+}
+
+Status tc_sweep_grouped(int nt, const TcItem* items, int count, int64_t ntiles_total, int sms, cudaStream_t s) {
+  if (count < 1 || ntiles_total < 1) return Status::Ok();
+  TcArgs args;
+  args.items = items;
+  args.nitems = count;
+  args.ntiles_total = ntiles_total;
+  args.wait_ns = g_wait_ns ? g_wait_ns : tc::kWaitNs;
+  const int grid = (int)std::min<int64_t>(ntiles_total, sms);
+  // the per-launch tensor-map parameters are unused by the grouped kernel (each item has its own)
+  CUtensorMap unused;
+  memset(&unused, 0, sizeof(unused));
+  if (nt == 128)
+    sweep_tc_kernel<128, true><<<grid, kThreadsTc, TcLayout<128>::Smem, s>>>(unused, unused, unused, args);
+  else
+    sweep_tc_kernel<256, true><<<grid, kThreadsTc, TcLayout<256>::Smem, s>>>(unused, unused, unused, args);
+  HIKF_LAUNCH_CHECK("sweep_tc grouped");
   return Status::Ok();
 }
 

@@ -172,3 +172,19 @@ def test_c_program_links_and_calls_the_library(tmp_path, lib):
     r = subprocess.run([str(exe)], capture_output=True, text=True)
     assert r.returncode == 0, (r.returncode, r.stderr)
     assert r.stdout.split() == ["8", "64", "-1", "0", "1", "0"]
+
+
+def test_batch_rejects_bad_arguments_without_device_work(lib):
+    import ctypes as C
+    from paper_1404_3816_gb300 import binding
+    assert lib.hikf_assimilate_batch(None, None, -1) == binding.HIKF_EINVAL
+    assert b"count" in lib.hikf_last_error(None)
+    assert lib.hikf_assimilate_batch(None, None, 0) == binding.HIKF_OK      # an empty batch
+    assert lib.hikf_assimilate_batch(None, None, 2) == binding.HIKF_EINVAL
+    hs = (C.c_void_p * 2)(None, None)
+    ys = (C.c_void_p * 2)(None, None)
+    assert lib.hikf_assimilate_batch(hs, ys, 2) == binding.HIKF_EINVAL     # a NULL handle
+    assert b"NULL" in lib.hikf_last_error(None)
+    with pytest.raises(binding.HikfError) as e:
+        binding.assimilate_batch([object()], [])
+    assert e.value.code == binding.HIKF_EINVAL

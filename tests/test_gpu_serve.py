@@ -15,8 +15,8 @@ def _streams():
             W.small(grid=(96, 80), n=64, steps=5, seed=44)]
 
 
-@pytest.mark.parametrize("precision", ["fp32", "mixed"])
-def test_results_identical_alone_and_in_the_mix(precision):
+@pytest.mark.parametrize("precision,batch", [("fp32", True), ("mixed", True), ("mixed", False)])
+def test_results_identical_alone_and_in_the_mix(precision, batch):
     from paper_1404_3816_gb300 import binding, serve
     streams = _streams()
     alone = []
@@ -26,7 +26,7 @@ def test_results_identical_alone_and_in_the_mix(precision):
             for y in Y:
                 f.assimilate(y)
             alone.append((f.mean(), f.variance()))
-    server = serve.Server(hbm_budget_bytes=64 << 30, precision=precision)
+    server = serve.Server(hbm_budget_bytes=64 << 30, precision=precision, batch=batch)
     try:
         for i, w in enumerate(streams):
             assert server.admit(i, w)
@@ -46,19 +46,45 @@ def test_results_identical_alone_and_in_the_mix(precision):
         server.close()
 
 
-def test_admission_rejects_over_budget():
-    from paper_1404_3816_gb300 import serve
+def test_admission_queue_admits_when_memory_frees():
+    """A stream that does not fit waits (its measurements are held), is admitted when
+    another departs, and then gives the same result as alone; a stream that can never fit
+    is rejected."""
+    from paper_1404_3816_gb300 import binding, serve
     streams = _streams()
     need = [serve.footprint_bytes(w) for w in streams]
-    server = serve.Server(hbm_budget_bytes=need[0] + need[1] // 2)
+    Y1, _ = W.measurements(streams[1])
+    with binding.Filter.from_workload(streams[1], precision="mixed") as f:
+        for y in Y1:
+            f.assimilate(y)
+        alone = (f.mean(), f.variance())
+    server = serve.Server(hbm_budget_bytes=need[0] + need[1] // 2, precision="mixed")
     try:
-        assert server.admit(0, streams[0])
-        assert not server.admit(1, streams[1])      # would exceed the budget: rejected, not queued
+        assert server.admit(0, streams[0], queue=True)
+        assert not server.admit(1, streams[1], queue=True)   # waits: no room yet
+        assert server.stats()["waiting"] == 1 and server.stats()["rejected"] == 0
+        for y in Y1:
+            server.submit(1, y)                             # held while it waits
+        server.drain()
+        assert 1 not in server.streams
+        server.release(0)                                   # departs: stream 1 admitted
+        assert 1 in server.streams and server.stats()["departed"] == 1
+        server.drain()
+        f = server.streams[1].filt
+        assert np.array_equal(f.mean(), alone[0]) and np.array_equal(f.variance(), alone[1])
+        assert not server.admit(9, W.small(grid=(400, 400), n=64, seed=9), queue=True)  # never fits
         assert server.stats()["rejected"] == 1
-        server.release(0)
-        assert server.admit(1, streams[1])          # memory freed: admitted
     finally:
         server.close()
+
+
+def test_serving_with_departures_and_arrivals():
+    from paper_1404_3816_gb300 import serve
+    streams = _streams() + [W.small(grid=(48, 40), n=16, steps=5, seed=45), W.small(grid=(56, 56), n=24, seed=46)]
+    out = serve.run_serving(streams, rate=300.0, seconds=1.5, budget_bytes=64 << 30, precision="mixed",
+                            active=4, churn_per_s=3.0)
+    assert out["steps"] > 100 and out["departed"] >= 1 and out["arrived"] >= 1
+    assert out["p99_ms"] >= out["p50_ms"] > 0 and out["create_ms_p50"] > 0
 
 
 def test_poisson_serving_run_reports_latency():

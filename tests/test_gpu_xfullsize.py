@@ -234,8 +234,8 @@ def test_m2p21_3d_update_fp64_on_the_h2_product(B, case3d):
           f" vs exact-C_Q filter mean {rel(x, ref['x']):.3g} var {rel(v, ref['var']):.3g}")
     assert rel(x, model["x"]) < 1e-8
     assert rel(v, model["var"]) < 1e-10
-    assert rel(x, ref["x"]) < 5e-4          # 1.5e-4 measured
-    assert rel(v, ref["var"]) < 1e-4        # 2.8e-5 measured
+    assert rel(x, ref["x"]) < 2e-4          # 1.5e-4 measured: the floor set by the order-8 H^2 product
+    assert rel(v, ref["var"]) < 4e-5        # 2.8e-5 measured
 
 
 @pytest.mark.parametrize("form", ["eigen", "nspace"])
@@ -255,5 +255,5 @@ def test_m2p21_3d_fp32_forms_on_their_h2_product(B, case3d, form):
         f.sync()
         x, v = f.mean(), f.variance()
     print(f"\n3d fp32 {form}: vs exact-C_Q filter mean {rel(x, ref['x']):.3g} var {rel(v, ref['var']):.3g}")
-    assert rel(x, ref["x"]) < 5e-4          # 1.52e-4 measured
-    assert rel(v, ref["var"]) < 1e-4        # 2.78e-5 measured
+    assert rel(x, ref["x"]) < 2e-4          # 1.52e-4 measured: the floor set by the order-8 H^2 product
+    assert rel(v, ref["var"]) < 4e-5        # 2.78e-5 measured
