@@ -87,10 +87,9 @@ def test_tree_permutation_is_bit_exact(B, name):
 @pytest.mark.parametrize("prec", ["fp32", "fp64", "mixed"])
 @pytest.mark.parametrize("name", list(CASES))
 def test_h2_product_matches_oracle_definition(B, name, prec):
-    """mixed: M2L on the tensor cores (split TF32); fp32/fp64: CUDA-core M2L."""
+    """mixed: M2L on the tensor cores (split TF32; n > 256 in passes of 256 rays, the filter
+    in the eigenbasis form); fp32/fp64: CUDA-core M2L."""
     w = CASES[name]()
-    if prec == "mixed" and w.n > 256:
-        pytest.skip("the tensor-core paths take n <= 256")
     with B.Filter.from_workload(w, precision=prec) as f:
         depth = f.info()["depth"]
         got = f.cq()
