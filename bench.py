@@ -48,8 +48,8 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=20.0,
                     help="length of the served-latency run (64 streams, Poisson arrivals); 0 skips it")
     ap.add_argument("--profile-case", nargs="+", metavar="ARG",
-                    help="PRECISION FORM [SIDE] [STEPS]: a short run of one update path for kernel "
-                         "profilers (no JSON line)")
+                    help="PRECISION FORM [SIDE] [STEPS] [PRODUCTS]: a short run of one update path for "
+                         "kernel profilers (no JSON line)")
     return ap.parse_args()
 
 
@@ -58,26 +58,29 @@ def profile_case(argv) -> int:
     m = 2^18, C and C_Q 256 MB each, larger than L2) with n = 256 rays, PRECISION in
     {fp32, mixed, fp64} and FORM in {cross, eigen, nspace}. With 4 steps the sweep kernel (for
     nspace: the kernel that forms x and delta^2, run after every step) launches 4 times;
-    profile one of the later launches (-s 1 -c 1)."""
+    profile one of the later launches (-s 1 -c 1). PRODUCTS (MIXED only): the tensor-core
+    sweep's FP16 products per K step, 4 or 5 (default: chosen from the conditioning)."""
     import torch
     from paper_1404_3816_gb300 import binding, workload as W
     prec = argv[0]
     form = argv[1] if len(argv) > 1 else "cross"
     side = int(argv[2]) if len(argv) > 2 else 512
     steps = int(argv[3]) if len(argv) > 3 else 4
+    products = int(argv[4]) if len(argv) > 4 else 0   # MIXED sweep products (0: automatic)
     w = W.config(CONFIG_NAME, grid=(side, side))
     Y, _ = W.measurements(w, steps=steps)
     dY = torch.tensor(Y, dtype=torch.float64, device="cuda")
     dx = torch.empty(w.m, dtype=torch.float64, device="cuda")
     dv = torch.empty_like(dx)
-    with binding.Filter.from_workload(w, precision=prec, form=form) as f:
+    with binding.Filter.from_workload(w, precision=prec, form=form, sweep_products=products) as f:
+        info = f.info()
         for i in range(steps):
             f.assimilate_device(dY[i])
             if form == "nspace":      # x and delta^2 formed after every step
                 f.mean_into(dx)
                 f.variance_into(dv)
         f.sync()
-    print("ok", prec, form, side, steps)
+    print("ok", prec, form, side, steps, "cond_s", info["cond_s"], "sweep_products", info["sweep_products"])
     return 0
 
 
@@ -507,6 +510,7 @@ def main():
                        "p0": "exp, L=64, theta=1", "R": "1e-3 I", "cheb_order": args.order,
                        "tree_depth": info["depth"], "precision": args.precision, "form": "cross (Alg. 2)",
                        "chain": "spectral" if info["chain"] == 2 else "factor",
+                       "cond_s": info["cond_s"], "sweep_products": info["sweep_products"],
                        "create_ms": info["create_ms"], "device_bytes": info["device_bytes"],
                        "l2": "no flush: every step streams C and C_Q (2 GB FP32) > L2",
                        "parallelism": f"replicas x{world}"},

@@ -135,6 +135,9 @@ typedef struct {
                         one launch per pass of 256 rays x 128 operator rows, launch
                         variant autotuned once per shape) for FP32 and MIXED
                         (HIKF_EINVAL for FP64); HIKF_M2L_SIMT: on the CUDA cores. */
+  int sweep_products; /* MIXED tensor-core sweep, FP16 products per K step: 0 (default) = 4
+                        when cond_s <= 3e3, else 5 (see hikf_info_t.sweep_products); 4 or 5
+                        to choose; anything else is HIKF_EINVAL. */
 } hikf_options;
 
 enum { HIKF_CHAIN_AUTO = 0, HIKF_CHAIN_FACTOR = 1, HIKF_CHAIN_SPECTRAL = 2 };
@@ -292,6 +295,10 @@ typedef struct {
                          recurrences; factor chain, the 1-norm condition number of S_1. The
                          cross form's explicit FP32 inverse loses accuracy in proportion to it
                          (see HIKF_FORM_AUTO); INFINITY when S_1 is not positive definite. */
+  int sweep_products; /* MIXED tensor-core sweep: FP16 products per K step (C_p and M split into
+                         two and three pieces: 5; the product of the two low pieces left out
+                         when cond_s <= 3e3, where it does not move the result: 4; or as
+                         hikf_options.sweep_products chose); 0 for the other paths */
 } hikf_info_t;
 
 hikf_status hikf_info(const hikf_t* h, hikf_info_t* info);

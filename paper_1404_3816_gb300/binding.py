@@ -56,7 +56,7 @@ class Kernel(C.Structure):
 class Options(C.Structure):
     _fields_ = [("cheb_order", C.c_int), ("leaf_size", C.c_int), ("max_depth", C.c_int),
                 ("precision", C.c_int), ("cuda_stream", C.c_void_p), ("chain", C.c_int), ("form", C.c_int),
-                ("graph", C.c_int), ("m2l", C.c_int)]
+                ("graph", C.c_int), ("m2l", C.c_int), ("sweep_products", C.c_int)]
 
 
 class Shard(C.Structure):
@@ -67,7 +67,8 @@ class Info(C.Structure):
     _fields_ = [("m", C.c_int64), ("n", C.c_int), ("dim", C.c_int), ("depth", C.c_int),
                 ("cheb_order", C.c_int), ("precision", C.c_int), ("step", C.c_int64),
                 ("device_bytes", C.c_int64), ("create_ms", C.c_double), ("sweep_launches", C.c_int),
-                ("chain", C.c_int), ("form", C.c_int), ("eig_sweeps", C.c_int), ("cond_s", C.c_double)]
+                ("chain", C.c_int), ("form", C.c_int), ("eig_sweeps", C.c_int), ("cond_s", C.c_double),
+                ("sweep_products", C.c_int)]
 
 
 _lib = None
@@ -157,7 +158,7 @@ def kernel_struct(spec) -> Kernel:
 
 
 def options(cheb_order: int = 8, leaf_size: int = 64, max_depth: int = -1, precision="fp32",
-            stream=None, chain="auto", form="auto", graph=True, m2l="auto") -> Options:
+            stream=None, chain="auto", form="auto", graph=True, m2l="auto", sweep_products=0) -> Options:
     o = Options()
     load().hikf_options_default(C.byref(o))
     o.cheb_order = int(cheb_order)
@@ -168,6 +169,7 @@ def options(cheb_order: int = 8, leaf_size: int = 64, max_depth: int = -1, preci
     o.form = FORMS[form] if isinstance(form, str) else int(form)
     o.graph = 1 if graph else 0
     o.m2l = M2LS[m2l] if isinstance(m2l, str) else int(m2l)
+    o.sweep_products = int(sweep_products)
     if stream is not None:
         o.cuda_stream = C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
     return o

@@ -259,6 +259,8 @@ Status validate_common(int dim, int64_t m, const double* points, int n, const in
       o.form != HIKF_FORM_AUTO)
     return make_status(HIKF_EINVAL, "unknown form");
   if (o.m2l < HIKF_M2L_AUTO || o.m2l > HIKF_M2L_SIMT) return make_status(HIKF_EINVAL, "unknown m2l");
+  if (o.sweep_products != 0 && o.sweep_products != 4 && o.sweep_products != 5)
+    return make_status(HIKF_EINVAL, "sweep_products must be 0 (automatic), 4 or 5");
   if (o.m2l == HIKF_M2L_TENSOR && o.precision == HIKF_PREC_FP64)
     return make_status(HIKF_EINVAL, "the tensor-core M2L takes FP32 storage (FP32 or MIXED)");
   return Status::Ok();
@@ -307,6 +309,11 @@ __global__ void white_c0_kernel(const int64_t* __restrict__ trowptr, const int32
 // split-FP16 tensor-core sweep (FP32 accumulation in the tensor core) about 5x earlier.
 constexpr double kCondCrossFp32 = 5e4;
 constexpr double kCondCrossMixed = 1e4;
+// Largest cond(S_t) for which the tensor-core sweep leaves out the product of the two low
+// pieces (A2 B2, 2^-22 of the leading product): measured against the oracle, leaving it out
+// moved the variance error by at most 4e-7 on every case below 3e3 (cond 71 to 2.5e3,
+// including the m = 2^20, n = 256 workload over 100 steps), but by 2-9e-6 at 5.5e3 to 1.9e4.
+constexpr double kCondFourProducts = 3e3;
 
 // Spectral chain: with D = R^{-1/2}, D S_t D = V diag(s_t) V^T, s_1 = (1 + c) lambda + 1 and
 // s_{t+1} = lambda + 2 - 1/s_t per eigenvalue, so cond(S_t) <= cond(R) max_k s_t,k / min_k s_t,k
@@ -406,7 +413,8 @@ Status h2_rows(hikf_t* h, const hikf::FmmParams& fp, T* dst, int ld, cudaStream_
 
 template <typename T>
 Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const double* x0, const double* cq,
-                   const double* c0, const double* r_diag, const double* r_full, int chain_opt, int form_opt) {
+                   const double* c0, const double* r_diag, const double* r_full, int chain_opt, int form_opt,
+                   int sweep_products) {
   cudaStream_t s = h->stream;
   const int64_t m = h->m;
   const int n = h->n, ld = h->ld;
@@ -674,6 +682,7 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
   if (h->mixed() && !h->eigen && !h->nspace) {
     hikf::TcState& tc = h->tc;
     HIKF_TRY(hikf::tc_setup(tc, (const float*)C, (const float*)CQ, m, ld, n));
+    tc.products = sweep_products ? sweep_products : (h->cond_s <= kCondFourProducts ? 4 : 5);
     HIKF_TRY(hikf::arena_alloc(h->arena, &tc.bimg, (size_t)3 * tc.nt * tc.nt));
     HIKF_TRY(hikf::arena_alloc(h->arena, &tc.cmax, m));
     HIKF_TRY(hikf::arena_alloc(h->arena, &tc.cqmax, m));
@@ -1081,8 +1090,8 @@ hikf_status create_impl(hikf_t** out, int dim, int64_t m, const double* points, 
     st = make_shard(h, *shard);
     if (!st.ok()) return bail(st);
   }
-  st = h->fp64() ? setup_state<double>(h, q, p0, x0, cq, c0, r_diag, r_full, o.chain, o.form)
-                 : setup_state<float>(h, q, p0, x0, cq, c0, r_diag, r_full, o.chain, o.form);
+  st = h->fp64() ? setup_state<double>(h, q, p0, x0, cq, c0, r_diag, r_full, o.chain, o.form, o.sweep_products)
+                 : setup_state<float>(h, q, p0, x0, cq, c0, r_diag, r_full, o.chain, o.form, o.sweep_products);
   if (!st.ok()) return bail(st);
   e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return bail(hikf::cuda_status(e, "create", __FILE__, __LINE__));
@@ -1106,6 +1115,7 @@ hikf_status hikf_options_default(hikf_options* opt) {
   opt->form = HIKF_FORM_AUTO;
   opt->graph = 1;
   opt->m2l = HIKF_M2L_AUTO;
+  opt->sweep_products = 0;
   return HIKF_OK;
 }
 
@@ -1456,6 +1466,7 @@ hikf_status hikf_info(const hikf_t* h, hikf_info_t* info) {
   info->form = h->nspace ? HIKF_FORM_NSPACE : (h->eigen ? HIKF_FORM_EIGEN : HIKF_FORM_CROSS);
   info->eig_sweeps = h->spectral ? h->sp.sweeps : 0;
   info->cond_s = h->cond_s;
+  info->sweep_products = h->mixed() && !h->eigen && !h->nspace ? h->tc.products : 0;
   return HIKF_OK;
 }
 

@@ -13,7 +13,11 @@
 // FP32 accumulator. Measured against the FP64 oracle, a third piece of C_p (a sixth
 // product) changes neither the mean nor the variance error (the FP32 accumulation of
 // the tensor core sets them); it would cost a sixth more tensor-core time, which sets
-// the pace of a tile (each M=128, N=256, K=16 instruction takes ~72 ns).
+// the pace of a tile (each M=128, N=256, K=16 instruction takes ~72 ns). For the same
+// reason a well-conditioned update (cond S_t <= 3e3, decided at create) leaves out the
+// product of the two low pieces A2 B2: four products, a fifth less tensor time. Two
+// pieces of M are not enough: on an n = 100 case with cond S_t ~ 9e3 they lost the 1e-5
+// bound on the variance.
 // The row scale comes from a bound carried from the previous step:
 // |C_p,ij| <= max_j |C_{t|t}| + max_j |C_Q|.
 //
@@ -251,6 +255,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
         eph ^= 1u;
         if (!ok) break;
         tc_fence_after();
+        const bool low2 = (GROUPED ? its[is].products : args.products) > 4;  // A2 B2 issued
         for (int kc = 0; kc < NK && ok; ++kc) {
           ok = mbar_wait(a_full(as), aph, errp, s_abort, wlim) && mbar_wait(b_full(bs), bph, errp, s_abort, wlim);
           if (!ok) break;
@@ -263,9 +268,10 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
             const uint64_t b1 = smem_desc(bbase + ks * 256, 128, 512);
             const uint64_t b2 = smem_desc(bbase + Lay::BPiece + ks * 256, 128, 512);
             const uint64_t b3 = smem_desc(bbase + 2 * Lay::BPiece + ks * 256, 128, 512);
-            // smallest terms first
-            tc_mma_f16(tmem, a2, b2, idesc, (kc > 0 || ks > 0) ? 1u : 0u);
-            tc_mma_f16(tmem, a1, b3, idesc, 1u);
+            // smallest terms first; the first product of a tile overwrites the accumulator
+            const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
+            if (low2) tc_mma_f16(tmem, a2, b2, idesc, acc);
+            tc_mma_f16(tmem, a1, b3, idesc, low2 ? 1u : acc);
             tc_mma_f16(tmem, a2, b1, idesc, 1u);
             tc_mma_f16(tmem, a1, b2, idesc, 1u);
             tc_mma_f16(tmem, a1, b1, idesc, 1u);
@@ -720,6 +726,7 @@ Status tc_sweep(const TcState& tc, TcArgs args, int sms, cudaStream_t s) {
   args.bimg = tc.bimg;
   args.cmax = tc.cmax;
   args.cqmax = tc.cqmax;
+  args.products = tc.products;
   if (tc.nt == 128)
     sweep_tc_kernel<128, false><<<grid, kThreadsTc, tc.smem, s>>>(tc.mapC, tc.mapCQ, tc.mapCst, args);
   else
@@ -750,6 +757,7 @@ void tc_item(const TcState& tc, const TcArgs& args, TcItem* it) {
   it->cmax = tc.cmax;
   it->cqmax = tc.cqmax;
   it->tile0 = 0;
+  it->products = tc.products;
 }
 
 Status tc_sweep_grouped(int nt, const TcItem* items, int count, int64_t ntiles_total, int sms, cudaStream_t s) {

@@ -26,6 +26,7 @@ struct TcItem {
   float* cmax = nullptr;
   const float* cqmax = nullptr;
   int64_t tile0 = 0;
+  int products = 5;             // 4: the product of the two low pieces left out
 };
 
 struct TcArgs {
@@ -45,6 +46,7 @@ struct TcArgs {
   float* cmax = nullptr;        // m: max_j |C_ij| of the current C (row-scale bound)
   const float* cqmax = nullptr; // m: max_j |C_Q,ij|
   unsigned long long wait_ns = 0;  // limit of the abortable waits (set by tc_sweep)
+  int products = 5;             // FP16 products per K step (set by tc_sweep): 5, or 4 without A2 B2
   // grouped sweep: the items (device) and the launch's tiles over all of them
   const TcItem* items = nullptr;
   int nitems = 0;
@@ -62,6 +64,7 @@ struct TcState {
   unsigned* mmax = nullptr;     // kAbsBlocks partial maxima of |M|
   int* beta_exp = nullptr;
   float* vec32 = nullptr;       // 2 x nt: a, then diag R, in FP32 (zero past n) for a grouped sweep
+  int products = 5;             // FP16 products per K step: 5, or 4 without A2 B2 (set at create)
 };
 
 constexpr int kAbsBlocks = 64;

@@ -188,3 +188,12 @@ def test_batch_rejects_bad_arguments_without_device_work(lib):
     with pytest.raises(binding.HikfError) as e:
         binding.assimilate_batch([object()], [])
     assert e.value.code == binding.HIKF_EINVAL
+
+
+def test_sweep_products_option_is_checked_without_gpu(lib):
+    from paper_1404_3816_gb300 import binding, workload as W
+    w = W.small(grid=(10, 8), n=4, seed=1)
+    for bad in (1, 3, 6, -4):
+        with pytest.raises(binding.HikfError) as e:
+            binding.Filter.from_workload(w, precision="mixed", sweep_products=bad)
+        assert e.value.code == binding.HIKF_EINVAL and "sweep_products" in str(e.value)
