@@ -242,7 +242,8 @@ hikf_status hikf_assimilate_device(hikf_t* h, const double* d_y);
  * in MIXED precision and the cross-covariance or spectral form run as ONE launch per MMA
  * width (n_t = 128 or 256) over the row tiles of all of them, so that many small filters
  * fill the SMs together; the rest of each step runs on the filter's own stream, and the
- * other filters take their ordinary step (hikf_assimilate_device). Every filter's result
+ * other filters take their ordinary step (hikf_assimilate_device); filters of different
+ * sweep_products (hikf_info) go in separate launches. Every filter's result
  * is bit-identical to hikf_assimilate_device with the same y. The filters' streams are
  * ordered against the shared launch by events (it runs on the first grouped filter's
  * stream); each handle's stream has passed its step once hikf_sync of that handle returns.
@@ -296,8 +297,8 @@ typedef struct {
                          cross form's explicit FP32 inverse loses accuracy in proportion to it
                          (see HIKF_FORM_AUTO); INFINITY when S_1 is not positive definite. */
   int sweep_products; /* MIXED tensor-core sweep: FP16 products per K step (C_p and M split into
-                         two and three pieces: 5; the product of the two low pieces left out
-                         when cond_s <= 3e3, where it does not move the result: 4; or as
+                         two and three pieces: 5; M in two pieces when cond_s <= 3e3, where the
+                         third does not move the result past 1e-5: 4; or as
                          hikf_options.sweep_products chose); 0 for the other paths */
 } hikf_info_t;
 

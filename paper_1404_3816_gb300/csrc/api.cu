@@ -309,10 +309,11 @@ __global__ void white_c0_kernel(const int64_t* __restrict__ trowptr, const int32
 // split-FP16 tensor-core sweep (FP32 accumulation in the tensor core) about 5x earlier.
 constexpr double kCondCrossFp32 = 5e4;
 constexpr double kCondCrossMixed = 1e4;
-// Largest cond(S_t) for which the tensor-core sweep leaves out the product of the two low
-// pieces (A2 B2, 2^-22 of the leading product): measured against the oracle, leaving it out
-// moved the variance error by at most 4e-7 on every case below 3e3 (cond 71 to 2.5e3,
-// including the m = 2^20, n = 256 workload over 100 steps), but by 2-9e-6 at 5.5e3 to 1.9e4.
+// Largest cond(S_t) for which the tensor-core sweep splits M into two FP16 pieces instead of
+// three (A1 B3, 2^-22 of the leading product, left out): measured against the oracle, the
+// variance error moved by at most 1.3e-6 on every case below 3e3 (cond 71 to 2.5e3, including
+// the m = 2^20, n = 256 workload over 100 steps, where it fell from 5.2e-6 to 4.7e-6), but two
+// pieces of M put an n = 100 case at cond 9.3e3 above 1e-5.
 constexpr double kCondFourProducts = 3e3;
 
 // Spectral chain: with D = R^{-1/2}, D S_t D = V diag(s_t) V^T, s_1 = (1 + c) lambda + 1 and
@@ -1295,12 +1296,13 @@ hikf_status hikf_assimilate_batch(hikf_t* const* hs, const double* const* d_y, i
     }
     if (e != cudaSuccess) return bfail(h, hikf::cuda_status(e, "order the batch", __FILE__, __LINE__));
   }
-  // one launch per MMA width n_t over the tiles of all its filters
-  for (int nt : {128, 256}) {
+  // one launch per MMA width n_t and product count over the tiles of all its filters
+  for (int key = 0; key < 4; ++key) {
+    const int nt = key < 2 ? 128 : 256, products = key % 2 == 0 ? 4 : 5;
     std::vector<hikf::TcItem> items;
     int64_t tiles = 0;
     for (hikf_t* h : grp) {
-      if (hikf::tc_nt(h->tc) != nt) continue;
+      if (hikf::tc_nt(h->tc) != nt || h->tc.products != products) continue;
       hikf::TcItem it;
       hikf::tc_item(h->tc, tc_args(h), &it);
       it.tile0 = tiles;
@@ -1317,7 +1319,7 @@ hikf_status hikf_assimilate_batch(hikf_t* const* hs, const double* const* d_y, i
       if (d_items) cudaFreeAsync(d_items, lead->stream);
       return bfail(lead, hikf::cuda_status(e, "batch items", __FILE__, __LINE__));
     }
-    Status st = hikf::tc_sweep_grouped(nt, d_items, (int)items.size(), tiles, lead->sms, lead->stream);
+    Status st = hikf::tc_sweep_grouped(nt, products, d_items, (int)items.size(), tiles, lead->sms, lead->stream);
     cudaFreeAsync(d_items, lead->stream);
     if (!st.ok()) return bfail(lead, st);
   }

@@ -13,10 +13,11 @@
 // FP32 accumulator. Measured against the FP64 oracle, a third piece of C_p (a sixth
 // product) changes neither the mean nor the variance error (the FP32 accumulation of
 // the tensor core sets them); it would cost a sixth more tensor-core time, which sets
-// the pace of a tile (each M=128, N=256, K=16 instruction takes ~72 ns). For the same
-// reason a well-conditioned update (cond S_t <= 3e3, decided at create) leaves out the
-// product of the two low pieces A2 B2: four products, a fifth less tensor time. Two
-// pieces of M are not enough: on an n = 100 case with cond S_t ~ 9e3 they lost the 1e-5
+// the pace of a tile (each M=128, N=256, K=16 instruction takes ~72 ns). A well-
+// conditioned update (cond S_t <= 3e3, decided at create) splits M into two pieces only:
+// four products (A1 B3 left out), a fifth less tensor time, and a third less B traffic from
+// L2 per chunk, which buys a three-stage B ring in the same shared memory. Two pieces of M
+// are not enough in general: on an n = 100 case with cond S_t ~ 9e3 they lost the 1e-5
 // bound on the variance.
 // The row scale comes from a bound carried from the previous step:
 // |C_p,ij| <= max_j |C_{t|t}| + max_j |C_Q|.
@@ -55,23 +56,24 @@ constexpr int kKC = 32;                  // K per stage
 constexpr int kGroups = 2;               // converter/epilogue warp groups (4 warps each, one per TMEM lane quarter)
 constexpr int kRawStages = 2;            // chunk j -> raw stage j % 2 (= its group)
 constexpr int kPiecesA = 2;              // FP16 pieces of alpha C_p (2 x 11 bits)
-constexpr int kPieces = 3;               // FP16 pieces of beta M (3 x 11 bits)
 constexpr int kAStages = 2;              // chunk j -> A stage j % 2 (= its group)
-constexpr int kBStages = 2;
 constexpr int kThreadsTc = 128 + 128 * kGroups;
 constexpr int kRawBytes = kBM * kKC * 4;          // one FP32 raw tile (C or C_Q): 16 KB
 constexpr int kAPieceBytes = kBM * kKC * 2;       // one FP16 A piece: 8 KB
 
-template <int NT>
+// PB: FP16 pieces of beta M (3: five products per K step; 2: four, for a well-conditioned
+// update); the B ring holds the same bytes either way: 2 stages of 3 pieces or 3 of 2
+template <int NT, int PB>
 struct TcLayout {
+  static constexpr int BStages = PB == 3 ? 2 : 3;
   static constexpr int BPiece = NT * kKC * 2;                        // one FP16 B piece per stage
   static constexpr int RawOff = 0;
   static constexpr int AOff = RawOff + kRawStages * 2 * kRawBytes;
   static constexpr int BOff = AOff + kAStages * kPiecesA * kAPieceBytes;
-  static constexpr int VecOff = BOff + kBStages * kPieces * BPiece;  // a (NT floats), r (NT floats)
+  static constexpr int VecOff = BOff + BStages * PB * BPiece;        // a (NT floats), r (NT floats)
   static constexpr int RedOff = VecOff + 2 * NT * 4;                 // group-0 partials: 128 x {rd hi, rd lo, x hi, x lo, max}
   static constexpr int BarOff = RedOff + 128 * 5 * 4;
-  static constexpr int NumBars = 2 * kRawStages + 2 * kAStages + 2 * kBStages + 5;
+  static constexpr int NumBars = 2 * kRawStages + 2 * kAStages + 2 * BStages + 5;
   static constexpr int Total = BarOff + NumBars * 8 + 16;
   static constexpr int Smem = Total + 1024;                          // slack for 1024-B alignment
 };
@@ -96,11 +98,12 @@ __device__ __forceinline__ float two_sum(float a, float b, float& err) {
 // GROUPED: the tiles of several filters (args.items, in the order of their tile0) in one
 // launch; every role walks the same flat tile order and finds a tile's filter with a cursor.
 // A tile of a filter whose step was rejected is skipped by every role alike.
-template <int NT, bool GROUPED>
+template <int NT, bool GROUPED, int PB>
 __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_constant__ CUtensorMap tmC,
                                                           const __grid_constant__ CUtensorMap tmCQ,
                                                           const __grid_constant__ CUtensorMap tmCst, TcArgs args) {
-  using Lay = TcLayout<NT>;
+  using Lay = TcLayout<NT, PB>;
+  constexpr int kBStages = Lay::BStages;
   constexpr int NK = NT / kKC;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -230,9 +233,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
           const int bs = (int)(j % kBStages);
           ok = mbar_wait(b_empty(bs), (uint32_t)(((j / kBStages) & 1) ^ 1), errp, s_abort, wlim);
           if (!ok) break;
-          const uint32_t bbase = smem_u32(smem + Lay::BOff + bs * kPieces * Lay::BPiece);
-          mbar_expect_tx(b_full(bs), kPieces * Lay::BPiece);
-          for (int pc = 0; pc < kPieces; ++pc)
+          const uint32_t bbase = smem_u32(smem + Lay::BOff + bs * PB * Lay::BPiece);
+          mbar_expect_tx(b_full(bs), PB * Lay::BPiece);
+          for (int pc = 0; pc < PB; ++pc)
             bulk_load(bbase + pc * Lay::BPiece, bimg + ((size_t)pc * NK + kc) * (Lay::BPiece / 2), Lay::BPiece,
                       b_full(bs));
         }
@@ -255,23 +258,22 @@ __global__ void __launch_bounds__(kThreadsTc, 1) sweep_tc_kernel(const __grid_co
         eph ^= 1u;
         if (!ok) break;
         tc_fence_after();
-        const bool low2 = (GROUPED ? its[is].products : args.products) > 4;  // A2 B2 issued
         for (int kc = 0; kc < NK && ok; ++kc) {
           ok = mbar_wait(a_full(as), aph, errp, s_abort, wlim) && mbar_wait(b_full(bs), bph, errp, s_abort, wlim);
           if (!ok) break;
           tc_fence_after();
           const uint32_t abase = smem_u32(smem + Lay::AOff + as * kPiecesA * kAPieceBytes);
-          const uint32_t bbase = smem_u32(smem + Lay::BOff + bs * kPieces * Lay::BPiece);
+          const uint32_t bbase = smem_u32(smem + Lay::BOff + bs * PB * Lay::BPiece);
           for (int ks = 0; ks < kKC / 16; ++ks) {
             const uint64_t a1 = smem_desc(abase + ks * 256, 128, 512);
             const uint64_t a2 = smem_desc(abase + kAPieceBytes + ks * 256, 128, 512);
             const uint64_t b1 = smem_desc(bbase + ks * 256, 128, 512);
             const uint64_t b2 = smem_desc(bbase + Lay::BPiece + ks * 256, 128, 512);
-            const uint64_t b3 = smem_desc(bbase + 2 * Lay::BPiece + ks * 256, 128, 512);
+            const uint64_t b3 = PB == 3 ? smem_desc(bbase + 2 * Lay::BPiece + ks * 256, 128, 512) : 0;
             // smallest terms first; the first product of a tile overwrites the accumulator
             const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
-            if (low2) tc_mma_f16(tmem, a2, b2, idesc, acc);
-            tc_mma_f16(tmem, a1, b3, idesc, low2 ? 1u : acc);
+            tc_mma_f16(tmem, a2, b2, idesc, acc);
+            if constexpr (PB == 3) tc_mma_f16(tmem, a1, b3, idesc, 1u);
             tc_mma_f16(tmem, a2, b1, idesc, 1u);
             tc_mma_f16(tmem, a1, b2, idesc, 1u);
             tc_mma_f16(tmem, a1, b1, idesc, 1u);
@@ -612,7 +614,7 @@ template <int NT>
 __global__ void pack_b_dyn_kernel(const float* __restrict__ Msw, int nt_src, int n, const int* __restrict__ beta_exp,
                                   __half* __restrict__ img, const double* __restrict__ a,
                                   const double* __restrict__ rd, float* __restrict__ vec32,
-                                  const int* __restrict__ flag) {
+                                  const int* __restrict__ flag, int pieces) {
   if (*flag) return;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)NT * NT) return;
@@ -623,16 +625,15 @@ __global__ void pack_b_dyn_kernel(const float* __restrict__ Msw, int nt_src, int
   const int nidx = (int)(t / NT), k = (int)(t % NT);
   const float v = (nidx < n && k < n) ? Msw[(int64_t)nidx * nt_src + k] * ldexpf(1.f, *beta_exp) : 0.f;
   const __half h1 = __float2half_rn(v);
-  const float r1 = v - __half2float(h1);
+  const float r1 = v - __half2float(h1);  // exact in FP32
   const __half h2 = __float2half_rn(r1);
-  const __half h3 = __float2half_rn(r1 - __half2float(h2));
   const int kc = k / kKC, kk = k % kKC;
   const size_t chunk = (size_t)NT * kKC;                   // halves per piece per chunk
   const size_t off = (size_t)kc * chunk + core_off(nidx, kk) / 2;
   const size_t piece = (size_t)(NT / kKC) * chunk;         // halves per piece (all chunks)
   img[off] = h1;
   img[piece + off] = h2;
-  img[2 * piece + off] = h3;
+  if (pieces == 3) img[2 * piece + off] = __float2half_rn(r1 - __half2float(h2));
 }
 
 // per-row max |value| of an m x ld FP32 matrix (row scale bounds)
@@ -674,17 +675,45 @@ inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 }  // namespace
 
+// One instantiation of the sweep: its entry point and dynamic shared memory
+struct TcKernel {
+  const void* fn;
+  int smem;
+};
+template <int NT, bool G, int PB>
+TcKernel tc_kernel_of() {
+  return {(const void*)sweep_tc_kernel<NT, G, PB>, TcLayout<NT, PB>::Smem};
+}
+TcKernel tc_kernel(int nt, bool grouped, int products) {
+  const int pb = products == 4 ? 2 : 3;
+  if (nt == 128) {
+    if (grouped) return pb == 2 ? tc_kernel_of<128, true, 2>() : tc_kernel_of<128, true, 3>();
+    return pb == 2 ? tc_kernel_of<128, false, 2>() : tc_kernel_of<128, false, 3>();
+  }
+  if (grouped) return pb == 2 ? tc_kernel_of<256, true, 2>() : tc_kernel_of<256, true, 3>();
+  return pb == 2 ? tc_kernel_of<256, false, 2>() : tc_kernel_of<256, false, 3>();
+}
+
 Status tc_setup(TcState& tc, const float* C, const float* CQ, int64_t m, int ld, int n) {
   if (ld > 256) return make_status(HIKF_EINVAL, "MIXED precision supports n <= 256");
   tc.nt = ld <= 128 ? 128 : 256;
   HIKF_TRY(encode_map(&tc.mapC, C, m, ld));
   HIKF_TRY(encode_map(&tc.mapCst, C, m, ld, 16));
   HIKF_TRY(encode_map(&tc.mapCQ, CQ, m, ld));
-  tc.smem = tc.nt == 128 ? TcLayout<128>::Smem : TcLayout<256>::Smem;
-  const void* fn = tc.nt == 128 ? (const void*)sweep_tc_kernel<128, false> : (const void*)sweep_tc_kernel<256, false>;
-  HIKF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, tc.smem));
-  const void* fg = tc.nt == 128 ? (const void*)sweep_tc_kernel<128, true> : (const void*)sweep_tc_kernel<256, true>;
-  HIKF_CUDA(cudaFuncSetAttribute(fg, cudaFuncAttributeMaxDynamicSharedMemorySize, tc.smem));
+  for (int grouped = 0; grouped < 2; ++grouped)
+    for (int products = 4; products <= 5; ++products) {
+      const TcKernel k = tc_kernel(tc.nt, grouped != 0, products);
+      HIKF_CUDA(cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, k.smem));
+    }
+  return Status::Ok();
+}
+
+// Launch one instantiation (the arguments as the kernel's parameter list)
+Status tc_launch(int nt, bool grouped, int products, int grid, const CUtensorMap& mC, const CUtensorMap& mCQ,
+                 const CUtensorMap& mCst, const TcArgs& args, cudaStream_t s) {
+  const TcKernel k = tc_kernel(nt, grouped, products);
+  void* params[] = {(void*)&mC, (void*)&mCQ, (void*)&mCst, (void*)&args};
+  HIKF_CUDA(cudaLaunchKernel(k.fn, dim3(grid), dim3(kThreadsTc), params, (size_t)k.smem, s));
   return Status::Ok();
 }
 
@@ -705,10 +734,10 @@ Status tc_pack(const TcState& tc, const float* Msw, int nt_src, int n, const dou
   const int64_t cnt = (int64_t)tc.nt * tc.nt;
   if (tc.nt == 128)
     pack_b_dyn_kernel<128><<<nblk(cnt, 256), 256, 0, s>>>(Msw, nt_src, n, tc.beta_exp, tc.bimg, a, rd, tc.vec32,
-                                                          flag);
+                                                          flag, tc.products == 4 ? 2 : 3);
   else
     pack_b_dyn_kernel<256><<<nblk(cnt, 256), 256, 0, s>>>(Msw, nt_src, n, tc.beta_exp, tc.bimg, a, rd, tc.vec32,
-                                                          flag);
+                                                          flag, tc.products == 4 ? 2 : 3);
   HIKF_LAUNCH_CHECK("pack_b");
   return Status::Ok();
 }
@@ -727,12 +756,7 @@ Status tc_sweep(const TcState& tc, TcArgs args, int sms, cudaStream_t s) {
   args.cmax = tc.cmax;
   args.cqmax = tc.cqmax;
   args.products = tc.products;
-  if (tc.nt == 128)
-    sweep_tc_kernel<128, false><<<grid, kThreadsTc, tc.smem, s>>>(tc.mapC, tc.mapCQ, tc.mapCst, args);
-  else
-    sweep_tc_kernel<256, false><<<grid, kThreadsTc, tc.smem, s>>>(tc.mapC, tc.mapCQ, tc.mapCst, args);
-  HIKF_LAUNCH_CHECK("sweep_tc");
-  return Status::Ok();
+  return tc_launch(tc.nt, false, tc.products, grid, tc.mapC, tc.mapCQ, tc.mapCst, args, s);
 }
 
 int tc_nt(const TcState& tc) { return tc.nt; }
@@ -760,7 +784,8 @@ void tc_item(const TcState& tc, const TcArgs& args, TcItem* it) {
   it->products = tc.products;
 }
 
-Status tc_sweep_grouped(int nt, const TcItem* items, int count, int64_t ntiles_total, int sms, cudaStream_t s) {
+Status tc_sweep_grouped(int nt, int products, const TcItem* items, int count, int64_t ntiles_total, int sms,
+                        cudaStream_t s) {
   if (count < 1 || ntiles_total < 1) return Status::Ok();
   TcArgs args;
   args.items = items;
@@ -771,12 +796,8 @@ Status tc_sweep_grouped(int nt, const TcItem* items, int count, int64_t ntiles_t
   // the per-launch tensor-map parameters are unused by the grouped kernel (each item has its own)
   CUtensorMap unused;
   memset(&unused, 0, sizeof(unused));
-  if (nt == 128)
-    sweep_tc_kernel<128, true><<<grid, kThreadsTc, TcLayout<128>::Smem, s>>>(unused, unused, unused, args);
-  else
-    sweep_tc_kernel<256, true><<<grid, kThreadsTc, TcLayout<256>::Smem, s>>>(unused, unused, unused, args);
-  HIKF_LAUNCH_CHECK("sweep_tc grouped");
-  return Status::Ok();
+  args.products = products;
+  return tc_launch(nt, true, products, grid, unused, unused, unused, args, s);
 }
 
 }  // namespace hikf

@@ -26,7 +26,7 @@ struct TcItem {
   float* cmax = nullptr;
   const float* cqmax = nullptr;
   int64_t tile0 = 0;
-  int products = 5;             // 4: the product of the two low pieces left out
+  int products = 5;             // 5 or 4 (M in three or two pieces); one value per launch
 };
 
 struct TcArgs {
@@ -46,7 +46,7 @@ struct TcArgs {
   float* cmax = nullptr;        // m: max_j |C_ij| of the current C (row-scale bound)
   const float* cqmax = nullptr; // m: max_j |C_Q,ij|
   unsigned long long wait_ns = 0;  // limit of the abortable waits (set by tc_sweep)
-  int products = 5;             // FP16 products per K step (set by tc_sweep): 5, or 4 without A2 B2
+  int products = 5;             // FP16 products per K step: 5 (M in three pieces) or 4 (two)
   // grouped sweep: the items (device) and the launch's tiles over all of them
   const TcItem* items = nullptr;
   int nitems = 0;
@@ -55,16 +55,15 @@ struct TcArgs {
 
 struct TcState {
   int nt = 256;                 // MMA N (128 or 256)
-  int smem = 0;
   CUtensorMap mapC, mapCQ;
   CUtensorMap mapCst;           // C, 32-column x 16-row boxes: the epilogue's tile stores
-  __half* bimg = nullptr;       // 3 x nt x nt FP16 images of beta M (three pieces)
+  __half* bimg = nullptr;       // 3 x nt x nt: FP16 images of beta M (three pieces, or two)
   float* cmax = nullptr;
   float* cqmax = nullptr;
   unsigned* mmax = nullptr;     // kAbsBlocks partial maxima of |M|
   int* beta_exp = nullptr;
   float* vec32 = nullptr;       // 2 x nt: a, then diag R, in FP32 (zero past n) for a grouped sweep
-  int products = 5;             // FP16 products per K step: 5, or 4 without A2 B2 (set at create)
+  int products = 5;             // FP16 products per K step: 5 (M in three pieces) or 4 (two; set at create)
 };
 
 constexpr int kAbsBlocks = 64;
@@ -78,10 +77,11 @@ Status tc_sweep(const TcState& tc, TcArgs args, int sms, cudaStream_t s);
 
 // Fill a grouped-sweep item from one filter's sweep state and arguments (tile0 left 0).
 void tc_item(const TcState& tc, const TcArgs& args, TcItem* item);
-// The sweeps of several filters with the same n_t in one launch: `items` (device, count items,
-// tile0 set) and their total tiles; nt = 128 or 256; err: set when a wait timed out (then
-// every item's err is set as well).
-Status tc_sweep_grouped(int nt, const TcItem* items, int count, int64_t ntiles_total, int sms, cudaStream_t s);
+// The sweeps of several filters with the same n_t and product count in one launch: `items`
+// (device, count items, tile0 set) and their total tiles; nt = 128 or 256, products = 4 or 5;
+// a wait that timed out sets every item's err.
+Status tc_sweep_grouped(int nt, int products, const TcItem* items, int count, int64_t ntiles_total, int sms,
+                        cudaStream_t s);
 int tc_nt(const TcState& tc);
 // Row tiles of an m-row sweep (the units of a grouped launch's flat tile order).
 int64_t tc_tiles(int64_t m);
