@@ -80,6 +80,14 @@ __global__ void vec_to_caller(const double* __restrict__ src, const int64_t* __r
   if (s < m) dst[perm[s]] = src[s];
 }
 
+// the same permutation as a gather (caller index i <- tree position iperm[i]): contiguous
+// writes, for outputs written straight into mapped host memory
+__global__ void vec_from_tree(const double* __restrict__ src, const int64_t* __restrict__ iperm, int64_t m,
+                              double* __restrict__ dst) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) dst[i] = src[iperm[i]];
+}
+
 __global__ void vec_to_tree(const double* __restrict__ src, const int64_t* __restrict__ perm, int64_t m,
                             double* __restrict__ dst) {
   int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -165,6 +173,7 @@ struct hikf_handle {
   double* x0t = nullptr;     // x_0 in tree order (n-space form)
   double var0 = 0.0;         // delta^2_0 = theta_0
   long long enq = 0;         // updates enqueued (host count)
+  long long clean_at = -1;   // value of enq when the step flag was last read as clear
   long long outs_at = -1;    // value of enq when x, delta^2 were last formed (n-space form)
   void* G = nullptr;   // eigenbasis state (HIKF_FORM_EIGEN), m x ld
   void* Gq = nullptr;  // C_Q W
@@ -318,42 +327,32 @@ constexpr double kCondFourProducts = 3e3;
 
 // Spectral chain: with D = R^{-1/2}, D S_t D = V diag(s_t) V^T, s_1 = (1 + c) lambda + 1 and
 // s_{t+1} = lambda + 2 - 1/s_t per eigenvalue, so cond(S_t) <= cond(R) max_k s_t,k / min_k s_t,k
-// (equality for R = sigma^2 I). The recurrence is run here over the steps until every s_k
-// has settled; each s_k moves monotonically to its fixed point s* = (lambda + 2 +
-// sqrt(lambda^2 + 4 lambda)) / 2, so past the last step run the ratio is bounded by
-// max_k max(s_T, s*) / min_k min(s_T, s*). The result bounds cond(S_t) for every t.
+// (equality for R = sigma^2 I). Both s_1 and the step map grow with lambda (c >= -1), so the
+// order of the s_k never changes: the largest and the smallest eigenvalue carry max_k and
+// min_k at every step, and only their two recurrences are run, until both have settled. Each
+// moves monotonically to its fixed point s* = (lambda + 2 + sqrt(lambda^2 + 4 lambda)) / 2,
+// so past the last step run the ratio is bounded by max(s_T, s*) / min(s_T, s*) of the two.
+// The result bounds cond(S_t) for every t.
 double spectral_cond_bound(const std::vector<double>& lam, const double* r_diag, int n, double c) {
-  std::vector<double> sv(n), sf(n);
-  double rmax = 0.0, rmin = INFINITY;
+  double lhi = 0.0, llo = INFINITY, rmax = 0.0, rmin = INFINITY;
   for (int k = 0; k < n; ++k) {
     const double l = std::max(lam[k], 0.0);
-    sv[k] = (1.0 + c) * l + 1.0;
-    sf[k] = 0.5 * (l + 2.0 + std::sqrt(l * l + 4.0 * l));
+    lhi = std::max(lhi, l);
+    llo = std::min(llo, l);
     rmax = std::max(rmax, r_diag[k]);
     rmin = std::min(rmin, r_diag[k]);
   }
-  double worst = 0.0;
+  auto fixed = [](double l) { return 0.5 * (l + 2.0 + std::sqrt(l * l + 4.0 * l)); };
+  double hi = (1.0 + c) * lhi + 1.0, lo = (1.0 + c) * llo + 1.0, worst = 0.0;
   for (int t = 0; t < 20000; ++t) {
-    double hi = 0.0, lo = INFINITY, move = 0.0;
-    for (int k = 0; k < n; ++k) {
-      hi = std::max(hi, sv[k]);
-      lo = std::min(lo, sv[k]);
-    }
     worst = std::max(worst, hi / lo);
-    for (int k = 0; k < n; ++k) {
-      const double l = std::max(lam[k], 0.0);
-      const double nx = l + 2.0 - 1.0 / sv[k];
-      move = std::max(move, std::fabs(nx - sv[k]) / sv[k]);
-      sv[k] = nx;
-    }
+    const double nh = lhi + 2.0 - 1.0 / hi, nl = llo + 2.0 - 1.0 / lo;
+    const double move = std::max(std::fabs(nh - hi) / hi, std::fabs(nl - lo) / lo);
+    hi = nh;
+    lo = nl;
     if (move < 1e-13) break;
   }
-  double hi = 0.0, lo = INFINITY;
-  for (int k = 0; k < n; ++k) {
-    hi = std::max(hi, std::max(sv[k], sf[k]));
-    lo = std::min(lo, std::min(sv[k], sf[k]));
-  }
-  worst = std::max(worst, hi / lo);
+  worst = std::max(worst, std::max(hi, fixed(lhi)) / std::min(lo, fixed(llo)));
   return (rmax / rmin) * worst;
 }
 
@@ -928,6 +927,7 @@ Status read_flag(hikf_t* h, int* out) {
   HIKF_CUDA(cudaStreamSynchronize(h->stream));
   *out = f[0] | (f[2] ? 8 : 0);
   if (f[2]) h->dead = true;
+  if (*out == 0) h->clean_at = h->enq;
   if (*out) HIKF_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int) * 4, h->stream));
   return Status::Ok();
 }
@@ -1219,10 +1219,13 @@ hikf_status hikf_assimilate(hikf_t* h, const double* y) {
   for (int r = 0; r < h->n; ++r)
     if (!std::isfinite(y[r])) return fail(h, hikf::make_status(HIKF_EINVAL, "non-finite measurement y"));
   int f = 0;
-  Status st = read_flag(h, &f);
-  if (!st.ok()) return fail(h, st);
-  if (f) return fail(h, hikf::make_status(f & 8 ? HIKF_ETIMEOUT : HIKF_ESTATE,
-                                          "an earlier asynchronous step failed: " + flag_status(f).msg));
+  Status st;
+  if (h->clean_at != h->enq) {  // steps were enqueued since the flag was last read clear
+    st = read_flag(h, &f);
+    if (!st.ok()) return fail(h, st);
+    if (f) return fail(h, hikf::make_status(f & 8 ? HIKF_ETIMEOUT : HIKF_ESTATE,
+                                            "an earlier asynchronous step failed: " + flag_status(f).msg));
+  }
   cudaError_t e = cudaMemcpyAsync(h->ybuf, y, sizeof(double) * h->n, cudaMemcpyHostToDevice, h->stream);
   if (e != cudaSuccess) return fail(h, hikf::cuda_status(e, "copy y", __FILE__, __LINE__));
   st = enqueue(h);
@@ -1356,6 +1359,21 @@ static hikf_status get_vec(hikf_t* h, const double* src, double* out, bool devic
   if (refuse_dead(h, &dead_code)) return dead_code;
   Status fs = form_outputs(h);
   if (!fs.ok()) return fail(h, fs);
+  if (!device) {
+    // page-locked host memory mapped into the device's address space (a pinned buffer): one
+    // kernel writes it directly, with one wait, instead of a device copy and a transfer
+    cudaPointerAttributes at;
+    memset(&at, 0, sizeof(at));
+    if (cudaPointerGetAttributes(&at, out) == cudaSuccess && at.type == cudaMemoryTypeHost && at.devicePointer) {
+      hikf::vec_from_tree<<<hikf::nblk(h->m, 256), 256, 0, h->stream>>>(src, h->tree.iperm, h->m,
+                                                                         (double*)at.devicePointer);
+      cudaError_t e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+      if (e != cudaSuccess) return fail(h, hikf::cuda_status(e, "vec_from_tree", __FILE__, __LINE__));
+      return HIKF_OK;
+    }
+    cudaGetLastError();  // an unregistered pointer may leave an error from the query
+  }
   hikf::vec_to_caller<<<hikf::nblk(h->m, 256), 256, 0, h->stream>>>(src, h->tree.perm, h->m,
                                                                      device ? out : h->outbuf);
   cudaError_t e = cudaGetLastError();
