@@ -73,7 +73,8 @@ __device__ __forceinline__ void dd_add(float& sh, float& sl, float ph, float pl)
 
 // x = x_0 + Gq b, delta^2 = delta^2_0 + t theta - sum_k h_k Gq_ik^2.
 // FP32 Gq: four lanes per row, each lane takes float4 column groups 4 (lane & 3) + 16 j
-// (so a warp reads 64 contiguous bytes of each of 8 rows per load); Gq b by FP32 products
+// (so a warp reads 64 contiguous bytes of each of 8 rows per load; four such loads in
+// flight per lane, since one at a time left the SM too few bytes in flight for HBM); Gq b by FP32 products
 // with a compensated sum (b as an FP32 pair), h Gq^2 with the square exact (TwoProd) and a
 // double-float sum, since delta^2_t is a small difference of large terms; FP64 result.
 // FP64 Gq: one warp per row in FP64.
@@ -100,28 +101,38 @@ __global__ void __launch_bounds__(256) nspace_outputs_f32_kernel(const float* __
     float xs = 0.f, xc = 0.f, vh = 0.f, vl = 0.f;
     if (live) {
       const float4* gr = reinterpret_cast<const float4*>(Gq + i * ld);
-      for (int c = 4 * sub; c < n; c += 16) {
-        const float4 g4 = __ldcs(gr + (c >> 2));
-        const float4 bh = *reinterpret_cast<const float4*>(sbh + c);
-        const float4 bl = *reinterpret_cast<const float4*>(sbl + c);
-        const float4 hh = *reinterpret_cast<const float4*>(shh + c);
-        const float4 hl = *reinterpret_cast<const float4*>(shl + c);
-        const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
-        const float bhv[4] = {bh.x, bh.y, bh.z, bh.w}, blv[4] = {bl.x, bl.y, bl.z, bl.w};
-        const float hhv[4] = {hh.x, hh.y, hh.z, hh.w}, hlv[4] = {hl.x, hl.y, hl.z, hl.w};
+      // four loads of the row in flight per lane (the sums then take them in column order)
+      for (int c0 = 4 * sub; c0 < n; c0 += 64) {
+        float4 gq[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          // x: FMA product, Kahan-compensated sum
-          const float p = fmaf(gv[u], bhv[u], gv[u] * blv[u]);
-          const float y = p - xc;
-          const float t = xs + y;
-          xc = (t - xs) - y;
-          xs = t;
-          // delta^2: (qh + ql) = Gq^2 exactly, times (hh + hl), double-float sum
-          const float qh = gv[u] * gv[u];
-          const float ql = fmaf(gv[u], gv[u], -qh);
-          const float r = qh * hhv[u];
-          dd_add(vh, vl, r, fmaf(qh, hhv[u], -r) + (qh * hlv[u] + ql * hhv[u]));
+        for (int k = 0; k < 4; ++k)
+          if (c0 + 16 * k < n) gq[k] = __ldcs(gr + ((c0 + 16 * k) >> 2));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int c = c0 + 16 * k;
+          if (c >= n) break;
+          const float4 g4 = gq[k];
+          const float4 bh = *reinterpret_cast<const float4*>(sbh + c);
+          const float4 bl = *reinterpret_cast<const float4*>(sbl + c);
+          const float4 hh = *reinterpret_cast<const float4*>(shh + c);
+          const float4 hl = *reinterpret_cast<const float4*>(shl + c);
+          const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
+          const float bhv[4] = {bh.x, bh.y, bh.z, bh.w}, blv[4] = {bl.x, bl.y, bl.z, bl.w};
+          const float hhv[4] = {hh.x, hh.y, hh.z, hh.w}, hlv[4] = {hl.x, hl.y, hl.z, hl.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            // x: FMA product, Kahan-compensated sum
+            const float p = fmaf(gv[u], bhv[u], gv[u] * blv[u]);
+            const float y = p - xc;
+            const float t = xs + y;
+            xc = (t - xs) - y;
+            xs = t;
+            // delta^2: (qh + ql) = Gq^2 exactly, times (hh + hl), double-float sum
+            const float qh = gv[u] * gv[u];
+            const float ql = fmaf(gv[u], gv[u], -qh);
+            const float r = qh * hhv[u];
+            dd_add(vh, vl, r, fmaf(qh, hhv[u], -r) + (qh * hlv[u] + ql * hhv[u]));
+          }
         }
       }
     }
