@@ -56,6 +56,7 @@ class _Stream:
     pin: object = None     # pinned host ring of max_inflight measurement vectors
     dev: object = None     # device ring of the same
     cuda_stream: object = None  # the handle's CUDA stream (torch view)
+    events: object = None  # one completion event per slot of the rings, created once
     issued: int = 0
 
 
@@ -143,7 +144,7 @@ class Server:
             # free the staging rings while the handle's stream exists: the pinned-memory
             # allocator records an event on every stream that copied from a block when the
             # block is freed
-            st.pin = st.dev = st.cuda_stream = None
+            st.pin = st.dev = st.cuda_stream = st.events = None
             st.inflight.clear()
             st.filt.close()
         with self.lock:
@@ -202,6 +203,7 @@ class Server:
                     st.pin = torch.empty((self.max_inflight, st.workload.n), dtype=torch.float64).pin_memory()
                     st.dev = torch.empty((self.max_inflight, st.workload.n), dtype=torch.float64, device="cuda")
                     st.cuda_stream = torch.cuda.ExternalStream(st.filt.stream)
+                    st.events = [torch.cuda.Event() for _ in range(self.max_inflight)]
                 t_arr, y = st.queue.popleft()
                 # the slot's previous request has completed (at most max_inflight in flight)
                 k = st.issued % self.max_inflight
@@ -217,7 +219,7 @@ class Server:
                 for st, k, _ in rnd:
                     st.filt.assimilate_device(st.dev[k])
             for st, k, t_arr in rnd:
-                ev = torch.cuda.Event()
+                ev = st.events[k]  # the slot's previous request has completed
                 ev.record(st.cuda_stream)
                 st.inflight.append((t_arr, ev))
                 st.issued += 1
