@@ -17,7 +17,8 @@
 // next; the sources of a box are accumulated in groups (at most ~4096 products per
 // output element per group) whose partials are summed on the CUDA cores, because the
 // tensor core's FP32 accumulation drifts over long chains (3D boxes have up to 189
-// sources of up to 512 nodes). The number of pipeline stages and of CTAs per SM are chosen by a small
+// sources of up to 512 nodes). A pipeline stage is one 128-ray half of a K chunk (with its
+// operator chunk), so that up to four stages fit. The number of pipeline stages and of CTAs per SM are chosen by a small
 // autotuner that times each feasible variant once per problem shape (the outputs of
 // all variants are identical) and remembers the fastest for the process. Bounded
 // waits as in the sweep kernel.
@@ -195,12 +196,14 @@ __device__ int interaction_count(int64_t B, int lev, int dim, const int64_t* __r
   return cnt;
 }
 
+// A pipeline stage holds one 128-ray half of a K chunk of W (two pieces) and the operator
+// chunk (two pieces): the operator chunk, small, is copied once per half, so that a stage
+// stays small enough for three or four of them in shared memory
 template <int NPAD, int HALVES, int STAGES>
 struct TcM2lCfg {
-  static constexpr int LDP = 128 * HALVES;
-  static constexpr int A_CHUNK = LDP * 128;   // bytes of one A piece chunk
+  static constexpr int A_HALF = 128 * 128;    // bytes of one A piece for one half (128 rays x 32 K)
   static constexpr int B_CHUNK = NPAD * 128;  // bytes of one B piece chunk
-  static constexpr int STAGE = 2 * A_CHUNK + 2 * B_CHUNK;
+  static constexpr int STAGE = 2 * A_HALF + 2 * B_CHUNK;
   static constexpr int ACC_COLS = HALVES * NPAD;  // TMEM columns per accumulator buffer
   static constexpr int TMEM_COLS = 2 * ACC_COLS <= 32 ? 32 : (2 * ACC_COLS <= 64 ? 64 : (2 * ACC_COLS <= 128 ? 128
                                                          : (2 * ACC_COLS <= 256 ? 256 : 512)));
@@ -216,7 +219,7 @@ __global__ void __launch_bounds__(kThreads, 1) m2l_tc_kernel(Dims d, LevelTab lt
                                                              const unsigned char* __restrict__ kimg,
                                                              float* __restrict__ Lx, int* __restrict__ err) {
   using Cfg = TcM2lCfg<NPAD, HALVES, STAGES>;
-  constexpr int A_CHUNK = Cfg::A_CHUNK, B_CHUNK = Cfg::B_CHUNK, STAGE = Cfg::STAGE;
+  constexpr int A_HALF = Cfg::A_HALF, B_CHUNK = Cfg::B_CHUNK, STAGE = Cfg::STAGE;
   constexpr int ACC_COLS = Cfg::ACC_COLS, TMEM_COLS = Cfg::TMEM_COLS;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -266,18 +269,22 @@ __global__ void __launch_bounds__(kThreads, 1) m2l_tc_kernel(Dims d, LevelTab lt
         const unsigned char* wl = wimg + (box0 - wbox0) * d.a_box_bytes;
         const unsigned char* kl = kimg + (int64_t)(lev - 2) * noff * d.b_off_bytes;
         for (int e = 0; e < nil && ok; ++e) {
-          for (int kc = 0; kc < d.nkc && ok; ++kc, ++j) {
-            const int s = (int)(j % STAGES);
-            ok = mbar_wait(empty(s), (uint32_t)(((j / STAGES) & 1) ^ 1), err, s_abort);
-            if (!ok) break;
-            const uint32_t dst = smem_u32(smem + s * STAGE);
-            mbar_expect_tx(full(s), STAGE);
-            const unsigned char* a = wl + (int64_t)il_src[e] * d.a_box_bytes + (int64_t)kc * d.a_chunk_bytes;
-            bulk_load(dst, a, A_CHUNK, full(s));
-            bulk_load(dst + A_CHUNK, a + (int64_t)d.nkc * d.a_chunk_bytes, A_CHUNK, full(s));
-            const unsigned char* bsrc = kl + (int64_t)il_off[e] * d.b_off_bytes + (int64_t)kc * d.b_chunk_bytes;
-            bulk_load(dst + 2 * A_CHUNK, bsrc, B_CHUNK, full(s));
-            bulk_load(dst + 2 * A_CHUNK + B_CHUNK, bsrc + (int64_t)d.nkc * d.b_chunk_bytes, B_CHUNK, full(s));
+          for (int kc = 0; kc < d.nkc && ok; ++kc) {
+            for (int h = 0; h < HALVES && ok; ++h, ++j) {
+              const int s = (int)(j % STAGES);
+              ok = mbar_wait(empty(s), (uint32_t)(((j / STAGES) & 1) ^ 1), err, s_abort);
+              if (!ok) break;
+              const uint32_t dst = smem_u32(smem + s * STAGE);
+              mbar_expect_tx(full(s), STAGE);
+              // the half's rows of the chunk: 128-row groups are contiguous in the image
+              const unsigned char* a =
+                  wl + (int64_t)il_src[e] * d.a_box_bytes + (int64_t)kc * d.a_chunk_bytes + (int64_t)h * A_HALF;
+              bulk_load(dst, a, A_HALF, full(s));
+              bulk_load(dst + A_HALF, a + (int64_t)d.nkc * d.a_chunk_bytes, A_HALF, full(s));
+              const unsigned char* bsrc = kl + (int64_t)il_off[e] * d.b_off_bytes + (int64_t)kc * d.b_chunk_bytes;
+              bulk_load(dst + 2 * A_HALF, bsrc, B_CHUNK, full(s));
+              bulk_load(dst + 2 * A_HALF + B_CHUNK, bsrc + (int64_t)d.nkc * d.b_chunk_bytes, B_CHUNK, full(s));
+            }
           }
         }
       }
@@ -310,26 +317,26 @@ __global__ void __launch_bounds__(kThreads, 1) m2l_tc_kernel(Dims d, LevelTab lt
             tc_fence_after();
             dacc = tmem + (uint32_t)(buf * ACC_COLS);
           }
-          for (int kc = 0; kc < d.nkc && ok; ++kc, ++j) {
-            const int s = (int)(j % STAGES);
-            ok = mbar_wait(full(s), (uint32_t)((j / STAGES) & 1), err, s_abort);
-            if (!ok) break;
-            tc_fence_after();
-            const uint32_t base = smem_u32(smem + s * STAGE);
-            for (int h = 0; h < HALVES; ++h) {
+          for (int kc = 0; kc < d.nkc && ok; ++kc) {
+            for (int h = 0; h < HALVES && ok; ++h, ++j) {
+              const int s = (int)(j % STAGES);
+              ok = mbar_wait(full(s), (uint32_t)((j / STAGES) & 1), err, s_abort);
+              if (!ok) break;
+              tc_fence_after();
+              const uint32_t base = smem_u32(smem + s * STAGE);
               for (int ks = 0; ks < kKC / 8; ++ks) {
-                const uint64_t a1 = smem_desc(base + h * 16384 + ks * 256, 128, 1024);
-                const uint64_t a2 = smem_desc(base + A_CHUNK + h * 16384 + ks * 256, 128, 1024);
-                const uint64_t b1 = smem_desc(base + 2 * A_CHUNK + ks * 256, 128, 1024);
-                const uint64_t b2 = smem_desc(base + 2 * A_CHUNK + B_CHUNK + ks * 256, 128, 1024);
+                const uint64_t a1 = smem_desc(base + ks * 256, 128, 1024);
+                const uint64_t a2 = smem_desc(base + A_HALF + ks * 256, 128, 1024);
+                const uint64_t b1 = smem_desc(base + 2 * A_HALF + ks * 256, 128, 1024);
+                const uint64_t b2 = smem_desc(base + 2 * A_HALF + B_CHUNK + ks * 256, 128, 1024);
                 const uint32_t dd = dacc + (uint32_t)(h * NPAD);
                 const uint32_t acc = (ge > 0 || kc > 0 || ks > 0) ? 1u : 0u;
                 tc_mma_tf32(dd, a2, b1, idesc, acc);
                 tc_mma_tf32(dd, a1, b2, idesc, 1u);
                 tc_mma_tf32(dd, a1, b1, idesc, 1u);
               }
+              tc_commit(empty(s));
             }
-            tc_commit(empty(s));
           }
           if (ok && (ge == d.group - 1 || e == nil - 1)) {
             tc_commit(acc_full0 + 8u * buf);  // a partial over this group of sources
@@ -420,6 +427,8 @@ Status launch_npad_halves(const Variant& v, const Dims& d, const LevelTab& lt, i
                           const unsigned char* kimg, float* Lx, int* err, int sms, cudaStream_t s) {
   const int64_t nitems = lt.item0[lt.nlev];
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(nitems, (int64_t)sms * v.per_sm));
+  if (v.stages == 4)
+    return launch_variant<NPAD, HALVES, 4>(d, lt, dim, wbox0, nsrc, npts, wimg, kimg, Lx, err, grid, s);
   if (v.stages == 3)
     return launch_variant<NPAD, HALVES, 3>(d, lt, dim, wbox0, nsrc, npts, wimg, kimg, Lx, err, grid, s);
   return launch_variant<NPAD, HALVES, 2>(d, lt, dim, wbox0, nsrc, npts, wimg, kimg, Lx, err, grid, s);
@@ -443,7 +452,7 @@ Status launch(const Variant& v, const Dims& d, const LevelTab& lt, int dim, int6
 
 // shared memory and TMEM of one CTA of a variant (for the feasibility of stages and CTAs per SM)
 void variant_footprint(int npad, int halves, int stages, int* smem, int* tmem_cols) {
-  const int stage = 2 * (128 * halves) * 128 + 2 * npad * 128;
+  const int stage = 2 * 128 * 128 + 2 * npad * 128;
   *smem = stages * stage + (2 * stages + 5) * 8 + 64 + 1024;
   const int acc = 2 * halves * npad;
   *tmem_cols = acc <= 32 ? 32 : (acc <= 64 ? 64 : (acc <= 128 ? 128 : (acc <= 256 ? 256 : 512)));
@@ -451,7 +460,7 @@ void variant_footprint(int npad, int halves, int stages, int* smem, int* tmem_co
 
 std::vector<Variant> feasible_variants(int npad, int halves) {
   std::vector<Variant> out;
-  for (int st = 2; st <= 3; ++st) {
+  for (int st = 2; st <= 4; ++st) {
     int smem = 0, tcols = 0;
     variant_footprint(npad, halves, st, &smem, &tcols);
     if (smem > 227 * 1024) continue;
