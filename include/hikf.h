@@ -270,8 +270,10 @@ hikf_status hikf_get_mean_device(hikf_t* h, double* d_out);
 hikf_status hikf_get_variance_device(hikf_t* h, double* d_out);
 
 /* Test hooks: the H^2 product C_Q and the current C_{t|t} (host, m x n FP64,
- * row-major, caller's order); the tree permutation (host, m int64: entry s is
- * the caller index of the s-th point in tree order). Synchronous. */
+ * row-major, caller's order; on a sharded filter the rank's rows, count x n, in the
+ * rank's order of hikf_shard_caller_index); the tree permutation (host, m int64:
+ * entry s is the caller index of the s-th point in tree order; not on a shard).
+ * Synchronous. */
 hikf_status hikf_get_cq(hikf_t* h, double* out);
 hikf_status hikf_get_cross(hikf_t* h, double* out);
 hikf_status hikf_get_perm(hikf_t* h, int64_t* out);
@@ -338,8 +340,9 @@ void hikf_destroy(hikf_t* h);
  *                    H_r C_1,r (2 n^2 doubles), through the caller's all-reduce callback;
  *   every step:      the sum over ranks of the partial n-vector H_r x_r (the innovation),
  *                    done by the caller between hikf_shard_step_begin and _end.
- * The H^2 product is formed on every rank (H is small and replicated, so no multipole halo
- * is needed) and each rank keeps its rows. Forms: cross and eigen (HIKF_FORM_NSPACE is
+ * H is small and replicated, so every rank runs the upward pass of the H^2 product over all
+ * sources (no multipole halo is exchanged) and the downward pass (M2L, L2L, L2P, P2P) only
+ * for the boxes that hold its rows: no rank forms another rank's rows of C_Q. Forms: cross and eigen (HIKF_FORM_NSPACE is
  * refused); diagonal R only. Updates are enqueued on the handle's stream without a graph.
  */
 typedef int (*hikf_allreduce_fn)(double* d_buf, int64_t count, void* ctx); /* sum in place over the ranks,

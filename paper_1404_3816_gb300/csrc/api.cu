@@ -71,7 +71,7 @@ __global__ void rows_to_caller(const T* __restrict__ src, const int64_t* __restr
   if (t >= m * n) return;
   int64_t s = t / n;
   int c = (int)(t % n);
-  dst[perm[s] * n + c] = (double)src[s * ld + c];
+  dst[(perm ? perm[s] : s) * n + c] = (double)src[s * ld + c];
 }
 
 __global__ void vec_to_caller(const double* __restrict__ src, const int64_t* __restrict__ perm, int64_t m,
@@ -394,21 +394,13 @@ Status factor_cond(const double* dS, int n, double* scratch, cudaStream_t s, dou
   return Status::Ok();
 }
 
-// The H^2 product into dst (the handle's rows, m x ld). A shard forms it for all m_full rows
-// (H is replicated, so every rank has every source) and keeps its own rows.
+// The H^2 product into dst (the handle's rows, m x ld). H is replicated, so every rank has
+// every source and runs the upward pass whole; the downward pass of a shard covers only the
+// boxes that hold its rows [r0, r0 + m) of the tree order, and no rank forms another's rows.
 template <typename T>
 Status h2_rows(hikf_t* h, const hikf::FmmParams& fp, T* dst, int ld, cudaStream_t s) {
   if (!h->shard) return hikf::h2_product<T>(h->tree, h->Hfull, fp, dst, ld, s);
-  T* full = nullptr;
-  HIKF_CUDA(cudaMallocAsync((void**)&full, sizeof(T) * (size_t)h->m_full * ld, s));
-  Status st = hikf::h2_product<T>(h->tree, h->Hfull, fp, full, ld, s);
-  if (st.ok()) {
-    cudaError_t e = cudaMemcpyAsync(dst, full + (size_t)h->r0 * ld, sizeof(T) * (size_t)h->m * ld,
-                                    cudaMemcpyDeviceToDevice, s);
-    if (e != cudaSuccess) st = hikf::cuda_status(e, "shard rows", __FILE__, __LINE__);
-  }
-  cudaFreeAsync(full, s);
-  return st;
+  return hikf::h2_product<T>(h->tree, h->Hfull, fp, dst, ld, s, h->r0, h->r0 + h->m);
 }
 
 template <typename T>
@@ -1395,9 +1387,10 @@ hikf_status hikf_get_variance_device(hikf_t* h, double* d_out) {
 
 static hikf_status get_mat(hikf_t* h, const void* src, double* out) {
   if (!h || !out) return h ? fail(h, hikf::make_status(HIKF_EINVAL, "out is NULL")) : HIKF_EINVAL;
-  if (h->shard) return fail(h, hikf::make_status(HIKF_ESTATE, "not available on a sharded filter"));
   double* d = nullptr;
   const size_t bytes = sizeof(double) * (size_t)h->m * h->n;
+  // a shard returns its own rows in its order (hikf_shard_caller_index maps them)
+  const int64_t* perm = h->shard ? nullptr : h->tree.perm;
   cudaError_t e = cudaMallocAsync((void**)&d, bytes, h->stream);
   if (e != cudaSuccess) return fail(h, hikf::cuda_status(e, "cudaMallocAsync", __FILE__, __LINE__));
   void* unw = nullptr;
@@ -1422,10 +1415,10 @@ static hikf_status get_mat(hikf_t* h, const void* src, double* out) {
   }
   if (h->fp64())
     hikf::rows_to_caller<double><<<hikf::nblk(h->m * h->n, 256), 256, 0, h->stream>>>(
-        (const double*)src, h->tree.perm, h->m, h->n, h->ld, d);
+        (const double*)src, perm, h->m, h->n, h->ld, d);
   else
     hikf::rows_to_caller<float><<<hikf::nblk(h->m * h->n, 256), 256, 0, h->stream>>>(
-        (const float*)src, h->tree.perm, h->m, h->n, h->ld, d);
+        (const float*)src, perm, h->m, h->n, h->ld, d);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, bytes, cudaMemcpyDeviceToHost, h->stream);
   cudaFreeAsync(d, h->stream);
@@ -1460,6 +1453,7 @@ hikf_status hikf_get_cross(hikf_t* h, double* out) {
 
 hikf_status hikf_get_perm(hikf_t* h, int64_t* out) {
   if (!h || !out) return HIKF_EINVAL;
+  if (h->shard) return fail(h, hikf::make_status(HIKF_ESTATE, "a sharded filter: hikf_shard_caller_index"));
   cudaError_t e = cudaMemcpyAsync(out, h->tree.perm, sizeof(int64_t) * h->m, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return fail(h, hikf::cuda_status(e, "get perm", __FILE__, __LINE__));

@@ -43,6 +43,7 @@ struct Geo {
 };
 
 __host__ __device__ inline int64_t cmin64(int64_t a, int64_t b) { return a < b ? a : b; }
+__host__ __device__ inline int64_t cmax64(int64_t a, int64_t b) { return a > b ? a : b; }
 
 __host__ __device__ constexpr int ipow_c(int b, int e) { return e == 0 ? 1 : b * ipow_c(b, e - 1); }
 
@@ -142,10 +143,11 @@ __global__ void m2l_table(Geo g, const double* __restrict__ tab, T* __restrict__
   kop[t] = (T)kernel_value_d(r2, g.pow, g.theta, g.length, g.shape, g.kdiag);
 }
 
-// per-box count of H^T nonzeros (sources) below the box
+// per-box count of H^T nonzeros (sources) below the box, and of the box's target points in
+// the rows [row0, row1) being formed
 __global__ void box_sources(const int64_t* __restrict__ leaf_start, const int64_t* __restrict__ trowptr,
                             const int64_t* __restrict__ box_offset_d, int depth, int dim, int64_t nbox,
-                            int64_t* __restrict__ nsrc, int64_t* __restrict__ npts) {
+                            int64_t row0, int64_t row1, int64_t* __restrict__ nsrc, int64_t* __restrict__ npts) {
   int64_t gb = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (gb >= nbox) return;
   int lev = 0;
@@ -154,7 +156,7 @@ __global__ void box_sources(const int64_t* __restrict__ leaf_start, const int64_
   int64_t span = (int64_t)1 << (dim * (depth - lev));
   int64_t p0 = leaf_start[b * span], p1 = leaf_start[(b + 1) * span];
   nsrc[gb] = trowptr[p1] - trowptr[p0];
-  npts[gb] = p1 - p0;
+  npts[gb] = max((int64_t)0, min(p1, row1) - max(p0, row0));
 }
 
 // 1-D weights s_p(u, xi_k) for k < p, u in [-1, 1]
@@ -728,7 +730,8 @@ __global__ void __launch_bounds__(kThreads) l2p_p2p_kernel(Geo g, const double* 
                                                            const double* __restrict__ tval,
                                                            const double* __restrict__ tab,
                                                            const int64_t* __restrict__ nsrc, int64_t leaf_box0,
-                                                           int nch, const T* __restrict__ Lx, T* __restrict__ out) {
+                                                           int nch, const T* __restrict__ Lx, int64_t row0,
+                                                           int64_t row1, T* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int p = g.p, q = g.q, ld = g.ld, dim = g.dim, L = g.depth;
   T* tj = reinterpret_cast<T*>(smem_raw);
@@ -747,8 +750,9 @@ __global__ void __launch_bounds__(kThreads) l2p_p2p_kernel(Geo g, const double* 
   int* zc = reinterpret_cast<int*>(zv + kNzStage);              // and their ray indices
   __shared__ int se_cnt[2];                                     // crossed sources per staging warp
   const int64_t b = blockIdx.x;
-  const int64_t p0 = leaf_start[b], p1 = leaf_start[b + 1];
-  if (p1 == p0) return;
+  // the leaf's points within the rows being formed; out holds row row0 first
+  const int64_t p0 = cmax64(leaf_start[b], row0), p1 = cmin64(leaf_start[b + 1], row1);
+  if (p1 <= p0) return;
   for (int t = threadIdx.x; t < p * p; t += blockDim.x) tj[t] = (T)tab[t];
   int64_t cb[3] = {0, 0, 0};
   for (int bit = 0; bit < L; ++bit)
@@ -893,7 +897,7 @@ __global__ void __launch_bounds__(kThreads) l2p_p2p_kernel(Geo g, const double* 
       }
       for (int t = threadIdx.x; t < cnt * nch; t += blockDim.x) {
         int ii = t / nch, r = t % nch;
-        if (r < w) out[(ps + ii) * (int64_t)ld + r0 + r] = Cs[ii * (nch + 1) + r];
+        if (r < w) out[(ps + ii - row0) * (int64_t)ld + r0 + r] = Cs[ii * (nch + 1) + r];
       }
       __syncthreads();
     }
@@ -911,7 +915,8 @@ Status set_smem(const void* fn, size_t bytes) {
 }  // namespace
 
 template <typename T>
-Status h2_product(const Tree& t, const SparseH& h, const FmmParams& fp, T* out, int ldc, cudaStream_t s) {
+Status h2_product(const Tree& t, const SparseH& h, const FmmParams& fp, T* out, int ldc, cudaStream_t s,
+                  int64_t row0, int64_t row1) {
   Geo g;
   for (int d = 0; d < 3; ++d) g.lo[d] = t.lo[d];
   g.side = t.side;
@@ -932,8 +937,10 @@ Status h2_product(const Tree& t, const SparseH& h, const FmmParams& fp, T* out, 
   const int p = g.p, q = g.q, L = t.depth, dim = t.dim;
   const int64_t nbox = t.nbox_total;
   const int64_t m = t.m;
+  if (row1 < 0) row1 = m;
+  if (row0 < 0 || row1 > m || row0 >= row1) return make_status(HIKF_EINVAL, "H^2 product: empty or bad row range");
 
-  HIKF_CUDA(cudaMemsetAsync(out, 0, sizeof(T) * (size_t)m * ldc, s));
+  HIKF_CUDA(cudaMemsetAsync(out, 0, sizeof(T) * (size_t)(row1 - row0) * ldc, s));
   // column chunk: keep q * nch * sizeof(T) * 3 within ~150 KB
   int nch = 128;
   while (nch > 32 && (size_t)q * nch * sizeof(T) * 3 > 150 * 1024) nch /= 2;
@@ -950,7 +957,8 @@ Status h2_product(const Tree& t, const SparseH& h, const FmmParams& fp, T* out, 
   HIKF_CUDA(cudaMemcpyAsync(boff, t.box_offset, sizeof(int64_t) * (L + 2), cudaMemcpyHostToDevice, s));
   cheb_tables<<<1, 512, 0, s>>>(p, tab);
   HIKF_LAUNCH_CHECK("cheb_tables");
-  box_sources<<<nblk(nbox, kThreads), kThreads, 0, s>>>(t.leaf_start, h.trowptr, boff, L, dim, nbox, nsrc, npts);
+  box_sources<<<nblk(nbox, kThreads), kThreads, 0, s>>>(t.leaf_start, h.trowptr, boff, L, dim, nbox, row0, row1,
+                                                         nsrc, npts);
   HIKF_LAUNCH_CHECK("box_sources");
 
   const int64_t leaf0 = t.box_offset[L];
@@ -1052,7 +1060,7 @@ Status h2_product(const Tree& t, const SparseH& h, const FmmParams& fp, T* out, 
     size_t sm = smem_pts + sizeof(T) * ((size_t)kPT * (nchp + 1) + kPT * 6 + 4) + sizeof(int64_t) * 2 * kPT + p2p;
     HIKF_TRY(set_smem<T>((const void*)l2p_p2p_kernel<T>, sm));
     l2p_p2p_kernel<T><<<(unsigned)t.nleaf, kThreads, sm, s>>>(g, t.pts, t.leaf_start, h.trowptr, h.tcol, h.tval,
-                                                                tab, nsrc, leaf0, nchp, Lx, out);
+                                                                tab, nsrc, leaf0, nchp, Lx, row0, row1, out);
     HIKF_LAUNCH_CHECK("l2p_p2p");
   }
   HIKF_CUDA(cudaFreeAsync(tab, s));
@@ -1065,7 +1073,9 @@ Status h2_product(const Tree& t, const SparseH& h, const FmmParams& fp, T* out, 
   return Status::Ok();
 }
 
-template Status h2_product<float>(const Tree&, const SparseH&, const FmmParams&, float*, int, cudaStream_t);
-template Status h2_product<double>(const Tree&, const SparseH&, const FmmParams&, double*, int, cudaStream_t);
+template Status h2_product<float>(const Tree&, const SparseH&, const FmmParams&, float*, int, cudaStream_t, int64_t,
+                                  int64_t);
+template Status h2_product<double>(const Tree&, const SparseH&, const FmmParams&, double*, int, cudaStream_t, int64_t,
+                                   int64_t);
 
 }  // namespace hikf

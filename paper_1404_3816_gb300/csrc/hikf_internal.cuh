@@ -112,9 +112,12 @@ struct FmmParams {
   int sms = 1;
 };
 
-// out: [m x ldc] in tree order (T = float or double); columns >= n are zero.
+// out: rows [row0, row1) of the m x ldc product in tree order (T = float or double), row row0
+// first; columns >= n are zero. row1 < 0 means m. Only the target boxes that hold one of those
+// rows take part in the downward pass (M2L, L2L, L2P, P2P); the upward pass covers every source.
 template <typename T>
-Status h2_product(const Tree& t, const SparseH& h, const FmmParams& fp, T* out, int ldc, cudaStream_t s);
+Status h2_product(const Tree& t, const SparseH& h, const FmmParams& fp, T* out, int ldc, cudaStream_t s,
+                  int64_t row0 = 0, int64_t row1 = -1);
 
 int auto_depth(int64_t m, int dim, int leaf_size);
 

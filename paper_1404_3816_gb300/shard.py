@@ -133,6 +133,18 @@ class ShardedFilter:
         B._check(B.load().hikf_shard_get_variance(self.h, B._dp(out)), self.h)
         return out
 
+    def cq_local(self) -> np.ndarray:
+        """The rank's rows of the H^2 product C_Q (count x n, the rank's order)."""
+        out = np.empty((self.count, self.n))
+        B._check(B.load().hikf_get_cq(self.h, B._dp(out)), self.h)
+        return out
+
+    def cross_local(self) -> np.ndarray:
+        """The rank's rows of C_{t|t} (count x n, the rank's order)."""
+        out = np.empty((self.count, self.n))
+        B._check(B.load().hikf_get_cross(self.h, B._dp(out)), self.h)
+        return out
+
     def info(self) -> dict:
         i = B.Info()
         B._check(B.load().hikf_info(self.h, C.byref(i)), self.h)

@@ -119,6 +119,56 @@ def test_sharded_filter_equals_single_handle(nranks, prec, form, chain):
     assert rel(x, ref["x"]) < tol and rel(v, ref["var"]) < tol
 
 
+def _shard_products(w, nranks, **opts):
+    """Each rank's (caller index, C_Q rows, C_{1|0} rows) after create, ranks created in turn."""
+    from paper_1404_3816_gb300 import shard
+    comm = ThreadComm(nranks)
+    out, errs = [None] * nranks, []
+
+    def work(r):
+        try:
+            f = shard.ShardedFilter(comm.rank_view(r), w.points, w.q, w.h_rowptr, w.h_col, w.h_val, w.r_diag, w.x0,
+                                    w.p0, cheb_order=w.cheb_order, leaf_size=w.leaf_size, **opts)
+            out[r] = (f.caller_index(), f.cq_local(), f.cross_local(), f.info())
+            f.close()
+        except BaseException as e:
+            errs.append(e)
+            comm.bar.abort()
+
+    threads = [threading.Thread(target=work, args=(r,)) for r in range(nranks)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join(timeout=300)
+    if errs:
+        raise errs[0]
+    return out
+
+
+@pytest.mark.parametrize("nranks,prec,grid,leaf", [(2, "fp64", (61, 43), 16), (3, "fp64", (150, 131), 32),
+                                                   (3, "fp32", (150, 131), 32), (4, "mixed", (150, 131), 32),
+                                                   (3, "mixed", (97, 89), 64)])
+def test_sharded_h2_product_forms_exactly_the_ranks_rows(nranks, prec, grid, leaf):
+    """Each rank runs the downward pass of the H^2 product only for the boxes holding its rows;
+    its rows equal those of the whole product bit for bit (every row's sums are the same code
+    in the same order), and C_{1|0} (= C_Q (1 + 100) here) likewise."""
+    from paper_1404_3816_gb300 import binding as B
+    w = W.small(grid=grid, n=29, steps=1, seed=64)
+    w.leaf_size = leaf
+    parts = _shard_products(w, nranks, precision=prec)
+    with B.Filter.from_workload(w, precision=prec) as f:
+        cq1, c1 = f.cq(), f.cross()
+        depth = f.info()["depth"]
+    assert depth >= 3                                      # boxes cut by the rank boundaries at several levels
+    seen = np.zeros(w.m, dtype=int)
+    for idx, cq, c, info in parts:
+        assert info["depth"] == depth
+        seen[idx] += 1
+        np.testing.assert_array_equal(cq, cq1[idx])
+        np.testing.assert_array_equal(c, c1[idx])
+    assert (seen == 1).all()
+
+
 def test_sharded_filter_rejects_the_nspace_form_and_bad_ranks():
     from paper_1404_3816_gb300 import binding as B, shard
     w = W.small(grid=(20, 18), n=6, steps=1, seed=63)
