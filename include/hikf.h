@@ -387,6 +387,13 @@ hikf_status hikf_shard_get_variance(hikf_t* h, double* out);
  * tensor-core work in flight, frees its tensor memory and returns. */
 hikf_status hikf_test_set_wait_limit(uint64_t ns);
 
+/* Device memory: the filters' state and the scratch of a create come from one
+ * stream-ordered pool per device that the library owns. Freed memory stays cached in it,
+ * up to 16 GiB, so that the next create reuses it without mapping pages again (a handle's
+ * buffers return to it at hikf_destroy). This returns every cached byte to the device;
+ * memory held by live handles is not affected. HIKF_ECUDA on a CUDA error. */
+hikf_status hikf_release_cached_memory(void);
+
 /*
  * hikf_h2_qht — the H^2 product alone (Alg. 2 precomputation, Sec. 3.2:
  * Q H^T = [Q h^(1) ... Q h^(n)]), without a filter. Arguments as in

@@ -37,7 +37,7 @@ EXPORTED = ["hikf_options_default", "hikf_create", "hikf_create_dense_r", "hikf_
             "hikf_profile_enable", "hikf_profile_read", "hikf_spd_inverse", "hikf_spd_inverse_noalloc",
             "hikf_test_set_wait_limit", "hikf_create_shard", "hikf_shard_rows", "hikf_shard_caller_index",
             "hikf_shard_step_begin", "hikf_shard_step_end", "hikf_shard_get_mean", "hikf_shard_get_variance",
-            "hikf_assimilate_batch"]
+            "hikf_assimilate_batch", "hikf_release_cached_memory"]
 
 # hikf_allreduce_fn: int (*)(double* d_buf, int64_t count, void* ctx)
 ALLREDUCE_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int64, C.c_void_p)
@@ -114,6 +114,7 @@ def load(path: Optional[os.PathLike] = None) -> C.CDLL:
     lib.hikf_spd_inverse_noalloc.argtypes = [vp, C.c_int, vp, vp]
     lib.hikf_h2_qht.argtypes = [C.c_int, C.c_int64, dp, Kernel, C.c_int, ip, ip, dp, C.POINTER(Options), dp]
     lib.hikf_test_set_wait_limit.argtypes = [C.c_uint64]
+    lib.hikf_release_cached_memory.argtypes = []
     lib.hikf_create_shard.argtypes = [C.POINTER(H), C.POINTER(Shard), C.c_int, C.c_int64, dp, Kernel, C.c_int, ip, ip,
                                       dp, dp, dp, Kernel, C.POINTER(Options)]
     lib.hikf_shard_rows.argtypes = [H, ip, ip]
@@ -409,6 +410,11 @@ def _spd_args(d_S, d_M):
 
 def _stream_ptr(stream):
     return None if stream is None else C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+
+
+def release_cached_memory() -> None:
+    """Return the device memory cached in the library's pool (freed state and create scratch)."""
+    _check(load().hikf_release_cached_memory(), None)
 
 
 def spd_inverse(d_S, d_M, stream=None):

@@ -3,6 +3,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <mutex>
+
 #include <algorithm>
 #include <chrono>
 #include <new>
@@ -28,14 +30,65 @@ Status cuda_status(cudaError_t e, const char* what, const char* file, int line) 
   return make_status(e == cudaErrorMemoryAllocation ? HIKF_ENOMEM : HIKF_ECUDA, m);
 }
 
+namespace {
+constexpr int kMaxPoolDevices = 64;
+std::mutex g_pool_mutex;
+cudaMemPool_t g_pools[kMaxPoolDevices] = {};
+
+cudaError_t pool_for(int dev, cudaMemPool_t* out) {
+  if (dev < 0 || dev >= kMaxPoolDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_pool_mutex);
+  if (!g_pools[dev]) {
+    cudaMemPoolProps pr;
+    memset(&pr, 0, sizeof(pr));
+    pr.allocType = cudaMemAllocationTypePinned;
+    pr.handleTypes = cudaMemHandleTypeNone;
+    pr.location.type = cudaMemLocationTypeDevice;
+    pr.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = cudaMemPoolCreate(&pool, &pr);
+    if (e != cudaSuccess) return e;
+    uint64_t keep = kPoolKeepBytes;
+    e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) {
+      cudaMemPoolDestroy(pool);
+      return e;
+    }
+    g_pools[dev] = pool;
+  }
+  *out = g_pools[dev];
+  return cudaSuccess;
+}
+}  // namespace
+
+cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t s) {
+  *p = nullptr;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  cudaMemPool_t pool = nullptr;
+  if (e == cudaSuccess) e = pool_for(dev, &pool);
+  if (e != cudaSuccess) return e;
+  return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
+cudaError_t pool_trim_all() {
+  std::lock_guard<std::mutex> lk(g_pool_mutex);
+  for (cudaMemPool_t pool : g_pools)
+    if (pool) {
+      cudaError_t e = cudaMemPoolTrimTo(pool, 0);
+      if (e != cudaSuccess) return e;
+    }
+  return cudaSuccess;
+}
+
 Status Arena::alloc(void** p, size_t nbytes) {
   *p = nullptr;
   if (count >= 64) return make_status(HIKF_ENOMEM, "arena full");
   if (nbytes == 0) nbytes = 16;
-  cudaError_t e = cudaMalloc(p, nbytes);
+  cudaError_t e = pool_malloc(p, nbytes, stream);
   if (e != cudaSuccess) {
     *p = nullptr;
-    return cuda_status(e, "cudaMalloc", __FILE__, __LINE__);
+    return cuda_status(e, "device allocation", __FILE__, __LINE__);
   }
   ptrs[count++] = *p;
   bytes += (int64_t)nbytes;
@@ -43,7 +96,7 @@ Status Arena::alloc(void** p, size_t nbytes) {
 }
 
 void Arena::release() {
-  for (int i = 0; i < count; ++i) cudaFree(ptrs[i]);
+  for (int i = 0; i < count; ++i) cudaFreeAsync(ptrs[i], stream);
   count = 0;
   bytes = 0;
 }
@@ -361,8 +414,8 @@ double spectral_cond_bound(const std::vector<double>& lam, const double* r_diag,
 Status factor_cond(const double* dS, int n, double* scratch, cudaStream_t s, double* cond) {
   double* dM = nullptr;
   int* dflag = nullptr;
-  HIKF_CUDA(cudaMallocAsync((void**)&dM, sizeof(double) * (size_t)n * n, s));
-  HIKF_CUDA(cudaMallocAsync((void**)&dflag, sizeof(int) * 2, s));
+  HIKF_CUDA(hikf::pool_malloc((void**)&dM, sizeof(double) * (size_t)n * n, s));
+  HIKF_CUDA(hikf::pool_malloc((void**)&dflag, sizeof(int) * 2, s));
   Status st = hikf::spd_inverse_f64(dS, n, dM, scratch, dflag, s);
   std::vector<double> S((size_t)n * n), M((size_t)n * n);
   int f[2] = {0, 0};
@@ -417,7 +470,7 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
   h->CQ = CQ;
   if (cq) {
     double* d = nullptr;
-    HIKF_CUDA(cudaMallocAsync((void**)&d, sizeof(double) * (size_t)m * n, s));
+    HIKF_CUDA(hikf::pool_malloc((void**)&d, sizeof(double) * (size_t)m * n, s));
     HIKF_CUDA(cudaMemcpyAsync(d, cq, sizeof(double) * (size_t)m * n, cudaMemcpyHostToDevice, s));
     hikf::rows_to_tree<T><<<hikf::nblk(m * ld, 256), 256, 0, s>>>(d, h->tree.perm, m, n, ld, CQ);
     HIKF_LAUNCH_CHECK("rows_to_tree");
@@ -471,11 +524,11 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
     HIKF_TRY(hikf::arena_alloc(h->arena, &h->LT, nn0));
     HIKF_TRY(hikf::arena_alloc(h->arena, &h->eraw, n));
     HIKF_TRY(hikf::arena_alloc(h->arena, &h->yw, n));
-    HIKF_CUDA(cudaMallocAsync((void**)&dR, sizeof(double) * nn0, s));
-    HIKF_CUDA(cudaMallocAsync((void**)&w1, sizeof(double) * nn0, s));
-    HIKF_CUDA(cudaMallocAsync((void**)&w2, sizeof(double) * nn0, s));
-    HIKF_CUDA(cudaMallocAsync((void**)&linvT, sizeof(double) * nn0, s));
-    HIKF_CUDA(cudaMallocAsync((void**)&wflag, sizeof(int) * 2, s));
+    HIKF_CUDA(hikf::pool_malloc((void**)&dR, sizeof(double) * nn0, s));
+    HIKF_CUDA(hikf::pool_malloc((void**)&w1, sizeof(double) * nn0, s));
+    HIKF_CUDA(hikf::pool_malloc((void**)&w2, sizeof(double) * nn0, s));
+    HIKF_CUDA(hikf::pool_malloc((void**)&linvT, sizeof(double) * nn0, s));
+    HIKF_CUDA(hikf::pool_malloc((void**)&wflag, sizeof(int) * 2, s));
     HIKF_CUDA(cudaMemcpyAsync(dR, r_full, sizeof(double) * nn0, cudaMemcpyHostToDevice, s));
     HIKF_TRY(hikf::launch_whiten_factors(dR, n, w1, w2, h->Linv, linvT, h->LT, wflag, s));
     int wf[2] = {0, 0};
@@ -483,7 +536,7 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
     HIKF_CUDA(cudaStreamSynchronize(s));
     if (wf[0] & 2) return hikf::make_status(HIKF_EINVAL, "R is not positive definite");
     T* tmp = nullptr;
-    HIKF_CUDA(cudaMallocAsync((void**)&tmp, sizeof(T) * (size_t)m * ld, s));
+    HIKF_CUDA(hikf::pool_malloc((void**)&tmp, sizeof(T) * (size_t)m * ld, s));
     HIKF_TRY(hikf::gemm_rows_small<T>(CQ, m, ld, n, linvT, tmp, s));
     HIKF_CUDA(cudaMemcpyAsync(CQ, tmp, sizeof(T) * (size_t)m * ld, cudaMemcpyDeviceToDevice, s));
     HIKF_TRY(hikf::gemm_rows_small<T>(C, m, ld, n, linvT, tmp, s));
@@ -497,7 +550,7 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
   }
   // n x n products H A of the whitened operator: L^{-1} (H A), in place through a scratch
   double* wscr = nullptr;
-  if (h->whiten) HIKF_CUDA(cudaMallocAsync((void**)&wscr, sizeof(double) * (size_t)n * n, s));
+  if (h->whiten) HIKF_CUDA(hikf::pool_malloc((void**)&wscr, sizeof(double) * (size_t)n * n, s));
   auto whiten_nn = [&](double* A) -> Status {
     if (!h->whiten) return Status::Ok();
     HIKF_TRY(hikf::launch_left_lower(h->Linv, A, n, wscr, s));
@@ -513,8 +566,8 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
     // x_0 of all points in tree order, then the rank's rows
     double *xc = nullptr, *xt = nullptr;
     const int64_t mf = h->m_full;
-    HIKF_CUDA(cudaMallocAsync((void**)&xc, sizeof(double) * mf, s));
-    HIKF_CUDA(cudaMallocAsync((void**)&xt, sizeof(double) * mf, s));
+    HIKF_CUDA(hikf::pool_malloc((void**)&xc, sizeof(double) * mf, s));
+    HIKF_CUDA(hikf::pool_malloc((void**)&xt, sizeof(double) * mf, s));
     if (x0) HIKF_CUDA(cudaMemcpyAsync(xc, x0, sizeof(double) * mf, cudaMemcpyHostToDevice, s));
     hikf::vec_to_tree<<<hikf::nblk(mf, 256), 256, 0, s>>>(x0 ? xc : nullptr, h->tree.perm, mf, xt);
     HIKF_LAUNCH_CHECK("vec_to_tree");
@@ -538,9 +591,9 @@ Status setup_state(hikf_t* h, const hikf_kernel& q, const hikf_kernel& p0, const
   HIKF_TRY(hikf::arena_alloc(h->arena, &h->S, (size_t)n * n));
   HIKF_CUDA(cudaMemcpyAsync(h->rd, r_diag, sizeof(double) * n, cudaMemcpyHostToDevice, s));
   double *hcq = nullptr, *a1 = nullptr, *zero = nullptr;
-  HIKF_CUDA(cudaMallocAsync((void**)&hcq, sizeof(double) * 2 * (size_t)n * n, s));  // [H C_Q | H C_1]
+  HIKF_CUDA(hikf::pool_malloc((void**)&hcq, sizeof(double) * 2 * (size_t)n * n, s));  // [H C_Q | H C_1]
   a1 = hcq + (size_t)n * n;
-  HIKF_CUDA(cudaMallocAsync((void**)&zero, sizeof(double) * n, s));
+  HIKF_CUDA(hikf::pool_malloc((void**)&zero, sizeof(double) * n, s));
   HIKF_CUDA(cudaMemsetAsync(zero, 0, sizeof(double) * n, s));
   HIKF_TRY(hikf::launch_gather_hc<T>(h->H, CQ, ld, hcq, 0, s));
   HIKF_TRY(hikf::launch_gather_hc<T>(h->H, C, ld, a1, 0, s));
@@ -1060,6 +1113,7 @@ hikf_status create_impl(hikf_t** out, int dim, int64_t m, const double* points, 
     if (e != cudaSuccess) return bail(hikf::cuda_status(e, "cudaStreamCreate", __FILE__, __LINE__));
     h->own_stream = true;
   }
+  h->arena.stream = h->stream;
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1069,8 +1123,8 @@ hikf_status create_impl(hikf_t** out, int dim, int64_t m, const double* points, 
   const int dmax = dim == 2 ? hikf::kMaxDepth2D : hikf::kMaxDepth3D;
   if (h->tree.depth > dmax) return bail(hikf::make_status(HIKF_EINVAL, "automatic depth too large; raise leaf_size"));
   double* d_pts = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&d_pts, sizeof(double) * (size_t)m * dim, h->stream);
-  if (e != cudaSuccess) return bail(hikf::cuda_status(e, "cudaMallocAsync", __FILE__, __LINE__));
+  cudaError_t e = hikf::pool_malloc((void**)&d_pts, sizeof(double) * (size_t)m * dim, h->stream);
+  if (e != cudaSuccess) return bail(hikf::cuda_status(e, "device allocation", __FILE__, __LINE__));
   e = cudaMemcpyAsync(d_pts, points, sizeof(double) * (size_t)m * dim, cudaMemcpyHostToDevice, h->stream);
   if (e != cudaSuccess) return bail(hikf::cuda_status(e, "cudaMemcpyAsync", __FILE__, __LINE__));
   st = hikf::build_tree(h->tree, h->arena, d_pts, h->stream);
@@ -1307,7 +1361,7 @@ hikf_status hikf_assimilate_batch(hikf_t* const* hs, const double* const* d_y, i
     if (items.empty()) continue;
     hikf::TcItem* d_items = nullptr;
     const size_t bytes = sizeof(hikf::TcItem) * items.size();
-    cudaError_t e = cudaMallocAsync((void**)&d_items, bytes, lead->stream);
+    cudaError_t e = hikf::pool_malloc((void**)&d_items, bytes, lead->stream);
     if (e == cudaSuccess)  // pageable source: staged before the call returns
       e = cudaMemcpyAsync(d_items, items.data(), bytes, cudaMemcpyHostToDevice, lead->stream);
     if (e != cudaSuccess) {
@@ -1391,16 +1445,16 @@ static hikf_status get_mat(hikf_t* h, const void* src, double* out) {
   const size_t bytes = sizeof(double) * (size_t)h->m * h->n;
   // a shard returns its own rows in its order (hikf_shard_caller_index maps them)
   const int64_t* perm = h->shard ? nullptr : h->tree.perm;
-  cudaError_t e = cudaMallocAsync((void**)&d, bytes, h->stream);
-  if (e != cudaSuccess) return fail(h, hikf::cuda_status(e, "cudaMallocAsync", __FILE__, __LINE__));
+  cudaError_t e = hikf::pool_malloc((void**)&d, bytes, h->stream);
+  if (e != cudaSuccess) return fail(h, hikf::cuda_status(e, "device allocation", __FILE__, __LINE__));
   void* unw = nullptr;
   if (h->whiten) {
     // the matrices are held in the whitened measurement space: C = C' L^T for the caller
     const size_t tb = (h->fp64() ? sizeof(double) : sizeof(float)) * (size_t)h->m * h->ld;
-    e = cudaMallocAsync(&unw, tb, h->stream);
+    e = hikf::pool_malloc(&unw, tb, h->stream);
     if (e != cudaSuccess) {
       cudaFreeAsync(d, h->stream);
-      return fail(h, hikf::cuda_status(e, "cudaMallocAsync", __FILE__, __LINE__));
+      return fail(h, hikf::cuda_status(e, "device allocation", __FILE__, __LINE__));
     }
     Status st = h->fp64() ? hikf::gemm_rows_small<double>((const double*)src, h->m, h->ld, h->n, h->LT,
                                                           (double*)unw, h->stream)
@@ -1538,9 +1592,16 @@ void hikf_destroy(hikf_t* h) {
   for (auto& e : h->gev)
     if (e) cudaEventDestroy(e);
   h->arena.release();
+  if (h->stream) cudaStreamSynchronize(h->stream);  // the frees are done before the stream goes
   for (auto& e : h->ev) cudaEventDestroy(e);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
+}
+
+hikf_status hikf_release_cached_memory(void) {
+  cudaError_t e = hikf::pool_trim_all();
+  if (e != cudaSuccess) return fail(nullptr, hikf::cuda_status(e, "release cached memory", __FILE__, __LINE__));
+  return HIKF_OK;
 }
 
 hikf_status hikf_spd_inverse(const double* d_S, int n, double* d_M, void* stream) {
@@ -1549,9 +1610,9 @@ hikf_status hikf_spd_inverse(const double* d_S, int n, double* d_M, void* stream
   cudaStream_t s = (cudaStream_t)stream;
   double* scratch = nullptr;
   int* flag = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&scratch, sizeof(double) * (size_t)n * n, s);
-  if (e == cudaSuccess) e = cudaMallocAsync((void**)&flag, sizeof(int) * 2, s);
-  if (e != cudaSuccess) return fail(nullptr, hikf::cuda_status(e, "cudaMallocAsync", __FILE__, __LINE__));
+  cudaError_t e = hikf::pool_malloc((void**)&scratch, sizeof(double) * (size_t)n * n, s);
+  if (e == cudaSuccess) e = hikf::pool_malloc((void**)&flag, sizeof(int) * 2, s);
+  if (e != cudaSuccess) return fail(nullptr, hikf::cuda_status(e, "device allocation", __FILE__, __LINE__));
   Status st = hikf::spd_inverse_f64(d_S, n, d_M, scratch, flag, s);
   int f[2] = {0, 0};
   if (st.ok()) {

@@ -950,10 +950,10 @@ Status h2_product(const Tree& t, const SparseH& h, const FmmParams& fp, T* out, 
   int64_t *nsrc = nullptr, *npts = nullptr, *boff = nullptr;
   T *W = nullptr, *Lx = nullptr, *kop = nullptr;
   const size_t boxbytes = sizeof(T) * (size_t)q * ldc;
-  HIKF_CUDA(cudaMallocAsync((void**)&tab, sizeof(double) * 3 * kPMax * kPMax, s));
-  HIKF_CUDA(cudaMallocAsync((void**)&nsrc, sizeof(int64_t) * nbox, s));
-  HIKF_CUDA(cudaMallocAsync((void**)&npts, sizeof(int64_t) * nbox, s));
-  HIKF_CUDA(cudaMallocAsync((void**)&boff, sizeof(int64_t) * (L + 2), s));
+  HIKF_CUDA(hikf::pool_malloc((void**)&tab, sizeof(double) * 3 * kPMax * kPMax, s));
+  HIKF_CUDA(hikf::pool_malloc((void**)&nsrc, sizeof(int64_t) * nbox, s));
+  HIKF_CUDA(hikf::pool_malloc((void**)&npts, sizeof(int64_t) * nbox, s));
+  HIKF_CUDA(hikf::pool_malloc((void**)&boff, sizeof(int64_t) * (L + 2), s));
   HIKF_CUDA(cudaMemcpyAsync(boff, t.box_offset, sizeof(int64_t) * (L + 2), cudaMemcpyHostToDevice, s));
   cheb_tables<<<1, 512, 0, s>>>(p, tab);
   HIKF_LAUNCH_CHECK("cheb_tables");
@@ -964,13 +964,13 @@ Status h2_product(const Tree& t, const SparseH& h, const FmmParams& fp, T* out, 
   const int64_t leaf0 = t.box_offset[L];
   const size_t smem_pts = sizeof(T) * (kPMax * kPMax + kPT * 3 * kPMax + (size_t)kPT * q);
   if (L >= 2) {
-    HIKF_CUDA(cudaMallocAsync((void**)&W, boxbytes * nbox, s));
-    HIKF_CUDA(cudaMallocAsync((void**)&Lx, boxbytes * nbox, s));
+    HIKF_CUDA(hikf::pool_malloc((void**)&W, boxbytes * nbox, s));
+    HIKF_CUDA(hikf::pool_malloc((void**)&Lx, boxbytes * nbox, s));
     HIKF_CUDA(cudaMemsetAsync(W, 0, boxbytes * nbox, s));
     HIKF_CUDA(cudaMemsetAsync(Lx, 0, boxbytes * nbox, s));
     const int noff = ipow(7, dim);
     const int64_t ktotal = (int64_t)(L - 1) * noff * q * q;
-    HIKF_CUDA(cudaMallocAsync((void**)&kop, sizeof(T) * ktotal, s));
+    HIKF_CUDA(hikf::pool_malloc((void**)&kop, sizeof(T) * ktotal, s));
     m2l_table<T><<<nblk(ktotal, kThreads), kThreads, 0, s>>>(g, tab, kop, ktotal);
     HIKF_LAUNCH_CHECK("m2l_table");
     // P2M
@@ -998,7 +998,7 @@ Status h2_product(const Tree& t, const SparseH& h, const FmmParams& fp, T* out, 
     const bool tc = fp.tensor_m2l && sizeof(T) == 4 && m2l_tc_supported(q, ldc) && L - 1 <= 16;
     if (tc) {
       int* err = nullptr;
-      HIKF_CUDA(cudaMallocAsync((void**)&err, sizeof(int), s));
+      HIKF_CUDA(hikf::pool_malloc((void**)&err, sizeof(int), s));
       HIKF_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
       M2lTcAll ma;
       ma.dim = dim;

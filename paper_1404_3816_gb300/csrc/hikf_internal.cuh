@@ -49,10 +49,24 @@ hikf_status set_global_error(const Status& s);
 
 // Device memory arena of one handle: every buffer is cudaMalloc'ed at create
 // and released at destroy.
+// Device memory of the library comes from one stream-ordered pool per device that keeps up
+// to kPoolKeepBytes of freed memory for reuse (the next create's scratch and state reuse it
+// without mapping pages again); pool_trim_all() returns the cached memory to the device.
+constexpr uint64_t kPoolKeepBytes = 16ull << 30;
+cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t s);
+template <typename T>
+inline cudaError_t pool_malloc(T** p, size_t bytes, cudaStream_t s) {
+  return pool_malloc(reinterpret_cast<void**>(p), bytes, s);
+}
+cudaError_t pool_trim_all();
+
+// A handle's long-lived buffers: allocated from the pool in the order of `stream`, released
+// in that order by release() (the caller has synchronised the stream first).
 struct Arena {
   void* ptrs[64];
   int count = 0;
   int64_t bytes = 0;
+  cudaStream_t stream = nullptr;
   Status alloc(void** p, size_t nbytes);
   void release();
 };

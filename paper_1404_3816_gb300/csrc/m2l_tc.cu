@@ -499,7 +499,7 @@ Status m2l_tc_all(const M2lTcAll& a, cudaStream_t s) {
   // operator images of all levels for one pass of up to 128 operator rows (MMA N)
   const int64_t b_chunk_max = 128 * 128, b_off_max = 2 * (int64_t)nkc * b_chunk_max;
   unsigned char* kimg = nullptr;
-  HIKF_CUDA(cudaMallocAsync((void**)&kimg, (size_t)((int64_t)a.nlev * noff * b_off_max), s));
+  HIKF_CUDA(hikf::pool_malloc((void**)&kimg, (size_t)((int64_t)a.nlev * noff * b_off_max), s));
   Status st;
   // passes of up to 256 rays (two 128-row MMA halves); W is packed once per ray pass
   for (int r0 = 0; r0 < a.ld && st.ok(); r0 += 256) {
@@ -514,7 +514,7 @@ Status m2l_tc_all(const M2lTcAll& a, cudaStream_t s) {
     d.a_chunk_bytes = (int64_t)d.ldp * 128;
     d.a_box_bytes = 2 * (int64_t)d.nkc * d.a_chunk_bytes;
     unsigned char* wimg = nullptr;
-    HIKF_CUDA(cudaMallocAsync((void**)&wimg, (size_t)(nboxes * d.a_box_bytes), s));
+    HIKF_CUDA(hikf::pool_malloc((void**)&wimg, (size_t)(nboxes * d.a_box_bytes), s));
     const int64_t wthreads = nboxes * (int64_t)d.nkc * (kKC / 4) * d.ldp;
     pack_w_kernel<<<nblk(wthreads, 256), 256, 0, s>>>(a.W, wbox0, nboxes, a.nsrc, d, wimg);
     HIKF_LAUNCH_CHECK("pack_w");

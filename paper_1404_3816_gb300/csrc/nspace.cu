@@ -225,7 +225,7 @@ template <typename T>
 Status nspace_cross(const SpectralState& sp, const NspaceState& ns, const double* rd, int64_t m, int ld, int n,
                     const T* Gq, T* out, cudaStream_t s) {
   double* B = nullptr;
-  HIKF_CUDA(cudaMallocAsync((void**)&B, sizeof(double) * (size_t)n * n, s));
+  HIKF_CUDA(hikf::pool_malloc((void**)&B, sizeof(double) * (size_t)n * n, s));
   nspace_wtr_kernel<<<nb((int64_t)n * n, 256), 256, 0, s>>>(sp.W64, rd, ns.gam, n, B);
   HIKF_LAUNCH_CHECK("nspace_wtr");
   HIKF_TRY(gemm_rows_small<T>(Gq, m, ld, n, B, out, s));

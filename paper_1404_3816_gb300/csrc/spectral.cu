@@ -86,17 +86,6 @@ __device__ __forceinline__ void rr_pair(int r, int k, int N, int& p, int& q) {
     q = t;
   }
 }
-// index of the pair that holds a in round r, and a's partner
-__device__ __forceinline__ int rr_slot(int r, int a, int N, int& partner) {
-  if (a == N - 1 || a == r) {
-    partner = a == r ? N - 1 : r;
-    return 0;
-  }
-  partner = rr_mod(2 * r - a, N - 1);
-  const int d = rr_mod(a - r, N - 1);
-  return min(d, N - 1 - d);
-}
-
 // One Jacobi rotation J (J_pp = J_qq = c, J_pq = s, J_qp = -s) with (J^T A J)_pq = 0:
 // t = tan(phi) is the smaller root of t^2 + 2 tau t - 1 = 0, tau = (a_qq - a_pp) / (2 a_pq).
 // With d = a_qq - a_pp, b = 2 a_pq, h = hypot(d, b), u = h + |d| this is t = sign(d) b / u,
@@ -138,164 +127,207 @@ __device__ __forceinline__ bool jacobi_rotation(double app, double aqq, double a
 
 constexpr int kJacThreads = 256;
 
-// A (N x N, row-major, symmetric) -> diag(lambda) in place; VT (N x N) -> V^T (row j =
-// eigenvector j). diag and pq are round-parity double buffers (2 x N and 2 x N/2): the
-// rotations of a round read only them, and the round's updates write the other parity,
-// so a CTA that is still forming rotations never sees A change under it, and one grid
-// barrier per round suffices. Every CTA forms all N/2 rotations of a round itself (the
-// same inputs give the same rotations and the same convergence decision in every CTA),
-// with each index's slot and partner in the next round, which tell a block's thread
-// which of its four new entries to export. The updates are dealt to the CTAs as tasks:
-// block row i of A (blocks j >= i, the diagonal block included, each written with its
-// mirror) or column pair k of V. Every entry of A and V has one writer per round.
-// info[0] = 1 when max_sweeps sweeps did not converge; *sweeps = sweeps run.
+// Per index i, the effect of one round: the rotation of i's pair acts on rows (and on
+// columns) as new_i = al_i old_i + be_i old_j with j = jp_i, its partner; td_i gives the
+// rotated diagonal entry a_ii + td_i a_ij, and on_i whether the pair was rotated (its
+// off-diagonal entry is then exactly zero).
+struct JacRound {
+  int jp[kMaxN];
+  int on[kMaxN];
+  double al[kMaxN], be[kMaxN], td[kMaxN];
+};
+
+__device__ __forceinline__ void jac_record(JacRound& R, int p, int q, bool on, double c, double s, double t) {
+  R.jp[p] = q;
+  R.jp[q] = p;
+  R.on[p] = R.on[q] = on ? 1 : 0;
+  R.al[p] = R.al[q] = c;
+  R.be[p] = -s;  // new_p = c old_p - s old_q
+  R.be[q] = s;   // new_q = s old_p + c old_q
+  R.td[p] = -t;  // a_pp - t a_pq
+  R.td[q] = t;   // a_qq + t a_pq
+}
+
+// Entry (x, y) of A after one round R, from the entries of A before it.
+__device__ __forceinline__ double jac_after(const double* __restrict__ A, int N, const JacRound& R, int x, int y) {
+  const int jx = R.jp[x];
+  if (y == x) return fma(R.td[x], A[(int64_t)x * N + jx], A[(int64_t)x * N + x]);
+  if (y == jx) return R.on[x] ? 0.0 : A[(int64_t)x * N + y];
+  const int jy = R.jp[y];
+  const double u = fma(R.be[y], A[(int64_t)x * N + jy], R.al[y] * A[(int64_t)x * N + y]);
+  const double w = fma(R.be[y], A[(int64_t)jx * N + jy], R.al[y] * A[(int64_t)jx * N + y]);
+  return fma(R.be[x], w, R.al[x] * u);
+}
+
+// A (N x N, row-major, symmetric) -> diag(lambda); VT (N x N) -> V^T (row j = eigenvector
+// j). A and VT are parity double buffers (2 x N x N each; the input in parity 0): a step
+// reads one parity and writes every entry of the other, so a CTA still reading never sees
+// an entry change under it. One step applies two consecutive rounds of the cyclic order
+// (round-robin pairing, every pair meeting once per N - 1 rounds) behind one grid barrier:
+// every CTA forms the first round's rotations from A, then the second round's from the
+// entries that the first round leaves on that round's pairs (each a combination of at most
+// four entries of A), and the update writes A after both rounds as J2^T (J1^T A J1) J2 in
+// blocks of the second round's pairs (each block's four entries from a 4 x 4 set of A).
+// Every CTA forms the same rotations and the same decisions. Tasks: block row i of the
+// second round's pairs (blocks j >= i, each with its mirror) or its column pair k of V.
+// The iteration ends after N - 1 consecutive rounds without a rotation (no entry left
+// above the thresholds) or max_sweeps x (N - 1) rounds. out[0] = 1 when it did not
+// converge, out[1] = sweeps run (rounds / (N - 1), rounded up), out[4] = the parity that
+// holds the result.
 __global__ void __launch_bounds__(kJacThreads) eig_jacobi_kernel(double* __restrict__ A, double* __restrict__ VT,
-                                                                 int N, int max_sweeps,
-                                                                 double* __restrict__ diag,
-                                                                 double* __restrict__ pq,
-                                                                 unsigned* bar, int* err, int* info,
-                                                                 int* sweeps) {
-  __shared__ double sc[kMaxN / 2], ssn[kMaxN / 2], st[kMaxN / 2];
-  __shared__ int spi[kMaxN / 2], sqi[kMaxN / 2], son[kMaxN / 2];
-  __shared__ int sslp[kMaxN / 2], sptp[kMaxN / 2], sslq[kMaxN / 2], sptq[kMaxN / 2];
-  __shared__ int s_rot;
+                                                                 int N, int max_sweeps, unsigned* bar, int* err,
+                                                                 int* out) {
+  __shared__ JacRound R1;
+  __shared__ int sp2[kMaxN / 2], sq2[kMaxN / 2], son2[kMaxN / 2];
+  __shared__ double sc2[kMaxN / 2], ss2[kMaxN / 2], st2[kMaxN / 2];
+  __shared__ double sapp[kMaxN / 2], saqq[kMaxN / 2], sapq[kMaxN / 2];
+  __shared__ int s_rot1, s_rot2;
   __shared__ volatile int s_abort;
+  __shared__ double s_dmax;
   const int P = N / 2;
+  const int64_t NN = (int64_t)N * N;
   const int tid = threadIdx.x;
-  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + tid, gthreads = (int64_t)gridDim.x * blockDim.x;  // setup only
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + tid, gthreads = (int64_t)gridDim.x * blockDim.x;
   unsigned gen = 0;
   if (tid == 0) s_abort = 0;
-  // V = I; round-0 inputs into parity 0
-  for (int64_t u = gtid; u < (int64_t)N * N; u += gthreads) VT[u] = (u / N == u % N) ? 1.0 : 0.0;
-  for (int64_t u = gtid; u < N; u += gthreads) diag[u] = A[u * N + u];
-  for (int64_t k = gtid; k < P; k += gthreads) {
-    int p, q;
-    rr_pair(0, (int)k, N, p, q);
-    pq[k] = A[(int64_t)p * N + q];
-  }
+  for (int64_t u = gtid; u < NN; u += gthreads) VT[u] = (u / N == u % N) ? 1.0 : 0.0;
   if (!grid_barrier(bar, gen, err, &s_abort)) return;
   // absolute floor for a negligible off-diagonal entry: eps max|a_ii| / N, so the entries
   // left out add up (Frobenius) to at most eps max|a_ii|, the backward error of any FP64
   // eigensolver. It ends the iteration on graded spectra (a smooth kernel's), where the
   // entries coupling the smallest eigenvalues carry rounding from rotations with the
-  // largest ones and never fall below eps relative to their own diagonal. Every CTA forms
-  // the same value.
-  __shared__ double s_dmax;
+  // largest ones and never fall below eps relative to their own diagonal.
   if (tid == 0) {
     double m = 0.0;
-    for (int i = 0; i < N; ++i) m = fmax(m, fabs(diag[i]));
+    for (int i = 0; i < N; ++i) m = fmax(m, fabs(A[(int64_t)i * N + i]));
     s_dmax = m;
   }
   __syncthreads();
   const double floor_abs = 2.220446049250313e-16 * s_dmax / N;
-  int par = 0, sw = 0;
-  bool converged = false;
-  for (; sw < max_sweeps && !converged; ++sw) {
-    if (tid == 0) s_rot = 0;
-    for (int r = 0; r + 1 < N; ++r) {
-      const int rn = r + 2 < N ? r + 1 : 0;  // the next round (wraps into the next sweep)
-      const double* dg = diag + par * N;
-      const double* pg = pq + par * P;
-      double* dn = diag + (par ^ 1) * N;
-      double* pn = pq + (par ^ 1) * P;
-      __syncthreads();
-      for (int k = tid; k < P; k += blockDim.x) {
-        int p, q;
-        rr_pair(r, k, N, p, q);
-        double c, s_, t;
-        const bool on = jacobi_rotation(dg[p], dg[q], pg[k], floor_abs, c, s_, t);
-        if (on) atomicAdd(&s_rot, 1);
-        sc[k] = c;
-        ssn[k] = s_;
-        st[k] = t;
-        spi[k] = p;
-        sqi[k] = q;
-        son[k] = on ? 1 : 0;
-        // where p and q go in the next round: the slot of their pair and their partner
-        int pp, pq2;
-        sslp[k] = rr_slot(rn, p, N, pp);
-        sptp[k] = pp;
-        sslq[k] = rr_slot(rn, q, N, pq2);
-        sptq[k] = pq2;
-      }
-      __syncthreads();
-      // updates: tasks 0 .. P-1 are the block rows i (blocks j >= i), tasks P .. 2P-1 the
-      // column pairs of V; tasks are dealt to the CTAs in turn
-      for (int task = blockIdx.x; task < 2 * P; task += gridDim.x) {
-        if (task < P) {
-          const int i = task, p = spi[i], q = sqi[i];
-          for (int j = i + tid; j < P; j += blockDim.x) {
-            if (j == i) {  // diagonal block: a_pp - t a_pq, a_qq + t a_pq, a_pq -> 0
-              const double t = st[i], apq = A[(int64_t)p * N + q];
-              const double app = A[(int64_t)p * N + p] - t * apq, aqq = A[(int64_t)q * N + q] + t * apq;
-              A[(int64_t)p * N + p] = app;
-              A[(int64_t)q * N + q] = aqq;
-              A[(int64_t)p * N + q] = 0.0;
-              A[(int64_t)q * N + p] = 0.0;
-              dn[p] = app;
-              dn[q] = aqq;
-              if (sptp[i] == q) pn[sslp[i]] = 0.0;  // N = 2: the same pair meets again
-              continue;
-            }
-            const int u0 = spi[j], v0 = sqi[j];
-            double x00 = A[(int64_t)p * N + u0], x01 = A[(int64_t)p * N + v0];
-            double x10 = A[(int64_t)q * N + u0], x11 = A[(int64_t)q * N + v0];
-            if (son[i] | son[j]) {
-              const double c1 = sc[i], s1 = ssn[i], c2 = sc[j], s2 = ssn[j];
-              // rows: J_i^T X
-              const double y00 = c1 * x00 - s1 * x10, y01 = c1 * x01 - s1 * x11;
-              const double y10 = s1 * x00 + c1 * x10, y11 = s1 * x01 + c1 * x11;
-              // columns: Y J_j
-              x00 = c2 * y00 - s2 * y01;
-              x01 = s2 * y00 + c2 * y01;
-              x10 = c2 * y10 - s2 * y11;
-              x11 = s2 * y10 + c2 * y11;
-              A[(int64_t)p * N + u0] = x00;
-              A[(int64_t)p * N + v0] = x01;
-              A[(int64_t)q * N + u0] = x10;
-              A[(int64_t)q * N + v0] = x11;
-              A[(int64_t)u0 * N + p] = x00;
-              A[(int64_t)v0 * N + p] = x01;
-              A[(int64_t)u0 * N + q] = x10;
-              A[(int64_t)v0 * N + q] = x11;
-            }
-            // export the entries that form a pair of the next round
-            if (sptp[i] == u0) pn[sslp[i]] = x00;
-            if (sptp[i] == v0) pn[sslp[i]] = x01;
-            if (sptq[i] == u0) pn[sslq[i]] = x10;
-            if (sptq[i] == v0) pn[sslq[i]] = x11;
-          }
-        } else {
-          const int k = task - P;
-          if (!son[k]) continue;
-          const double c = sc[k], s_ = ssn[k];
-          double* vp = VT + (int64_t)spi[k] * N;
-          double* vq = VT + (int64_t)sqi[k] * N;
-          for (int comp = tid; comp < N; comp += blockDim.x) {
-            const double a = vp[comp], b = vq[comp];
-            vp[comp] = c * a - s_ * b;
-            vq[comp] = s_ * a + c * b;
-          }
-        }
-      }
-      par ^= 1;
-      if (!grid_barrier(bar, gen, err, &s_abort)) return;
+  const int64_t cycle = N - 1, max_rounds = (int64_t)max_sweeps * cycle;
+  int par = 0;
+  int64_t g = 0, quiet = 0;
+  while (g < max_rounds && quiet < cycle) {
+    const double* Ac = A + par * NN;
+    const double* Vc = VT + par * NN;
+    double* An = A + (par ^ 1) * NN;
+    double* Vn = VT + (par ^ 1) * NN;
+    const int r1 = (int)(g % cycle), r2 = (int)((g + 1) % cycle);
+    if (tid == 0) {
+      s_rot1 = 0;
+      s_rot2 = 0;
     }
     __syncthreads();
-    converged = s_rot == 0;
-    __syncthreads();  // every thread has read s_rot before thread 0 resets it for the next sweep
+    // round r1: rotations from A
+    for (int k = tid; k < P; k += blockDim.x) {
+      int p, q;
+      rr_pair(r1, k, N, p, q);
+      double c, s_, t;
+      const bool on = jacobi_rotation(Ac[(int64_t)p * N + p], Ac[(int64_t)q * N + q], Ac[(int64_t)p * N + q],
+                                      floor_abs, c, s_, t);
+      if (on) atomicAdd(&s_rot1, 1);
+      jac_record(R1, p, q, on, c, s_, t);
+    }
+    __syncthreads();
+    // round r2: rotations from the entries round r1 leaves on r2's pairs
+    for (int k = tid; k < P; k += blockDim.x) {
+      int p, q;
+      rr_pair(r2, k, N, p, q);
+      const double app = jac_after(Ac, N, R1, p, p), aqq = jac_after(Ac, N, R1, q, q);
+      const double apq = jac_after(Ac, N, R1, p, q);
+      double c, s_, t;
+      const bool on = jacobi_rotation(app, aqq, apq, floor_abs, c, s_, t);
+      if (on) atomicAdd(&s_rot2, 1);
+      sp2[k] = p;
+      sq2[k] = q;
+      son2[k] = on ? 1 : 0;
+      sc2[k] = c;
+      ss2[k] = s_;
+      st2[k] = t;
+      sapp[k] = app;
+      saqq[k] = aqq;
+      sapq[k] = apq;
+    }
+    __syncthreads();
+    for (int task = blockIdx.x; task < 2 * P; task += gridDim.x) {
+      if (task < P) {
+        const int i = task, p = sp2[i], q = sq2[i];
+        for (int j = i + tid; j < P; j += blockDim.x) {
+          if (j == i) {  // diagonal block: a_pp - t a_pq, a_qq + t a_pq, a_pq -> 0
+            double app = sapp[i], aqq = saqq[i], apq = sapq[i];
+            if (son2[i]) {
+              const double t = st2[i];
+              app = fma(-t, apq, app);
+              aqq = fma(t, apq, aqq);
+              apq = 0.0;
+            }
+            An[(int64_t)p * N + p] = app;
+            An[(int64_t)q * N + q] = aqq;
+            An[(int64_t)p * N + q] = apq;
+            An[(int64_t)q * N + p] = apq;
+            continue;
+          }
+          const int u0 = sp2[j], v0 = sq2[j];
+          double x00 = jac_after(Ac, N, R1, p, u0), x01 = jac_after(Ac, N, R1, p, v0);
+          double x10 = jac_after(Ac, N, R1, q, u0), x11 = jac_after(Ac, N, R1, q, v0);
+          if (son2[i] | son2[j]) {
+            const double c1 = sc2[i], s1 = ss2[i], c2 = sc2[j], s2 = ss2[j];
+            // rows: J_i^T X
+            const double y00 = c1 * x00 - s1 * x10, y01 = c1 * x01 - s1 * x11;
+            const double y10 = s1 * x00 + c1 * x10, y11 = s1 * x01 + c1 * x11;
+            // columns: Y J_j
+            x00 = c2 * y00 - s2 * y01;
+            x01 = s2 * y00 + c2 * y01;
+            x10 = c2 * y10 - s2 * y11;
+            x11 = s2 * y10 + c2 * y11;
+          }
+          An[(int64_t)p * N + u0] = x00;
+          An[(int64_t)p * N + v0] = x01;
+          An[(int64_t)q * N + u0] = x10;
+          An[(int64_t)q * N + v0] = x11;
+          An[(int64_t)u0 * N + p] = x00;
+          An[(int64_t)v0 * N + p] = x01;
+          An[(int64_t)u0 * N + q] = x10;
+          An[(int64_t)v0 * N + q] = x11;
+        }
+      } else {
+        // rows p, q of V^T after both rounds (V <- V J1 J2)
+        const int k = task - P, p = sp2[k], q = sq2[k];
+        const int jp = R1.jp[p], jq = R1.jp[q];
+        const double alp = R1.al[p], bep = R1.be[p], alq = R1.al[q], beq = R1.be[q];
+        const double c = sc2[k], s_ = ss2[k];
+        const bool on = son2[k] != 0;
+        for (int comp = tid; comp < N; comp += blockDim.x) {
+          const double a = fma(bep, Vc[(int64_t)jp * N + comp], alp * Vc[(int64_t)p * N + comp]);
+          const double b = fma(beq, Vc[(int64_t)jq * N + comp], alq * Vc[(int64_t)q * N + comp]);
+          Vn[(int64_t)p * N + comp] = on ? c * a - s_ * b : a;
+          Vn[(int64_t)q * N + comp] = on ? s_ * a + c * b : b;
+        }
+      }
+    }
+    // the rotation counts were final at the CTA barrier before the update; every thread
+    // reads them before the grid barrier, ahead of the next step's reset
+    const int n1 = s_rot1, n2 = s_rot2;
+    par ^= 1;
+    if (!grid_barrier(bar, gen, err, &s_abort)) return;
+    quiet = n1 ? 0 : quiet + 1;
+    quiet = n2 ? 0 : quiet + 1;
+    g += 2;
   }
   if (blockIdx.x == 0 && tid == 0) {
-    *info = converged ? 0 : 1;
-    *sweeps = sw;
+    out[0] = quiet >= cycle ? 0 : 1;
+    out[1] = (int)((g + cycle - 1) / cycle);
+    out[4] = par;
   }
 }
 
-// lambda_j = A_jj, V (n x n, row i = component i) from V^T (N x N)
-__global__ void eig_jacobi_out_kernel(const double* __restrict__ A, const double* __restrict__ VT, int N, int n,
-                                      double* __restrict__ lam, double* __restrict__ V) {
+// lambda_j = A_jj, V (n x n, row i = component i) from V^T (N x N), in the parity *par
+__global__ void eig_jacobi_out_kernel(const double* __restrict__ A2, const double* __restrict__ VT2, int N, int n,
+                                      const int* __restrict__ par, double* __restrict__ lam, double* __restrict__ V) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)n * n) return;
+  const double* A = A2 + (int64_t)*par * N * N;
+  const double* VT = VT2 + (int64_t)*par * N * N;
   const int i = (int)(t / n), j = (int)(t % n);
   V[t] = VT[(int64_t)j * N + i];
   if (i == 0) lam[j] = A[(int64_t)j * N + j];
@@ -448,14 +480,13 @@ Status spectral_setup(SpectralState& sp, const double* hcq_sym, const double* rd
   const int N = n + (n & 1);  // even; an odd n gets one zero row and column
   const int64_t nn = (int64_t)n * n, NN = (int64_t)N * N;
   constexpr int kMaxSweeps = 60;
-  double *A = nullptr, *VT = nullptr, *V = nullptr, *dbuf = nullptr;
+  double *A = nullptr, *VT = nullptr, *V = nullptr;
   int* ints = nullptr;
-  HIKF_CUDA(cudaMallocAsync((void**)&A, sizeof(double) * NN, s));
-  HIKF_CUDA(cudaMallocAsync((void**)&VT, sizeof(double) * NN, s));
-  HIKF_CUDA(cudaMallocAsync((void**)&V, sizeof(double) * nn, s));
-  HIKF_CUDA(cudaMallocAsync((void**)&dbuf, sizeof(double) * 3 * N, s));  // diag[2][N], pq[2][N/2]
-  HIKF_CUDA(cudaMallocAsync((void**)&ints, 4 * sizeof(int), s));         // info, sweeps, barrier, error
-  HIKF_CUDA(cudaMemsetAsync(ints, 0, 4 * sizeof(int), s));
+  HIKF_CUDA(hikf::pool_malloc((void**)&A, sizeof(double) * 2 * NN, s));   // two parities
+  HIKF_CUDA(hikf::pool_malloc((void**)&VT, sizeof(double) * 2 * NN, s));
+  HIKF_CUDA(hikf::pool_malloc((void**)&V, sizeof(double) * nn, s));
+  HIKF_CUDA(hikf::pool_malloc((void**)&ints, 8 * sizeof(int), s));  // info, sweeps, barrier, error, parity
+  HIKF_CUDA(cudaMemsetAsync(ints, 0, 8 * sizeof(int), s));
   scale_b_kernel<<<nblk(NN, 256), 256, 0, s>>>(hcq_sym, rd, n, N, A);
   HIKF_LAUNCH_CHECK("scale_b");
   {
@@ -469,17 +500,14 @@ Status spectral_setup(SpectralState& sp, const double* hcq_sym, const double* rd
     double* Ap = A;
     double* Vp = VT;
     int Np = N, msw = kMaxSweeps;
-    double* dp = dbuf;
-    double* pp = dbuf + 2 * N;
     unsigned* bp = reinterpret_cast<unsigned*>(ints + 2);
     int* errp = ints + 3;
-    int* infop = ints;
-    int* swp = ints + 1;
-    void* args[] = {&Ap, &Vp, &Np, &msw, &dp, &pp, &bp, &errp, &infop, &swp};
+    int* outp = ints;
+    void* args[] = {&Ap, &Vp, &Np, &msw, &bp, &errp, &outp};
     HIKF_CUDA(cudaLaunchCooperativeKernel((const void*)eig_jacobi_kernel, dim3(grid), dim3(kJacThreads), args, 0, s));
     HIKF_LAUNCH_CHECK("eig_jacobi");
   }
-  eig_jacobi_out_kernel<<<nblk(nn, 256), 256, 0, s>>>(A, VT, N, n, sp.lam, V);
+  eig_jacobi_out_kernel<<<nblk(nn, 256), 256, 0, s>>>(A, VT, N, n, ints + 4, sp.lam, V);
   HIKF_LAUNCH_CHECK("eig_jacobi_out");
   spec_init_kernel<<<nblk(nn, 256), 256, 0, s>>>(V, sp.lam, rd, n, c, sp.W64, sp.W32, sp.s, flag);
   HIKF_LAUNCH_CHECK("spec_init");
@@ -489,7 +517,6 @@ Status spectral_setup(SpectralState& sp, const double* hcq_sym, const double* rd
   HIKF_CUDA(cudaFreeAsync(A, s));
   HIKF_CUDA(cudaFreeAsync(VT, s));
   HIKF_CUDA(cudaFreeAsync(V, s));
-  HIKF_CUDA(cudaFreeAsync(dbuf, s));
   HIKF_CUDA(cudaFreeAsync(ints, s));
   sp.sweeps = hinfo[1];
   if (hinfo[3]) return make_status(HIKF_ETIMEOUT, "a bounded grid barrier in the Jacobi eigensolver timed out");
@@ -812,7 +839,7 @@ template <typename T>
 Status eigen_cross(const SpectralState& sp, const double* rd, int64_t m, int ld, int n, const T* G, const T* Gq,
                    T* out, cudaStream_t s) {
   double* B = nullptr;
-  HIKF_CUDA(cudaMallocAsync((void**)&B, sizeof(double) * (size_t)n * n, s));
+  HIKF_CUDA(hikf::pool_malloc((void**)&B, sizeof(double) * (size_t)n * n, s));
   wtr_kernel<<<nb((int64_t)n * n, 256), 256, 0, s>>>(sp.W64, rd, n, B);
   HIKF_LAUNCH_CHECK("wtr");
   dim3 grid((unsigned)((m + 63) / 64), (unsigned)((ld + 63) / 64));

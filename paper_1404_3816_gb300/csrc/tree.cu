@@ -280,7 +280,7 @@ Status build_tree(Tree& t, Arena& arena, const double* d_pts, cudaStream_t s) {
   // bounding box
   int nb = std::min<int64_t>(1024, (m + kThreads - 1) / kThreads);
   double* d_part = nullptr;
-  HIKF_CUDA(cudaMallocAsync((void**)&d_part, sizeof(double) * 6 * nb, s));
+  HIKF_CUDA(hikf::pool_malloc((void**)&d_part, sizeof(double) * 6 * nb, s));
   bbox_partial<<<nb, kThreads, 0, s>>>(d_pts, m, dim, d_part);
   HIKF_LAUNCH_CHECK("bbox_partial");
   std::vector<double> part(6 * nb);
@@ -305,12 +305,12 @@ Status build_tree(Tree& t, Arena& arena, const double* d_pts, cudaStream_t s) {
   uint64_t *k0 = nullptr, *k1 = nullptr;
   int64_t *v0 = nullptr, *v1 = nullptr, *hist = nullptr, *tmp = nullptr;
   const int nbl = (int)((m + kTile - 1) / kTile);
-  HIKF_CUDA(cudaMallocAsync((void**)&k0, sizeof(uint64_t) * m, s));
-  HIKF_CUDA(cudaMallocAsync((void**)&k1, sizeof(uint64_t) * m, s));
-  HIKF_CUDA(cudaMallocAsync((void**)&v0, sizeof(int64_t) * m, s));
-  HIKF_CUDA(cudaMallocAsync((void**)&v1, sizeof(int64_t) * m, s));
-  HIKF_CUDA(cudaMallocAsync((void**)&hist, sizeof(int64_t) * 256 * (size_t)nbl * 2, s));
-  HIKF_CUDA(cudaMallocAsync((void**)&tmp, sizeof(int64_t) * (2 * (256 * (size_t)nbl / kTile + 2) + 8), s));
+  HIKF_CUDA(hikf::pool_malloc((void**)&k0, sizeof(uint64_t) * m, s));
+  HIKF_CUDA(hikf::pool_malloc((void**)&k1, sizeof(uint64_t) * m, s));
+  HIKF_CUDA(hikf::pool_malloc((void**)&v0, sizeof(int64_t) * m, s));
+  HIKF_CUDA(hikf::pool_malloc((void**)&v1, sizeof(int64_t) * m, s));
+  HIKF_CUDA(hikf::pool_malloc((void**)&hist, sizeof(int64_t) * 256 * (size_t)nbl * 2, s));
+  HIKF_CUDA(hikf::pool_malloc((void**)&tmp, sizeof(int64_t) * (2 * (256 * (size_t)nbl / kTile + 2) + 8), s));
   leaf_keys<<<nblk(m, kThreads), kThreads, 0, s>>>(d_pts, m, dim, t.depth, t.lo[0], t.lo[1], t.lo[2], w, k0, v0);
   HIKF_LAUNCH_CHECK("leaf_keys");
   const int bits = dim * t.depth;
@@ -362,10 +362,10 @@ Status build_sparse(SparseH& h, Arena& arena, const Tree& t, const int64_t* h_ro
   HIKF_TRY(arena_alloc(arena, &h.tval, std::max<int64_t>(nnz, 1)));
   HIKF_CUDA(cudaMemcpyAsync(h.rowptr, h_rowptr, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s));
   int64_t *d_col = nullptr, *count = nullptr, *cursor = nullptr, *tmp = nullptr;
-  HIKF_CUDA(cudaMallocAsync((void**)&d_col, sizeof(int64_t) * std::max<int64_t>(nnz, 1), s));
-  HIKF_CUDA(cudaMallocAsync((void**)&count, sizeof(int64_t) * (m + 1), s));
-  HIKF_CUDA(cudaMallocAsync((void**)&cursor, sizeof(int64_t) * (m + 1), s));
-  HIKF_CUDA(cudaMallocAsync((void**)&tmp, sizeof(int64_t) * (2 * ((m + 1) / kTile + 2) + 8), s));
+  HIKF_CUDA(hikf::pool_malloc((void**)&d_col, sizeof(int64_t) * std::max<int64_t>(nnz, 1), s));
+  HIKF_CUDA(hikf::pool_malloc((void**)&count, sizeof(int64_t) * (m + 1), s));
+  HIKF_CUDA(hikf::pool_malloc((void**)&cursor, sizeof(int64_t) * (m + 1), s));
+  HIKF_CUDA(hikf::pool_malloc((void**)&tmp, sizeof(int64_t) * (2 * ((m + 1) / kTile + 2) + 8), s));
   HIKF_CUDA(cudaMemsetAsync(count, 0, sizeof(int64_t) * (m + 1), s));
   HIKF_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int64_t) * (m + 1), s));
   if (nnz > 0) {

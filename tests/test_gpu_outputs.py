@@ -61,3 +61,26 @@ def test_failed_asynchronous_step_is_reported_by_the_next_synchronous_step():
         for y in Y:
             g.assimilate(y)
         assert np.array_equal(g.mean(), x) and np.array_equal(g.variance(), v)
+
+
+def test_library_pool_caches_freed_memory_until_released():
+    """A destroyed filter's buffers and the create's scratch stay in the library's pool (for
+    the next create) until hikf_release_cached_memory returns them to the device."""
+    import torch
+    from paper_1404_3816_gb300 import binding as B
+    w = W.small(grid=(320, 300), n=64, steps=1, seed=93)
+    torch.cuda.synchronize()
+    B.release_cached_memory()
+    free0 = torch.cuda.mem_get_info()[0]
+    with B.Filter.from_workload(w, precision="mixed") as f:
+        held = f.info()["device_bytes"]
+    free1 = torch.cuda.mem_get_info()[0]
+    B.release_cached_memory()
+    free2 = torch.cuda.mem_get_info()[0]
+    assert held > 2 * w.m * 64 * 4                        # C and C_Q at least
+    assert free2 - free1 >= held // 2                     # cached after destroy, returned now
+    assert abs(free2 - free0) <= 64 << 20
+    with B.Filter.from_workload(w, precision="mixed") as f:   # the pool serves a create again
+        Y, _ = W.measurements(w)
+        f.assimilate(Y[0])
+        assert np.isfinite(f.mean()).all()
