@@ -471,33 +471,46 @@ def main():
         dist.barrier()
 
     # e2e through the C ABI with host buffers every step: y in from pinned memory, the step,
-    # mean and variance out to pinned memory. Pipelined (the value): the copies and calls are
-    # enqueued on the handle's stream (hikf_assimilate_device, hikf_get_*_device, copies from
-    # and to page-locked memory), so step t's readback overlaps step t+1, with one wait at the
-    # end; blocking (beside it): hikf_assimilate, hikf_get_mean, hikf_get_variance per step.
+    # mean and variance out to pinned memory. Pipelined (the value): y's copy, the step and
+    # the gathers of x and delta^2 into caller order (hikf_assimilate_device,
+    # hikf_get_*_device) are enqueued on the handle's stream, and the device-to-host copies
+    # of step t on a second stream from a double-buffered device copy, so they run on the copy
+    # engine while step t+1 computes; one wait at the end. Blocking (beside it):
+    # hikf_assimilate, hikf_get_mean, hikf_get_variance per step.
     ne2e = max(1, args.e2e_steps)
     pin_y = torch.tensor(Y[:ne2e], dtype=torch.float64).pin_memory()
     out_x = torch.empty((2, w.m), dtype=torch.float64).pin_memory()
     out_v = torch.empty((2, w.m), dtype=torch.float64).pin_memory()
     dev_y = torch.empty((2, n), dtype=torch.float64, device="cuda")
-    dev_x = torch.empty(w.m, dtype=torch.float64, device="cuda")
+    dev_x = torch.empty((2, w.m), dtype=torch.float64, device="cuda")
     dev_v = torch.empty_like(dev_x)
     fst = torch.cuda.ExternalStream(f.stream)
+    cst = torch.cuda.Stream()
+    ready = [torch.cuda.Event(), torch.cuda.Event()]
+    done = [torch.cuda.Event(), torch.cuda.Event()]
     f.sync()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     t0 = time.perf_counter()
-    with torch.cuda.stream(fst):
-        for t in range(ne2e):
-            dev_y[t % 2].copy_(pin_y[t], non_blocking=True)
-            f.assimilate_device(dev_y[t % 2])
-            f.mean_into(dev_x)
-            f.variance_into(dev_v)
-            out_x[t % 2].copy_(dev_x, non_blocking=True)
-            out_v[t % 2].copy_(dev_v, non_blocking=True)
+    for t in range(ne2e):
+        b = t % 2
+        with torch.cuda.stream(fst):
+            if t >= 2:
+                fst.wait_event(done[b])          # slot b's copies of step t - 2 have left
+            dev_y[b].copy_(pin_y[t], non_blocking=True)
+            f.assimilate_device(dev_y[b])
+            f.mean_into(dev_x[b])
+            f.variance_into(dev_v[b])
+            ready[b].record(fst)
+        with torch.cuda.stream(cst):
+            cst.wait_event(ready[b])
+            out_x[b].copy_(dev_x[b], non_blocking=True)
+            out_v[b].copy_(dev_v[b], non_blocking=True)
+            done[b].record(cst)
     f.sync()
     fst.synchronize()
+    cst.synchronize()
     e2e_value, _ = job_rate(ne2e, time.perf_counter() - t0, world, device="cuda")
     y_np = pin_y.numpy()
     if world > 1:
@@ -511,6 +524,7 @@ def main():
     # the page-locked buffers were copied on the handle's stream: free them while it exists
     # (freeing one records an event on every stream that used it)
     del y_np, pin_y, out_x, out_v, dev_y, dev_x, dev_v
+    cst.synchronize()
     f.close()
 
     def roofline(prec, form, ms):
@@ -544,8 +558,10 @@ def main():
             "gpu_launches": int(info["sweep_launches"]) * args.steps,
             "e2e": {"value": e2e_value, "unit": "steps/s", "h2d_bytes_per_step": 8 * n,
                     "d2h_bytes_per_step": 16 * m, "steps": ne2e,
-                    "how": "pinned y in, mean and variance out to pinned memory every step; copies and "
-                           "calls enqueued on the handle's stream (device entry points), one wait at the end",
+                    "how": "pinned y in, mean and variance out to pinned memory every step; y's copy, the "
+                           "step and the gathers to caller order on the handle's stream (device entry points), "
+                           "the device-to-host copies on a second stream from a double-buffered device copy, "
+                           "overlapping the next step; one wait at the end",
                     "blocking": {"value": e2e_sync, "unit": "steps/s",
                                  "how": "hikf_assimilate, hikf_get_mean, hikf_get_variance per step"}},
             "roofline": roofline(args.precision, "cross", head["sweep_ms"]), "clocks": head["clocks"]}

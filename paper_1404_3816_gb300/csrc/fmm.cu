@@ -775,14 +775,17 @@ __global__ void __launch_bounds__(kThreads) l2p_p2p_kernel(Geo g, const double* 
     __syncthreads();
     for (int r0 = 0; r0 < ld; r0 += nch) {
       const int w = min(nch, ld - r0);
-      // L2P: a 4-point x 8-column register tile per thread; L rows read as 16-byte vectors
+      // L2P: a PT-point x 8-column register tile per thread (8 points in FP32, so each entry
+      // of L is read by kPT / 8 threads; 4 in FP64, for the registers); L rows read as
+      // 16-byte vectors; every output sums over a in the same order whatever PT is
       {
-        const int ncg = nch / 8, ntile = (kPT / 4) * ncg;
+        constexpr int PT = sizeof(T) == 4 ? 8 : 4;
+        const int ncg = nch / 8, ntile = (kPT / PT) * ncg;
         for (int t = threadIdx.x; t < ntile; t += blockDim.x) {
-          const int i0 = (t / ncg) * 4, c0 = (t % ncg) * 8;
-          T acc[4][8];
+          const int i0 = (t / ncg) * PT, c0 = (t % ncg) * 8;
+          T acc[PT][8];
 #pragma unroll
-          for (int u = 0; u < 4; ++u)
+          for (int u = 0; u < PT; ++u)
 #pragma unroll
             for (int v = 0; v < 8; ++v) acc[u][v] = (T)0;
           if (L >= 2 && i0 < cnt && c0 < w) {
@@ -790,17 +793,17 @@ __global__ void __launch_bounds__(kThreads) l2p_p2p_kernel(Geo g, const double* 
             for (int a = 0; a < q; ++a) {
               T lv[8];
               load8(lrow + (int64_t)a * ld, lv);
-              T sv[4];
+              T sv[PT];
 #pragma unroll
-              for (int u = 0; u < 4; ++u) sv[u] = i0 + u < cnt ? S[(i0 + u) * q + a] : (T)0;
+              for (int u = 0; u < PT; ++u) sv[u] = i0 + u < cnt ? S[(i0 + u) * q + a] : (T)0;
 #pragma unroll
-              for (int u = 0; u < 4; ++u)
+              for (int u = 0; u < PT; ++u)
 #pragma unroll
                 for (int v = 0; v < 8; ++v) acc[u][v] += sv[u] * lv[v];
             }
           }
 #pragma unroll
-          for (int u = 0; u < 4; ++u)
+          for (int u = 0; u < PT; ++u)
 #pragma unroll
             for (int v = 0; v < 8; ++v) Cs[(i0 + u) * (nch + 1) + c0 + v] = acc[u][v];
         }
