@@ -94,7 +94,8 @@ typedef struct {
                         m <= leaf_size * 2^(dim L)). Default -1. */
   int precision;     /* HIKF_PREC_*. Default HIKF_PREC_FP32. */
   void* cuda_stream; /* cudaStream_t the handle runs on; NULL = a stream the handle
-                        creates and owns. Default NULL. */
+                        creates and owns. A caller's stream must outlive the handle
+                        (hikf_destroy frees the handle's memory in its order). Default NULL. */
   int chain;         /* how S_t^{-1} = (H C_{t|t-1} + R)^{-1} is formed each step:
                         HIKF_CHAIN_AUTO (default): spectral when P_0 = c Q (c >= 0,
                         including P_0 = 0) and C_Q is computed, else factor;
@@ -326,7 +327,8 @@ void* hikf_stream(const hikf_t* h);
  * last failed hikf_create on this thread (h == NULL). Never NULL. */
 const char* hikf_last_error(const hikf_t* h);
 
-/* Free the handle and all of its device memory. NULL is ignored. */
+/* Free the handle and all of its device memory (back to the library's pool, in the order
+ * of the handle's stream, after waiting for the stream's work). NULL is ignored. */
 void hikf_destroy(hikf_t* h);
 
 /*
