@@ -43,6 +43,13 @@ def test_options_default_without_gpu(lib):
     assert o.cheb_order == 8 and o.leaf_size == 64 and o.max_depth == -1 and o.precision == 0
 
 
+def test_release_cached_memory_without_a_pool(lib):
+    # the library's pool is made on the first device allocation; with none made, releasing
+    # the cache is a no-op that needs no device
+    from paper_1404_3816_gb300 import binding
+    binding.release_cached_memory()
+
+
 def test_invalid_arguments_are_rejected_before_any_device_work(lib):
     import numpy as np
     from paper_1404_3816_gb300 import binding, workload as W
